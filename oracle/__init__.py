@@ -1,0 +1,19 @@
+"""Plain, slow FP64 CPU oracle for the Stokes layer-operator apply on SH drop surfaces.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this package: only the
+tests, the smoke check and the CPU-baseline leg of the benchmark use it.  It shares no code
+with the CUDA library (no kernels, tables, constants or helpers); both sides consume the
+same seeded inputs.
+
+Modules, each following the passage of Sorgentone & Tornberg (arXiv 1707.02156) it cites:
+  sh        grid, normalised Legendre functions, analysis/synthesis, derivatives (Sec. 1.1, 2.1, App. A)
+  wigner    Wigner small-d matrices and coefficient rotation (App. B)
+  geometry  fundamental forms, normal, curvature, interfacial force (Table 2, Sec. 1)
+  layer     singular self quadrature (Thm 1, Sec. 2.2), regular and upsampled pair sums and the
+            region split (Sec. 2.3), near-singular interpolation (Sec. 2.3), Galerkin projection (Sec. 1.2)
+  gmres     restarted GMRES with modified Gram-Schmidt (Sec. 7)
+  brute     adaptive polar quadrature used only to pin the singular rule
+
+Parity unpinned: the absolute accuracy of the near-singular (Omega_2) interpolation on
+deformed shapes has no closed form; it is reported against brute force, not pinned.
+"""
