@@ -1,0 +1,179 @@
+/*
+ * bie.h -- C ABI of the GB300 library for the Stokes single- and double-layer operators on
+ * drop surfaces represented by spherical-harmonic (SH) expansions, after Sorgentone & Tornberg,
+ * "A highly accurate boundary integral equation method for surfactant-laden drops in 3D"
+ * (arXiv 1707.02156).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Degrees.  Drop d has SH degree p[d] (1 <= p <= BIE_MAX_P).  Its Gauss grid (Sec. 2.1) has
+ *   p+1 latitudes theta_j = arccos t_j (t_j the Gauss-Legendre nodes, ascending, so theta descends)
+ *   and 2p+2 longitudes phi_k = pi k/(p+1); N_g(p) = (p+1)(2p+2) grid points.
+ * Coefficients (Sec. 1.1, 1.2).  Real-packed per scalar: (p+1)^2 doubles, index n(n+1)+m holds
+ *   Re f_n^m for m >= 0 and Im f_n^{|m|} for m < 0 (real functions: f_n^{-m} = (-1)^m conj f_n^m).
+ *   Orthonormal Y_n^m with the Condon-Shortley phase.
+ * Multi-drop arrays are drop-major: [drop][comp][(p[d]+1)^2] for coefficients and
+ *   [drop][comp][j][k] for grids, each drop's block following the previous one.
+ * Pointers.  Arrays named "coef", "grid" or "_dev" are DEVICE pointers (cudaMalloc'd memory of the
+ *   context's device); the small per-drop arrays p, p_out, pq, lambda, euler are HOST pointers.
+ *   The caller owns every buffer it passes; the library never frees them and keeps no pointer to
+ *   them after the call returns (bie_geometry_setup copies what it needs).
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls
+ *   are asynchronous with respect to the host unless stated; results are ready when the stream is.
+ * Errors.  Every call returns a status code; nothing throws or aborts.  On an error the output
+ *   buffers are unspecified.  bie_strerror() names a code; bie_last_error() describes the last
+ *   failure of the calling thread in words.
+ * Normalisation (Eq. main_eq, mu = 1, xh = x0 - x, r = |xh|):
+ *   G(xh) f = f/r + (xh.f) xh/r^3,   u.T(xh).n = -6 (u.xh)(xh.n) xh/r^5,
+ *   single layer  S[f](x0) = -(1/4pi) sum_j int_{gamma_j} f.G dS,
+ *   double layer  D[u](x0) = (1/4pi) sum_j (lambda_j - 1) PV int_{gamma_j} u.T.n dS,
+ *   so Eq. main_eq reads (lambda_i + 1) u - D[u] = 2 u_inf + S[f].  With BIE_RAW the calls return
+ *   the unscaled operators (1/8pi) int f.G and (1/4pi) PV int u.T.n instead.
+ */
+#ifndef BIE_H
+#define BIE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BIE_MAX_P 64
+
+enum bie_status {
+  BIE_OK = 0,
+  BIE_EINVAL = 1,    /* bad argument (degree out of range, null pointer, bad flag) */
+  BIE_ENOMEM = 2,    /* device or host allocation failed */
+  BIE_ECUDA = 3,     /* a CUDA runtime call failed (see bie_last_error) */
+  BIE_ENOCONV = 4,   /* iterative solve did not reach its tolerance: best iterate returned */
+  BIE_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+  BIE_EOVERLAP = 6,  /* drops intersect: a grid point lies inside, or on, another drop */
+  BIE_ENOTSUP = 7    /* feature not supported for these arguments */
+};
+
+/* precision flags (the low byte), OR-able with BIE_RAW */
+#define BIE_FP64 0   /* every step in double precision */
+#define BIE_MIXED 1  /* rotation, synthesis and pair sums in FP32; geometry, analysis in FP64 */
+#define BIE_RAW 0x100
+#define BIE_GRID_OUT 0x200  /* applies: write the values at the grid targets, [drop][3][j][k], instead
+                               of their Galerkin projection (for sampled checks against a reference) */
+
+typedef struct bie_ctx bie_ctx;
+typedef struct bie_geom bie_geom;
+
+typedef struct bie_config {
+  int device;        /* CUDA device ordinal */
+  int upsample;      /* U: the intermediate region uses the grid of degree U(p+1)-1 (Sec. 2.3), >= 1 */
+  double a_tilde;    /* A: Omega_0 / Omega_1 boundary at distance A*h (Sec. 2.3; the paper uses 5) */
+  int n_interp;      /* L: check points of the near-singular interpolation (Sec. 2.3; 8) */
+} bie_config;
+
+/* Fill a config with the paper's defaults: device 0, U = 4, A = 5, L = 8. */
+void bie_config_default(bie_config* cfg);
+
+/* Create a context on cfg->device.  Plan tables are built lazily per degree and cached. */
+int bie_create(bie_ctx** ctx, const bie_config* cfg);
+void bie_destroy(bie_ctx* ctx);
+const char* bie_strerror(int status);
+const char* bie_last_error(void);
+
+/* SH analysis, Eq. back_transf_discr (Sec. 2.1): grid values on the degree-p[d] grid ->
+ * degree-p[d] coefficients, for ndrop drops with ncomp scalar components each.
+ * grid: [drop][comp][p+1][2p+2] (device), coef: [drop][comp][(p+1)^2] (device). */
+int bie_sh_analyze(bie_ctx* ctx, int ndrop, const int* p, int ncomp, const double* grid, double* coef,
+                   void* stream);
+
+/* SH synthesis, Eq. spharm_ex, on the Gauss grid of degree p_out[d] (zero padding for
+ * p_out > p: the upsampling of Sec. 1.3; p_out < p is rejected).
+ * coef: [drop][comp][(p+1)^2], grid: [drop][comp][p_out+1][2p_out+2] (device). */
+int bie_sh_synthesize(bie_ctx* ctx, int ndrop, const int* p, const int* p_out, int ncomp, const double* coef,
+                      double* grid, void* stream);
+
+/* Rotation of SH coefficients, App. B: coef_out holds the expansion of g(s) = f(R s) with
+ * R = R_z(alpha) R_y(beta) R_z(gamma) (z-y-z Euler angles, active rotations), so the pole of g is
+ * the point (theta, phi) = (beta, alpha) of f.  euler: host [ndrop][3] = (alpha, beta, gamma).
+ * coef, coef_out: [drop][comp][(p+1)^2] (device, must not overlap). */
+int bie_rotate(bie_ctx* ctx, int ndrop, const int* p, int ncomp, const double* coef, const double* euler,
+               double* coef_out, void* stream);
+
+/* Geometry of ndrop drops (Table 2; Sec. 2.2 rotated-grid cache; Sec. 2.3 regions), built once per
+ * shape and reused by every apply and solve on it.
+ *   p[d]   SH degree of drop d (host), pq[d] degree of its self (singular) quadrature grid,
+ *          p <= pq <= 2p+1 (pq = 2p+1 is the "upsampled 2x for quadrature" rule);
+ *   xcoef  [drop][3][(p+1)^2] device coefficients of x(theta, phi);
+ *   lambda host [ndrop] viscosity ratios.
+ * Synchronous: returns when the geometry is ready.  BIE_EOVERLAP if a grid point of one drop lies
+ * inside another.  The geometry owns its device memory until bie_geometry_destroy. */
+int bie_geometry_setup(bie_ctx* ctx, int ndrop, const int* p, const int* pq, const double* xcoef,
+                       const double* lambda, bie_geom** geom, void* stream);
+void bie_geometry_destroy(bie_geom* geom);
+
+typedef struct bie_geom_info {
+  int ndrop;
+  long long ncoef;        /* 3 * sum_d (p_d+1)^2: length of a vector-density coefficient array */
+  long long ntarget;      /* sum_d N_g(p_d) */
+  long long self_pairs;   /* sum_d N_g(p_d) * N_g(pq_d): pairs of the singular self rule */
+  long long far_pairs;    /* (target, source) pairs of the regular rule on standard grids (Omega_0) */
+  long long up_pairs;     /* pairs of the upsampled rule (Omega_1) */
+  long long near_targets; /* (target, drop) pairs in Omega_2 */
+  long long near_pairs;   /* pairs evaluated at Omega_2 check points */
+  double cache_bytes;     /* device bytes held by the geometry */
+} bie_geom_info;
+int bie_geometry_info(const bie_geom* geom, bie_geom_info* info);
+
+/* Interfacial force f = -2 sigma K n - grad_gamma sigma (Sec. 1, Table 2), computed on the grid of
+ * degree 2p+1 and truncated to degree p (Sec. 1.3).  gammacoef: [drop][1][(p+1)^2] device surfactant
+ * coefficients; sigma = 1 + E ln(1 - x_s Gamma) (Eq. langmuir) when x_s > 0, else 1 - E Gamma.
+ * fcoef: [drop][3][(p+1)^2] device output. */
+int bie_interfacial_force(bie_ctx* ctx, const bie_geom* geom, const double* gammacoef, double elasticity,
+                          double x_s, double* fcoef, void* stream);
+
+/* Single-layer apply (Eq. main_eq, Sec. 2.2-2.3, Galerkin projection of Sec. 1.2):
+ * out = coefficients of S[f] at every drop's grid targets.  fcoef: [drop][3][(p+1)^2] (device);
+ * precision: BIE_FP64 or BIE_MIXED, optionally | BIE_RAW. */
+int bie_apply_single(bie_ctx* ctx, const bie_geom* geom, const double* fcoef, double* out_coef, int precision,
+                     void* stream);
+
+/* Double-layer apply, same layout: out = coefficients of D[u] (the GMRES matvec's operator part). */
+int bie_apply_double(bie_ctx* ctx, const bie_geom* geom, const double* ucoef, double* out_coef, int precision,
+                     void* stream);
+
+typedef struct bie_solve_opts {
+  int precision;      /* BIE_FP64: FP64 GMRES; BIE_MIXED: mixed GMRES inside FP64 iterative refinement */
+  double tol;         /* relative residual target ||b - A u|| / ||b|| (FP64-accurate residual) */
+  int restart;        /* GMRES restart length (<= 64) */
+  int max_iter;       /* total GMRES iterations allowed */
+  double inner_tol;   /* mixed only: relative tolerance of each inner solve */
+  int max_refine;     /* mixed only: outer refinement steps allowed */
+} bie_solve_opts;
+
+typedef struct bie_solve_info {
+  int iterations;        /* GMRES iterations (all inner solves) */
+  int refinements;       /* outer refinement steps (mixed) */
+  int applies_fp64;      /* FP64 double-layer applies */
+  int applies_mixed;     /* mixed double-layer applies */
+  double residual;       /* final FP64 relative residual */
+  int converged;
+} bie_solve_info;
+
+void bie_solve_opts_default(bie_solve_opts* opts);
+
+/* Solve Eq. main_eq in coefficient space: (lambda_i + 1) u_i - D[u]_i = b_i, Sec. 7 (GMRES).
+ * rhs: [drop][3][(p+1)^2] device right-hand side b (form it as 2 u_inf + S[f] with
+ * bie_apply_single); u: device initial guess in, solution out.  Synchronous (the Krylov loop reads
+ * back one scalar block per iteration).  BIE_ENOCONV if tol was not reached (best iterate kept). */
+int bie_solve(bie_ctx* ctx, const bie_geom* geom, const double* rhs, double* u, const bie_solve_opts* opts,
+              bie_solve_info* info, void* stream);
+
+/* Host-side plan tables, exported so the host logic can be checked without a GPU.
+ *   which 0: Gauss-Legendre nodes (n = P+1 doubles) then weights (n doubles), P = a
+ *   which 1: Legendre table kind b (0 value, 1 d/dtheta, 2 d2/dtheta2) for degree a on the grid of
+ *            degree c: layout [m][n][j], 0 <= m <= n <= a
+ *   which 2: dense Wigner small-d matrix of degree a at angle x: [(2a+1)][(2a+1)], rows m', cols m
+ *   which 3: singular weights of Thm 1 on the grid of degree a (a+1 doubles)
+ * Writes at most `cap` doubles to out and returns the count needed (negative on bad arguments). */
+long long bie_debug_table(int which, int a, int b, int c, double x, double* out, long long cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIE_H */

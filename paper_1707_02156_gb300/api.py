@@ -1,0 +1,234 @@
+"""Thin Python binding of libbie.so (argument marshalling only).
+
+Every step of the operator apply and the solve runs in the library's CUDA kernels; this module
+only converts torch tensors to raw device pointers and checks status codes.  There is no CPU
+fallback: if the library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+c_int, c_double, c_ll, c_void = ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p
+P_int = ctypes.POINTER(ctypes.c_int)
+P_double = ctypes.POINTER(ctypes.c_double)
+
+BIE_FP64, BIE_MIXED, BIE_RAW, BIE_GRID_OUT = 0, 1, 0x100, 0x200
+STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT", 6: "EOVERLAP", 7: "ENOTSUP"}
+
+
+class bie_config(ctypes.Structure):
+    _fields_ = [("device", c_int), ("upsample", c_int), ("a_tilde", c_double), ("n_interp", c_int)]
+
+
+class bie_geom_info(ctypes.Structure):
+    _fields_ = [("ndrop", c_int), ("ncoef", c_ll), ("ntarget", c_ll), ("self_pairs", c_ll), ("far_pairs", c_ll),
+                ("up_pairs", c_ll), ("near_targets", c_ll), ("near_pairs", c_ll), ("cache_bytes", c_double)]
+
+
+class bie_solve_opts(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("tol", c_double), ("restart", c_int), ("max_iter", c_int),
+                ("inner_tol", c_double), ("max_refine", c_int)]
+
+
+class bie_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", c_int), ("refinements", c_int), ("applies_fp64", c_int), ("applies_mixed", c_int),
+                ("residual", c_double), ("converged", c_int)]
+
+
+EXPORTS = {
+    "bie_config_default": (None, [ctypes.POINTER(bie_config)]),
+    "bie_create": (c_int, [ctypes.POINTER(c_void), ctypes.POINTER(bie_config)]),
+    "bie_destroy": (None, [c_void]),
+    "bie_strerror": (ctypes.c_char_p, [c_int]),
+    "bie_last_error": (ctypes.c_char_p, []),
+    "bie_sh_analyze": (c_int, [c_void, c_int, P_int, c_int, c_void, c_void, c_void]),
+    "bie_sh_synthesize": (c_int, [c_void, c_int, P_int, P_int, c_int, c_void, c_void, c_void]),
+    "bie_rotate": (c_int, [c_void, c_int, P_int, c_int, c_void, P_double, c_void, c_void]),
+    "bie_geometry_setup": (c_int, [c_void, c_int, P_int, P_int, c_void, P_double, ctypes.POINTER(c_void), c_void]),
+    "bie_geometry_destroy": (None, [c_void]),
+    "bie_geometry_info": (c_int, [c_void, ctypes.POINTER(bie_geom_info)]),
+    "bie_interfacial_force": (c_int, [c_void, c_void, c_void, c_double, c_double, c_void, c_void]),
+    "bie_apply_single": (c_int, [c_void, c_void, c_void, c_void, c_int, c_void]),
+    "bie_apply_double": (c_int, [c_void, c_void, c_void, c_void, c_int, c_void]),
+    "bie_solve_opts_default": (None, [ctypes.POINTER(bie_solve_opts)]),
+    "bie_solve": (c_int, [c_void, c_void, c_void, c_void, ctypes.POINTER(bie_solve_opts),
+                          ctypes.POINTER(bie_solve_info), c_void]),
+    "bie_debug_table": (c_ll, [c_int, c_int, c_int, c_int, c_double, P_double, c_ll]),
+}
+
+_LIB = None
+
+
+def lib(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libbie.so (raises if it is missing and build_if_missing is False)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libbie.so not built ({path}); run paper_1707_02156_gb300.build")
+            _build.build()
+        L = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class BIEError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}: {lib().bie_last_error().decode()}")
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise BIEError(st, what)
+
+
+def _ptr(t: torch.Tensor) -> int:
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ints(v):
+    v = [int(x) for x in v]
+    return (ctypes.c_int * len(v))(*v)
+
+
+def _doubles(v):
+    v = [float(x) for x in v]
+    return (ctypes.c_double * len(v))(*v)
+
+
+def ncoef(p: int) -> int:
+    return (p + 1) * (p + 1)
+
+
+def ngrid(p: int) -> int:
+    return (p + 1) * (2 * p + 2)
+
+
+class Context:
+    """A library context on one CUDA device (plan tables cached per degree)."""
+
+    def __init__(self, device: int = 0, upsample: int = 4, a_tilde: float = 5.0, n_interp: int = 8):
+        L = lib()
+        cfg = bie_config()
+        L.bie_config_default(ctypes.byref(cfg))
+        cfg.device, cfg.upsample, cfg.a_tilde, cfg.n_interp = device, upsample, a_tilde, n_interp
+        h = c_void()
+        _check(L.bie_create(ctypes.byref(h), ctypes.byref(cfg)), "bie_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bie_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sh_analyze(self, p, ncomp: int, grid: torch.Tensor, coef: torch.Tensor):
+        _check(lib().bie_sh_analyze(self.h, len(p), _ints(p), ncomp, _ptr(grid), _ptr(coef), _stream()),
+               "bie_sh_analyze")
+        return coef
+
+    def sh_synthesize(self, p, p_out, ncomp: int, coef: torch.Tensor, grid: torch.Tensor):
+        _check(lib().bie_sh_synthesize(self.h, len(p), _ints(p), _ints(p_out), ncomp, _ptr(coef), _ptr(grid),
+                                       _stream()), "bie_sh_synthesize")
+        return grid
+
+    def rotate(self, p, ncomp: int, coef: torch.Tensor, euler, out: torch.Tensor):
+        flat = [float(a) for e in euler for a in e]
+        _check(lib().bie_rotate(self.h, len(p), _ints(p), ncomp, _ptr(coef), _doubles(flat), _ptr(out), _stream()),
+               "bie_rotate")
+        return out
+
+    def geometry(self, p, pq, xcoef: torch.Tensor, lam) -> "Geometry":
+        return Geometry(self, p, pq, xcoef, lam)
+
+
+class Geometry:
+    """Shape-dependent data of ndrop drops, reused by every apply and solve on that shape."""
+
+    def __init__(self, ctx: Context, p, pq, xcoef: torch.Tensor, lam):
+        self.ctx = ctx
+        self.p, self.pq = list(p), list(pq)
+        h = c_void()
+        _check(lib().bie_geometry_setup(ctx.h, len(p), _ints(p), _ints(pq), _ptr(xcoef), _doubles(lam),
+                                        ctypes.byref(h), _stream()), "bie_geometry_setup")
+        self.h = h
+        info = bie_geom_info()
+        _check(lib().bie_geometry_info(self.h, ctypes.byref(info)), "bie_geometry_info")
+        self.info = {k: getattr(info, k) for k, _ in bie_geom_info._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bie_geometry_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_single(self, f: torch.Tensor, out: torch.Tensor, precision: int = BIE_FP64, raw: bool = False,
+                     grid_out: bool = False):
+        flag = precision | (BIE_RAW if raw else 0) | (BIE_GRID_OUT if grid_out else 0)
+        _check(lib().bie_apply_single(self.ctx.h, self.h, _ptr(f), _ptr(out), flag, _stream()), "bie_apply_single")
+        return out
+
+    def apply_double(self, u: torch.Tensor, out: torch.Tensor, precision: int = BIE_FP64, raw: bool = False,
+                     grid_out: bool = False):
+        flag = precision | (BIE_RAW if raw else 0) | (BIE_GRID_OUT if grid_out else 0)
+        _check(lib().bie_apply_double(self.ctx.h, self.h, _ptr(u), _ptr(out), flag, _stream()), "bie_apply_double")
+        return out
+
+    def interfacial_force(self, gamma: torch.Tensor, elasticity: float, x_s: float, out: torch.Tensor):
+        _check(lib().bie_interfacial_force(self.ctx.h, self.h, _ptr(gamma), elasticity, x_s, _ptr(out), _stream()),
+               "bie_interfacial_force")
+        return out
+
+    def solve(self, rhs: torch.Tensor, u: torch.Tensor, precision: int = BIE_FP64, tol: float = 1e-10,
+              restart: int = 30, max_iter: int = 300, inner_tol: float = 1e-5, max_refine: int = 10,
+              raise_on_noconv: bool = True) -> dict:
+        o = bie_solve_opts()
+        lib().bie_solve_opts_default(ctypes.byref(o))
+        o.precision, o.tol, o.restart, o.max_iter, o.inner_tol, o.max_refine = (
+            precision, tol, restart, max_iter, inner_tol, max_refine)
+        info = bie_solve_info()
+        st = lib().bie_solve(self.ctx.h, self.h, _ptr(rhs), _ptr(u), ctypes.byref(o), ctypes.byref(info), _stream())
+        res = {k: getattr(info, k) for k, _ in bie_solve_info._fields_}
+        if st == 4 and not raise_on_noconv:
+            return res
+        _check(st, "bie_solve")
+        return res
+
+
+def debug_table(which: int, a: int, b: int = 0, c: int = 0, x: float = 0.0):
+    """Host plan tables of the library (no GPU needed), as a Python list."""
+    L = lib()
+    n = L.bie_debug_table(which, a, b, c, x, None, 0)
+    if n < 0:
+        raise ValueError("bad table request")
+    buf = (ctypes.c_double * n)()
+    L.bie_debug_table(which, a, b, c, x, buf, n)
+    return list(buf)

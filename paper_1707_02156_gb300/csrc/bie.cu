@@ -1,0 +1,954 @@
+// C ABI entry points: context and plan caches, transforms, geometry set-up, the layer-operator
+// applies (Eq. main_eq) and the GMRES solve (Sec. 7).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+#include "tables.h"
+
+namespace bie {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static const double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct DevBuf {
+  T* ptr = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    n = 0;
+  }
+  int alloc(size_t count) {
+    if (count <= n && ptr) return BIE_OK;
+    release();
+    if (count == 0) return BIE_OK;
+    cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+    if (e != cudaSuccess) {
+      ptr = nullptr;
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return BIE_ENOMEM;
+    }
+    n = count;
+    return BIE_OK;
+  }
+  int upload(const T* host, size_t count) {
+    BIE_TRY(alloc(count));
+    if (count) BIE_CUDA_TRY(cudaMemcpy(ptr, host, count * sizeof(T), cudaMemcpyHostToDevice));
+    return BIE_OK;
+  }
+  int upload(const std::vector<T>& v) { return upload(v.data(), v.size()); }
+};
+
+template <typename T>
+static int upload_as(DevBuf<T>& dst, const std::vector<double>& v) {
+  std::vector<T> tmp(v.begin(), v.end());
+  return dst.upload(tmp);
+}
+
+// ---------------------------------------------------------------------------------------------
+// plans: tables for coefficients of degree p on the grid of degree P
+// ---------------------------------------------------------------------------------------------
+struct Plan {
+  int p = 0, P = 0;
+  DevBuf<double> T0, T1, T2, A, cs, wsin, wsq;
+  DevBuf<float> T0f, csf;
+  template <typename R>
+  const R* T0_() const;
+  template <typename R>
+  const R* cs_() const;
+};
+template <>
+const double* Plan::T0_<double>() const {
+  return T0.ptr;
+}
+template <>
+const float* Plan::T0_<float>() const {
+  return T0f.ptr;
+}
+template <>
+const double* Plan::cs_<double>() const {
+  return cs.ptr;
+}
+template <>
+const float* Plan::cs_<float>() const {
+  return csf.ptr;
+}
+
+struct WigPlan {  // rotation blocks for the p+1 latitudes of the degree-p grid
+  int p = 0;
+  long long stride = 0;
+  DevBuf<double> blk;
+  DevBuf<float> blkf;
+  template <typename R>
+  const R* blk_() const;
+};
+template <>
+const double* WigPlan::blk_<double>() const {
+  return blk.ptr;
+}
+template <>
+const float* WigPlan::blk_<float>() const {
+  return blkf.ptr;
+}
+
+}  // namespace bie
+
+struct bie_ctx {
+  bie_config cfg;
+  std::mutex mu;
+  std::map<std::pair<int, int>, std::unique_ptr<bie::Plan>> plans;
+  std::map<int, std::unique_ptr<bie::WigPlan>> wigs;
+  bie::DevBuf<double> scratch;  // analysis workspace
+};
+
+namespace bie {
+
+static int get_plan(bie_ctx* ctx, int p, int P, Plan** out) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto key = std::make_pair(p, P);
+  auto it = ctx->plans.find(key);
+  if (it != ctx->plans.end()) {
+    *out = it->second.get();
+    return BIE_OK;
+  }
+  std::unique_ptr<Plan> pl(new Plan());
+  pl->p = p;
+  pl->P = P;
+  std::vector<double> v;
+  legendre_table(p, P, 0, v);
+  BIE_TRY(pl->T0.upload(v));
+  BIE_TRY(upload_as(pl->T0f, v));
+  legendre_table(p, P, 1, v);
+  BIE_TRY(pl->T1.upload(v));
+  legendre_table(p, P, 2, v);
+  BIE_TRY(pl->T2.upload(v));
+  analysis_table(p, P, v);
+  BIE_TRY(pl->A.upload(v));
+  phase_table(p, P, v);
+  BIE_TRY(pl->cs.upload(v));
+  BIE_TRY(upload_as(pl->csf, v));
+  std::vector<double> t, w, ws;
+  gauss_legendre(P + 1, t, w);
+  singular_weights(P, ws);
+  std::vector<double> wsin(P + 1), wsq(P + 1);
+  for (int j = 0; j <= P; ++j) {
+    double s = std::sqrt((1.0 - t[j]) * (1.0 + t[j]));
+    wsin[j] = kPi / (P + 1) * w[j] / s;
+    wsq[j] = ws[j] / s;
+  }
+  BIE_TRY(pl->wsin.upload(wsin));
+  BIE_TRY(pl->wsq.upload(wsq));
+  *out = pl.get();
+  ctx->plans[key] = std::move(pl);
+  return BIE_OK;
+}
+
+static int get_wig(bie_ctx* ctx, int p, WigPlan** out) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->wigs.find(p);
+  if (it != ctx->wigs.end()) {
+    *out = it->second.get();
+    return BIE_OK;
+  }
+  std::unique_ptr<WigPlan> wp(new WigPlan());
+  wp->p = p;
+  wp->stride = wigner_block_stride(p);
+  std::vector<double> t, w;
+  gauss_legendre(p + 1, t, w);
+  std::vector<double> blk((size_t)(p + 1) * wp->stride);
+  for (int a = 0; a <= p; ++a) wigner_blocks(p, std::acos(t[a]), blk.data() + (size_t)a * wp->stride);
+  BIE_TRY(wp->blk.upload(blk));
+  BIE_TRY(upload_as(wp->blkf, blk));
+  *out = wp.get();
+  ctx->wigs[p] = std::move(wp);
+  return BIE_OK;
+}
+
+static inline long long ncoef(int p) { return (long long)(p + 1) * (p + 1); }
+static inline long long ngrid(int P) { return (long long)(P + 1) * (2 * P + 2); }
+
+static int check_degrees(int ndrop, const int* p) {
+  if (ndrop <= 0 || !p) {
+    set_error("ndrop must be positive and p non-null");
+    return BIE_EINVAL;
+  }
+  for (int d = 0; d < ndrop; ++d)
+    if (p[d] < 1 || p[d] > BIE_MAX_P) {
+      set_error("degree out of range [1, BIE_MAX_P]");
+      return BIE_EINVAL;
+    }
+  return BIE_OK;
+}
+
+}  // namespace bie
+
+// ---------------------------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------------------------
+struct bie_geom {
+  bie_ctx* ctx = nullptr;
+  int ndrop = 0;
+  std::vector<int> p, pq;
+  std::vector<double> lambda;
+  std::vector<long long> coef_off;  // start of drop d's [3][(p+1)^2] block (doubles)
+  std::vector<long long> tgt_off;   // first target of drop d
+  long long ncoef_total = 0, ntarget = 0;
+  bie::DevBuf<double> xcoef;        // copy of the shape coefficients
+  bie::DevBuf<double> rec_std;      // [drop][7][N_g] targets / standard-grid sources
+  bie::DevBuf<double> vals;         // [drop][3][N_g] apply values at the grid targets
+  bie::DevBuf<double> lamc;         // lambda of the drop owning each coefficient
+  struct Group {
+    int p = 0, pq = 0;
+    std::vector<int> drops;
+    int chunk = 1;                          // drops per apply chunk
+    bie::DevBuf<long long> foff3, goff3, val_off;
+    bie::DevBuf<double> wS, wD, wSraw, wDraw;
+    bie::DevBuf<double> cache64;            // [gdrop][N_g][7][nq]
+    bie::DevBuf<float> cache32;
+  };
+  std::vector<std::unique_ptr<Group>> groups;
+  bie::DevBuf<double> ws64;   // apply workspace
+  bie::DevBuf<float> ws32;
+  bie::DevBuf<double> anaF;   // analysis workspace
+  bie_geom_info info{};
+};
+
+namespace bie {
+
+static const long long kWorkBudget = 3LL << 30;  // bytes of apply temporaries per precision
+
+// apply temporaries per drop: rotated coefficients, Legendre partial sums, rotated grid values
+static long long apply_floats_per_drop(int p, int pq) {
+  long long ng = ngrid(p), nq = ngrid(pq);
+  return ng * 3 * ncoef(p) + ng * 3 * (long long)(p + 1) * (pq + 1) * 2 + ng * 3 * nq;
+}
+
+static int analyze_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, const double* vals, double* out,
+                         cudaStream_t s) {
+  Plan* pl;
+  BIE_TRY(get_plan(ctx, G.p, G.p, &pl));
+  long long nf = (long long)G.drops.size() * 3;
+  BIE_TRY(g->anaF.alloc(nf * (G.p + 1) * (G.p + 1) * 2));
+  return launch_analyze(vals, G.goff3.ptr, 0, nf, G.p, G.p, pl->cs.ptr, pl->A.ptr, g->anaF.ptr, out, G.foff3.ptr,
+                        0, s);
+}
+
+template <typename R>
+static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s) {
+  bie_ctx* ctx = g->ctx;
+  for (auto& Gp : g->groups) {
+    auto& G = *Gp;
+    const int p = G.p, pq = G.pq;
+    Plan *pl, *pp;
+    WigPlan* wp;
+    BIE_TRY(get_plan(ctx, p, pq, &pl));
+    BIE_TRY(get_plan(ctx, p, p, &pp));
+    BIE_TRY(get_wig(ctx, p, &wp));
+    const long long ng = ngrid(p), nq = ngrid(pq);
+    const long long per = apply_floats_per_drop(p, pq);
+    R* work;
+    if (sizeof(R) == 8) {
+      BIE_TRY(g->ws64.alloc(per * G.chunk));
+      work = reinterpret_cast<R*>(g->ws64.ptr);
+    } else {
+      BIE_TRY(g->ws32.alloc(per * G.chunk));
+      work = reinterpret_cast<R*>(g->ws32.ptr);
+    }
+    const R* cache = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.cache64.ptr)
+                                    : reinterpret_cast<const R*>(G.cache32.ptr);
+    const double* wts = kind == 0 ? (raw ? G.wSraw.ptr : G.wS.ptr) : (raw ? G.wDraw.ptr : G.wD.ptr);
+    const int nd = (int)G.drops.size();
+    for (int c0 = 0; c0 < nd; c0 += G.chunk) {
+      const int cn = std::min(G.chunk, nd - c0);
+      R* RC = work;
+      R* H = RC + cn * ng * 3 * ncoef(p);
+      R* RHO = H + cn * ng * 3 * (long long)(p + 1) * (pq + 1) * 2;
+      BIE_TRY((launch_rotate<double, R>(dens, G.foff3.ptr + 3 * c0, 3, cn, p, wp->blk_<R>(), wp->stride, p + 1,
+                                        2 * p + 2, pp->cs_<R>(), RC, ng * 3 * ncoef(p), s)));
+      BIE_TRY((launch_leg_synth<R, R>(RC, nullptr, ncoef(p), cn * ng * 3, p, pl->T0_<R>(), pq + 1, H, 0, s)));
+      BIE_TRY((launch_phi_synth<R, R>(H, cn * ng * 3, p, pq, pl->cs_<R>(), RHO, nullptr, nq, s)));
+      BIE_TRY(launch_self_pairs<R>(kind, cache + (long long)c0 * ng * 7 * nq, RHO, cn, (int)ng, nq, wts + c0,
+                                   G.val_off.ptr + c0, g->vals.ptr, s));
+    }
+  }
+  return BIE_OK;
+}
+
+static int layer_apply(bie_ctx* ctx, const bie_geom* gc, int kind, const double* dens, double* out, int precision,
+                       cudaStream_t s) {
+  bie_geom* g = const_cast<bie_geom*>(gc);
+  if (!ctx || !g || !dens || !out) {
+    set_error("null argument");
+    return BIE_EINVAL;
+  }
+  const bool raw = (precision & BIE_RAW) != 0;
+  const int prec = precision & 0xff;
+  if (prec != BIE_FP64 && prec != BIE_MIXED) {
+    set_error("precision must be BIE_FP64 or BIE_MIXED");
+    return BIE_EINVAL;
+  }
+  if (prec == BIE_FP64)
+    BIE_TRY(self_apply<double>(g, kind, raw, dens, s));
+  else
+    BIE_TRY(self_apply<float>(g, kind, raw, dens, s));
+  if (g->ndrop > 1) {
+    set_error("multi-drop apply not available in this build");
+    return BIE_ENOTSUP;
+  }
+  if (precision & BIE_GRID_OUT) {
+    BIE_CUDA_TRY(cudaMemcpyAsync(out, g->vals.ptr, 3 * g->ntarget * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return BIE_OK;
+  }
+  for (auto& G : g->groups) BIE_TRY(analyze_group(ctx, g, *G, g->vals.ptr, out, s));
+  return BIE_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// geometry set-up
+// ---------------------------------------------------------------------------------------------
+// x, x_theta, x_phi of ncomp=3 fields on the grid of degree P from coefficients of degree p.
+static int synth_xderivs(bie_ctx* ctx, const double* coef, const long long* field_off, long long coef_stride,
+                         long long nfield, int p, int P, double* H, double* X, double* Xt, double* Xp,
+                         cudaStream_t s) {
+  Plan* pl;
+  BIE_TRY(get_plan(ctx, p, P, &pl));
+  const long long N = ngrid(P);
+  BIE_TRY((launch_leg_synth<double, double>(coef, field_off, coef_stride, nfield, p, pl->T0.ptr, P + 1, H, 0, s)));
+  BIE_TRY((launch_phi_synth<double, double>(H, nfield, p, P, pl->cs.ptr, X, nullptr, N, s)));
+  BIE_TRY((launch_leg_synth<double, double>(coef, field_off, coef_stride, nfield, p, pl->T0.ptr, P + 1, H, 1, s)));
+  BIE_TRY((launch_phi_synth<double, double>(H, nfield, p, P, pl->cs.ptr, Xp, nullptr, N, s)));
+  BIE_TRY((launch_leg_synth<double, double>(coef, field_off, coef_stride, nfield, p, pl->T1.ptr, P + 1, H, 0, s)));
+  BIE_TRY((launch_phi_synth<double, double>(H, nfield, p, P, pl->cs.ptr, Xt, nullptr, N, s)));
+  return BIE_OK;
+}
+
+static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream_t s) {
+  const int p = G.p, pq = G.pq;
+  const long long ng = ngrid(p), nq = ngrid(pq), nc = ncoef(p);
+  const int nd = (int)G.drops.size();
+  // offsets
+  std::vector<long long> foff3(3 * nd), goff3(3 * nd), voff(nd);
+  std::vector<double> wS(nd), wD(nd), wSr(nd), wDr(nd);
+  for (int i = 0; i < nd; ++i) {
+    int d = G.drops[i];
+    for (int c = 0; c < 3; ++c) {
+      foff3[3 * i + c] = g->coef_off[d] + c * nc;
+      goff3[3 * i + c] = 3 * g->tgt_off[d] + c * ng;
+    }
+    voff[i] = 3 * g->tgt_off[d];
+    wS[i] = -1.0 / (4 * kPi);
+    wD[i] = (g->lambda[d] - 1.0) / (4 * kPi);
+    wSr[i] = 1.0 / (8 * kPi);
+    wDr[i] = 1.0 / (4 * kPi);
+  }
+  BIE_TRY(G.foff3.upload(foff3));
+  BIE_TRY(G.goff3.upload(goff3));
+  BIE_TRY(G.val_off.upload(voff));
+  BIE_TRY(G.wS.upload(wS));
+  BIE_TRY(G.wD.upload(wD));
+  BIE_TRY(G.wSraw.upload(wSr));
+  BIE_TRY(G.wDraw.upload(wDr));
+  G.chunk = (int)std::max(1LL, std::min<long long>(nd, kWorkBudget / (8 * apply_floats_per_drop(p, pq))));
+
+  // standard grid: targets and regular-rule sources, one drop at a time
+  {
+    Plan* pl;
+    BIE_TRY(get_plan(ctx, p, p, &pl));
+    DevBuf<double> tmp;
+    BIE_TRY(tmp.alloc(3 * (p + 1) * (p + 1) * 2 + 9 * ng));
+    double* H = tmp.ptr;
+    double* X = H + 3 * (p + 1) * (p + 1) * 2;
+    for (int i = 0; i < nd; ++i) {
+      int d = G.drops[i];
+      BIE_TRY(synth_xderivs(ctx, g->xcoef.ptr + g->coef_off[d], nullptr, nc, 3, p, p, H, X, X + 3 * ng,
+                            X + 6 * ng, s));
+      BIE_TRY(launch_surface(X, X + 3 * ng, X + 6 * ng, 1, p, pl->wsin.ptr, g->rec_std.ptr + 7 * g->tgt_off[d], s));
+    }
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+
+  // rotated-grid cache of the singular rule (Sec. 2.2), chunked over drops
+  Plan *pl, *pp;
+  WigPlan* wp;
+  BIE_TRY(get_plan(ctx, p, pq, &pl));
+  BIE_TRY(get_plan(ctx, p, p, &pp));
+  BIE_TRY(get_wig(ctx, p, &wp));
+  BIE_TRY(G.cache64.alloc((size_t)nd * ng * 7 * nq));
+  BIE_TRY(G.cache32.alloc((size_t)nd * ng * 7 * nq));
+  const long long per = ng * 3 * nc + ng * 3 * (long long)(p + 1) * (pq + 1) * 2 + 3 * ng * 3 * nq;
+  int chunk = (int)std::max(1LL, std::min<long long>(nd, (2 * kWorkBudget) / (8 * per)));
+  DevBuf<double> work;
+  BIE_TRY(work.alloc((size_t)chunk * per));
+  for (int c0 = 0; c0 < nd; c0 += chunk) {
+    const int cn = std::min(chunk, nd - c0);
+    double* RC = work.ptr;
+    double* H = RC + cn * ng * 3 * nc;
+    double* X = H + cn * ng * 3 * (long long)(p + 1) * (pq + 1) * 2;
+    double* Xt = X + cn * ng * 3 * nq;
+    double* Xp = Xt + cn * ng * 3 * nq;
+    // x coefficients of the chunk's drops: field offsets into the geometry's copy
+    BIE_TRY((launch_rotate<double, double>(g->xcoef.ptr, G.foff3.ptr + 3 * c0, 3, cn, p, wp->blk.ptr, wp->stride,
+                                           p + 1, 2 * p + 2, pp->cs.ptr, RC, ng * 3 * nc, s)));
+    BIE_TRY(synth_xderivs(ctx, RC, nullptr, nc, cn * ng * 3, p, pq, H, X, Xt, Xp, s));
+    const double* rec0 = g->rec_std.ptr + 7 * g->tgt_off[G.drops[c0]];
+    BIE_TRY(launch_rotgeo<double>(X, Xt, Xp, cn, (int)ng, pq, rec0, pl->wsq.ptr,
+                                  G.cache64.ptr + (long long)c0 * ng * 7 * nq, s));
+    BIE_TRY(launch_rotgeo<float>(X, Xt, Xp, cn, (int)ng, pq, rec0, pl->wsq.ptr,
+                                 G.cache32.ptr + (long long)c0 * ng * 7 * nq, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return BIE_OK;
+}
+
+}  // namespace bie
+
+// ---------------------------------------------------------------------------------------------
+// GMRES helpers (device vectors, host Hessenberg)
+// ---------------------------------------------------------------------------------------------
+namespace bie {
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 120;
+
+// partial[i][b] = sum over block b's slice of V_i . w   (i < k)
+__global__ void k_multidot(const double* __restrict__ V, long long ldv, const double* __restrict__ w, long long n,
+                           int k, double* __restrict__ partial) {
+  __shared__ double sh[kRedThreads / 32];
+  const int i = blockIdx.y;
+  const double* v = V + (long long)i * ldv;
+  double acc = 0;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x)
+    acc += v[x] * w[x];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int q = 0; q < kRedThreads / 32; ++q) t += sh[q];
+    partial[(long long)i * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int nb, int k, double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  double t = 0;
+  for (int b = 0; b < nb; ++b) t += partial[(long long)i * nb + b];
+  out[i] = t;
+}
+
+// w -= sum_i h[i] V_i
+__global__ void k_sub_comb(double* __restrict__ w, const double* __restrict__ V, long long ldv,
+                           const double* __restrict__ h, int k, long long n) {
+  long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  double t = w[x];
+  for (int i = 0; i < k; ++i) t -= h[i] * V[(long long)i * ldv + x];
+  w[x] = t;
+}
+
+// y = a*x + b*y
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+
+// y = (lam+1) u - d   (system operator of Eq. main_eq from the double-layer apply d)
+__global__ void k_sysop(const double* __restrict__ lam, const double* __restrict__ u, const double* __restrict__ d,
+                        double* __restrict__ y, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (lam[i] + 1.0) * u[i] - d[i];
+}
+
+// x += V^T y (y on the device, k entries)
+__global__ void k_add_comb(double* __restrict__ x, const double* __restrict__ V, long long ldv,
+                           const double* __restrict__ y, int k, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double t = x[i];
+  for (int q = 0; q < k; ++q) t += y[q] * V[(long long)q * ldv + i];
+  x[i] = t;
+}
+
+inline unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+struct Krylov {
+  long long n = 0;
+  int m = 0;
+  DevBuf<double> V, w, tmp, partial, hdev;
+};
+
+static int dots(Krylov& K, const double* V, int k, const double* w, std::vector<double>& out, cudaStream_t s) {
+  dim3 grid(kRedBlocks, k);
+  k_multidot<<<grid, kRedThreads, 0, s>>>(V, K.n, w, K.n, k, K.partial.ptr);
+  BIE_CUDA_TRY(cudaGetLastError());
+  k_sum_partials<<<(k + 127) / 128, 128, 0, s>>>(K.partial.ptr, kRedBlocks, k, K.hdev.ptr);
+  BIE_CUDA_TRY(cudaGetLastError());
+  out.resize(k);
+  BIE_CUDA_TRY(cudaMemcpyAsync(out.data(), K.hdev.ptr, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return BIE_OK;
+}
+
+static int norm2(Krylov& K, const double* x, double* out, cudaStream_t s) {
+  std::vector<double> h;
+  BIE_TRY(dots(K, x, 1, x, h, s));
+  *out = std::sqrt(std::max(0.0, h[0]));
+  return BIE_OK;
+}
+
+// system matvec y = (lambda+1) u - D[u] at precision prec
+static int sys_matvec(bie_ctx* ctx, const bie_geom* g, const double* u, double* y, double* tmp, int prec,
+                      bie_solve_info* info, cudaStream_t s) {
+  BIE_TRY(layer_apply(ctx, g, 1, u, tmp, prec, s));
+  if (prec == BIE_FP64)
+    info->applies_fp64++;
+  else
+    info->applies_mixed++;
+  k_sysop<<<nblk(g->ncoef_total), 256, 0, s>>>(g->lamc.ptr, u, tmp, y, g->ncoef_total);
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+// Restarted GMRES (Sec. 7) with classical Gram-Schmidt and one re-orthogonalisation, FP64 Krylov
+// basis; the operator is applied at precision prec.  x holds the initial guess (zero if x_is_zero).
+static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, double* x, bool x_is_zero, double tol,
+                 int restart, int max_iter, Krylov& K, bie_solve_info* info, double* relres, cudaStream_t s) {
+  const long long n = g->ncoef_total;
+  const int m = restart;
+  double* r = K.tmp.ptr;            // residual
+  double* t2 = K.tmp.ptr + n;       // apply temporary
+  double bnorm;
+  BIE_TRY(norm2(K, b, &bnorm, s));
+  if (bnorm == 0.0) {
+    BIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    *relres = 0;
+    return BIE_OK;
+  }
+  int it = 0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol, h2;
+  while (true) {
+    // r = b - A x
+    if (x_is_zero) {
+      BIE_CUDA_TRY(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      BIE_TRY(sys_matvec(ctx, g, x, r, t2, prec, info, s));
+      k_axpby<<<nblk(n), 256, 0, s>>>(1.0, b, -1.0, r, n);
+      BIE_CUDA_TRY(cudaGetLastError());
+    }
+    double beta;
+    BIE_TRY(norm2(K, r, &beta, s));
+    *relres = beta / bnorm;
+    if (beta / bnorm <= tol || it >= max_iter) return beta / bnorm <= tol ? BIE_OK : BIE_ENOCONV;
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    double* V = K.V.ptr;
+    k_axpby<<<nblk(n), 256, 0, s>>>(1.0 / beta, r, 0.0, V, n);
+    BIE_CUDA_TRY(cudaGetLastError());
+    int k_used = 0;
+    for (int k = 0; k < m; ++k) {
+      double* vk1 = V + (long long)(k + 1) * n;
+      BIE_TRY(sys_matvec(ctx, g, V + (long long)k * n, vk1, t2, prec, info, s));
+      // CGS with one re-orthogonalisation
+      BIE_TRY(dots(K, V, k + 1, vk1, hcol, s));
+      BIE_CUDA_TRY(cudaMemcpyAsync(K.hdev.ptr, hcol.data(), (k + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+      k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, K.hdev.ptr, k + 1, n);
+      BIE_CUDA_TRY(cudaGetLastError());
+      BIE_TRY(dots(K, V, k + 1, vk1, h2, s));
+      BIE_CUDA_TRY(cudaMemcpyAsync(K.hdev.ptr, h2.data(), (k + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+      k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, K.hdev.ptr, k + 1, n);
+      BIE_CUDA_TRY(cudaGetLastError());
+      for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = hcol[i] + h2[i];
+      double hn;
+      BIE_TRY(norm2(K, vk1, &hn, s));
+      H[(size_t)(k + 1) * m + k] = hn;
+      if (hn > 0) {
+        k_axpby<<<nblk(n), 256, 0, s>>>(1.0 / hn, vk1, 0.0, vk1, n);
+        BIE_CUDA_TRY(cudaGetLastError());
+      }
+      for (int i = 0; i < k; ++i) {
+        double a = H[(size_t)i * m + k], bb = H[(size_t)(i + 1) * m + k];
+        H[(size_t)i * m + k] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * bb;
+      }
+      double a = H[(size_t)k * m + k], bb = H[(size_t)(k + 1) * m + k];
+      double den = std::hypot(a, bb);
+      cs[k] = a / den;
+      sn[k] = bb / den;
+      H[(size_t)k * m + k] = den;
+      H[(size_t)(k + 1) * m + k] = 0;
+      gv[k + 1] = -sn[k] * gv[k];
+      gv[k] = cs[k] * gv[k];
+      ++it;
+      info->iterations++;
+      k_used = k + 1;
+      if (std::fabs(gv[k + 1]) / bnorm <= tol || it >= max_iter || hn == 0) break;
+    }
+    std::vector<double> y(k_used);
+    for (int i = k_used - 1; i >= 0; --i) {
+      double t = gv[i];
+      for (int q = i + 1; q < k_used; ++q) t -= H[(size_t)i * m + q] * y[q];
+      y[i] = t / H[(size_t)i * m + i];
+    }
+    BIE_CUDA_TRY(cudaMemcpyAsync(K.hdev.ptr, y.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_add_comb<<<nblk(n), 256, 0, s>>>(x, V, n, K.hdev.ptr, k_used, n);
+    BIE_CUDA_TRY(cudaGetLastError());
+    x_is_zero = false;
+  }
+}
+
+}  // namespace bie
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------------
+using namespace bie;
+
+extern "C" {
+
+void bie_config_default(bie_config* cfg) {
+  if (!cfg) return;
+  cfg->device = 0;
+  cfg->upsample = 4;
+  cfg->a_tilde = 5.0;
+  cfg->n_interp = 8;
+}
+
+const char* bie_strerror(int st) {
+  switch (st) {
+    case BIE_OK: return "ok";
+    case BIE_EINVAL: return "invalid argument";
+    case BIE_ENOMEM: return "out of memory";
+    case BIE_ECUDA: return "CUDA error";
+    case BIE_ENOCONV: return "iterative solve did not converge";
+    case BIE_ETIMEOUT: return "bounded device wait timed out";
+    case BIE_EOVERLAP: return "drops overlap";
+    case BIE_ENOTSUP: return "not supported";
+    default: return "unknown status";
+  }
+}
+
+const char* bie_last_error(void) { return g_last_error.c_str(); }
+
+int bie_create(bie_ctx** out, const bie_config* cfg) {
+  if (!out) return BIE_EINVAL;
+  *out = nullptr;
+  bie_config c;
+  bie_config_default(&c);
+  if (cfg) c = *cfg;
+  if (c.upsample < 1 || c.a_tilde <= 1.0 || c.n_interp < 1 || c.n_interp > 16) {
+    set_error("bad config");
+    return BIE_EINVAL;
+  }
+  int ndev = 0;
+  BIE_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (c.device < 0 || c.device >= ndev) {
+    set_error("device ordinal out of range");
+    return BIE_EINVAL;
+  }
+  BIE_CUDA_TRY(cudaSetDevice(c.device));
+  bie_ctx* ctx = new bie_ctx();
+  ctx->cfg = c;
+  *out = ctx;
+  return BIE_OK;
+}
+
+void bie_destroy(bie_ctx* ctx) { delete ctx; }
+
+int bie_sh_analyze(bie_ctx* ctx, int ndrop, const int* p, int ncomp, const double* grid, double* coef,
+                   void* stream) {
+  if (!ctx || !grid || !coef || ncomp <= 0) return BIE_EINVAL;
+  BIE_TRY(check_degrees(ndrop, p));
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  long long go = 0, co = 0;
+  for (int d = 0; d < ndrop; ++d) {
+    Plan* pl;
+    BIE_TRY(get_plan(ctx, p[d], p[d], &pl));
+    BIE_TRY(ctx->scratch.alloc((size_t)ncomp * (p[d] + 1) * (p[d] + 1) * 2));
+    BIE_TRY(launch_analyze(grid + go, nullptr, ngrid(p[d]), ncomp, p[d], p[d], pl->cs.ptr, pl->A.ptr,
+                           ctx->scratch.ptr, coef + co, nullptr, ncoef(p[d]), s));
+    go += ncomp * ngrid(p[d]);
+    co += ncomp * ncoef(p[d]);
+  }
+  return BIE_OK;
+}
+
+int bie_sh_synthesize(bie_ctx* ctx, int ndrop, const int* p, const int* p_out, int ncomp, const double* coef,
+                      double* grid, void* stream) {
+  if (!ctx || !grid || !coef || !p_out || ncomp <= 0) return BIE_EINVAL;
+  BIE_TRY(check_degrees(ndrop, p));
+  for (int d = 0; d < ndrop; ++d)
+    if (p_out[d] < p[d] || p_out[d] > 4 * BIE_MAX_P) {
+      set_error("p_out must satisfy p <= p_out <= 4*BIE_MAX_P");
+      return BIE_EINVAL;
+    }
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  long long go = 0, co = 0;
+  for (int d = 0; d < ndrop; ++d) {
+    Plan* pl;
+    BIE_TRY(get_plan(ctx, p[d], p_out[d], &pl));
+    BIE_TRY(ctx->scratch.alloc((size_t)ncomp * (p[d] + 1) * (p_out[d] + 1) * 2));
+    BIE_TRY((launch_leg_synth<double, double>(coef + co, nullptr, ncoef(p[d]), ncomp, p[d], pl->T0.ptr,
+                                              p_out[d] + 1, ctx->scratch.ptr, 0, s)));
+    BIE_TRY((launch_phi_synth<double, double>(ctx->scratch.ptr, ncomp, p[d], p_out[d], pl->cs.ptr, grid + go,
+                                              nullptr, ngrid(p_out[d]), s)));
+    go += ncomp * ngrid(p_out[d]);
+    co += ncomp * ncoef(p[d]);
+  }
+  return BIE_OK;
+}
+
+int bie_rotate(bie_ctx* ctx, int ndrop, const int* p, int ncomp, const double* coef, const double* euler,
+               double* coef_out, void* stream) {
+  if (!ctx || !coef || !coef_out || !euler || ncomp <= 0) return BIE_EINVAL;
+  BIE_TRY(check_degrees(ndrop, p));
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  long long co = 0;
+  for (int d = 0; d < ndrop; ++d) {
+    const int pd = p[d];
+    std::vector<double> blk(wigner_block_stride(pd));
+    wigner_blocks(pd, euler[3 * d + 1], blk.data());
+    std::vector<double> ph((size_t)(pd + 1) * 2);
+    for (int m = 0; m <= pd; ++m) {
+      ph[2 * m] = std::cos(m * euler[3 * d]);
+      ph[2 * m + 1] = std::sin(m * euler[3 * d]);
+    }
+    std::vector<long long> foff(ncomp);
+    for (int c = 0; c < ncomp; ++c) foff[c] = co + c * ncoef(pd);
+    DevBuf<double> dblk, dph;
+    DevBuf<long long> dfo;
+    BIE_TRY(dblk.upload(blk));
+    BIE_TRY(dph.upload(ph));
+    BIE_TRY(dfo.upload(foff));
+    BIE_TRY((launch_rotate<double, double>(coef, dfo.ptr, ncomp, 1, pd, dblk.ptr, (long long)blk.size(), 1, 1,
+                                           dph.ptr, coef_out + co, 0, s)));
+    BIE_TRY(launch_phase(coef_out + co, ncomp, pd, euler[3 * d + 2], s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));  // the staged tables are released on return
+    co += ncomp * ncoef(pd);
+  }
+  return BIE_OK;
+}
+
+int bie_geometry_setup(bie_ctx* ctx, int ndrop, const int* p, const int* pq, const double* xcoef,
+                       const double* lambda, bie_geom** out, void* stream) {
+  if (!ctx || !out || !xcoef || !lambda || !pq) return BIE_EINVAL;
+  *out = nullptr;
+  BIE_TRY(check_degrees(ndrop, p));
+  for (int d = 0; d < ndrop; ++d)
+    if (pq[d] < p[d] || pq[d] > 2 * p[d] + 1) {
+      set_error("pq must satisfy p <= pq <= 2p+1");
+      return BIE_EINVAL;
+    }
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<bie_geom> g(new bie_geom());
+  g->ctx = ctx;
+  g->ndrop = ndrop;
+  g->p.assign(p, p + ndrop);
+  g->pq.assign(pq, pq + ndrop);
+  g->lambda.assign(lambda, lambda + ndrop);
+  g->coef_off.resize(ndrop);
+  g->tgt_off.resize(ndrop);
+  long long co = 0, to = 0;
+  for (int d = 0; d < ndrop; ++d) {
+    g->coef_off[d] = co;
+    g->tgt_off[d] = to;
+    co += 3 * ncoef(p[d]);
+    to += ngrid(p[d]);
+  }
+  g->ncoef_total = co;
+  g->ntarget = to;
+  BIE_TRY(g->xcoef.alloc(co));
+  BIE_CUDA_TRY(cudaMemcpyAsync(g->xcoef.ptr, xcoef, co * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  BIE_TRY(g->rec_std.alloc(7 * to));
+  BIE_TRY(g->vals.alloc(3 * to));
+  {
+    std::vector<double> lc(co);
+    for (int d = 0; d < ndrop; ++d)
+      std::fill(lc.begin() + g->coef_off[d], lc.begin() + g->coef_off[d] + 3 * ncoef(p[d]), lambda[d]);
+    BIE_TRY(g->lamc.upload(lc));
+  }
+  // group drops of equal (p, pq)
+  std::map<std::pair<int, int>, int> gi;
+  for (int d = 0; d < ndrop; ++d) {
+    auto key = std::make_pair(p[d], pq[d]);
+    if (!gi.count(key)) {
+      gi[key] = (int)g->groups.size();
+      g->groups.emplace_back(new bie_geom::Group());
+      g->groups.back()->p = p[d];
+      g->groups.back()->pq = pq[d];
+    }
+    g->groups[gi[key]]->drops.push_back(d);
+  }
+  long long self_pairs = 0;
+  for (auto& G : g->groups) {
+    BIE_TRY(setup_group(ctx, g.get(), *G, s));
+    self_pairs += (long long)G->drops.size() * ngrid(G->p) * ngrid(G->pq);
+  }
+  if (ndrop > 1) {
+    set_error("multi-drop geometry not available in this build");
+    return BIE_ENOTSUP;
+  }
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  g->info.ndrop = ndrop;
+  g->info.ncoef = co;
+  g->info.ntarget = to;
+  g->info.self_pairs = self_pairs;
+  double bytes = 0;
+  for (auto& G : g->groups) bytes += G->cache64.n * 8.0 + G->cache32.n * 4.0;
+  bytes += g->rec_std.n * 8.0 + g->vals.n * 8.0 + g->xcoef.n * 8.0;
+  g->info.cache_bytes = bytes;
+  *out = g.release();
+  return BIE_OK;
+}
+
+void bie_geometry_destroy(bie_geom* g) { delete g; }
+
+int bie_geometry_info(const bie_geom* g, bie_geom_info* info) {
+  if (!g || !info) return BIE_EINVAL;
+  *info = g->info;
+  return BIE_OK;
+}
+
+int bie_interfacial_force(bie_ctx*, const bie_geom*, const double*, double, double, double*, void*) {
+  set_error("interfacial force not available in this build");
+  return BIE_ENOTSUP;
+}
+
+int bie_apply_single(bie_ctx* ctx, const bie_geom* g, const double* fcoef, double* out, int precision,
+                     void* stream) {
+  if (!ctx) return BIE_EINVAL;
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  return layer_apply(ctx, g, 0, fcoef, out, precision, (cudaStream_t)stream);
+}
+
+int bie_apply_double(bie_ctx* ctx, const bie_geom* g, const double* ucoef, double* out, int precision,
+                     void* stream) {
+  if (!ctx) return BIE_EINVAL;
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  return layer_apply(ctx, g, 1, ucoef, out, precision, (cudaStream_t)stream);
+}
+
+void bie_solve_opts_default(bie_solve_opts* o) {
+  if (!o) return;
+  o->precision = BIE_FP64;
+  o->tol = 1e-10;
+  o->restart = 30;
+  o->max_iter = 300;
+  o->inner_tol = 1e-5;
+  o->max_refine = 10;
+}
+
+int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, const bie_solve_opts* opts,
+              bie_solve_info* info, void* stream) {
+  if (!ctx || !g || !rhs || !u || !opts || !info) return BIE_EINVAL;
+  if (opts->restart < 1 || opts->restart > 64 || opts->tol <= 0 || opts->max_iter < 1) {
+    set_error("bad solve options");
+    return BIE_EINVAL;
+  }
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::memset(info, 0, sizeof(*info));
+  const long long n = g->ncoef_total;
+  Krylov K;
+  K.n = n;
+  K.m = opts->restart;
+  BIE_TRY(K.V.alloc((size_t)(opts->restart + 1) * n));
+  BIE_TRY(K.tmp.alloc(3 * n));
+  BIE_TRY(K.partial.alloc((size_t)kRedBlocks * (opts->restart + 1)));
+  BIE_TRY(K.hdev.alloc(opts->restart + 1));
+  double rel = 0;
+  int st;
+  if ((opts->precision & 0xff) == BIE_FP64) {
+    st = gmres(ctx, g, BIE_FP64, rhs, u, false, opts->tol, opts->restart, opts->max_iter, K, info, &rel, s);
+    info->residual = rel;
+    info->converged = st == BIE_OK;
+    return st;
+  }
+  // mixed: FP64 residual outside, mixed-precision GMRES correction inside
+  DevBuf<double> r, dx, t;
+  BIE_TRY(r.alloc(n));
+  BIE_TRY(dx.alloc(n));
+  BIE_TRY(t.alloc(n));
+  double bnorm;
+  BIE_TRY(norm2(K, rhs, &bnorm, s));
+  int left = opts->max_iter;
+  for (int outer = 0;; ++outer) {
+    BIE_TRY(sys_matvec(ctx, g, u, r.ptr, t.ptr, BIE_FP64, info, s));
+    k_axpby<<<nblk(n), 256, 0, s>>>(1.0, rhs, -1.0, r.ptr, n);
+    BIE_CUDA_TRY(cudaGetLastError());
+    double rn;
+    BIE_TRY(norm2(K, r.ptr, &rn, s));
+    rel = bnorm > 0 ? rn / bnorm : 0.0;
+    info->residual = rel;
+    if (rel <= opts->tol) {
+      info->converged = 1;
+      return BIE_OK;
+    }
+    if (outer >= opts->max_refine || left <= 0) return BIE_ENOCONV;
+    info->refinements++;
+    int before = info->iterations;
+    double inner_rel;
+    BIE_CUDA_TRY(cudaMemsetAsync(dx.ptr, 0, n * sizeof(double), s));
+    st = gmres(ctx, g, BIE_MIXED, r.ptr, dx.ptr, true, opts->inner_tol, opts->restart, left, K, info, &inner_rel, s);
+    if (st != BIE_OK && st != BIE_ENOCONV) return st;
+    left -= info->iterations - before;
+    k_axpby<<<nblk(n), 256, 0, s>>>(1.0, dx.ptr, 1.0, u, n);
+    BIE_CUDA_TRY(cudaGetLastError());
+  }
+}
+
+long long bie_debug_table(int which, int a, int b, int c, double x, double* out, long long cap) {
+  std::vector<double> v;
+  if (which == 0) {
+    if (a < 0 || a > 4 * BIE_MAX_P) return -1;
+    std::vector<double> t, w;
+    gauss_legendre(a + 1, t, w);
+    v = t;
+    v.insert(v.end(), w.begin(), w.end());
+  } else if (which == 1) {
+    if (a < 0 || a > BIE_MAX_P || c < a || c > 4 * BIE_MAX_P || b < 0 || b > 2) return -1;
+    legendre_table(a, c, b, v);
+  } else if (which == 2) {
+    if (a < 0 || a > 2 * BIE_MAX_P) return -1;
+    v.resize((size_t)(2 * a + 1) * (2 * a + 1));
+    wigner_small_d(a, x, v.data());
+  } else if (which == 3) {
+    if (a < 0 || a > 4 * BIE_MAX_P) return -1;
+    singular_weights(a, v);
+  } else {
+    return -1;
+  }
+  if (out) std::memcpy(out, v.data(), sizeof(double) * std::min<long long>(cap, (long long)v.size()));
+  return (long long)v.size();
+}
+
+}  // extern "C"

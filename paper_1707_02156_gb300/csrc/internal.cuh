@@ -1,0 +1,72 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/bie.h"
+
+namespace bie {
+
+void set_error(const std::string& msg);
+
+#define BIE_CUDA_TRY(expr)                                                                     \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      ::bie::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));                    \
+      return BIE_ECUDA;                                                                        \
+    }                                                                                          \
+  } while (0)
+
+#define BIE_TRY(expr)              \
+  do {                             \
+    int s_ = (expr);               \
+    if (s_ != BIE_OK) return s_;   \
+  } while (0)
+
+__host__ __device__ inline long long leg_row(int p, int m, int n, int nj) {
+  long long before = (long long)m * (p + 1) - (long long)m * (m - 1) / 2;
+  return (before + (n - m)) * nj;
+}
+
+// ---- transforms (transforms.cu) ----
+// Legendre step of synthesis: H[f][m][j] = sum_n c_f(n,m) T[m][n][j] (complex, m >= 0), with an
+// optional phi-derivative factor (i m)^dphi.  Coefficients of field f start at
+// field_off ? field_off[f] : f * coef_stride.
+template <typename CT, typename R>
+int launch_leg_synth(const CT* coef, const long long* field_off, long long coef_stride, long long nfield, int p,
+                     const R* T, int nj, R* H, int dphi, cudaStream_t s);
+// phi step of synthesis: out[f][j][k] = Re sum_m fac_m H[f][m][j] e^{i m phi_k}, k < 2P+2
+template <typename R, typename OT>
+int launch_phi_synth(const R* H, long long nfield, int p, int P, const R* cs, OT* out,
+                     const long long* out_off, long long out_stride, cudaStream_t s);
+// analysis: grid (degree P) -> coefficients (degree p_out), FP64
+int launch_analyze(const double* grid, const long long* grid_off, long long grid_stride, long long nfield, int P,
+                   int p_out, const double* cs, const double* A, double* F, double* coef,
+                   const long long* coef_off, long long coef_stride, cudaStream_t s);
+// rotation (App. B): out[ld][a*nb+b][c] = blocks(a) applied to e^{i m alpha_b} coef[ld][c]
+template <typename CT, typename R>
+int launch_rotate(const CT* coef, const long long* field_off, int ncomp, long long ndrop, int p, const R* blocks,
+                  long long blk_stride, int na, int nb, const R* ph, R* out, long long out_drop_stride,
+                  cudaStream_t s);
+// multiply coefficients by e^{i m gamma} (in place), ncomp fields per drop
+int launch_phase(double* coef, long long nfield, int p, double gamma, cudaStream_t s);
+
+// ---- pair sums and geometry (pairs.cu) ----
+// Surface quantities from x, x_theta, x_phi grids [f=drop*3+c][j][k]: writes SoA source records
+// [drop][7][N] = (x, n, wgt*J) with wgt the regular weight (pi/(P+1)) w_j, J = W/sin(theta_j).
+int launch_surface(const double* X, const double* Xt, const double* Xp, long long ndrop, int P,
+                   const double* wsin /*[j] = w_j pi/(P+1)/sin theta_j*/, double* rec, cudaStream_t s);
+// Rotated-grid cache for ndrop drops of ng targets each: cache[t][7][nq] = (x0 - x', n',
+// w^s_j W'/sin theta_j) on the degree-pq grid; x0 read from the standard-grid records rec_std.
+template <typename R>
+int launch_rotgeo(const double* X, const double* Xt, const double* Xp, long long ndrop, int ng, int pq,
+                  const double* rec_std, const double* wsq, R* cache, cudaStream_t s);
+// Singular self pair sum (Thm 1): vals[val_off[d] + c*ng + t] = wts[d] * sum_q K(xh_q) rho_q wJ_q.
+template <typename R>
+int launch_self_pairs(int kind, const R* cache, const R* rho, long long ndrop, int ng, long long nq,
+                      const double* wts, const long long* val_off, double* vals, cudaStream_t s);
+
+}  // namespace bie

@@ -1,0 +1,63 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol declared in include/bie.h, and its
+host-side plan tables agree with the oracle (no GPU needed)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import layer, sh, wigner
+from paper_1707_02156_gb300 import api, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return api.lib()
+
+
+def test_exports_match_header(L):
+    hdr = open(os.path.join(ROOT, "include", "bie.h")).read()
+    names = set(re.findall(r"\b(bie_[a-z_0-9]+)\s*\(", hdr))
+    assert names, "no declarations found"
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert names == set(api.EXPORTS), sorted(names ^ set(api.EXPORTS))
+
+
+def test_gauss_legendre_nodes(L):
+    for P in (0, 5, 16, 65, 131):
+        v = np.array(api.debug_table(0, P))
+        t, w = v[:P + 1], v[P + 1:]
+        tr, wr = sh.gauss_legendre(P + 1)
+        assert np.max(np.abs(t - tr)) <= 2.3e-16
+        assert np.max(np.abs(w - wr) / wr) <= 4.5e-16
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_legendre_tables_match_oracle(L, kind):
+    p, P = 12, 25
+    v = np.array(api.debug_table(1, p, kind, P))
+    _, _, theta, _ = sh.gauss_grid(P)
+    tabs = sh.legendre_dtheta(p, theta)
+    ref = tabs[kind]
+    i = 0
+    for m in range(p + 1):
+        for n in range(m, p + 1):
+            assert np.max(np.abs(v[i:i + P + 1] - ref[n, m])) < 1e-12 * max(1, n * n), (m, n)
+            i += P + 1
+
+
+def test_wigner_small_d_matches_oracle(L):
+    for n in (0, 1, 7, 32, 48):
+        for beta in (0.05, 1.3, 3.05, -0.7):
+            v = np.array(api.debug_table(2, n, x=beta)).reshape(2 * n + 1, 2 * n + 1)
+            assert np.max(np.abs(v - wigner.small_d(n, beta))) < 2e-13
+
+
+def test_singular_weights_match_oracle(L):
+    for pq in (8, 33, 65):
+        v = np.array(api.debug_table(3, pq))
+        assert np.max(np.abs(v - layer.singular_weights(pq))) < 1e-14
