@@ -1,0 +1,336 @@
+"""Benchmark of the Stokes layer-operator apply and solve on SH drop surfaces (one JSON line).
+
+Workload (default): one drop of SH degree p = 32, sphere plus a seeded SH perturbation of
+amplitude 0.05 (degrees 1..6), viscosity ratio 5, shear u_inf = (z, 0, 0), self quadrature on the
+grid of degree 2p+1 = 65.  One step = the right-hand side 2 u_inf + S[f] (FP64) followed by the
+mixed-precision GMRES solve with FP64 iterative refinement to a relative residual of 1e-10.
+value = Stokes pair interactions evaluated per second (singular self-rule pairs of every operator
+apply in the step, divided by the step time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BIE matvec time & Stokes pair-interactions/s, FP64 vs mixed at 1e-8 rel err"
+UNIT = "pair-interactions/s"
+WORKLOAD = "one drop p=32 (sphere + 0.05 SH perturbation, n<=6), lambda=5, shear (z,0,0), self rule on the p_q=65 grid"
+FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
+FP64_ALU_PEAK = 1.25                              # TFLOP/s: nominal GB300 FP64 rate
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# algorithmic work of the singular self kernels, per target (FMA = 2 flops, rsqrt = 1)
+# ------------------------------------------------------------------------------------------------
+def self_work_per_target(name: str, p: int, pq: int, kind: str = "D"):
+    """(flops, bytes) of one target of the self kernel `name` (self_fourier_* or self_direct_*)."""
+    esize = 8 if name.endswith("f64") else 4
+    wig = sum((n + 1) ** 2 + n * n for n in range(p + 1))          # rotation blocks of one latitude
+    rot = 2.0 * 3 * wig                                              # three components
+    leg = 3.0 * (pq + 1) * (2 * (p + 1) + 4 * sum(p + 1 - m for m in range(1, p + 1)))
+    nq = (pq + 1) * (2 * pq + 2)
+    if "fourier" in name:
+        contr = 36.0 * (pq + 1) * (p + 1)                           # 3x3 complex symmetric times h_m
+        return rot + leg + contr, 12.0 * (pq + 1) * (p + 1) * esize  # Mhat read once per apply
+    phi = 3.0 * (pq + 1) * (pq + 1) * (4 * p + 2)                    # longitude pairs, even/odd orders
+    pair = (32.0 if kind == "D" else 29.0) * nq
+    return rot + leg + phi + pair, nq * (7 if kind == "D" else 4) * esize
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1707_02156_gb300 import api, build, inputs
+    build.build()
+    ctx = api.Context(local)
+    w = inputs.perturbed_drop()
+    p, pq = w.p[0], w.pq[0]
+    x = torch.tensor(w.xcoef, device="cuda")
+    geo = ctx.geometry(w.p, w.pq, x, w.lam)
+    nco = geo.info["ncoef"]
+    pairs_per_apply = geo.info["self_pairs"]
+    f = torch.tensor(w.density, device="cuda")
+    uinf = torch.zeros(nco, dtype=torch.float64, device="cuda")
+    uinf.view(3, -1)[0] = x.view(3, -1)[2] * w.shear   # u_inf = (z, 0, 0): linear, exactly band-limited
+    rhs = torch.zeros_like(uinf)
+    u = torch.zeros_like(uinf)
+    stream = torch.cuda.current_stream()
+
+    def step(precision, uvec, rhs_out):
+        geo.rhs(uinf, f, rhs_out)                           # b = 2 u_inf + S[f], FP64
+        uvec.zero_()
+        info = geo.solve(rhs_out, uvec, precision=precision, tol=1e-10, inner_tol=1e-5)
+        return info
+
+    # warm-up
+    for _ in range(args.warmup):
+        info = step(1, u, rhs)
+    torch.cuda.synchronize()
+
+    # timed region: K mixed solves
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = api.launch_count()
+    applies = 0
+    ctx.profile(True)
+    with ClockSampler(local) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            info = step(1, u, rhs)
+            applies += 1 + info["applies_fp64"] + info["applies_mixed"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    phases = ctx.profile_read()
+    ctx.profile(False)
+    launches = api.launch_count() - launches0
+    ms_total = ev0.elapsed_time(ev1)
+    t_local = ms_total / 1e3
+    if world > 1:
+        t = torch.tensor([t_local], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    ms_step = 1e3 * t_max / args.steps
+    value = world * applies * pairs_per_apply / t_max
+    u_mixed = u.clone()
+    mixed_info = info
+
+    # FP64 reference solve on the GPU (same step, plain FP64 path), and the accuracy of mixed vs FP64
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    u64 = torch.zeros_like(u)
+    step(0, u64, rhs)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    info64 = step(0, u64, rhs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    rel = float(torch.linalg.norm(u_mixed - u64) / torch.linalg.norm(u64))
+
+    # matvec times (double layer) at each precision
+    out = torch.zeros_like(u)
+    mv = {}
+    for prec in (0, 1):
+        for _ in range(3):
+            geo.apply_double(u64, out, precision=prec)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(10):
+            geo.apply_double(u64, out, precision=prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        mv[prec] = a.elapsed_time(b) / 10
+
+    # end to end through the public API with host buffers: H2D of (f, u_inf), step, D2H of u
+    f_h = torch.tensor(w.density).pin_memory()
+    uinf_h = uinf.cpu().pin_memory()
+    u_h = torch.zeros(nco, dtype=torch.float64).pin_memory()
+    e0.record(stream)
+    n_e2e = max(3, args.steps // 2)
+    for _ in range(n_e2e):
+        f.copy_(f_h, non_blocking=True)
+        uinf.copy_(uinf_h, non_blocking=True)
+        step(1, u, rhs)
+        u_h.copy_(u, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3 / n_e2e
+    e2e_value = world * (applies / args.steps) * pairs_per_apply / e2e_s
+
+    # roofline of the dominant kernel in the timed region (the self kernel with the largest total time)
+    selfk = {k: v for k, v in phases.items() if k.startswith("self_")}
+    dom_name, (dom_ms, dom_calls) = max(selfk.items(), key=lambda kv: kv[1][0])
+    ntarget = geo.info["ntarget"]
+    fl, by = self_work_per_target(dom_name, p, pq)
+    flops, nbytes = fl * ntarget, by * ntarget
+    avg_s = dom_ms / 1e3 / max(1, dom_calls)
+    f64 = dom_name.endswith("f64")
+    peak = FP64_ALU_PEAK if f64 else FP32_ALU_PEAK
+    achieved = flops / avg_s / 1e12
+    roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "algorithmic_flops_per_launch": flops,
+            "algorithmic_bytes_per_launch": nbytes, "hbm_gbs_achieved": nbytes / avg_s / 1e9,
+            "avg_launch_ms": avg_s * 1e3,
+            "peak_source": ("nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64 peak available)" if f64 else
+                            "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz")}
+
+    cpu = cpu_baseline_sample(w, budget_s=15.0) if rank == 0 else None
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "p": p, "p_q": pq, "targets": ntarget,
+                   "pairs_per_apply": pairs_per_apply, "step": "rhs (FP64 S apply) + mixed GMRES solve, tol 1e-10",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2: rotated-geometry cache 0.53 GB FP32 + 1.06 GB FP64 read per apply"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * nco * 8, "d2h_bytes_per_step": nco * 8},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "phases_ms": {k: {"ms": v[0], "calls": v[1]} for k, v in phases.items()},
+        "solve": {"mixed_ms": ms_step, "fp64_ms": fp64_ms, "speedup_vs_fp64": fp64_ms / ms_step,
+                  "mixed_iterations": mixed_info["iterations"], "mixed_refinements": mixed_info["refinements"],
+                  "mixed_applies_fp64": mixed_info["applies_fp64"], "mixed_applies_f32": mixed_info["applies_mixed"],
+                  "fp64_iterations": info64["iterations"], "rel_err_mixed_vs_fp64": rel,
+                  "residual_mixed": mixed_info["residual"], "residual_fp64": info64["residual"]},
+        "matvec": {"fp64_ms": mv[0], "mixed_ms": mv[1], "pairs_per_s_fp64": pairs_per_apply / (mv[0] / 1e3),
+                   "pairs_per_s_mixed": pairs_per_apply / (mv[1] / 1e3)},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline_sample(w, budget_s=15.0, lats=None):
+    """The FP64 oracle's singular self rule (one double-layer apply) on a sample of latitudes."""
+    from oracle import layer
+    p, pq = w.p[0], w.pq[0]
+    q = layer.SelfQuadrature(w.xcoef.reshape(3, -1), p, pq, cache=False)
+    nb = 2 * p + 2
+    done, t0 = 0, time.perf_counter()
+    lat_list = lats if lats is not None else [0, p // 2, p, 1, p - 1, p // 3, 2 * p // 3]
+    for a in lat_list:
+        q.apply(w.density, "D", lats=[a])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    pairs = done * nb * (pq + 1) * (2 * pq + 2)
+    return {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle FP64 singular self rule (rotated geometry + density, double layer), "
+                      f"{done} of {p + 1} latitudes = {done * nb} of {(p + 1) * nb} targets of the p=32, p_q=65 drop"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1707_02156_gb300 import inputs
+    w = inputs.perturbed_drop()
+    p, pq = w.p[0], w.pq[0]
+    for _ in range(args.warmup):
+        cpu_baseline_sample(w, budget_s=0.0, lats=[0])
+    t0 = time.perf_counter()
+    pairs = 0
+    for i in range(args.steps):
+        r = cpu_baseline_sample(w, budget_s=0.0, lats=[i % (p + 1)])
+        pairs += (2 * p + 2) * (pq + 1) * (2 * pq + 2)
+    dt = time.perf_counter() - t0
+    v = pairs / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "oracle double-layer self rule at one latitude (66 targets)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "one latitude (66 of 2178 targets) of one FP64 double-layer apply per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -65,9 +65,12 @@ typedef struct bie_config {
   int upsample;      /* U: the intermediate region uses the grid of degree U(p+1)-1 (Sec. 2.3), >= 1 */
   double a_tilde;    /* A: Omega_0 / Omega_1 boundary at distance A*h (Sec. 2.3; the paper uses 5) */
   int n_interp;      /* L: check points of the near-singular interpolation (Sec. 2.3; 8) */
+  int self_direct;   /* 0: singular self term in Fourier form (phi transform of the kernel weights built
+                        once per geometry, the default); 1: direct form (phi synthesis and kernel
+                        evaluation at every quadrature point on every apply) */
 } bie_config;
 
-/* Fill a config with the paper's defaults: device 0, U = 4, A = 5, L = 8. */
+/* Fill a config with the paper's defaults: device 0, U = 4, A = 5, L = 8, Fourier form. */
 void bie_config_default(bie_config* cfg);
 
 /* Create a context on cfg->device.  Plan tables are built lazily per degree and cached. */
@@ -137,6 +140,13 @@ int bie_apply_single(bie_ctx* ctx, const bie_geom* geom, const double* fcoef, do
 int bie_apply_double(bie_ctx* ctx, const bie_geom* geom, const double* ucoef, double* out_coef, int precision,
                      void* stream);
 
+/* Right-hand side of Eq. main_eq in coefficient space: rhs = 2 u_inf + S[f] with the FP64 single
+ * layer.  uinf: [drop][3][(p+1)^2] device coefficients of the far field at the drop surfaces (a
+ * linear flow is exactly band-limited: u_inf = (z, 0, 0) has the z coefficients of x in its first
+ * component); fcoef: interfacial force coefficients; rhs: device output (must not alias the inputs). */
+int bie_rhs(bie_ctx* ctx, const bie_geom* geom, const double* uinf, const double* fcoef, double* rhs,
+            void* stream);
+
 typedef struct bie_solve_opts {
   int precision;      /* BIE_FP64: FP64 GMRES; BIE_MIXED: mixed GMRES inside FP64 iterative refinement */
   double tol;         /* relative residual target ||b - A u|| / ||b|| (FP64-accurate residual) */
@@ -163,6 +173,25 @@ void bie_solve_opts_default(bie_solve_opts* opts);
  * back one scalar block per iteration).  BIE_ENOCONV if tol was not reached (best iterate kept). */
 int bie_solve(bie_ctx* ctx, const bie_geom* geom, const double* rhs, double* u, const bie_solve_opts* opts,
               bie_solve_info* info, void* stream);
+
+/* Per-phase timing.  bie_profile(ctx, 1) starts recording CUDA events around each phase of the
+ * library's work (on the stream each phase is launched on); bie_profile(ctx, 0) stops and discards.
+ * bie_profile_read synchronises on the recorded events, returns per-phase totals (milliseconds and
+ * number of timed calls, at most cap entries, *count = number of phases) and clears the record.
+ * Phases: "self_fourier_f64/f32" and "self_direct_f64/f32" (rotation + Legendre step + the
+ * singular pair sum of Thm 1), "kernel_dft" (Fourier-form factors, once per geometry), "analyze" (Galerkin
+ * projection), "interdrop" (regular and upsampled pair sums), "near" (near-singular step),
+ * "source_synth" (source densities on the standard/upsampled grids), "gmres_vec". */
+typedef struct bie_phase_stat {
+  char name[24];
+  double ms;
+  long long calls;
+} bie_phase_stat;
+int bie_profile(bie_ctx* ctx, int enable);
+int bie_profile_read(bie_ctx* ctx, bie_phase_stat* stats, int cap, int* count);
+
+/* Number of CUDA kernels the library has launched in this process (all contexts). */
+long long bie_launch_count(void);
 
 /* Host-side plan tables, exported so the host logic can be checked without a GPU.
  *   which 0: Gauss-Legendre nodes (n = P+1 doubles) then weights (n doubles), P = a

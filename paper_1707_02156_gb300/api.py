@@ -22,7 +22,8 @@ STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIME
 
 
 class bie_config(ctypes.Structure):
-    _fields_ = [("device", c_int), ("upsample", c_int), ("a_tilde", c_double), ("n_interp", c_int)]
+    _fields_ = [("device", c_int), ("upsample", c_int), ("a_tilde", c_double), ("n_interp", c_int),
+                ("self_direct", c_int)]
 
 
 class bie_geom_info(ctypes.Structure):
@@ -40,6 +41,10 @@ class bie_solve_info(ctypes.Structure):
                 ("residual", c_double), ("converged", c_int)]
 
 
+class bie_phase_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("ms", c_double), ("calls", c_ll)]
+
+
 EXPORTS = {
     "bie_config_default": (None, [ctypes.POINTER(bie_config)]),
     "bie_create": (c_int, [ctypes.POINTER(c_void), ctypes.POINTER(bie_config)]),
@@ -55,9 +60,13 @@ EXPORTS = {
     "bie_interfacial_force": (c_int, [c_void, c_void, c_void, c_double, c_double, c_void, c_void]),
     "bie_apply_single": (c_int, [c_void, c_void, c_void, c_void, c_int, c_void]),
     "bie_apply_double": (c_int, [c_void, c_void, c_void, c_void, c_int, c_void]),
+    "bie_rhs": (c_int, [c_void, c_void, c_void, c_void, c_void, c_void]),
     "bie_solve_opts_default": (None, [ctypes.POINTER(bie_solve_opts)]),
     "bie_solve": (c_int, [c_void, c_void, c_void, c_void, ctypes.POINTER(bie_solve_opts),
                           ctypes.POINTER(bie_solve_info), c_void]),
+    "bie_profile": (c_int, [c_void, c_int]),
+    "bie_profile_read": (c_int, [c_void, ctypes.POINTER(bie_phase_stat), c_int, P_int]),
+    "bie_launch_count": (c_ll, []),
     "bie_debug_table": (c_ll, [c_int, c_int, c_int, c_int, c_double, P_double, c_ll]),
 }
 
@@ -124,11 +133,13 @@ def ngrid(p: int) -> int:
 class Context:
     """A library context on one CUDA device (plan tables cached per degree)."""
 
-    def __init__(self, device: int = 0, upsample: int = 4, a_tilde: float = 5.0, n_interp: int = 8):
+    def __init__(self, device: int = 0, upsample: int = 4, a_tilde: float = 5.0, n_interp: int = 8,
+                 self_direct: bool = False):
         L = lib()
         cfg = bie_config()
         L.bie_config_default(ctypes.byref(cfg))
         cfg.device, cfg.upsample, cfg.a_tilde, cfg.n_interp = device, upsample, a_tilde, n_interp
+        cfg.self_direct = 1 if self_direct else 0
         h = c_void()
         _check(L.bie_create(ctypes.byref(h), ctypes.byref(cfg)), "bie_create")
         self.h = h
@@ -160,6 +171,17 @@ class Context:
         _check(lib().bie_rotate(self.h, len(p), _ints(p), ncomp, _ptr(coef), _doubles(flat), _ptr(out), _stream()),
                "bie_rotate")
         return out
+
+    def profile(self, enable: bool):
+        """Start (True) or stop (False) per-phase CUDA-event timing inside the library."""
+        _check(lib().bie_profile(self.h, 1 if enable else 0), "bie_profile")
+
+    def profile_read(self) -> dict:
+        """Per-phase {name: (total_ms, calls)} since profiling started; clears the record."""
+        buf = (bie_phase_stat * 32)()
+        n = ctypes.c_int()
+        _check(lib().bie_profile_read(self.h, buf, 32, ctypes.byref(n)), "bie_profile_read")
+        return {buf[i].name.decode(): (buf[i].ms, buf[i].calls) for i in range(min(n.value, 32))}
 
     def geometry(self, p, pq, xcoef: torch.Tensor, lam) -> "Geometry":
         return Geometry(self, p, pq, xcoef, lam)
@@ -207,6 +229,11 @@ class Geometry:
                "bie_interfacial_force")
         return out
 
+    def rhs(self, uinf: torch.Tensor, f: torch.Tensor, out: torch.Tensor):
+        """out = 2 u_inf + S[f] (FP64), the right-hand side of the boundary integral equation."""
+        _check(lib().bie_rhs(self.ctx.h, self.h, _ptr(uinf), _ptr(f), _ptr(out), _stream()), "bie_rhs")
+        return out
+
     def solve(self, rhs: torch.Tensor, u: torch.Tensor, precision: int = BIE_FP64, tol: float = 1e-10,
               restart: int = 30, max_iter: int = 300, inner_tol: float = 1e-5, max_refine: int = 10,
               raise_on_noconv: bool = True) -> dict:
@@ -221,6 +248,11 @@ class Geometry:
             return res
         _check(st, "bie_solve")
         return res
+
+
+def launch_count() -> int:
+    """Kernels launched by libbie.so in this process."""
+    return int(lib().bie_launch_count())
 
 
 def debug_table(which: int, a: int, b: int = 0, c: int = 0, x: float = 0.0):

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -116,6 +117,12 @@ const float* WigPlan::blk_<float>() const {
 
 struct bie_ctx {
   bie_config cfg;
+  struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<std::pair<std::string, size_t>> recs;  // name, index of the start event
+  } prof;
   std::mutex mu;
   std::map<std::pair<int, int>, std::unique_ptr<bie::Plan>> plans;
   std::map<int, std::unique_ptr<bie::WigPlan>> wigs;
@@ -123,6 +130,32 @@ struct bie_ctx {
 };
 
 namespace bie {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+
+// Per-phase CUDA-event timing on the launching stream (enabled by bie_profile).
+struct Phase {
+  bie_ctx* ctx;
+  cudaStream_t s;
+  size_t idx = (size_t)-1;
+  Phase(bie_ctx* c, const char* name, cudaStream_t st) : ctx(c), s(st) {
+    if (!ctx || !ctx->prof.on) return;
+    auto& P = ctx->prof;
+    while (P.pool.size() < P.used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      P.pool.push_back(e);
+    }
+    idx = P.used;
+    P.used += 2;
+    P.recs.emplace_back(name, idx);
+    cudaEventRecord(P.pool[idx], s);
+  }
+  ~Phase() {
+    if (idx != (size_t)-1) cudaEventRecord(ctx->prof.pool[idx + 1], s);
+  }
+};
 
 static int get_plan(bie_ctx* ctx, int p, int P, Plan** out) {
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -206,6 +239,10 @@ static int check_degrees(int ndrop, const int* p) {
 // ---------------------------------------------------------------------------------------------
 // geometry
 // ---------------------------------------------------------------------------------------------
+namespace bie {
+struct Krylov;
+}
+
 struct bie_geom {
   bie_ctx* ctx = nullptr;
   int ndrop = 0;
@@ -221,28 +258,22 @@ struct bie_geom {
   struct Group {
     int p = 0, pq = 0;
     std::vector<int> drops;
-    int chunk = 1;                          // drops per apply chunk
     bie::DevBuf<long long> foff3, goff3, val_off;
     bie::DevBuf<double> wS, wD, wSraw, wDraw;
-    bie::DevBuf<double> cache64;            // [gdrop][N_g][7][nq]
-    bie::DevBuf<float> cache32;
+    bie::DevBuf<double> cache64;            // [gdrop][N_g][7][nq] rotated geometry (Sec. 2.2)
+    bie::DevBuf<float> cache32;             // FP32 copy, made on the first direct-form mixed apply
+    bie::DevBuf<double> mhat64[2];          // phi transforms of the kernel weights, S and D (Fourier form)
+    bie::DevBuf<float> mhat32[2];
   };
   std::vector<std::unique_ptr<Group>> groups;
-  bie::DevBuf<double> ws64;   // apply workspace
-  bie::DevBuf<float> ws32;
   bie::DevBuf<double> anaF;   // analysis workspace
+  bie::Krylov* kry = nullptr;  // solve workspace, kept between solves
   bie_geom_info info{};
 };
 
 namespace bie {
 
-static const long long kWorkBudget = 3LL << 30;  // bytes of apply temporaries per precision
-
-// apply temporaries per drop: rotated coefficients, Legendre partial sums, rotated grid values
-static long long apply_floats_per_drop(int p, int pq) {
-  long long ng = ngrid(p), nq = ngrid(pq);
-  return ng * 3 * ncoef(p) + ng * 3 * (long long)(p + 1) * (pq + 1) * 2 + ng * 3 * nq;
-}
+static const long long kWorkBudget = 3LL << 30;  // bytes of set-up temporaries per chunk
 
 static int analyze_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, const double* vals, double* out,
                          cudaStream_t s) {
@@ -250,13 +281,29 @@ static int analyze_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, const do
   BIE_TRY(get_plan(ctx, G.p, G.p, &pl));
   long long nf = (long long)G.drops.size() * 3;
   BIE_TRY(g->anaF.alloc(nf * (G.p + 1) * (G.p + 1) * 2));
+  Phase ph(ctx, "analyze", s);
   return launch_analyze(vals, G.goff3.ptr, 0, nf, G.p, G.p, pl->cs.ptr, pl->A.ptr, g->anaF.ptr, out, G.foff3.ptr,
                         0, s);
 }
 
+// Fourier-form operator factors of one group, built on first use from the FP64 geometry cache.
+static int ensure_mhat(bie_ctx* ctx, bie_geom::Group& G, int kind, cudaStream_t s) {
+  if (G.mhat64[kind].ptr) return BIE_OK;
+  Plan* pl;
+  BIE_TRY(get_plan(ctx, G.p, G.pq, &pl));
+  const long long nt = (long long)G.drops.size() * ngrid(G.p);
+  const long long n = nt * 12 * (long long)(G.pq + 1) * (G.p + 1);
+  BIE_TRY(G.mhat64[kind].alloc(n));
+  BIE_TRY(G.mhat32[kind].alloc(n));
+  Phase ph(ctx, "kernel_dft", s);
+  return launch_kernel_dft(kind, G.cache64.ptr, nt, G.p, G.pq, pl->cs.ptr, G.mhat64[kind].ptr, G.mhat32[kind].ptr, s);
+}
+
+// Singular self part of every drop (Sec. 2.2): one launch per degree group.
 template <typename R>
 static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s) {
   bie_ctx* ctx = g->ctx;
+  const bool direct = ctx->cfg.self_direct != 0;
   for (auto& Gp : g->groups) {
     auto& G = *Gp;
     const int p = G.p, pq = G.pq;
@@ -265,31 +312,27 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
     BIE_TRY(get_plan(ctx, p, pq, &pl));
     BIE_TRY(get_plan(ctx, p, p, &pp));
     BIE_TRY(get_wig(ctx, p, &wp));
-    const long long ng = ngrid(p), nq = ngrid(pq);
-    const long long per = apply_floats_per_drop(p, pq);
-    R* work;
-    if (sizeof(R) == 8) {
-      BIE_TRY(g->ws64.alloc(per * G.chunk));
-      work = reinterpret_cast<R*>(g->ws64.ptr);
-    } else {
-      BIE_TRY(g->ws32.alloc(per * G.chunk));
-      work = reinterpret_cast<R*>(g->ws32.ptr);
-    }
-    const R* cache = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.cache64.ptr)
-                                    : reinterpret_cast<const R*>(G.cache32.ptr);
     const double* wts = kind == 0 ? (raw ? G.wSraw.ptr : G.wS.ptr) : (raw ? G.wDraw.ptr : G.wD.ptr);
-    const int nd = (int)G.drops.size();
-    for (int c0 = 0; c0 < nd; c0 += G.chunk) {
-      const int cn = std::min(G.chunk, nd - c0);
-      R* RC = work;
-      R* H = RC + cn * ng * 3 * ncoef(p);
-      R* RHO = H + cn * ng * 3 * (long long)(p + 1) * (pq + 1) * 2;
-      BIE_TRY((launch_rotate<double, R>(dens, G.foff3.ptr + 3 * c0, 3, cn, p, wp->blk_<R>(), wp->stride, p + 1,
-                                        2 * p + 2, pp->cs_<R>(), RC, ng * 3 * ncoef(p), s)));
-      BIE_TRY((launch_leg_synth<R, R>(RC, nullptr, ncoef(p), cn * ng * 3, p, pl->T0_<R>(), pq + 1, H, 0, s)));
-      BIE_TRY((launch_phi_synth<R, R>(H, cn * ng * 3, p, pq, pl->cs_<R>(), RHO, nullptr, nq, s)));
-      BIE_TRY(launch_self_pairs<R>(kind, cache + (long long)c0 * ng * 7 * nq, RHO, cn, (int)ng, nq, wts + c0,
-                                   G.val_off.ptr + c0, g->vals.ptr, s));
+    const long long nd = (long long)G.drops.size();
+    if (direct) {
+      if (sizeof(R) == 4 && !G.cache32.ptr) {
+        BIE_TRY(G.cache32.alloc(G.cache64.n));
+        BIE_TRY(launch_to_float(G.cache64.ptr, G.cache32.ptr, (long long)G.cache64.n, s));
+      }
+      const R* cache = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.cache64.ptr)
+                                      : reinterpret_cast<const R*>(G.cache32.ptr);
+      Phase ph(ctx, sizeof(R) == 8 ? "self_direct_f64" : "self_direct_f32", s);
+      BIE_TRY(launch_self_direct<R>(kind, dens, G.foff3.ptr, nd, p, pq, wp->blk_<R>(), wp->stride, pp->cs_<R>(),
+                                    pl->T0_<R>(), pl->cs_<R>(), cache, wts, G.val_off.ptr, g->vals.ptr,
+                                    sizeof(R) == 8 ? 96 * 1024 : 40 * 1024, s));
+    } else {
+      BIE_TRY(ensure_mhat(ctx, G, kind, s));
+      const R* M = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.mhat64[kind].ptr)
+                                  : reinterpret_cast<const R*>(G.mhat32[kind].ptr);
+      Phase ph(ctx, sizeof(R) == 8 ? "self_fourier_f64" : "self_fourier_f32", s);
+      BIE_TRY(launch_self_fourier<R>(dens, G.foff3.ptr, nd, p, pq, wp->blk_<R>(), wp->stride, pp->cs_<R>(),
+                                     pl->T0_<R>(), M, wts, G.val_off.ptr, g->vals.ptr,
+                                     sizeof(R) == 8 ? 96 * 1024 : 48 * 1024, s));
     }
   }
   return BIE_OK;
@@ -369,7 +412,6 @@ static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream
   BIE_TRY(G.wD.upload(wD));
   BIE_TRY(G.wSraw.upload(wSr));
   BIE_TRY(G.wDraw.upload(wDr));
-  G.chunk = (int)std::max(1LL, std::min<long long>(nd, kWorkBudget / (8 * apply_floats_per_drop(p, pq))));
 
   // standard grid: targets and regular-rule sources, one drop at a time
   {
@@ -395,7 +437,6 @@ static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream
   BIE_TRY(get_plan(ctx, p, p, &pp));
   BIE_TRY(get_wig(ctx, p, &wp));
   BIE_TRY(G.cache64.alloc((size_t)nd * ng * 7 * nq));
-  BIE_TRY(G.cache32.alloc((size_t)nd * ng * 7 * nq));
   const long long per = ng * 3 * nc + ng * 3 * (long long)(p + 1) * (pq + 1) * 2 + 3 * ng * 3 * nq;
   int chunk = (int)std::max(1LL, std::min<long long>(nd, (2 * kWorkBudget) / (8 * per)));
   DevBuf<double> work;
@@ -414,8 +455,6 @@ static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream
     const double* rec0 = g->rec_std.ptr + 7 * g->tgt_off[G.drops[c0]];
     BIE_TRY(launch_rotgeo<double>(X, Xt, Xp, cn, (int)ng, pq, rec0, pl->wsq.ptr,
                                   G.cache64.ptr + (long long)c0 * ng * 7 * nq, s));
-    BIE_TRY(launch_rotgeo<float>(X, Xt, Xp, cn, (int)ng, pq, rec0, pl->wsq.ptr,
-                                 G.cache32.ptr + (long long)c0 * ng * 7 * nq, s));
     BIE_CUDA_TRY(cudaStreamSynchronize(s));
   }
   return BIE_OK;
@@ -499,14 +538,16 @@ inline unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
 struct Krylov {
   long long n = 0;
   int m = 0;
-  DevBuf<double> V, w, tmp, partial, hdev;
+  DevBuf<double> V, w, tmp, partial, hdev, r, dx, t;
 };
 
 static int dots(Krylov& K, const double* V, int k, const double* w, std::vector<double>& out, cudaStream_t s) {
   dim3 grid(kRedBlocks, k);
   k_multidot<<<grid, kRedThreads, 0, s>>>(V, K.n, w, K.n, k, K.partial.ptr);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   k_sum_partials<<<(k + 127) / 128, 128, 0, s>>>(K.partial.ptr, kRedBlocks, k, K.hdev.ptr);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   out.resize(k);
   BIE_CUDA_TRY(cudaMemcpyAsync(out.data(), K.hdev.ptr, k * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -529,7 +570,9 @@ static int sys_matvec(bie_ctx* ctx, const bie_geom* g, const double* u, double* 
     info->applies_fp64++;
   else
     info->applies_mixed++;
+  Phase ph(ctx, "gmres_vec", s);
   k_sysop<<<nblk(g->ncoef_total), 256, 0, s>>>(g->lamc.ptr, u, tmp, y, g->ncoef_total);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -549,6 +592,11 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
     *relres = 0;
     return BIE_OK;
   }
+  if (!x_is_zero) {  // a zero initial guess needs no operator apply for its residual
+    double xn;
+    BIE_TRY(norm2(K, x, &xn, s));
+    x_is_zero = xn == 0.0;
+  }
   int it = 0;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol, h2;
   while (true) {
@@ -558,7 +606,8 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
     } else {
       BIE_TRY(sys_matvec(ctx, g, x, r, t2, prec, info, s));
       k_axpby<<<nblk(n), 256, 0, s>>>(1.0, b, -1.0, r, n);
-      BIE_CUDA_TRY(cudaGetLastError());
+      count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
     }
     double beta;
     BIE_TRY(norm2(K, r, &beta, s));
@@ -569,7 +618,8 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
     gv[0] = beta;
     double* V = K.V.ptr;
     k_axpby<<<nblk(n), 256, 0, s>>>(1.0 / beta, r, 0.0, V, n);
-    BIE_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
     int k_used = 0;
     for (int k = 0; k < m; ++k) {
       double* vk1 = V + (long long)(k + 1) * n;
@@ -578,18 +628,21 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
       BIE_TRY(dots(K, V, k + 1, vk1, hcol, s));
       BIE_CUDA_TRY(cudaMemcpyAsync(K.hdev.ptr, hcol.data(), (k + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
       k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, K.hdev.ptr, k + 1, n);
-      BIE_CUDA_TRY(cudaGetLastError());
+      count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
       BIE_TRY(dots(K, V, k + 1, vk1, h2, s));
       BIE_CUDA_TRY(cudaMemcpyAsync(K.hdev.ptr, h2.data(), (k + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
       k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, K.hdev.ptr, k + 1, n);
-      BIE_CUDA_TRY(cudaGetLastError());
+      count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
       for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = hcol[i] + h2[i];
       double hn;
       BIE_TRY(norm2(K, vk1, &hn, s));
       H[(size_t)(k + 1) * m + k] = hn;
       if (hn > 0) {
         k_axpby<<<nblk(n), 256, 0, s>>>(1.0 / hn, vk1, 0.0, vk1, n);
-        BIE_CUDA_TRY(cudaGetLastError());
+        count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
       }
       for (int i = 0; i < k; ++i) {
         double a = H[(size_t)i * m + k], bb = H[(size_t)(i + 1) * m + k];
@@ -617,7 +670,8 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
     }
     BIE_CUDA_TRY(cudaMemcpyAsync(K.hdev.ptr, y.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, s));
     k_add_comb<<<nblk(n), 256, 0, s>>>(x, V, n, K.hdev.ptr, k_used, n);
-    BIE_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
     x_is_zero = false;
   }
 }
@@ -637,6 +691,7 @@ void bie_config_default(bie_config* cfg) {
   cfg->upsample = 4;
   cfg->a_tilde = 5.0;
   cfg->n_interp = 8;
+  cfg->self_direct = 0;
 }
 
 const char* bie_strerror(int st) {
@@ -823,14 +878,18 @@ int bie_geometry_setup(bie_ctx* ctx, int ndrop, const int* p, const int* pq, con
   g->info.ntarget = to;
   g->info.self_pairs = self_pairs;
   double bytes = 0;
-  for (auto& G : g->groups) bytes += G->cache64.n * 8.0 + G->cache32.n * 4.0;
+  for (auto& G : g->groups) bytes += G->cache64.n * 8.0;
   bytes += g->rec_std.n * 8.0 + g->vals.n * 8.0 + g->xcoef.n * 8.0;
   g->info.cache_bytes = bytes;
   *out = g.release();
   return BIE_OK;
 }
 
-void bie_geometry_destroy(bie_geom* g) { delete g; }
+void bie_geometry_destroy(bie_geom* g) {
+  if (!g) return;
+  delete g->kry;
+  delete g;
+}
 
 int bie_geometry_info(const bie_geom* g, bie_geom_info* info) {
   if (!g || !info) return BIE_EINVAL;
@@ -857,6 +916,18 @@ int bie_apply_double(bie_ctx* ctx, const bie_geom* g, const double* ucoef, doubl
   return layer_apply(ctx, g, 1, ucoef, out, precision, (cudaStream_t)stream);
 }
 
+int bie_rhs(bie_ctx* ctx, const bie_geom* g, const double* uinf, const double* fcoef, double* rhs, void* stream) {
+  if (!ctx || !g || !uinf || !fcoef || !rhs) return BIE_EINVAL;
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  BIE_TRY(layer_apply(ctx, g, 0, fcoef, rhs, BIE_FP64, s));
+  Phase ph(ctx, "gmres_vec", s);
+  k_axpby<<<nblk(g->ncoef_total), 256, 0, s>>>(2.0, uinf, 1.0, rhs, g->ncoef_total);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
 void bie_solve_opts_default(bie_solve_opts* o) {
   if (!o) return;
   o->precision = BIE_FP64;
@@ -878,7 +949,12 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
   cudaStream_t s = (cudaStream_t)stream;
   std::memset(info, 0, sizeof(*info));
   const long long n = g->ncoef_total;
-  Krylov K;
+  bie_geom* gm = const_cast<bie_geom*>(g);
+  if (!gm->kry || gm->kry->m < opts->restart) {
+    delete gm->kry;
+    gm->kry = new bie::Krylov();
+  }
+  bie::Krylov& K = *gm->kry;
   K.n = n;
   K.m = opts->restart;
   BIE_TRY(K.V.alloc((size_t)(opts->restart + 1) * n));
@@ -894,17 +970,23 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
     return st;
   }
   // mixed: FP64 residual outside, mixed-precision GMRES correction inside
-  DevBuf<double> r, dx, t;
+  DevBuf<double>&r = K.r, &dx = K.dx, &t = K.t;
   BIE_TRY(r.alloc(n));
   BIE_TRY(dx.alloc(n));
   BIE_TRY(t.alloc(n));
-  double bnorm;
+  double bnorm, unorm;
   BIE_TRY(norm2(K, rhs, &bnorm, s));
+  BIE_TRY(norm2(K, u, &unorm, s));
   int left = opts->max_iter;
   for (int outer = 0;; ++outer) {
-    BIE_TRY(sys_matvec(ctx, g, u, r.ptr, t.ptr, BIE_FP64, info, s));
-    k_axpby<<<nblk(n), 256, 0, s>>>(1.0, rhs, -1.0, r.ptr, n);
-    BIE_CUDA_TRY(cudaGetLastError());
+    if (outer == 0 && unorm == 0.0) {  // r = b for a zero initial guess
+      BIE_CUDA_TRY(cudaMemcpyAsync(r.ptr, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      BIE_TRY(sys_matvec(ctx, g, u, r.ptr, t.ptr, BIE_FP64, info, s));
+      k_axpby<<<nblk(n), 256, 0, s>>>(1.0, rhs, -1.0, r.ptr, n);
+      count_launch();
+      BIE_CUDA_TRY(cudaGetLastError());
+    }
     double rn;
     BIE_TRY(norm2(K, r.ptr, &rn, s));
     rel = bnorm > 0 ? rn / bnorm : 0.0;
@@ -922,9 +1004,51 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
     if (st != BIE_OK && st != BIE_ENOCONV) return st;
     left -= info->iterations - before;
     k_axpby<<<nblk(n), 256, 0, s>>>(1.0, dx.ptr, 1.0, u, n);
-    BIE_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
   }
 }
+
+int bie_profile(bie_ctx* ctx, int enable) {
+  if (!ctx) return BIE_EINVAL;
+  ctx->prof.on = enable != 0;
+  ctx->prof.used = 0;
+  ctx->prof.recs.clear();
+  return BIE_OK;
+}
+
+int bie_profile_read(bie_ctx* ctx, bie_phase_stat* stats, int cap, int* count) {
+  if (!ctx || !count || (cap > 0 && !stats)) return BIE_EINVAL;
+  auto& P = ctx->prof;
+  std::vector<std::string> names;
+  std::vector<double> ms;
+  std::vector<long long> n;
+  for (auto& r : P.recs) {
+    BIE_CUDA_TRY(cudaEventSynchronize(P.pool[r.second + 1]));
+    float t = 0;
+    BIE_CUDA_TRY(cudaEventElapsedTime(&t, P.pool[r.second], P.pool[r.second + 1]));
+    size_t k = std::find(names.begin(), names.end(), r.first) - names.begin();
+    if (k == names.size()) {
+      names.push_back(r.first);
+      ms.push_back(0);
+      n.push_back(0);
+    }
+    ms[k] += t;
+    n[k] += 1;
+  }
+  *count = (int)names.size();
+  for (int i = 0; i < (int)names.size() && i < cap; ++i) {
+    std::memset(stats[i].name, 0, sizeof(stats[i].name));
+    std::strncpy(stats[i].name, names[i].c_str(), sizeof(stats[i].name) - 1);
+    stats[i].ms = ms[i];
+    stats[i].calls = n[i];
+  }
+  P.used = 0;
+  P.recs.clear();
+  return BIE_OK;
+}
+
+long long bie_launch_count(void) { return g_launches.load(); }
 
 long long bie_debug_table(int which, int a, int b, int c, double x, double* out, long long cap) {
   std::vector<double> v;

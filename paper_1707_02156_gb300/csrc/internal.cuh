@@ -10,6 +10,7 @@
 namespace bie {
 
 void set_error(const std::string& msg);
+void count_launch(int n = 1);  // kernel launches issued by the library (all threads)
 
 #define BIE_CUDA_TRY(expr)                                                                     \
   do {                                                                                         \
@@ -64,9 +65,20 @@ int launch_surface(const double* X, const double* Xt, const double* Xp, long lon
 template <typename R>
 int launch_rotgeo(const double* X, const double* Xt, const double* Xp, long long ndrop, int ng, int pq,
                   const double* rec_std, const double* wsq, R* cache, cudaStream_t s);
-// Singular self pair sum (Thm 1): vals[val_off[d] + c*ng + t] = wts[d] * sum_q K(xh_q) rho_q wJ_q.
+// Singular self interaction (Thm 1, Sec. 2.2), one block per target of ndrop drops of degree p:
+// direct form against the rotated-geometry cache, or Fourier form against Mhat (see self.cu).
 template <typename R>
-int launch_self_pairs(int kind, const R* cache, const R* rho, long long ndrop, int ng, long long nq,
-                      const double* wts, const long long* val_off, double* vals, cudaStream_t s);
+int launch_self_direct(int kind, const double* dens, const long long* foff3, long long ndrop, int p, int pq,
+                       const R* wblk, long long wstride, const R* ph, const R* T0, const R* cs, const R* cache,
+                       const double* wts, const long long* val_off, double* vals, size_t smem_budget,
+                       cudaStream_t s);
+int launch_kernel_dft(int kind, const double* cache, long long ntarget, int p, int pq, const double* cs, double* M64,
+                      float* M32, cudaStream_t s);
+template <typename R>
+int launch_self_fourier(const double* dens, const long long* foff3, long long ndrop, int p, int pq, const R* wblk,
+                        long long wstride, const R* ph, const R* T0, const R* Mhat, const double* wts,
+                        const long long* val_off, double* vals, size_t smem_budget, cudaStream_t s);
+// out[i] = (float) in[i]
+int launch_to_float(const double* in, float* out, long long n, cudaStream_t s);
 
 }  // namespace bie

@@ -1,6 +1,9 @@
 // Surface geometry, rotated-grid cache and pair-sum kernels (Table 2, Thm 1, Sec. 2.1-2.3).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
+#include "device.cuh"
 #include "internal.cuh"
 
 namespace bie {
@@ -74,94 +77,27 @@ __global__ void k_rotgeo(const double* __restrict__ X, const double* __restrict_
   o[6 * nq + q] = (R)(wsq[j] * W);
 }
 
-template <typename R>
-__device__ inline R rsqrt_(R v);
-template <>
-__device__ inline double rsqrt_<double>(double v) {
-  return 1.0 / sqrt(v);
-}
-template <>
-__device__ inline float rsqrt_<float>(float v) {
-  return rsqrtf(v);
-}
-
-template <typename R>
-__device__ inline void block_sum3(R& a, R& b, R& c, R* sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-    c += __shfl_down_sync(0xffffffffu, c, o);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) {
-    sh[w * 3] = a;
-    sh[w * 3 + 1] = b;
-    sh[w * 3 + 2] = c;
-  }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    a = l < nw ? sh[l * 3] : (R)0;
-    b = l < nw ? sh[l * 3 + 1] : (R)0;
-    c = l < nw ? sh[l * 3 + 2] : (R)0;
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-      c += __shfl_down_sync(0xffffffffu, c, o);
-    }
-  }
-}
-
-// One block per target: sum over the nq points of its rotated grid (Thm 1).
-template <typename R, int KIND>
-__global__ void k_self_pairs(const R* __restrict__ cache, const R* __restrict__ rho, int ng, long long nq,
-                             const double* __restrict__ wts, const long long* __restrict__ val_off,
-                             double* __restrict__ vals) {
-  __shared__ R sh[3 * 32];
-  const long long t = blockIdx.x;
-  const R* g = cache + t * 7 * nq;
-  const R* rh = rho + t * 3 * nq;
-  R s0 = 0, s1 = 0, s2 = 0;
-  for (long long q = threadIdx.x; q < nq; q += blockDim.x) {
-    R x0 = g[q], x1 = g[nq + q], x2 = g[2 * nq + q];
-    R w = g[6 * nq + q];
-    R r0 = rh[q], r1 = rh[nq + q], r2 = rh[2 * nq + q];
-    R rr = x0 * x0 + x1 * x1 + x2 * x2;
-    R ri = rsqrt_<R>(rr);
-    R xr = x0 * r0 + x1 * r1 + x2 * r2;
-    if (KIND == 0) {  // Stokeslet: rho/r + xh (xh.rho)/r^3
-      R wi = w * ri;
-      R c = wi * xr * ri * ri;
-      s0 += wi * r0 + c * x0;
-      s1 += wi * r1 + c * x1;
-      s2 += wi * r2 + c * x2;
-    } else {  // stresslet: -6 (rho.xh)(xh.n) xh / r^5
-      R xn = x0 * g[3 * nq + q] + x1 * g[4 * nq + q] + x2 * g[5 * nq + q];
-      R ri2 = ri * ri;
-      R c = (R)(-6) * w * xr * xn * ri2 * ri2 * ri;
-      s0 += c * x0;
-      s1 += c * x1;
-      s2 += c * x2;
-    }
-  }
-  block_sum3<R>(s0, s1, s2, sh);
-  if (threadIdx.x == 0) {
-    long long ld = t / ng, tl = t - ld * ng;
-    double wt = wts[ld];
-    double* v = vals + val_off[ld] + tl;
-    v[0] = wt * (double)s0;
-    v[ng] = wt * (double)s1;
-    v[2 * (long long)ng] = wt * (double)s2;
-  }
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
 }
 
 }  // namespace
+
+int launch_to_float(const double* in, float* out, long long n, cudaStream_t s) {
+  if (n == 0) return BIE_OK;
+  k_to_float<<<blocks_for(n), kThreads, 0, s>>>(in, out, n);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
 
 int launch_surface(const double* X, const double* Xt, const double* Xp, long long ndrop, int P,
                    const double* wsin, double* rec, cudaStream_t s) {
   long long n = ndrop * (long long)(P + 1) * (2 * P + 2);
   if (n == 0) return BIE_OK;
   k_surface<<<blocks_for(n), kThreads, 0, s>>>(X, Xt, Xp, ndrop, P, wsin, rec);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -172,20 +108,7 @@ int launch_rotgeo(const double* X, const double* Xt, const double* Xp, long long
   long long n = ndrop * ng * (long long)(pq + 1) * (2 * pq + 2);
   if (n == 0) return BIE_OK;
   k_rotgeo<R><<<blocks_for(n), kThreads, 0, s>>>(X, Xt, Xp, ndrop, ng, pq, rec_std, wsq, cache);
-  BIE_CUDA_TRY(cudaGetLastError());
-  return BIE_OK;
-}
-
-template <typename R>
-int launch_self_pairs(int kind, const R* cache, const R* rho, long long ndrop, int ng, long long nq,
-                      const double* wts, const long long* val_off, double* vals, cudaStream_t s) {
-  long long nt = ndrop * ng;
-  if (nt == 0) return BIE_OK;
-  if (nt > 0x7fffffffLL) return BIE_EINVAL;
-  if (kind == 0)
-    k_self_pairs<R, 0><<<(unsigned)nt, kThreads, 0, s>>>(cache, rho, ng, nq, wts, val_off, vals);
-  else
-    k_self_pairs<R, 1><<<(unsigned)nt, kThreads, 0, s>>>(cache, rho, ng, nq, wts, val_off, vals);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -194,9 +117,5 @@ template int launch_rotgeo<double>(const double*, const double*, const double*, 
                                    const double*, double*, cudaStream_t);
 template int launch_rotgeo<float>(const double*, const double*, const double*, long long, int, int, const double*,
                                   const double*, float*, cudaStream_t);
-template int launch_self_pairs<double>(int, const double*, const double*, long long, int, long long,
-                                       const double*, const long long*, double*, cudaStream_t);
-template int launch_self_pairs<float>(int, const float*, const float*, long long, int, long long, const double*,
-                                      const long long*, double*, cudaStream_t);
-
 }  // namespace bie
+

@@ -1,0 +1,400 @@
+// Singular self interaction of every drop (Thm 1, Sec. 2.2, App. B): one block per target.
+//
+// Both forms rotate the density so that the target sits at the pole (App. B, real blocks of the
+// latitude's Wigner matrices applied to e^{i m phi_b} rho_n^m) and run the Legendre step of the
+// synthesis on the degree-pq grid, h_m(theta_j) = sum_n rho'_n^m P~_n^m(cos theta_j), in shared memory.
+//
+//  * direct form: the phi step rho'(theta_j, phi_k) = h_0 + 2 Re sum_m h_m e^{i m phi_k} is evaluated
+//    for the longitude pair (k, k + pq + 1) from the even and odd orders, and the Stokeslet or
+//    stresslet pair sum of Thm 1 is accumulated against the cached rotated geometry;
+//  * Fourier form: the same double sum reassociated exactly,
+//        sum_{j,k} M_jk rho'_jk = sum_j sum_m c_m Re[ Mhat_jm h_m(theta_j) ],   c_0 = 1, c_m = 2,
+//    with M_jk the 3x3 kernel weight of the quadrature point (w^s_j K(x0 - x') W'/sin theta_j, geometry
+//    only) and Mhat_jm = sum_k M_jk e^{i m phi_k} its phi transform, built once per geometry.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace bie {
+namespace {
+
+// Stages 0-1: g = e^{i m phi_b} rho_n^m (three components) then the rotation, rc = rotated
+// coefficients (real-packed, [3][(p+1)^2]).  g and rc are shared-memory arrays.
+template <typename R>
+__device__ void rotate_target(const double* __restrict__ dens, const long long* __restrict__ foff3, long long ld,
+                              int p, int a, int b, const R* __restrict__ wblk, long long wstride,
+                              const R* __restrict__ ph, R* rc, R* g) {
+  const int nc = (p + 1) * (p + 1);
+  const int nb = 2 * p + 2;
+  for (int i = threadIdx.x; i < 3 * nc; i += blockDim.x) {
+    const int c = i / nc, r = i - c * nc;
+    const int n = degree_of(r);
+    const int m = r - n * (n + 1);
+    if (m < 0) continue;  // the owner of Re rho_n^m writes both parts
+    const double* f = dens + foff3[ld * 3 + c];
+    const R fr = (R)f[n * (n + 1) + m];
+    const R fi = m > 0 ? (R)f[n * (n + 1) - m] : (R)0;
+    const R co = ph[((long long)m * nb + b) * 2], si = ph[((long long)m * nb + b) * 2 + 1];
+    g[c * nc + n * (n + 1) + m] = fr * co - fi * si;
+    if (m > 0) g[c * nc + n * (n + 1) - m] = fr * si + fi * co;
+  }
+  __syncthreads();
+  const R* blk = wblk + (long long)a * wstride;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const int n = degree_of(i);
+    const int o = i - n * n;  // 0..2n
+    // blocks of degree n start after sum_{k<n} (k+1)^2 + k^2 entries
+    const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
+    const R* g0 = g + n * (n + 1);
+    R a0 = 0, a1 = 0, a2 = 0;
+    int dst;
+    if (o <= n) {
+      const R* Cr = blk + boff + (long long)o * (n + 1);
+      for (int m = 0; m <= n; ++m) {
+        const R cv = Cr[m];
+        a0 += cv * g0[m];
+        a1 += cv * g0[nc + m];
+        a2 += cv * g0[2 * nc + m];
+      }
+      dst = n * (n + 1) + o;
+    } else {
+      const int mp = o - n;
+      const R* Sr = blk + boff + (long long)(n + 1) * (n + 1) + (long long)(mp - 1) * n;
+      for (int m = 1; m <= n; ++m) {
+        const R sv = Sr[m - 1];
+        a0 += sv * g0[-m];
+        a1 += sv * g0[nc - m];
+        a2 += sv * g0[2 * nc - m];
+      }
+      dst = n * (n + 1) - mp;
+    }
+    rc[dst] = a0;
+    rc[nc + dst] = a1;
+    rc[2 * nc + dst] = a2;
+  }
+  __syncthreads();
+}
+
+// Stage 2: h[c][jj][m] (complex) = sum_n rc[c](n, m) T0[m][n][j0 + jj] for jj < jn.
+template <typename R>
+__device__ void legendre_chunk(const R* rc, int p, int nq_j, int j0, int jn, const R* __restrict__ T0, R* h) {
+  const int nc = (p + 1) * (p + 1);
+  const long long cstride = (long long)jn * (p + 1) * 2;
+  for (int i = threadIdx.x; i < (p + 1) * jn; i += blockDim.x) {
+    const int m = i / jn, jj = i - m * jn;
+    const R* Tm = T0 + leg_row(p, m, m, nq_j) + j0 + jj;
+    R r0 = 0, r1 = 0, r2 = 0, i0 = 0, i1 = 0, i2 = 0;
+    for (int n = m; n <= p; ++n) {
+      const R tv = Tm[(long long)(n - m) * nq_j];
+      const int re = n * (n + 1) + m;
+      r0 += rc[re] * tv;
+      r1 += rc[nc + re] * tv;
+      r2 += rc[2 * nc + re] * tv;
+      if (m > 0) {
+        const int im = n * (n + 1) - m;
+        i0 += rc[im] * tv;
+        i1 += rc[nc + im] * tv;
+        i2 += rc[2 * nc + im] * tv;
+      }
+    }
+    R* hh = h + ((long long)jj * (p + 1) + m) * 2;
+    hh[0] = r0;
+    hh[1] = i0;
+    hh[cstride] = r1;
+    hh[cstride + 1] = i1;
+    hh[2 * cstride] = r2;
+    hh[2 * cstride + 1] = i2;
+  }
+  __syncthreads();
+}
+
+template <typename R>
+__device__ inline void write_target(R s0, R s1, R s2, const double* __restrict__ wts,
+                                    const long long* __restrict__ val_off, double* __restrict__ vals, long long ld,
+                                    int tl, int ng) {
+  __shared__ R red[3 * 32];
+  block_sum3<R>(s0, s1, s2, red);
+  if (threadIdx.x == 0) {
+    const double wt = wts[ld];
+    double* v = vals + val_off[ld] + tl;
+    v[0] = wt * (double)s0;
+    v[ng] = wt * (double)s1;
+    v[2 * (long long)ng] = wt * (double)s2;
+  }
+}
+
+// ---- direct form ----
+template <typename R, int KIND>
+__global__ void __launch_bounds__(256) k_self_direct(
+    const double* __restrict__ dens, const long long* __restrict__ foff3, int p, int pq, const R* __restrict__ wblk,
+    long long wstride, const R* __restrict__ ph, const R* __restrict__ T0, const R* __restrict__ cs,
+    const R* __restrict__ cache, int ng, const double* __restrict__ wts, const long long* __restrict__ val_off,
+    double* __restrict__ vals, int jc) {
+  extern __shared__ unsigned char smem_raw[];
+  R* rc = reinterpret_cast<R*>(smem_raw);
+  const int nc = (p + 1) * (p + 1);
+  R* un = rc + 3 * nc;
+  const long long t = blockIdx.x;
+  const long long ld = t / ng;
+  const int tl = (int)(t - ld * ng);
+  const int a = tl / (2 * p + 2), b = tl - a * (2 * p + 2);
+  const int nq_j = pq + 1, nk = 2 * pq + 2, half = pq + 1;
+  const long long nq = (long long)nq_j * nk;
+  rotate_target<R>(dens, foff3, ld, p, a, b, wblk, wstride, ph, rc, un);
+  const R* geo = cache + t * 7 * nq;
+  R s0 = 0, s1 = 0, s2 = 0;
+  for (int j0 = 0; j0 < nq_j; j0 += jc) {
+    const int jn = min(jc, nq_j - j0);
+    legendre_chunk<R>(rc, p, nq_j, j0, jn, T0, un);
+    const long long cstride = (long long)jn * (p + 1) * 2;
+    for (int i = threadIdx.x; i < jn * half; i += blockDim.x) {
+      const int jj = i / half, k = i - jj * half;
+      const R* hh = un + (long long)jj * (p + 1) * 2;
+      R e0 = hh[0], e1 = hh[cstride], e2 = hh[2 * cstride];
+      R o0 = 0, o1 = 0, o2 = 0;
+      for (int m = 1; m <= p; ++m) {
+        const R co = cs[((long long)m * nk + k) * 2], si = cs[((long long)m * nk + k) * 2 + 1];
+        const R* hm = hh + 2 * m;
+        const R v0 = 2 * (hm[0] * co - hm[1] * si);
+        const R v1 = 2 * (hm[cstride] * co - hm[cstride + 1] * si);
+        const R v2 = 2 * (hm[2 * cstride] * co - hm[2 * cstride + 1] * si);
+        if (m & 1) {
+          o0 += v0;
+          o1 += v1;
+          o2 += v2;
+        } else {
+          e0 += v0;
+          e1 += v1;
+          e2 += v2;
+        }
+      }
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const long long q = (long long)(j0 + jj) * nk + k + side * half;
+        const R r0 = side ? e0 - o0 : e0 + o0;
+        const R r1 = side ? e1 - o1 : e1 + o1;
+        const R r2 = side ? e2 - o2 : e2 + o2;
+        const R x0 = geo[q], x1 = geo[nq + q], x2 = geo[2 * nq + q];
+        const R w = geo[6 * nq + q];
+        const R ri = rsqrt_<R>(x0 * x0 + x1 * x1 + x2 * x2);
+        const R xr = x0 * r0 + x1 * r1 + x2 * r2;
+        if (KIND == 0) {
+          const R wi = w * ri;
+          const R c = wi * xr * ri * ri;
+          s0 += wi * r0 + c * x0;
+          s1 += wi * r1 + c * x1;
+          s2 += wi * r2 + c * x2;
+        } else {
+          const R xn = x0 * geo[3 * nq + q] + x1 * geo[4 * nq + q] + x2 * geo[5 * nq + q];
+          const R ri2 = ri * ri;
+          const R c = (R)(-6) * w * xr * xn * ri2 * ri2 * ri;
+          s0 += c * x0;
+          s1 += c * x1;
+          s2 += c * x2;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  write_target<R>(s0, s1, s2, wts, val_off, vals, ld, tl, ng);
+}
+
+// ---- Fourier form: set-up of Mhat (FP64, optional FP32 copy) ----
+// Mhat[t][e][ri][j][m], e over (xx, yy, zz, xy, xz, yz), ri = real / imaginary part.
+constexpr int kDftJ = 3;
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_kernel_dft(const double* __restrict__ cache, int pq, int p,
+                                                    const double* __restrict__ cs, double* __restrict__ M64,
+                                                    float* __restrict__ M32) {
+  __shared__ double sm[kDftJ * 6 * 2 * 132];  // [jj][e][S/D][k < half] for half <= 132
+  const long long t = blockIdx.x;
+  const int nq_j = pq + 1, nk = 2 * pq + 2, half = pq + 1;
+  const long long nq = (long long)nq_j * nk;
+  const double* geo = cache + t * 7 * nq;
+  const long long plane = (long long)nq_j * (p + 1);
+  double* o64 = M64 + t * 12 * plane;
+  float* o32 = M32 ? M32 + t * 12 * plane : nullptr;
+  for (int j0 = 0; j0 < nq_j; j0 += kDftJ) {
+    const int jn = min(kDftJ, nq_j - j0);
+    for (int i = threadIdx.x; i < jn * half; i += blockDim.x) {
+      const int jj = i / half, k = i - jj * half;
+      double Mv[2][6];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const long long q = (long long)(j0 + jj) * nk + k + side * half;
+        const double x0 = geo[q], x1 = geo[nq + q], x2 = geo[2 * nq + q], w = geo[6 * nq + q];
+        const double ri = 1.0 / sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+        double d, c;
+        if (KIND == 0) {
+          d = w * ri;
+          c = w * ri * ri * ri;
+        } else {
+          const double xn = x0 * geo[3 * nq + q] + x1 * geo[4 * nq + q] + x2 * geo[5 * nq + q];
+          const double ri2 = ri * ri;
+          d = 0.0;
+          c = -6.0 * w * xn * ri2 * ri2 * ri;
+        }
+        Mv[side][0] = d + c * x0 * x0;
+        Mv[side][1] = d + c * x1 * x1;
+        Mv[side][2] = d + c * x2 * x2;
+        Mv[side][3] = c * x0 * x1;
+        Mv[side][4] = c * x0 * x2;
+        Mv[side][5] = c * x1 * x2;
+      }
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        sm[((jj * 6 + e) * 2 + 0) * 132 + k] = Mv[0][e] + Mv[1][e];  // even orders
+        sm[((jj * 6 + e) * 2 + 1) * 132 + k] = Mv[0][e] - Mv[1][e];  // odd orders
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < jn * 6 * (p + 1); i += blockDim.x) {
+      const int m = i % (p + 1);
+      const int r = i / (p + 1);
+      const int e = r % 6, jj = r / 6;
+      const double* src = sm + ((jj * 6 + e) * 2 + (m & 1)) * 132;
+      double re = 0, im = 0;
+      for (int k = 0; k < half; ++k) {
+        re += src[k] * cs[((long long)m * nk + k) * 2];
+        im += src[k] * cs[((long long)m * nk + k) * 2 + 1];
+      }
+      const long long o = (long long)(j0 + jj) * (p + 1) + m;
+      o64[(2 * e) * plane + o] = re;
+      o64[(2 * e + 1) * plane + o] = im;
+      if (o32) {
+        o32[(2 * e) * plane + o] = (float)re;
+        o32[(2 * e + 1) * plane + o] = (float)im;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- Fourier form: apply ----
+template <typename R>
+__global__ void __launch_bounds__(256) k_self_fourier(
+    const double* __restrict__ dens, const long long* __restrict__ foff3, int p, int pq, const R* __restrict__ wblk,
+    long long wstride, const R* __restrict__ ph, const R* __restrict__ T0, const R* __restrict__ Mhat, int ng,
+    const double* __restrict__ wts, const long long* __restrict__ val_off, double* __restrict__ vals, int jc) {
+  extern __shared__ unsigned char smem_raw[];
+  R* rc = reinterpret_cast<R*>(smem_raw);
+  const int nc = (p + 1) * (p + 1);
+  R* un = rc + 3 * nc;
+  const long long t = blockIdx.x;
+  const long long ld = t / ng;
+  const int tl = (int)(t - ld * ng);
+  const int a = tl / (2 * p + 2), b = tl - a * (2 * p + 2);
+  const int nq_j = pq + 1;
+  const long long plane = (long long)nq_j * (p + 1);
+  const R* M = Mhat + t * 12 * plane;
+  rotate_target<R>(dens, foff3, ld, p, a, b, wblk, wstride, ph, rc, un);
+  R s0 = 0, s1 = 0, s2 = 0;
+  for (int j0 = 0; j0 < nq_j; j0 += jc) {
+    const int jn = min(jc, nq_j - j0);
+    legendre_chunk<R>(rc, p, nq_j, j0, jn, T0, un);
+    const long long cstride = (long long)jn * (p + 1) * 2;
+    for (int i = threadIdx.x; i < jn * (p + 1); i += blockDim.x) {
+      const int jj = i / (p + 1), m = i - jj * (p + 1);
+      const R* hh = un + ((long long)jj * (p + 1) + m) * 2;
+      const R hr0 = hh[0], hi0 = hh[1], hr1 = hh[cstride], hi1 = hh[cstride + 1];
+      const R hr2 = hh[2 * cstride], hi2 = hh[2 * cstride + 1];
+      const long long o = (long long)(j0 + jj) * (p + 1) + m;
+      R Mr[6], Mi[6];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        Mr[e] = M[(2 * e) * plane + o];
+        Mi[e] = M[(2 * e + 1) * plane + o];
+      }
+      const R cm = m == 0 ? (R)1 : (R)2;
+      // rows of the symmetric matrix: (xx xy xz), (xy yy yz), (xz yz zz)
+      s0 += cm * (Mr[0] * hr0 + Mr[3] * hr1 + Mr[4] * hr2 - Mi[0] * hi0 - Mi[3] * hi1 - Mi[4] * hi2);
+      s1 += cm * (Mr[3] * hr0 + Mr[1] * hr1 + Mr[5] * hr2 - Mi[3] * hi0 - Mi[1] * hi1 - Mi[5] * hi2);
+      s2 += cm * (Mr[4] * hr0 + Mr[5] * hr1 + Mr[2] * hr2 - Mi[4] * hi0 - Mi[5] * hi1 - Mi[2] * hi2);
+    }
+    __syncthreads();
+  }
+  write_target<R>(s0, s1, s2, wts, val_off, vals, ld, tl, ng);
+}
+
+template <typename R>
+int pick_jc(int p, int pq, size_t budget, size_t* smem) {
+  const size_t nc = (size_t)(p + 1) * (p + 1);
+  const size_t fixed = sizeof(R) * 3 * nc;
+  int jc = (int)((budget > 2 * fixed ? budget - fixed : 0) / (sizeof(R) * 6 * (p + 1)));
+  jc = std::max(1, std::min(jc, pq + 1));
+  *smem = fixed + sizeof(R) * std::max(3 * nc, (size_t)6 * (p + 1) * jc);
+  return jc;
+}
+
+}  // namespace
+
+template <typename R>
+int launch_self_direct(int kind, const double* dens, const long long* foff3, long long ndrop, int p, int pq,
+                       const R* wblk, long long wstride, const R* ph, const R* T0, const R* cs, const R* cache,
+                       const double* wts, const long long* val_off, double* vals, size_t smem_budget,
+                       cudaStream_t s) {
+  const int ng = (p + 1) * (2 * p + 2);
+  const long long nt = ndrop * ng;
+  if (nt == 0) return BIE_OK;
+  if (nt > 0x7fffffffLL) return BIE_EINVAL;
+  size_t smem;
+  const int jc = pick_jc<R>(p, pq, smem_budget, &smem);
+  auto kern = kind == 0 ? k_self_direct<R, 0> : k_self_direct<R, 1>;
+  if (smem > 48 * 1024) BIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)nt, 256, smem, s>>>(dens, foff3, p, pq, wblk, wstride, ph, T0, cs, cache, ng, wts, val_off, vals,
+                                       jc);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+int launch_kernel_dft(int kind, const double* cache, long long ntarget, int p, int pq, const double* cs, double* M64,
+                      float* M32, cudaStream_t s) {
+  if (ntarget == 0) return BIE_OK;
+  if (pq + 1 > 132 || ntarget > 0x7fffffffLL) return BIE_EINVAL;
+  if (kind == 0)
+    k_kernel_dft<0><<<(unsigned)ntarget, 256, 0, s>>>(cache, pq, p, cs, M64, M32);
+  else
+    k_kernel_dft<1><<<(unsigned)ntarget, 256, 0, s>>>(cache, pq, p, cs, M64, M32);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+template <typename R>
+int launch_self_fourier(const double* dens, const long long* foff3, long long ndrop, int p, int pq, const R* wblk,
+                        long long wstride, const R* ph, const R* T0, const R* Mhat, const double* wts,
+                        const long long* val_off, double* vals, size_t smem_budget, cudaStream_t s) {
+  const int ng = (p + 1) * (2 * p + 2);
+  const long long nt = ndrop * ng;
+  if (nt == 0) return BIE_OK;
+  if (nt > 0x7fffffffLL) return BIE_EINVAL;
+  size_t smem;
+  const int jc = pick_jc<R>(p, pq, smem_budget, &smem);
+  if (smem > 48 * 1024)
+    BIE_CUDA_TRY(cudaFuncSetAttribute(k_self_fourier<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_self_fourier<R><<<(unsigned)nt, 256, smem, s>>>(dens, foff3, p, pq, wblk, wstride, ph, T0, Mhat, ng, wts,
+                                                    val_off, vals, jc);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+template int launch_self_direct<double>(int, const double*, const long long*, long long, int, int, const double*,
+                                        long long, const double*, const double*, const double*, const double*,
+                                        const double*, const long long*, double*, size_t, cudaStream_t);
+template int launch_self_direct<float>(int, const double*, const long long*, long long, int, int, const float*,
+                                       long long, const float*, const float*, const float*, const float*,
+                                       const double*, const long long*, double*, size_t, cudaStream_t);
+template int launch_self_fourier<double>(const double*, const long long*, long long, int, int, const double*,
+                                         long long, const double*, const double*, const double*, const double*,
+                                         const long long*, double*, size_t, cudaStream_t);
+template int launch_self_fourier<float>(const double*, const long long*, long long, int, int, const float*,
+                                        long long, const float*, const float*, const float*, const double*,
+                                        const long long*, double*, size_t, cudaStream_t);
+
+}  // namespace bie

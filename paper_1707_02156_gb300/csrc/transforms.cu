@@ -226,6 +226,7 @@ int launch_leg_synth(const CT* coef, const long long* field_off, long long coef_
   long long n = nfield * (long long)(p + 1) * nj;
   if (n == 0) return BIE_OK;
   k_leg_synth<CT, R><<<blocks_for(n), kThreads, 0, s>>>(coef, field_off, coef_stride, nfield, p, T, nj, H, dphi);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -236,6 +237,7 @@ int launch_phi_synth(const R* H, long long nfield, int p, int P, const R* cs, OT
   long long n = nfield * (long long)(P + 1) * (P + 1);
   if (n == 0) return BIE_OK;
   k_phi_synth<R, OT><<<blocks_for(n), kThreads, 0, s>>>(H, nfield, p, P, cs, out, out_off, out_stride);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -246,9 +248,11 @@ int launch_analyze(const double* grid, const long long* grid_off, long long grid
   long long n1 = nfield * (long long)(p_out + 1) * (P + 1);
   if (n1 == 0) return BIE_OK;
   k_phi_analyze<<<blocks_for(n1), kThreads, 0, s>>>(grid, grid_off, grid_stride, nfield, P, p_out, cs, F);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   long long n2 = nfield * (long long)(p_out + 1) * (p_out + 2) / 2;
   k_leg_analyze<<<blocks_for(n2), kThreads, 0, s>>>(F, nfield, P, p_out, A, coef, coef_off, coef_stride);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -269,6 +273,7 @@ int launch_rotate(const CT* coef, const long long* field_off, int ncomp, long lo
   if (nblk > 0x7fffffffLL) return BIE_EINVAL;
   k_rotate<CT, R><<<(unsigned)nblk, 128, smem, s>>>(coef, field_off, ncomp, p, blocks, blk_stride, na, nb, ph, out,
                                                     out_drop_stride);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
@@ -277,6 +282,7 @@ int launch_phase(double* coef, long long nfield, int p, double gamma, cudaStream
   long long n = nfield * (long long)(p + 1) * (p + 1);
   if (n == 0 || gamma == 0.0) return BIE_OK;
   k_phase<<<blocks_for(n), kThreads, 0, s>>>(coef, nfield, p, gamma);
+  count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }

@@ -17,13 +17,13 @@ FP64_TOL = 1e-12
 MIXED_TOL = 2e-5
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=[False, True], ids=["fourier", "direct"])
+def ctx(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1707_02156_gb300 import api, build
     build.build()
-    return api.Context(0)
+    return api.Context(0, self_direct=request.param)
 
 
 def dev(a):
