@@ -98,6 +98,30 @@ int bie_sh_synthesize(bie_ctx* ctx, int ndrop, const int* p, const int* p_out, i
 int bie_rotate(bie_ctx* ctx, int ndrop, const int* p, int ncomp, const double* coef, const double* euler,
                double* coef_out, void* stream);
 
+/* Allocation-free variant of bie_rotate.  The paper has no counterpart: this is an interface of
+ * the library for callers that cannot allocate device memory -- code issuing work while a stream
+ * is being captured into a CUDA graph (cudaMalloc/cudaFree are not capturable), frameworks that
+ * own all device memory through their own pool and forbid other allocations, and loops that must
+ * not touch the allocator or its implicit synchronisation.  bie_rotate allocates and frees small
+ * per-call tables; bie_rotate_noalloc stages the same tables in one fixed array of
+ * BIE_NOALLOC_SCRATCH_DOUBLES doubles (1.4 MiB) compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   Arguments, layout and result: as bie_rotate; degrees 1 <= p <= BIE_NOALLOC_MAX_P.  A request
+ *   whose tables (the Wigner blocks of degree p, 2(p+1) phases and ncomp offsets) do not fit the
+ *   array is rejected with BIE_EINVAL and a message in bie_last_error(), before any GPU work.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ *   capture begins.
+ *   Sharing: every call uses the same array and leaves the last drop's tables in it.  Each call
+ *   writes every entry it reads before reading it, so nothing needs to start at zero.  Calls whose
+ *   GPU work overlaps -- on different streams, or from several host threads -- race on the array:
+ *   issue them on one stream or serialise them. */
+#define BIE_NOALLOC_MAX_P 64
+#define BIE_NOALLOC_SCRATCH_DOUBLES 184320
+int bie_rotate_noalloc(bie_ctx* ctx, int ndrop, const int* p, int ncomp, const double* coef, const double* euler,
+                       double* coef_out, void* stream);
+
 /* Geometry of ndrop drops (Table 2; Sec. 2.2 rotated-grid cache; Sec. 2.3 regions), built once per
  * shape and reused by every apply and solve on it.
  *   p[d]   SH degree of drop d (host), pq[d] degree of its self (singular) quadrature grid,

@@ -54,6 +54,7 @@ EXPORTS = {
     "bie_sh_analyze": (c_int, [c_void, c_int, P_int, c_int, c_void, c_void, c_void]),
     "bie_sh_synthesize": (c_int, [c_void, c_int, P_int, P_int, c_int, c_void, c_void, c_void]),
     "bie_rotate": (c_int, [c_void, c_int, P_int, c_int, c_void, P_double, c_void, c_void]),
+    "bie_rotate_noalloc": (c_int, [c_void, c_int, P_int, c_int, c_void, P_double, c_void, c_void]),
     "bie_geometry_setup": (c_int, [c_void, c_int, P_int, P_int, c_void, P_double, ctypes.POINTER(c_void), c_void]),
     "bie_geometry_destroy": (None, [c_void]),
     "bie_geometry_info": (c_int, [c_void, ctypes.POINTER(bie_geom_info)]),
@@ -182,6 +183,13 @@ class Context:
         n = ctypes.c_int()
         _check(lib().bie_profile_read(self.h, buf, 32, ctypes.byref(n)), "bie_profile_read")
         return {buf[i].name.decode(): (buf[i].ms, buf[i].calls) for i in range(min(n.value, 32))}
+
+    def rotate_noalloc(self, p, ncomp: int, coef: torch.Tensor, euler, out: torch.Tensor):
+        """bie_rotate without device allocation (tables staged in the library's fixed device array)."""
+        flat = [float(a) for e in euler for a in e]
+        _check(lib().bie_rotate_noalloc(self.h, len(p), _ints(p), ncomp, _ptr(coef), _doubles(flat), _ptr(out),
+                                        _stream()), "bie_rotate_noalloc")
+        return out
 
     def geometry(self, p, pq, xcoef: torch.Tensor, lam) -> "Geometry":
         return Geometry(self, p, pq, xcoef, lam)

@@ -157,6 +157,8 @@ struct Phase {
   }
 };
 
+int ctx_device(const bie_ctx* ctx) { return ctx->cfg.device; }
+
 static int get_plan(bie_ctx* ctx, int p, int P, Plan** out) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   auto key = std::make_pair(p, P);

@@ -11,6 +11,7 @@ namespace bie {
 
 void set_error(const std::string& msg);
 void count_launch(int n = 1);  // kernel launches issued by the library (all threads)
+int ctx_device(const bie_ctx* ctx);  // CUDA device ordinal of a context
 
 #define BIE_CUDA_TRY(expr)                                                                     \
   do {                                                                                         \
