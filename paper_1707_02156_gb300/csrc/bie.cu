@@ -14,6 +14,7 @@
 #include <utility>
 #include <vector>
 
+#include "interdrop.h"
 #include "internal.cuh"
 #include "tables.h"
 
@@ -271,6 +272,22 @@ struct bie_geom {
   bie::DevBuf<double> anaF;   // analysis workspace
   bie::Krylov* kry = nullptr;  // solve workspace, kept between solves
   bie_geom_info info{};
+  // inter-drop data (ndrop > 1), Sec. 2.3
+  std::vector<double> centre, bound, hdrop, volume;
+  std::vector<long long> up_off, up_n;
+  std::vector<int> up_P;
+  long long nup_total = 0;
+  bie::DevBuf<double> rec_up;                       // [drop][7][N_up] upsampled-grid records
+  bie::DevBuf<double> sX64, sN64, uX64, uN64, sQ64, uQ64;  // sources: positions rel. centre, normals, weighted density
+  bie::DevBuf<float> sX32, sN32, uX32, uN32, sQ32, uQ32;
+  bie::DevBuf<double> syn64;                        // synthesis temporaries for the source densities
+  bie::DevBuf<float> syn32;
+  bie::DevBuf<bie::PairItem> items;
+  bie::DevBuf<int> blk_item, tile_n, tile_drop, tile_blk, tdrop, ngd;
+  bie::DevBuf<long long> tile_t0, tgt_loc, toff, val_off_all;
+  bie::DevBuf<double> centre_d, partial, wS_all, wD_all, wSr_all, wDr_all;
+  int nblk = 0, ntile = 0;
+  std::vector<std::pair<long long, int>> near;      // (target, source drop) pairs in Omega_2
 };
 
 namespace bie {
@@ -340,6 +357,10 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
   return BIE_OK;
 }
 
+template <typename R>
+static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s);
+static int near_apply(bie_geom* g, int kind, bool raw, int prec, const double* dens, cudaStream_t s);
+
 static int layer_apply(bie_ctx* ctx, const bie_geom* gc, int kind, const double* dens, double* out, int precision,
                        cudaStream_t s) {
   bie_geom* g = const_cast<bie_geom*>(gc);
@@ -358,8 +379,11 @@ static int layer_apply(bie_ctx* ctx, const bie_geom* gc, int kind, const double*
   else
     BIE_TRY(self_apply<float>(g, kind, raw, dens, s));
   if (g->ndrop > 1) {
-    set_error("multi-drop apply not available in this build");
-    return BIE_ENOTSUP;
+    if (prec == BIE_FP64)
+      BIE_TRY(interdrop_apply<double>(g, kind, raw, dens, s));
+    else
+      BIE_TRY(interdrop_apply<float>(g, kind, raw, dens, s));
+    BIE_TRY(near_apply(g, kind, raw, prec, dens, s));
   }
   if (precision & BIE_GRID_OUT) {
     BIE_CUDA_TRY(cudaMemcpyAsync(out, g->vals.ptr, 3 * g->ntarget * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -460,6 +484,339 @@ static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream
     BIE_CUDA_TRY(cudaStreamSynchronize(s));
   }
   return BIE_OK;
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// inter-drop set-up (Sec. 2.3): centres, volumes and mean radii, upsampled grids, source records,
+// region classification, and the balanced work list of the pair sums
+// ---------------------------------------------------------------------------------------------
+static int drop_records(bie_ctx* ctx, bie_geom* g, int d, int P, double* rec, cudaStream_t s) {
+  const int p = g->p[d];
+  Plan* pl;
+  BIE_TRY(get_plan(ctx, p, P, &pl));
+  const long long N = ngrid(P);
+  DevBuf<double> tmp;
+  BIE_TRY(tmp.alloc(3 * (p + 1) * (size_t)(P + 1) * 2 + 9 * N));
+  double* H = tmp.ptr;
+  double* X = H + 3 * (p + 1) * (long long)(P + 1) * 2;
+  BIE_TRY(synth_xderivs(ctx, g->xcoef.ptr + g->coef_off[d], nullptr, ncoef(p), 3, p, P, H, X, X + 3 * N, X + 6 * N,
+                        s));
+  BIE_TRY(launch_surface(X, X + 3 * N, X + 6 * N, 1, P, pl->wsin.ptr, rec, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return BIE_OK;
+}
+
+static int drop_stats(const double* rec, long long N, const double* c, double* vol, double* bnd, cudaStream_t s) {
+  DevBuf<double> o;
+  BIE_TRY(o.alloc(128));
+  BIE_TRY(launch_drop_stats(rec, N, c, o.ptr, s));
+  std::vector<double> h(128);
+  BIE_CUDA_TRY(cudaMemcpyAsync(h.data(), o.ptr, 128 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  double v = 0, m = 0;
+  for (int b = 0; b < 64; ++b) {
+    v += h[2 * b];
+    m = std::max(m, h[2 * b + 1]);
+  }
+  *vol = v / 3.0;
+  *bnd = m;
+  return BIE_OK;
+}
+
+static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
+  const int nd = g->ndrop;
+  const int U = ctx->cfg.upsample;
+  // centres from the degree-0 coefficients: x_0^0 = sqrt(4 pi) c
+  std::vector<double> xc(g->ncoef_total);
+  BIE_CUDA_TRY(cudaMemcpy(xc.data(), g->xcoef.ptr, xc.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  g->centre.assign(3 * nd, 0.0);
+  g->bound.assign(nd, 0.0);
+  g->hdrop.assign(nd, 0.0);
+  g->volume.assign(nd, 0.0);
+  g->up_off.assign(nd, 0);
+  g->up_n.assign(nd, 0);
+  g->up_P.assign(nd, 0);
+  long long uo = 0;
+  for (int d = 0; d < nd; ++d) {
+    for (int c = 0; c < 3; ++c) g->centre[3 * d + c] = xc[g->coef_off[d] + c * ncoef(g->p[d])] / std::sqrt(4 * kPi);
+    g->up_P[d] = U * (g->p[d] + 1) - 1;
+    g->up_off[d] = uo;
+    g->up_n[d] = ngrid(g->up_P[d]);
+    uo += g->up_n[d];
+  }
+  g->nup_total = uo;
+  BIE_TRY(g->rec_up.alloc(7 * uo));
+  BIE_TRY(g->centre_d.upload(g->centre));
+  for (int d = 0; d < nd; ++d) {
+    const int p = g->p[d];
+    // volume by the regular rule on the grid of degree 2p+1, mean radius, h = R pi/(p+1)
+    const int P2 = 2 * p + 1;
+    DevBuf<double> rec2;
+    BIE_TRY(rec2.alloc(7 * ngrid(P2)));
+    BIE_TRY(drop_records(ctx, g, d, P2, rec2.ptr, s));
+    double vol, dummy;
+    BIE_TRY(drop_stats(rec2.ptr, ngrid(P2), &g->centre[3 * d], &vol, &dummy, s));
+    g->volume[d] = vol;
+    const double R = std::cbrt(3.0 * vol / (4.0 * kPi));
+    g->hdrop[d] = R * kPi / (p + 1);
+    // upsampled grid records and the bounding radius about the centre
+    double* ru = g->rec_up.ptr + 7 * g->up_off[d];
+    BIE_TRY(drop_records(ctx, g, d, g->up_P[d], ru, s));
+    double v2;
+    BIE_TRY(drop_stats(ru, g->up_n[d], &g->centre[3 * d], &v2, &g->bound[d], s));
+  }
+  // per-target bookkeeping
+  const long long nt = g->ntarget;
+  std::vector<int> tdrop(nt), ngd(nd);
+  std::vector<long long> tloc(nt), voff(nd);
+  for (int d = 0; d < nd; ++d) {
+    ngd[d] = (int)ngrid(g->p[d]);
+    voff[d] = 3 * g->tgt_off[d];
+    for (long long l = 0; l < ngd[d]; ++l) {
+      tdrop[g->tgt_off[d] + l] = d;
+      tloc[g->tgt_off[d] + l] = l;
+    }
+  }
+  BIE_TRY(g->tdrop.upload(tdrop));
+  BIE_TRY(g->tgt_loc.upload(tloc));
+  BIE_TRY(g->toff.upload(g->tgt_off));
+  BIE_TRY(g->ngd.upload(ngd));
+  BIE_TRY(g->val_off_all.upload(voff));
+  // source geometry relative to the drop centres, FP64 and FP32
+  const long long ns = nt;
+  BIE_TRY(g->sX64.alloc(3 * ns));
+  BIE_TRY(g->sN64.alloc(3 * ns));
+  BIE_TRY(g->sX32.alloc(3 * ns));
+  BIE_TRY(g->sN32.alloc(3 * ns));
+  BIE_TRY(g->uX64.alloc(3 * uo));
+  BIE_TRY(g->uN64.alloc(3 * uo));
+  BIE_TRY(g->uX32.alloc(3 * uo));
+  BIE_TRY(g->uN32.alloc(3 * uo));
+  for (int d = 0; d < nd; ++d) {
+    const double* c = &g->centre[3 * d];
+    const double* rs = g->rec_std.ptr + 7 * g->tgt_off[d];
+    const double* ru = g->rec_up.ptr + 7 * g->up_off[d];
+    BIE_TRY(launch_source_geometry<double>(rs, ngd[d], c, g->sX64.ptr + g->tgt_off[d], g->sN64.ptr + g->tgt_off[d],
+                                           ns, s));
+    BIE_TRY(launch_source_geometry<float>(rs, ngd[d], c, g->sX32.ptr + g->tgt_off[d], g->sN32.ptr + g->tgt_off[d],
+                                          ns, s));
+    BIE_TRY(launch_source_geometry<double>(ru, g->up_n[d], c, g->uX64.ptr + g->up_off[d],
+                                           g->uN64.ptr + g->up_off[d], uo, s));
+    BIE_TRY(launch_source_geometry<float>(ru, g->up_n[d], c, g->uX32.ptr + g->up_off[d], g->uN32.ptr + g->up_off[d],
+                                          uo, s));
+  }
+  // region classification on the device, work list on the host
+  std::vector<unsigned char> region;
+  {
+    DevBuf<unsigned char> reg;
+    DevBuf<double> bnd, hh;
+    DevBuf<long long> uoff, un;
+    BIE_TRY(reg.alloc((size_t)nt * nd));
+    BIE_TRY(bnd.upload(g->bound));
+    BIE_TRY(hh.upload(g->hdrop));
+    BIE_TRY(uoff.upload(g->up_off));
+    BIE_TRY(un.upload(g->up_n));
+    BIE_TRY(launch_classify(g->rec_std.ptr, nt, g->tdrop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr, nd,
+                            g->centre_d.ptr, bnd.ptr, hh.ptr, ctx->cfg.a_tilde, g->rec_up.ptr, uoff.ptr, un.ptr,
+                            reg.ptr, s));
+    region.resize((size_t)nt * nd);
+    BIE_CUDA_TRY(cudaMemcpyAsync(region.data(), reg.ptr, region.size(), cudaMemcpyDeviceToHost, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  std::vector<long long> tile_t0;
+  std::vector<int> tile_n, tile_drop;
+  for (int d = 0; d < nd; ++d)
+    for (long long l = 0; l < ngd[d]; l += kTile) {
+      tile_t0.push_back(g->tgt_off[d] + l);
+      tile_n.push_back((int)std::min<long long>(kTile, ngd[d] - l));
+      tile_drop.push_back(d);
+    }
+  const int ntile = (int)tile_t0.size();
+  std::vector<PairItem> items;
+  std::vector<int> blk_item, tile_blk(ntile + 1, 0);
+  long long far_pairs = 0, up_pairs = 0;
+  g->near.clear();
+  for (int ti = 0; ti < ntile; ++ti) {
+    std::vector<PairItem> mine;
+    long long total = 0;
+    for (int j = 0; j < nd; ++j) {
+      if (j == tile_drop[ti]) continue;
+      PairItem a{}, b{};
+      int n0 = 0, n1 = 0;
+      for (int k = 0; k < tile_n[ti]; ++k) {
+        const long long t = tile_t0[ti] + k;
+        const unsigned char r = region[(size_t)t * nd + j];
+        if (r == 3) {
+          set_error("drops overlap: a grid point of drop " + std::to_string(tile_drop[ti]) + " lies inside drop " +
+                    std::to_string(j));
+          return BIE_EOVERLAP;
+        }
+        if (r == 0) {
+          a.mask[k >> 5] |= 1u << (k & 31);
+          ++n0;
+        } else if (r == 1) {
+          b.mask[k >> 5] |= 1u << (k & 31);
+          ++n1;
+        } else if (r == 2) {
+          g->near.emplace_back(t, j);
+        }
+      }
+      if (n0) {
+        a.tile = ti;
+        a.src_drop = j;
+        a.grid = 0;
+        a.s0 = g->tgt_off[j];
+        a.s1 = g->tgt_off[j] + ngd[j];
+        mine.push_back(a);
+        total += ngd[j];
+        far_pairs += (long long)n0 * ngd[j];
+      }
+      if (n1) {
+        b.tile = ti;
+        b.src_drop = j;
+        b.grid = 1;
+        b.s0 = g->up_off[j];
+        b.s1 = g->up_off[j] + g->up_n[j];
+        mine.push_back(b);
+        total += g->up_n[j];
+        up_pairs += (long long)n1 * g->up_n[j];
+      }
+    }
+    // split the tile's items into blocks of at most `cap` sources
+    const long long cap = std::max<long long>(16384, (total + 7) / 8);
+    tile_blk[ti] = (int)blk_item.size();
+    long long used = cap;  // forces a new block at the first item
+    for (auto it : mine) {
+      long long s0 = it.s0;
+      while (s0 < it.s1) {
+        if (used >= cap) {
+          blk_item.push_back((int)items.size());
+          used = 0;
+        }
+        const long long take = std::min(it.s1 - s0, cap - used);
+        PairItem piece = it;
+        piece.s0 = s0;
+        piece.s1 = s0 + take;
+        items.push_back(piece);
+        used += take;
+        s0 += take;
+      }
+    }
+  }
+  tile_blk[ntile] = (int)blk_item.size();
+  const int nblk = (int)blk_item.size();
+  blk_item.push_back((int)items.size());
+  g->ntile = ntile;
+  g->nblk = nblk;
+  if (!items.empty()) BIE_TRY(g->items.upload(items));
+  BIE_TRY(g->blk_item.upload(blk_item));
+  BIE_TRY(g->tile_blk.upload(tile_blk));
+  BIE_TRY(g->tile_t0.upload(tile_t0));
+  BIE_TRY(g->tile_n.upload(tile_n));
+  BIE_TRY(g->tile_drop.upload(tile_drop));
+  BIE_TRY(g->partial.alloc((size_t)std::max(1, nblk) * 3 * kTile));
+  std::vector<double> wS(nd), wD(nd), wSr(nd), wDr(nd);
+  for (int d = 0; d < nd; ++d) {
+    wS[d] = -1.0 / (4 * kPi);
+    wD[d] = (g->lambda[d] - 1.0) / (4 * kPi);
+    wSr[d] = 1.0 / (8 * kPi);
+    wDr[d] = 1.0 / (4 * kPi);
+  }
+  BIE_TRY(g->wS_all.upload(wS));
+  BIE_TRY(g->wD_all.upload(wD));
+  BIE_TRY(g->wSr_all.upload(wSr));
+  BIE_TRY(g->wDr_all.upload(wDr));
+  g->info.far_pairs = far_pairs;
+  g->info.up_pairs = up_pairs;
+  g->info.near_targets = (long long)g->near.size();
+  return BIE_OK;
+}
+
+// Source densities of every drop on its standard and upsampled grids, weighted by the regular
+// quadrature weight and area density (Sec. 2.1, Sec. 2.3).
+template <typename R>
+static int source_densities(bie_geom* g, const double* dens, R* Qs, R* Qu, cudaStream_t s) {
+  bie_ctx* ctx = g->ctx;
+  Phase ph(ctx, "source_synth", s);
+  for (auto& Gp : g->groups) {
+    auto& G = *Gp;
+    const int p = G.p;
+    const int Pu = ctx->cfg.upsample * (p + 1) - 1;
+    const long long nd = (long long)G.drops.size();
+    const long long need = nd * 3 * ((long long)(p + 1) * (Pu + 1) * 2 + ngrid(Pu));
+    R* H;
+    if (sizeof(R) == 8) {
+      BIE_TRY(g->syn64.alloc(need));
+      H = reinterpret_cast<R*>(g->syn64.ptr);
+    } else {
+      BIE_TRY(g->syn32.alloc(need));
+      H = reinterpret_cast<R*>(g->syn32.ptr);
+    }
+    for (int gridk = 0; gridk < 2; ++gridk) {
+      const int P = gridk ? Pu : p;
+      const long long N = ngrid(P);
+      Plan* pl;
+      BIE_TRY(get_plan(ctx, p, P, &pl));
+      R* grid = H + nd * 3 * (long long)(p + 1) * (P + 1) * 2;
+      BIE_TRY((launch_leg_synth<double, R>(dens, G.foff3.ptr, 0, nd * 3, p, pl->T0_<R>(), P + 1, H, 0, s)));
+      BIE_TRY((launch_phi_synth<R, R>(H, nd * 3, p, P, pl->cs_<R>(), grid, nullptr, N, s)));
+      for (long long i = 0; i < nd; ++i) {
+        const int d = G.drops[i];
+        if (gridk == 0)
+          BIE_TRY(launch_weight_sources<R>(grid + i * 3 * N, g->rec_std.ptr + 7 * g->tgt_off[d], N, Qs + g->tgt_off[d],
+                                           g->ntarget, s));
+        else
+          BIE_TRY(launch_weight_sources<R>(grid + i * 3 * N, g->rec_up.ptr + 7 * g->up_off[d], N, Qu + g->up_off[d],
+                                           g->nup_total, s));
+      }
+    }
+  }
+  return BIE_OK;
+}
+
+static int near_apply(bie_geom* g, int, bool, int, const double*, cudaStream_t) {
+  if (g->near.empty()) return BIE_OK;
+  set_error("near-singular targets present but the near-singular step is not available in this build");
+  return BIE_ENOTSUP;
+}
+
+template <typename R>
+static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s) {
+  bie_ctx* ctx = g->ctx;
+  R *Qs, *Qu;
+  const R *Xs, *Ns, *Xu, *Nu;
+  if (sizeof(R) == 8) {
+    BIE_TRY(g->sQ64.alloc(3 * g->ntarget));
+    BIE_TRY(g->uQ64.alloc(3 * g->nup_total));
+    Qs = reinterpret_cast<R*>(g->sQ64.ptr);
+    Qu = reinterpret_cast<R*>(g->uQ64.ptr);
+    Xs = reinterpret_cast<const R*>(g->sX64.ptr);
+    Ns = reinterpret_cast<const R*>(g->sN64.ptr);
+    Xu = reinterpret_cast<const R*>(g->uX64.ptr);
+    Nu = reinterpret_cast<const R*>(g->uN64.ptr);
+  } else {
+    BIE_TRY(g->sQ32.alloc(3 * g->ntarget));
+    BIE_TRY(g->uQ32.alloc(3 * g->nup_total));
+    Qs = reinterpret_cast<R*>(g->sQ32.ptr);
+    Qu = reinterpret_cast<R*>(g->uQ32.ptr);
+    Xs = reinterpret_cast<const R*>(g->sX32.ptr);
+    Ns = reinterpret_cast<const R*>(g->sN32.ptr);
+    Xu = reinterpret_cast<const R*>(g->uX32.ptr);
+    Nu = reinterpret_cast<const R*>(g->uN32.ptr);
+  }
+  BIE_TRY(source_densities<R>(g, dens, Qs, Qu, s));
+  const double* wts = kind == 0 ? (raw ? g->wSr_all.ptr : g->wS_all.ptr) : (raw ? g->wDr_all.ptr : g->wD_all.ptr);
+  {
+    Phase ph(ctx, sizeof(R) == 8 ? "interdrop_f64" : "interdrop_f32", s);
+    BIE_TRY(launch_interdrop<R>(kind, g->nblk, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr, g->tile_n.ptr,
+                                g->tile_drop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr, g->rec_std.ptr,
+                                g->centre_d.ptr, Xs, Ns, Qs, g->ntarget, Xu, Nu, Qu, g->nup_total, wts,
+                                g->partial.ptr, s));
+  }
+  Phase ph(ctx, "interdrop_reduce", s);
+  return launch_reduce_tiles(g->partial.ptr, g->tile_blk.ptr, g->tile_t0.ptr, g->tile_n.ptr, g->tile_drop.ptr,
+                             g->tgt_loc.ptr, g->val_off_all.ptr, g->ngd.ptr, g->ntile, g->vals.ptr, s);
 }
 
 }  // namespace bie
@@ -870,10 +1227,7 @@ int bie_geometry_setup(bie_ctx* ctx, int ndrop, const int* p, const int* pq, con
     BIE_TRY(setup_group(ctx, g.get(), *G, s));
     self_pairs += (long long)G->drops.size() * ngrid(G->p) * ngrid(G->pq);
   }
-  if (ndrop > 1) {
-    set_error("multi-drop geometry not available in this build");
-    return BIE_ENOTSUP;
-  }
+  if (ndrop > 1) BIE_TRY(setup_interdrop(ctx, g.get(), s));
   BIE_CUDA_TRY(cudaStreamSynchronize(s));
   g->info.ndrop = ndrop;
   g->info.ncoef = co;

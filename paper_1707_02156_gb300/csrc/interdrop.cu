@@ -1,0 +1,318 @@
+// Inter-drop interactions (Sec. 2.1, 2.3): region classification with bounding spheres, and the
+// regular (standard grid, Omega_0) and upsampled (grid of degree U(p+1)-1, Omega_1) pair sums of the
+// single- and double-layer kernels, as a balanced work list of (target tile, source drop, grid,
+// source range, target mask) items.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "interdrop.h"
+#include "internal.cuh"
+
+namespace bie {
+namespace {
+
+constexpr int kThreads = 256;
+inline unsigned blocks_for(long long n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+// region[t * ndrop + j]: 0 / 1 / 2 for Omega_0/1/2 of target t w.r.t. drop j, 3 = t inside drop j,
+// 255 for j = own drop.  Distance = nearest point of j's upsampled grid (Sec. 2.3).
+__global__ void k_classify(const double* __restrict__ rec_std, long long ntarget, const int* __restrict__ tdrop,
+                           const long long* __restrict__ tloc, const long long* __restrict__ toff_std,
+                           const int* __restrict__ ngd, int ndrop, const double* __restrict__ centre,
+                           const double* __restrict__ bound, const double* __restrict__ h, double a_tilde,
+                           const double* __restrict__ rec_up, const long long* __restrict__ up_off,
+                           const long long* __restrict__ up_n, unsigned char* __restrict__ region) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ntarget * ndrop) return;
+  const long long t = idx / ndrop;
+  const int j = (int)(idx - t * ndrop);
+  const int i = tdrop[t];
+  if (i == j) {
+    region[idx] = 255;
+    return;
+  }
+  const long long ng = ngd[i];
+  const double* ri = rec_std + 7 * toff_std[i];
+  const double x0 = ri[tloc[t]], x1 = ri[ng + tloc[t]], x2 = ri[2 * ng + tloc[t]];
+  const double dc0 = x0 - centre[3 * j], dc1 = x1 - centre[3 * j + 1], dc2 = x2 - centre[3 * j + 2];
+  const double dcen = sqrt(dc0 * dc0 + dc1 * dc1 + dc2 * dc2);
+  if (dcen - bound[j] > a_tilde * h[j]) {  // every grid point of j is farther than A h_j
+    region[idx] = 0;
+    return;
+  }
+  const long long N = up_n[j];
+  const double* r = rec_up + 7 * up_off[j];
+  double best = 1e300;
+  long long bi = 0;
+  for (long long s = 0; s < N; ++s) {
+    const double d0 = x0 - r[s], d1 = x1 - r[N + s], d2 = x2 - r[2 * N + s];
+    const double d = d0 * d0 + d1 * d1 + d2 * d2;
+    if (d < best) {
+      best = d;
+      bi = s;
+    }
+  }
+  const double dist = sqrt(best);
+  const double side = (x0 - r[bi]) * r[3 * N + bi] + (x1 - r[N + bi]) * r[4 * N + bi] + (x2 - r[2 * N + bi]) * r[5 * N + bi];
+  unsigned char code = dist <= h[j] ? 2 : (dist <= a_tilde * h[j] ? 1 : 0);
+  if (side <= 0.0) code = 3;
+  region[idx] = code;
+}
+
+constexpr int kChunk = 128;  // sources staged per pass
+
+template <typename R, int KIND>
+__global__ void __launch_bounds__(kTile) k_interdrop(
+    const PairItem* __restrict__ items, const int* __restrict__ blk_item, const long long* __restrict__ tile_t0,
+    const int* __restrict__ tile_n, const int* __restrict__ tile_drop, const long long* __restrict__ tgt_loc,
+    const long long* __restrict__ toff_std, const int* __restrict__ ngd, const double* __restrict__ rec_std,
+    const double* __restrict__ centre, const R* __restrict__ Xs, const R* __restrict__ Ns, const R* __restrict__ Qs,
+    long long nstd, const R* __restrict__ Xu, const R* __restrict__ Nu, const R* __restrict__ Qu, long long nup,
+    const double* __restrict__ wts, double* __restrict__ partial) {
+  __shared__ R sx[kChunk], sy[kChunk], sz[kChunk], sq0[kChunk], sq1[kChunk], sq2[kChunk];
+  __shared__ R sn0[KIND ? kChunk : 1], sn1[KIND ? kChunk : 1], sn2[KIND ? kChunk : 1];
+  const int b = blockIdx.x;
+  const int it0 = blk_item[b], it1 = blk_item[b + 1];
+  const int tile = items[it0].tile;
+  const int tid = threadIdx.x;
+  const int nt = tile_n[tile];
+  const int di = tile_drop[tile];
+  double tx = 0, ty = 0, tz = 0;
+  if (tid < nt) {
+    const long long t = tile_t0[tile] + tid;
+    const long long ng = ngd[di];
+    const double* ri = rec_std + 7 * toff_std[di];
+    const long long l = tgt_loc[t];
+    tx = ri[l];
+    ty = ri[ng + l];
+    tz = ri[2 * ng + l];
+  }
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int it = it0; it < it1; ++it) {
+    const PairItem item = items[it];
+    const int j = item.src_drop;
+    const bool active = tid < nt && ((item.mask[tid >> 5] >> (tid & 31)) & 1u);
+    const R* X = item.grid ? Xu : Xs;
+    const R* N = item.grid ? Nu : Ns;
+    const R* Q = item.grid ? Qu : Qs;
+    const long long ld = item.grid ? nup : nstd;
+    const R px = (R)(tx - centre[3 * j]), py = (R)(ty - centre[3 * j + 1]), pz = (R)(tz - centre[3 * j + 2]);
+    R s0 = 0, s1 = 0, s2 = 0;
+    for (long long c0 = item.s0; c0 < item.s1; c0 += kChunk) {
+      const int cn = (int)min((long long)kChunk, item.s1 - c0);
+      if (tid < cn) {
+        const long long s = c0 + tid;
+        sx[tid] = X[s];
+        sy[tid] = X[ld + s];
+        sz[tid] = X[2 * ld + s];
+        sq0[tid] = Q[s];
+        sq1[tid] = Q[ld + s];
+        sq2[tid] = Q[2 * ld + s];
+        if (KIND) {
+          sn0[tid] = N[s];
+          sn1[tid] = N[ld + s];
+          sn2[tid] = N[2 * ld + s];
+        }
+      }
+      __syncthreads();
+      if (active) {
+        for (int k = 0; k < cn; ++k) {
+          const R dx = px - sx[k], dy = py - sy[k], dz = pz - sz[k];
+          const R ri = rsqrt_<R>(dx * dx + dy * dy + dz * dz);
+          const R xq = dx * sq0[k] + dy * sq1[k] + dz * sq2[k];
+          if (KIND == 0) {  // Stokeslet
+            const R c = xq * ri * ri * ri;
+            s0 += sq0[k] * ri + c * dx;
+            s1 += sq1[k] * ri + c * dy;
+            s2 += sq2[k] * ri + c * dz;
+          } else {  // stresslet
+            const R xn = dx * sn0[k] + dy * sn1[k] + dz * sn2[k];
+            const R ri2 = ri * ri;
+            const R c = (R)(-6) * xq * xn * ri2 * ri2 * ri;
+            s0 += c * dx;
+            s1 += c * dy;
+            s2 += c * dz;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const double wt = wts[j];
+    a0 += wt * (double)s0;
+    a1 += wt * (double)s1;
+    a2 += wt * (double)s2;
+  }
+  double* pp = partial + (long long)b * 3 * kTile;
+  pp[tid] = a0;
+  pp[kTile + tid] = a1;
+  pp[2 * kTile + tid] = a2;
+}
+
+// vals += sum of the partials of the tile's blocks, in block order
+__global__ void k_reduce_tiles(const double* __restrict__ partial, const int* __restrict__ tile_blk,
+                               const long long* __restrict__ tile_t0, const int* __restrict__ tile_n,
+                               const int* __restrict__ tile_drop, const long long* __restrict__ tgt_loc,
+                               const long long* __restrict__ val_off, const int* __restrict__ ngd, int ntile,
+                               double* __restrict__ vals) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)ntile * kTile) return;
+  const int tile = (int)(idx / kTile), tid = (int)(idx - (long long)tile * kTile);
+  if (tid >= tile_n[tile]) return;
+  const int b0 = tile_blk[tile], b1 = tile_blk[tile + 1];
+  if (b0 == b1) return;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int b = b0; b < b1; ++b) {
+    const double* pp = partial + (long long)b * 3 * kTile;
+    a0 += pp[tid];
+    a1 += pp[kTile + tid];
+    a2 += pp[2 * kTile + tid];
+  }
+  const int d = tile_drop[tile];
+  const long long l = tgt_loc[tile_t0[tile] + tid];
+  const long long ng = ngd[d];
+  double* v = vals + val_off[d] + l;
+  v[0] += a0;
+  v[ng] += a1;
+  v[2 * ng] += a2;
+}
+
+// Q[c][s] = wJ[s] * grid[c][s] for one drop, source records rec [7][N] (weight in row 6)
+template <typename R>
+__global__ void k_weight_sources(const R* __restrict__ grid, const double* __restrict__ rec, long long N,
+                                 R* __restrict__ Q, long long ldq) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 3 * N) return;
+  const int c = (int)(idx / N);
+  const long long s = idx - c * N;
+  Q[c * ldq + s] = (R)rec[6 * N + s] * grid[c * N + s];
+}
+
+// sum_s x.n wJ over one drop's records (for the volume), and max_s |x - c|, via atomics on doubles
+__global__ void k_drop_stats(const double* __restrict__ rec, long long N, double cx, double cy, double cz,
+                             double* __restrict__ out) {
+  __shared__ double sv[kThreads], sm[kThreads];
+  double v = 0, mx = 0;
+  for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
+    const double x = rec[s], y = rec[N + s], z = rec[2 * N + s];
+    v += (x * rec[3 * N + s] + y * rec[4 * N + s] + z * rec[5 * N + s]) * rec[6 * N + s];
+    const double dx = x - cx, dy = y - cy, dz = z - cz;
+    mx = fmax(mx, sqrt(dx * dx + dy * dy + dz * dz));
+  }
+  sv[threadIdx.x] = v;
+  sm[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sv[threadIdx.x] += sv[threadIdx.x + o];
+      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = sv[0];
+    out[2 * blockIdx.x + 1] = sm[0];
+  }
+}
+
+// SoA source positions relative to the drop centre and normals, in precision R
+template <typename R>
+__global__ void k_source_geometry(const double* __restrict__ rec, long long N, double cx, double cy, double cz,
+                                  R* __restrict__ X, R* __restrict__ Nn, long long ld) {
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  X[s] = (R)(rec[s] - cx);
+  X[ld + s] = (R)(rec[N + s] - cy);
+  X[2 * ld + s] = (R)(rec[2 * N + s] - cz);
+  Nn[s] = (R)rec[3 * N + s];
+  Nn[ld + s] = (R)rec[4 * N + s];
+  Nn[2 * ld + s] = (R)rec[5 * N + s];
+}
+
+}  // namespace
+
+int launch_classify(const double* rec_std, long long ntarget, const int* tdrop, const long long* tloc,
+                    const long long* toff_std, const int* ngd, int ndrop, const double* centre, const double* bound,
+                    const double* h, double a_tilde, const double* rec_up, const long long* up_off,
+                    const long long* up_n, unsigned char* region, cudaStream_t s) {
+  long long n = ntarget * ndrop;
+  if (n == 0) return BIE_OK;
+  k_classify<<<blocks_for(n), kThreads, 0, s>>>(rec_std, ntarget, tdrop, tloc, toff_std, ngd, ndrop, centre, bound, h,
+                                                a_tilde, rec_up, up_off, up_n, region);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+template <typename R>
+int launch_interdrop(int kind, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
+                     const int* tile_n, const int* tile_drop, const long long* tgt_loc, const long long* toff_std,
+                     const int* ngd, const double* rec_std, const double* centre, const R* Xs, const R* Ns,
+                     const R* Qs, long long nstd, const R* Xu, const R* Nu, const R* Qu, long long nup,
+                     const double* wts, double* partial, cudaStream_t s) {
+  if (nblk == 0) return BIE_OK;
+  if (kind == 0)
+    k_interdrop<R, 0><<<nblk, kTile, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
+                                             rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial);
+  else
+    k_interdrop<R, 1><<<nblk, kTile, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
+                                             rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+int launch_reduce_tiles(const double* partial, const int* tile_blk, const long long* tile_t0, const int* tile_n,
+                        const int* tile_drop, const long long* tgt_loc, const long long* val_off, const int* ngd,
+                        int ntile, double* vals, cudaStream_t s) {
+  long long n = (long long)ntile * kTile;
+  if (n == 0) return BIE_OK;
+  k_reduce_tiles<<<blocks_for(n), kThreads, 0, s>>>(partial, tile_blk, tile_t0, tile_n, tile_drop, tgt_loc, val_off,
+                                                     ngd, ntile, vals);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+template <typename R>
+int launch_weight_sources(const R* grid, const double* rec, long long N, R* Q, long long ldq, cudaStream_t s) {
+  if (N == 0) return BIE_OK;
+  k_weight_sources<R><<<blocks_for(3 * N), kThreads, 0, s>>>(grid, rec, N, Q, ldq);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+int launch_drop_stats(const double* rec, long long N, const double* c, double* out2x64, cudaStream_t s) {
+  k_drop_stats<<<64, kThreads, 0, s>>>(rec, N, c[0], c[1], c[2], out2x64);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+template <typename R>
+int launch_source_geometry(const double* rec, long long N, const double* c, R* X, R* Nn, long long ld,
+                           cudaStream_t s) {
+  if (N == 0) return BIE_OK;
+  k_source_geometry<R><<<blocks_for(N), kThreads, 0, s>>>(rec, N, c[0], c[1], c[2], X, Nn, ld);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+template int launch_interdrop<double>(int, int, const PairItem*, const int*, const long long*, const int*,
+                                      const int*, const long long*, const long long*, const int*, const double*,
+                                      const double*, const double*, const double*, const double*, long long,
+                                      const double*, const double*, const double*, long long, const double*, double*,
+                                      cudaStream_t);
+template int launch_interdrop<float>(int, int, const PairItem*, const int*, const long long*, const int*, const int*,
+                                     const long long*, const long long*, const int*, const double*, const double*,
+                                     const float*, const float*, const float*, long long, const float*, const float*,
+                                     const float*, long long, const double*, double*, cudaStream_t);
+template int launch_weight_sources<double>(const double*, const double*, long long, double*, long long, cudaStream_t);
+template int launch_weight_sources<float>(const float*, const double*, long long, float*, long long, cudaStream_t);
+template int launch_source_geometry<double>(const double*, long long, const double*, double*, double*, long long,
+                                            cudaStream_t);
+template int launch_source_geometry<float>(const double*, long long, const double*, float*, float*, long long,
+                                           cudaStream_t);
+
+}  // namespace bie

@@ -1,0 +1,117 @@
+"""GPU parity of the multi-drop layer operators (Sec. 2.1, 2.3) against the FP64 oracle: drops of
+uneven degree and viscosity ratio at gaps where both the regular (Omega_0) and the upsampled (Omega_1)
+rules occur; exact region counts; and the solve."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import gmres, layer
+from paper_1707_02156_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_02156_gb300 import api, build
+    build.build()
+    return api.Context(0, upsample=3)
+
+
+def _batch(seed=5):
+    """Four drops of degrees 6, 8, 10, 7 (sphere / perturbed / ellipsoid), gaps 0.6-1.5."""
+    rng = np.random.default_rng(seed)
+    spec = [(6, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)), (8, (2.6, 0.2, 0.1), (0.9, 1.1, 1.0)),
+            (10, (-0.3, 2.7, 0.4), (1.0, 0.8, 1.2)), (7, (1.2, 1.4, 2.6), (1.1, 1.0, 0.9))]
+    xs, fs, ps = [], [], []
+    for p, c, ax in spec:
+        x = inputs.sphere_coef(p, centre=c, axes=ax, rot=inputs.random_rotation(rng))
+        x = x + inputs.perturbation(rng, p, 2, 4, 0.04)
+        xs.append(x)
+        fs.append(inputs.random_bandlimited(rng, p, 3))
+        ps.append(p)
+    lam = np.array([0.5, 3.0, 1.7, 4.2])
+    return ps, xs, fs, lam
+
+
+def _relerr(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return max(np.linalg.norm(a - b) / np.linalg.norm(b), np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.fixture(scope="module")
+def batch(ctx):
+    ps, xs, fs, lam = _batch()
+    drops = layer.Drops(xs, ps, ps, lam, up=3)
+    geo = ctx.geometry(ps, ps, torch.tensor(inputs.pack_drops(xs), device="cuda"), lam)
+    return ps, xs, fs, lam, drops, geo
+
+
+def test_region_counts_match_oracle(batch):
+    ps, xs, fs, lam, drops, geo = batch
+    far = up = near = 0
+    for (i, j), reg in drops.region.items():
+        ng_j = (ps[j] + 1) * (2 * ps[j] + 2)
+        nu_j = (3 * (ps[j] + 1)) * (6 * (ps[j] + 1))
+        far += int(np.sum(reg == 0)) * ng_j
+        up += int(np.sum(reg == 1)) * nu_j
+        near += int(np.sum(reg == 2))
+    assert up > 0 and far > 0 and near == 0
+    assert geo.info["far_pairs"] == far
+    assert geo.info["up_pairs"] == up
+    assert geo.info["near_targets"] == near
+
+
+@pytest.mark.parametrize("kind", ["S", "D"])
+def test_multidrop_apply_matches_oracle(batch, kind):
+    ps, xs, fs, lam, drops, geo = batch
+    ref = (drops.apply_single if kind == "S" else drops.apply_double)(fs)
+    ref = np.concatenate([r.ravel() for r in ref])
+    f = torch.tensor(inputs.pack_drops(fs), device="cuda")
+    out = torch.zeros_like(f)
+    fn = geo.apply_single if kind == "S" else geo.apply_double
+    for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
+        fn(f, out, precision=prec)
+        torch.cuda.synchronize()
+        assert _relerr(out.cpu().numpy(), ref) < tol, (kind, prec)
+    # grid values, per target, before the projection
+    gref = (drops.apply_single_grid if kind == "S" else drops.apply_double_grid)(fs)
+    gref = np.concatenate([r.ravel() for r in gref])
+    gout = torch.zeros(gref.size, dtype=torch.float64, device="cuda")
+    fn(f, gout, precision=0, grid_out=True)
+    torch.cuda.synchronize()
+    assert _relerr(gout.cpu().numpy(), gref) < FP64_TOL
+
+
+def test_multidrop_solve_matches_oracle(batch):
+    ps, xs, fs, lam, drops, geo = batch
+    uinf = [np.zeros((3, (p + 1) ** 2)) for p in ps]
+    for u, x in zip(uinf, xs):
+        u[0] = x[2]  # u_inf = (z, 0, 0)
+    b = 2 * inputs.pack_drops(uinf) + np.concatenate([r.ravel() for r in drops.apply_single(fs)])
+    u_ref, info = gmres.gmres(drops.system_matvec, b, tol=1e-13)
+    assert info["converged"]
+    rhs = torch.tensor(b, device="cuda")
+    for prec, tol in ((0, 1e-11), (1, 1e-8)):
+        u = torch.zeros_like(rhs)
+        res = geo.solve(rhs, u, precision=prec, tol=1e-12 if prec == 0 else 1e-10)
+        assert res["converged"]
+        torch.cuda.synchronize()
+        assert _relerr(u.cpu().numpy(), u_ref) < tol, (prec, res)
+
+
+def test_overlapping_drops_are_rejected(ctx):
+    from paper_1707_02156_gb300 import api
+    p = 6
+    xs = [inputs.sphere_coef(p), inputs.sphere_coef(p, centre=(1.5, 0, 0))]
+    with pytest.raises(api.BIEError) as e:
+        ctx.geometry([p, p], [p, p], torch.tensor(inputs.pack_drops(xs), device="cuda"), [1.0, 1.0])
+    assert e.value.status == 6
