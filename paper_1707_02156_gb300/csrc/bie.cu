@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "interdrop.h"
+#include "near.h"
 #include "internal.cuh"
 #include "tables.h"
 
@@ -288,6 +289,12 @@ struct bie_geom {
   bie::DevBuf<double> centre_d, partial, wS_all, wD_all, wSr_all, wDr_all;
   int nblk = 0, ntile = 0;
   std::vector<std::pair<long long, int>> near;      // (target, source drop) pairs in Omega_2
+  // near-singular step (Omega_2), Sec. 2.3
+  int nnear_tgt = 0;
+  bie::DevBuf<bie::NearPair> npairs;
+  bie::DevBuf<int> ntbeg, ngrid_l, pdeg_d;
+  bie::DevBuf<double> npts, ncv, selfvals, selfcoef, hdrop_d;
+  bie::DevBuf<long long> coef_off_d, up_off_d, up_n_d;
 };
 
 namespace bie {
@@ -360,6 +367,7 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
 template <typename R>
 static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s);
 static int near_apply(bie_geom* g, int kind, bool raw, int prec, const double* dens, cudaStream_t s);
+static int near_snapshot(bie_geom* g, cudaStream_t s);
 
 static int layer_apply(bie_ctx* ctx, const bie_geom* gc, int kind, const double* dens, double* out, int precision,
                        cudaStream_t s) {
@@ -379,6 +387,7 @@ static int layer_apply(bie_ctx* ctx, const bie_geom* gc, int kind, const double*
   else
     BIE_TRY(self_apply<float>(g, kind, raw, dens, s));
   if (g->ndrop > 1) {
+    if (!g->near.empty()) BIE_TRY(near_snapshot(g, s));
     if (prec == BIE_FP64)
       BIE_TRY(interdrop_apply<double>(g, kind, raw, dens, s));
     else
@@ -523,6 +532,8 @@ static int drop_stats(const double* rec, long long N, const double* c, double* v
   *bnd = m;
   return BIE_OK;
 }
+
+static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s);
 
 static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   const int nd = g->ndrop;
@@ -730,6 +741,9 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   g->info.far_pairs = far_pairs;
   g->info.up_pairs = up_pairs;
   g->info.near_targets = (long long)g->near.size();
+  BIE_TRY(g->up_off_d.upload(g->up_off));
+  BIE_TRY(g->up_n_d.upload(g->up_n));
+  if (!g->near.empty()) BIE_TRY(setup_near(ctx, g, s));
   return BIE_OK;
 }
 
@@ -775,10 +789,170 @@ static int source_densities(bie_geom* g, const double* dens, R* Qs, R* Qu, cudaS
   return BIE_OK;
 }
 
-static int near_apply(bie_geom* g, int, bool, int, const double*, cudaStream_t) {
+// Near-singular set-up (Sec. 2.3): seeds, closest points by damped Newton in a rotated frame with
+// the seed on the equator, check points x_l = x* + h_j sqrt(l) e and the grid of each.
+static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
+  auto& nr = g->near;
+  std::sort(nr.begin(), nr.end());
+  const int npair = (int)nr.size();
+  const int L = ctx->cfg.n_interp;
+  std::vector<NearPair> pairs(npair);
+  std::vector<int> tbeg;
+  for (int i = 0; i < npair; ++i) {
+    pairs[i].target = nr[i].first;
+    pairs[i].src_drop = nr[i].second;
+    if (i == 0 || nr[i].first != nr[i - 1].first) tbeg.push_back(i);
+  }
+  g->nnear_tgt = (int)tbeg.size();
+  tbeg.push_back(npair);
+  BIE_TRY(g->npairs.upload(pairs));
+  BIE_TRY(g->ntbeg.upload(tbeg));
+  DevBuf<int> seed;
+  BIE_TRY(seed.alloc(npair));
+  BIE_TRY(launch_near_seed(g->npairs.ptr, npair, g->rec_std.ptr, g->toff.ptr, g->ngd.ptr, g->tgt_loc.ptr,
+                           g->tdrop.ptr, seed.ptr, s));
+  std::vector<int> hseed(npair);
+  BIE_CUDA_TRY(cudaMemcpyAsync(hseed.data(), seed.ptr, npair * sizeof(int), cudaMemcpyDeviceToHost, s));
+  std::vector<double> rec(7 * g->ntarget);
+  BIE_CUDA_TRY(cudaMemcpyAsync(rec.data(), g->rec_std.ptr, rec.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  // rotated shape coefficients per pair: (alpha, beta) = (phi_b, theta_a - pi/2) puts the seed at the equator
+  std::vector<long long> xr_off(npair);
+  std::vector<double> alpha(npair), beta(npair), x0(3 * npair);
+  long long xo = 0;
+  for (int i = 0; i < npair; ++i) {
+    const int j = pairs[i].src_drop, p = g->p[j];
+    const int nb = 2 * p + 2;
+    std::vector<double> t, w;
+    gauss_legendre(p + 1, t, w);
+    const int a = hseed[i] / nb, b = hseed[i] % nb;
+    alpha[i] = kPi * b / (p + 1);
+    beta[i] = std::acos(t[a]) - 0.5 * kPi;
+    xr_off[i] = xo;
+    xo += 3 * ncoef(p);
+    const long long tt = pairs[i].target;
+    int di = 0;
+    while (di + 1 < g->ndrop && g->tgt_off[di + 1] <= tt) ++di;
+    const long long ngi = ngrid(g->p[di]), l = tt - g->tgt_off[di];
+    for (int c = 0; c < 3; ++c) x0[3 * i + c] = rec[7 * g->tgt_off[di] + c * ngi + l];
+  }
+  DevBuf<double> xr, dx0, res;
+  DevBuf<long long> dxo;
+  DevBuf<int> pdeg;
+  BIE_TRY(xr.alloc(xo));
+  for (int i = 0; i < npair; ++i) {
+    const int j = pairs[i].src_drop, p = g->p[j];
+    std::vector<double> blk(wigner_block_stride(p));
+    wigner_blocks(p, beta[i], blk.data());
+    std::vector<double> ph(2 * (p + 1));
+    for (int m = 0; m <= p; ++m) {
+      ph[2 * m] = std::cos(m * alpha[i]);
+      ph[2 * m + 1] = std::sin(m * alpha[i]);
+    }
+    std::vector<long long> fo(3);
+    for (int c = 0; c < 3; ++c) fo[c] = g->coef_off[j] + c * ncoef(p);
+    DevBuf<double> dblk, dph;
+    DevBuf<long long> dfo;
+    BIE_TRY(dblk.upload(blk));
+    BIE_TRY(dph.upload(ph));
+    BIE_TRY(dfo.upload(fo));
+    BIE_TRY((launch_rotate<double, double>(g->xcoef.ptr, dfo.ptr, 3, 1, p, dblk.ptr, (long long)blk.size(), 1, 1,
+                                           dph.ptr, xr.ptr + xr_off[i], 0, s)));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  std::vector<int> pd(g->p.begin(), g->p.end());
+  BIE_TRY(pdeg.upload(pd));
+  BIE_TRY(dxo.upload(xr_off));
+  BIE_TRY(dx0.upload(x0));
+  BIE_TRY(res.alloc(5 * npair));
+  BIE_TRY(launch_near_newton(g->npairs.ptr, npair, xr.ptr, pdeg.ptr, dxo.ptr, dx0.ptr, res.ptr, s));
+  std::vector<double> hres(5 * npair);
+  BIE_CUDA_TRY(cudaMemcpyAsync(hres.data(), res.ptr, hres.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<double> pts(3 * (size_t)npair * L);
+  for (int i = 0; i < npair; ++i) {
+    const int j = pairs[i].src_drop;
+    const double th = hres[5 * i], phv = hres[5 * i + 1];
+    const double xs[3] = {hres[5 * i + 2], hres[5 * i + 3], hres[5 * i + 4]};
+    double e[3], d0 = 0;
+    for (int c = 0; c < 3; ++c) {
+      e[c] = x0[3 * i + c] - xs[c];
+      d0 += e[c] * e[c];
+    }
+    d0 = std::sqrt(d0);
+    for (int c = 0; c < 3; ++c) e[c] /= d0;
+    pairs[i].d0 = d0;
+    // parameters of x* in drop j's own frame: v = R_z(alpha) R_y(beta) s(theta*, phi*)
+    const double sv[3] = {std::sin(th) * std::cos(phv), std::sin(th) * std::sin(phv), std::cos(th)};
+    const double cb = std::cos(beta[i]), sb = std::sin(beta[i]), ca = std::cos(alpha[i]), sa = std::sin(alpha[i]);
+    const double y0 = cb * sv[0] + sb * sv[2], y1 = sv[1], y2 = -sb * sv[0] + cb * sv[2];
+    const double v0 = ca * y0 - sa * y1, v1 = sa * y0 + ca * y1, v2 = y2;
+    pairs[i].theta_v = std::acos(std::max(-1.0, std::min(1.0, v2)));
+    pairs[i].phi_v = std::atan2(v1, v0);
+    for (int l = 1; l <= L; ++l)
+      for (int c = 0; c < 3; ++c) pts[3 * ((size_t)i * L + (l - 1)) + c] = xs[c] + g->hdrop[j] * std::sqrt((double)l) * e[c];
+  }
+  BIE_TRY(g->npairs.upload(pairs));
+  BIE_TRY(g->npts.upload(pts));
+  BIE_TRY(g->ngrid_l.alloc((size_t)npair * L));
+  {
+    DevBuf<double> bnd, hh;
+    DevBuf<long long> uoff, un;
+    BIE_TRY(bnd.upload(g->bound));
+    BIE_TRY(hh.upload(g->hdrop));
+    BIE_TRY(uoff.upload(g->up_off));
+    BIE_TRY(un.upload(g->up_n));
+    BIE_TRY(launch_near_checkgrid(g->npairs.ptr, npair, L, g->npts.ptr, g->centre_d.ptr, bnd.ptr, hh.ptr,
+                                  ctx->cfg.a_tilde, g->rec_up.ptr, uoff.ptr, un.ptr, g->ngrid_l.ptr, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  BIE_TRY(g->ncv.alloc(3 * (size_t)npair * L));
+  BIE_TRY(g->selfvals.alloc(3 * g->ntarget));
+  BIE_TRY(g->selfcoef.alloc(g->ncoef_total));
+  BIE_TRY(g->hdrop_d.upload(g->hdrop));
+  BIE_TRY(g->coef_off_d.upload(g->coef_off));
+  BIE_TRY(g->pdeg_d.upload(pd));
+  long long npairs_eval = 0;
+  std::vector<int> hgrid((size_t)npair * L);
+  BIE_CUDA_TRY(cudaMemcpy(hgrid.data(), g->ngrid_l.ptr, hgrid.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < npair; ++i)
+    for (int l = 0; l < L; ++l) {
+      const int j = pairs[i].src_drop;
+      npairs_eval += hgrid[(size_t)i * L + l] ? g->up_n[j] : ngrid(g->p[j]);
+    }
+  g->info.near_pairs = npairs_eval;
+  return BIE_OK;
+}
+
+// Self-interaction values of every drop as SH coefficients (weighted units): the on-surface
+// values of the near-singular interpolation come from these expansions.
+static int near_snapshot(bie_geom* g, cudaStream_t s) {
+  BIE_CUDA_TRY(cudaMemcpyAsync(g->selfvals.ptr, g->vals.ptr, 3 * g->ntarget * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
+  for (auto& G : g->groups) BIE_TRY(analyze_group(g->ctx, g, *G, g->selfvals.ptr, g->selfcoef.ptr, s));
+  return BIE_OK;
+}
+
+static int near_apply(bie_geom* g, int kind, bool raw, int prec, const double* dens, cudaStream_t s) {
   if (g->near.empty()) return BIE_OK;
-  set_error("near-singular targets present but the near-singular step is not available in this build");
-  return BIE_ENOTSUP;
+  bie_ctx* ctx = g->ctx;
+  const int npair = (int)g->near.size(), L = ctx->cfg.n_interp;
+  const double* wts = kind == 0 ? (raw ? g->wSr_all.ptr : g->wS_all.ptr) : (raw ? g->wDr_all.ptr : g->wD_all.ptr);
+  // The check-point values are always summed in FP64: the interpolation through (0, h sqrt(l)),
+  // l = 1..8, amplifies their errors by its Lebesgue constant (about 1.9e3 on [0, h]).
+  if (prec != BIE_FP64) {
+    BIE_TRY(g->sQ64.alloc(3 * g->ntarget));
+    BIE_TRY(g->uQ64.alloc(3 * g->nup_total));
+    BIE_TRY(source_densities<double>(g, dens, g->sQ64.ptr, g->uQ64.ptr, s));
+  }
+  Phase ph(ctx, "near", s);
+  BIE_TRY(launch_near_checks<double>(kind, g->npairs.ptr, npair, L, g->npts.ptr, g->ngrid_l.ptr, g->centre_d.ptr,
+                                     g->toff.ptr, g->ngd.ptr, g->up_off_d.ptr, g->up_n_d.ptr, g->sX64.ptr, g->sN64.ptr,
+                                     g->sQ64.ptr, g->ntarget, g->uX64.ptr, g->uN64.ptr, g->uQ64.ptr, g->nup_total,
+                                     wts, g->ncv.ptr, s));
+  return launch_near_interp(g->npairs.ptr, g->ntbeg.ptr, g->nnear_tgt, L, kind, g->selfcoef.ptr, dens,
+                            g->coef_off_d.ptr, g->pdeg_d.ptr, g->hdrop_d.ptr, wts, g->ncv.ptr, g->tdrop.ptr,
+                            g->tgt_loc.ptr, g->val_off_all.ptr, g->ngd.ptr, g->vals.ptr, s);
 }
 
 template <typename R>

@@ -1,0 +1,34 @@
+// Near-singular (Omega_2) step of Sec. 2.3: records and launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace bie {
+
+// One (target, source drop) pair of the nearest region, with its closest point.
+struct NearPair {
+  long long target;  // global target index
+  int src_drop;
+  int pad;
+  double d0;         // |x0 - x*|
+  double theta_v;    // parameters of x* in the source drop's own parametrisation
+  double phi_v;
+};
+
+int launch_near_seed(const NearPair* pairs, int npair, const double* rec_std, const long long* toff, const int* ngd,
+                     const long long* tgt_loc, const int* tdrop, int* seed, cudaStream_t s);
+int launch_near_newton(const NearPair* pairs, int npair, const double* xr, const int* pdeg, const long long* xr_off,
+                       const double* x0, double* result, cudaStream_t s);
+int launch_near_checkgrid(const NearPair* pairs, int npair, int L, const double* pts, const double* centre,
+                          const double* bound, const double* h, double a_tilde, const double* rec_up,
+                          const long long* up_off, const long long* up_n, int* grid, cudaStream_t s);
+template <typename R>
+int launch_near_checks(int kind, const NearPair* pairs, int npair, int L, const double* pts, const int* grid,
+                       const double* centre, const long long* toff, const int* ngd, const long long* up_off,
+                       const long long* up_n, const R* Xs, const R* Ns, const R* Qs, long long nstd, const R* Xu,
+                       const R* Nu, const R* Qu, long long nup, const double* wts, double* cv, cudaStream_t s);
+int launch_near_interp(const NearPair* pairs, const int* tbeg, int ntgt, int L, int kind, const double* selfcoef,
+                       const double* dens, const long long* coef_off, const int* pdeg, const double* hdrop,
+                       const double* wts, const double* cv, const int* tdrop, const long long* tgt_loc,
+                       const long long* val_off, const int* ngd, double* vals, cudaStream_t s);
+
+}  // namespace bie
