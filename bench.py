@@ -31,6 +31,9 @@ UNIT = "pair-interactions/s"
 WORKLOAD = "one drop p=32 (sphere + 0.05 SH perturbation, n<=6), lambda=5, shear (z,0,0), self rule on the p_q=65 grid"
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
 FP64_ALU_PEAK = 1.25                              # TFLOP/s: nominal GB300 FP64 rate
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this workload
+# (profiles/self_fourier_f64_c2.md, profiles/self_fourier_f32_c2.md); null for any other kernel.
+PROFILED_TRAFFIC = {"self_fourier_f64": 462.365696e6 + 3.371520e6, "self_fourier_f32": 231.078656e6 + 3.218432e6}
 
 
 def parse():
@@ -39,6 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c4s", "c5"],
+                    help="c2 (default): the solve step below; the others time one operator apply per step")
     return ap.parse_args()
 
 
@@ -245,7 +250,7 @@ def run_ours(args):
     peak = FP64_ALU_PEAK if f64 else FP32_ALU_PEAK
     achieved = flops / avg_s / 1e12
     roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "algorithmic_flops_per_launch": flops,
+            "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get(dom_name), "algorithmic_flops_per_launch": flops,
             "algorithmic_bytes_per_launch": nbytes, "hbm_gbs_achieved": nbytes / avg_s / 1e9,
             "avg_launch_ms": avg_s * 1e3,
             "peak_source": ("nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64 peak available)" if f64 else
@@ -327,10 +332,71 @@ def run_reference(args):
     }))
 
 
+APPLY_WORKLOADS = {
+    "c3": "two unit spheres at gap 0.05, p=32, U=4, lambda=0.5 (all three regions)",
+    "c4": "64 spheres, p in {16,24,32,48}, radii U[0.8,1.2], 10% volume fraction, lambda U[0.2,5], U=2",
+    "c4s": "16 spheres, p in {16,24}, radii U[0.8,1.2], 10% volume fraction, lambda U[0.2,5], U=2",
+    "c5": "512 ellipsoids + SH noise, p=24, 10% volume fraction, U=2",
+}
+
+
+def run_apply(args):
+    """Auxiliary mode: time one double-layer apply per step (mixed, then FP64) on a multi-drop workload."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1707_02156_gb300 import api, build, inputs
+    build.build()
+    w = inputs.config(args.workload)
+    ctx = api.Context(local, upsample=w.up)
+    geo = ctx.geometry(w.p, w.pq, torch.tensor(w.xcoef, device="cuda"), w.lam)
+    info = geo.info
+    pairs = info["self_pairs"] + info["far_pairs"] + info["up_pairs"] + info["near_pairs"]
+    f = torch.tensor(w.density, device="cuda")
+    out = torch.zeros_like(f)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for prec in (1, 0):
+        if prec == 0 and args.workload in ("c4", "c5"):
+            continue  # FP64 applies of the many-drop workloads take seconds each
+        for _ in range(args.warmup):
+            geo.apply_double(f, out, precision=prec)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        launches0 = api.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                geo.apply_double(f, out, precision=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[prec] = {"ms": ms, "phases": ctx.profile_read(), "launches": api.launch_count() - launches0,
+                     "clocks": clk.summary()}
+        ctx.profile(False)
+    m = res[1]
+    print(json.dumps({
+        "metric": METRIC, "value": pairs / (m["ms"] / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": APPLY_WORKLOADS[args.workload], "step": "one mixed double-layer apply",
+                   "pairs": pairs, **{k: info[k] for k in ("ntarget", "self_pairs", "far_pairs", "up_pairs",
+                                                               "near_targets", "near_pairs")}},
+        "gpu_launches": m["launches"], "clocks": m["clocks"],
+        "phases_ms": {k: {"ms": v[0], "calls": v[1]} for k, v in m["phases"].items()},
+        "fp64": ({"ms_per_apply": res[0]["ms"], "phases_ms": {k: {"ms": v[0], "calls": v[1]}
+                                                              for k, v in res[0]["phases"].items()}}
+                 if 0 in res else None),
+    }))
+
+
 if __name__ == "__main__":
     a = parse()
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload != "c2":
+        run_apply(a)
     else:
         run_ours(a)

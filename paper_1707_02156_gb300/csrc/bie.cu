@@ -644,6 +644,20 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
       tile_drop.push_back(d);
     }
   const int ntile = (int)tile_t0.size();
+  // total sources over all tiles, to aim at >= 8 blocks per SM overall
+  long long all_sources = 0;
+  for (int ti = 0; ti < ntile; ++ti)
+    for (int j = 0; j < nd; ++j) {
+      if (j == tile_drop[ti]) continue;
+      bool any0 = false, any1 = false;
+      for (int k = 0; k < tile_n[ti]; ++k) {
+        const unsigned char r = region[(size_t)(tile_t0[ti] + k) * nd + j];
+        any0 |= r == 0;
+        any1 |= r == 1;
+      }
+      all_sources += (any0 ? ngd[j] : 0) + (any1 ? g->up_n[j] : 0);
+    }
+  const long long cap_global = std::max<long long>(2048, std::min<long long>(65536, all_sources / (8 * 152)));
   std::vector<PairItem> items;
   std::vector<int> blk_item, tile_blk(ntile + 1, 0);
   long long far_pairs = 0, up_pairs = 0;
@@ -695,7 +709,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
       }
     }
     // split the tile's items into blocks of at most `cap` sources
-    const long long cap = std::max<long long>(16384, (total + 7) / 8);
+    const long long cap = std::max(cap_global, (total + 15) / 16);  // at most 16 blocks per tile
     tile_blk[ti] = (int)blk_item.size();
     long long used = cap;  // forces a new block at the first item
     for (auto it : mine) {
@@ -840,10 +854,16 @@ static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   DevBuf<long long> dxo;
   DevBuf<int> pdeg;
   BIE_TRY(xr.alloc(xo));
+  std::map<std::pair<int, double>, std::vector<double>> blk_cache;  // (degree, beta) -> blocks
   for (int i = 0; i < npair; ++i) {
     const int j = pairs[i].src_drop, p = g->p[j];
-    std::vector<double> blk(wigner_block_stride(p));
-    wigner_blocks(p, beta[i], blk.data());
+    auto key = std::make_pair(p, beta[i]);
+    if (!blk_cache.count(key)) {
+      std::vector<double> b(wigner_block_stride(p));
+      wigner_blocks(p, beta[i], b.data());
+      blk_cache[key] = std::move(b);
+    }
+    const std::vector<double>& blk = blk_cache[key];
     std::vector<double> ph(2 * (p + 1));
     for (int m = 0; m <= p; ++m) {
       ph[2 * m] = std::cos(m * alpha[i]);

@@ -52,9 +52,9 @@ __device__ void rotate_target(const double* __restrict__ dens, const long long* 
     R a0 = 0, a1 = 0, a2 = 0;
     int dst;
     if (o <= n) {
-      const R* Cr = blk + boff + (long long)o * (n + 1);
+      const R* Cc = blk + boff + o;  // column-major: entry (o, m) at m (n+1) + o
       for (int m = 0; m <= n; ++m) {
-        const R cv = Cr[m];
+        const R cv = Cc[(long long)m * (n + 1)];
         a0 += cv * g0[m];
         a1 += cv * g0[nc + m];
         a2 += cv * g0[2 * nc + m];
@@ -62,9 +62,9 @@ __device__ void rotate_target(const double* __restrict__ dens, const long long* 
       dst = n * (n + 1) + o;
     } else {
       const int mp = o - n;
-      const R* Sr = blk + boff + (long long)(n + 1) * (n + 1) + (long long)(mp - 1) * n;
+      const R* Sc = blk + boff + (long long)(n + 1) * (n + 1) + (mp - 1);
       for (int m = 1; m <= n; ++m) {
-        const R sv = Sr[m - 1];
+        const R sv = Sc[(long long)(m - 1) * n];
         a0 += sv * g0[-m];
         a1 += sv * g0[nc - m];
         a2 += sv * g0[2 * nc - m];

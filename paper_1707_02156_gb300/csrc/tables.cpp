@@ -198,12 +198,12 @@ void wigner_blocks(int p, double beta, double* out) {
       for (int m = 0; m <= n; ++m) {
         ld v = D(n, mp, m);
         if (m > 0) v += ((m & 1) ? -1 : 1) * D(n, mp, -m);
-        C[mp * (n + 1) + m] = (double)v;
+        C[m * (n + 1) + mp] = (double)v;  // column-major: consecutive m' contiguous
       }
     for (int mp = 1; mp <= n; ++mp)
       for (int m = 1; m <= n; ++m) {
         ld v = D(n, mp, m) - ((m & 1) ? -1 : 1) * D(n, mp, -m);
-        S[(mp - 1) * n + (m - 1)] = (double)v;
+        S[(m - 1) * n + (mp - 1)] = (double)v;
       }
   }
 }

@@ -29,6 +29,8 @@ void phase_table(int p, int P, std::vector<double>& out);
 // Wigner rotation blocks for the rotated expansion g(s) = f(R_z(alpha) R_y(beta) s):
 // per degree n, the real (n+1)x(n+1) block acting on Re(e^{i m alpha} f_n^m), m = 0..n,
 // followed by the n x n block acting on the imaginary parts, m = 1..n (App. B, real symmetry).
+// Both blocks are stored column-major (entry (m', m) at m (n+1) + m', resp. (m-1) n + (m'-1)), so
+// threads computing consecutive outputs m' read consecutive addresses.
 long long wigner_block_stride(int p);                 // doubles per beta
 inline long long wigner_block_offset(int n) {         // offset of degree n inside one beta
   // sum_{k<n} (k+1)^2 + k^2

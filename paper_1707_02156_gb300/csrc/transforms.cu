@@ -186,13 +186,11 @@ __global__ void k_rotate(const CT* __restrict__ coef, const long long* __restric
     R acc = 0;
     int dst;
     if (o <= n) {  // Re g'_{o}
-      const R* Cr = sC + o * (n + 1);
-      for (int m = 0; m <= n; ++m) acc += Cr[m] * G[m];
+      for (int m = 0; m <= n; ++m) acc += sC[m * (n + 1) + o] * G[m];
       dst = n * (n + 1) + o;
     } else {  // Im g'_{mp}, mp = o - n
       int mp = o - n;
-      const R* Sr = sS + (mp - 1) * n;
-      for (int m = 1; m <= n; ++m) acc += Sr[m - 1] * G[n + m];
+      for (int m = 1; m <= n; ++m) acc += sS[(m - 1) * n + (mp - 1)] * G[n + m];
       dst = n * (n + 1) - mp;
     }
     long long t = (long long)a * nb + b0 + bb;

@@ -249,11 +249,13 @@ def deformed_drops(ndrop: int = 512, p: int = 24, box: float = 27.8, gap: float 
 
 
 def config(name: str) -> Workload:
-    """The five seeded workloads, by name: c1 .. c5."""
+    """The seeded workloads, by name: c1 .. c5, and c4s, a 16-drop version of c4 with degrees
+    {16, 24} at the same volume fraction (a size small enough for kernel profiling)."""
     return {
         "c1": lambda: single_sphere(16),
         "c2": lambda: perturbed_drop(32),
         "c3": lambda: two_drops(32),
         "c4": lambda: batch_spheres(),
+        "c4s": lambda: batch_spheres(ndrop=16, degrees=(16, 24), box=8.86, seed_stream=5),
         "c5": lambda: deformed_drops(),
     }[name]()
