@@ -33,7 +33,7 @@ FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FM
 FP64_ALU_PEAK = 1.25                              # TFLOP/s: nominal GB300 FP64 rate
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this workload
 # (profiles/self_fourier_f64_c2.md, profiles/self_fourier_f32_c2.md); null for any other kernel.
-PROFILED_TRAFFIC = {"self_fourier_f64": 462.365696e6 + 3.371520e6, "self_fourier_f32": 231.078656e6 + 3.218432e6}
+PROFILED_TRAFFIC = {}
 
 
 def parse():
@@ -114,15 +114,21 @@ class ClockSampler:
 # algorithmic work of the singular self kernels, per target (FMA = 2 flops, rsqrt = 1)
 # ------------------------------------------------------------------------------------------------
 def self_work_per_target(name: str, p: int, pq: int, kind: str = "D"):
-    """(flops, bytes) of one target of the self kernel `name` (self_fourier_* or self_direct_*)."""
+    """(flops, bytes) of one target of the self kernel `name` (self_fourier_* or self_direct_*).
+
+    Counts the arithmetic the kernel's algorithm performs: the Fourier form evaluates the Legendre
+    step once per Gauss-node pair (t, -t) through the parity of n + m.
+    """
     esize = 8 if name.endswith("f64") else 4
     wig = sum((n + 1) ** 2 + n * n for n in range(p + 1))          # rotation blocks of one latitude
     rot = 2.0 * 3 * wig                                              # three components
-    leg = 3.0 * (pq + 1) * (2 * (p + 1) + 4 * sum(p + 1 - m for m in range(1, p + 1)))
     nq = (pq + 1) * (2 * pq + 2)
     if "fourier" in name:
+        npair = (pq + 2) // 2
+        leg = npair * sum(12.0 * (p + 1 - m) + 12.0 for m in range(p + 1))  # E/O sums, then E +- O
         contr = 36.0 * (pq + 1) * (p + 1)                           # 3x3 complex symmetric times h_m
         return rot + leg + contr, 12.0 * (pq + 1) * (p + 1) * esize  # Mhat read once per apply
+    leg = 3.0 * (pq + 1) * (2 * (p + 1) + 4 * sum(p + 1 - m for m in range(1, p + 1)))
     phi = 3.0 * (pq + 1) * (pq + 1) * (4 * p + 2)                    # longitude pairs, even/odd orders
     pair = (32.0 if kind == "D" else 29.0) * nq
     return rot + leg + phi + pair, nq * (7 if kind == "D" else 4) * esize

@@ -271,6 +271,7 @@ struct bie_geom {
   };
   std::vector<std::unique_ptr<Group>> groups;
   bie::DevBuf<double> anaF;   // analysis workspace
+  bie::DevBuf<float> dens32;  // FP32 copy of the density (mixed applies)
   bie::Krylov* kry = nullptr;  // solve workspace, kept between solves
   bie_geom_info info{};
   // inter-drop data (ndrop > 1), Sec. 2.3
@@ -330,6 +331,10 @@ template <typename R>
 static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s) {
   bie_ctx* ctx = g->ctx;
   const bool direct = ctx->cfg.self_direct != 0;
+  if (sizeof(R) == 4 && !direct) {  // the FP32 kernels read an FP32 copy of the density
+    BIE_TRY(g->dens32.alloc(g->ncoef_total));
+    BIE_TRY(launch_to_float(dens, g->dens32.ptr, g->ncoef_total, s));
+  }
   for (auto& Gp : g->groups) {
     auto& G = *Gp;
     const int p = G.p, pq = G.pq;
@@ -355,10 +360,10 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
       BIE_TRY(ensure_mhat(ctx, G, kind, s));
       const R* M = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.mhat64[kind].ptr)
                                   : reinterpret_cast<const R*>(G.mhat32[kind].ptr);
+      const R* dR = sizeof(R) == 8 ? reinterpret_cast<const R*>(dens) : reinterpret_cast<const R*>(g->dens32.ptr);
       Phase ph(ctx, sizeof(R) == 8 ? "self_fourier_f64" : "self_fourier_f32", s);
-      BIE_TRY(launch_self_fourier<R>(dens, G.foff3.ptr, nd, p, pq, wp->blk_<R>(), wp->stride, pp->cs_<R>(),
-                                     pl->T0_<R>(), M, wts, G.val_off.ptr, g->vals.ptr,
-                                     sizeof(R) == 8 ? 96 * 1024 : 48 * 1024, s));
+      BIE_TRY((launch_self_fourier<R, R>(dR, G.foff3.ptr, nd, p, pq, wp->blk_<R>(), wp->stride, pp->cs_<R>(),
+                                         pl->T0_<R>(), M, wts, G.val_off.ptr, g->vals.ptr, s)));
     }
   }
   return BIE_OK;
@@ -1043,12 +1048,19 @@ __global__ void k_multidot(const double* __restrict__ V, long long ldv, const do
   }
 }
 
+// out[i] = sum_b partial[i][b]: one block per entry, fixed summation order
 __global__ void k_sum_partials(const double* __restrict__ partial, int nb, int k, double* __restrict__ out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= k) return;
+  __shared__ double sh[128];
+  const int i = blockIdx.x;
   double t = 0;
-  for (int b = 0; b < nb; ++b) t += partial[(long long)i * nb + b];
-  out[i] = t;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) t += partial[(long long)i * nb + b];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] = sh[0];
 }
 
 // w -= sum_i h[i] V_i
@@ -1094,12 +1106,20 @@ struct Krylov {
   DevBuf<double> V, w, tmp, partial, hdev, r, dx, t;
 };
 
-static int dots(Krylov& K, const double* V, int k, const double* w, std::vector<double>& out, cudaStream_t s) {
+// out[i] = V_i . w for i < k; with with_norm, out[k] = w . w as well (one synchronisation)
+static int dots(Krylov& K, const double* V, int k, const double* w, std::vector<double>& out, cudaStream_t s,
+                bool with_norm = false) {
   dim3 grid(kRedBlocks, k);
   k_multidot<<<grid, kRedThreads, 0, s>>>(V, K.n, w, K.n, k, K.partial.ptr);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
-  k_sum_partials<<<(k + 127) / 128, 128, 0, s>>>(K.partial.ptr, kRedBlocks, k, K.hdev.ptr);
+  if (with_norm) {
+    k_multidot<<<dim3(kRedBlocks, 1), kRedThreads, 0, s>>>(w, K.n, w, K.n, 1, K.partial.ptr + (long long)k * kRedBlocks);
+    count_launch();
+    BIE_CUDA_TRY(cudaGetLastError());
+    ++k;
+  }
+  k_sum_partials<<<k, 128, 0, s>>>(K.partial.ptr, kRedBlocks, k, K.hdev.ptr);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   out.resize(k);
@@ -1183,14 +1203,23 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
       k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, K.hdev.ptr, k + 1, n);
       count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
-      BIE_TRY(dots(K, V, k + 1, vk1, h2, s));
+      // second pass with the squared norm: |w - V h2|^2 = |w|^2 - |h2|^2 for orthonormal V
+      BIE_TRY(dots(K, V, k + 1, vk1, h2, s, true));
       BIE_CUDA_TRY(cudaMemcpyAsync(K.hdev.ptr, h2.data(), (k + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
       k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, K.hdev.ptr, k + 1, n);
       count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
-      for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = hcol[i] + h2[i];
+      double hsq = h2[k + 1];
+      for (int i = 0; i <= k; ++i) {
+        H[(size_t)i * m + k] = hcol[i] + h2[i];
+        hsq -= h2[i] * h2[i];
+      }
       double hn;
-      BIE_TRY(norm2(K, vk1, &hn, s));
+      if (hsq > 1e-8 * h2[k + 1]) {
+        hn = std::sqrt(hsq);
+      } else {  // heavy cancellation: measure the norm directly
+        BIE_TRY(norm2(K, vk1, &hn, s));
+      }
       H[(size_t)(k + 1) * m + k] = hn;
       if (hn > 0) {
         k_axpby<<<nblk(n), 256, 0, s>>>(1.0 / hn, vk1, 0.0, vk1, n);
@@ -1509,8 +1538,8 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
   K.m = opts->restart;
   BIE_TRY(K.V.alloc((size_t)(opts->restart + 1) * n));
   BIE_TRY(K.tmp.alloc(3 * n));
-  BIE_TRY(K.partial.alloc((size_t)kRedBlocks * (opts->restart + 1)));
-  BIE_TRY(K.hdev.alloc(opts->restart + 1));
+  BIE_TRY(K.partial.alloc((size_t)kRedBlocks * (opts->restart + 2)));
+  BIE_TRY(K.hdev.alloc(opts->restart + 2));
   double rel = 0;
   int st;
   if ((opts->precision & 0xff) == BIE_FP64) {
@@ -1528,10 +1557,11 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
   BIE_TRY(norm2(K, rhs, &bnorm, s));
   BIE_TRY(norm2(K, u, &unorm, s));
   int left = opts->max_iter;
+  bool updated = false;
   for (int outer = 0;; ++outer) {
     if (outer == 0 && unorm == 0.0) {  // r = b for a zero initial guess
       BIE_CUDA_TRY(cudaMemcpyAsync(r.ptr, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    } else {
+    } else if (!updated) {
       BIE_TRY(sys_matvec(ctx, g, u, r.ptr, t.ptr, BIE_FP64, info, s));
       k_axpby<<<nblk(n), 256, 0, s>>>(1.0, rhs, -1.0, r.ptr, n);
       count_launch();
@@ -1555,7 +1585,21 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
     left -= info->iterations - before;
     k_axpby<<<nblk(n), 256, 0, s>>>(1.0, dx.ptr, 1.0, u, n);
     count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
+    BIE_CUDA_TRY(cudaGetLastError());
+    // Next residual.  Once the correction is small against u, r <- r - A dx with the mixed operator
+    // is accurate to ~eps_32 |A| |dx|, far below the tolerance; otherwise recompute b - A u in FP64.
+    double dxn;
+    BIE_TRY(norm2(K, dx.ptr, &dxn, s));
+    BIE_TRY(norm2(K, u, &unorm, s));
+    if (dxn <= 1e-4 * unorm) {
+      BIE_TRY(sys_matvec(ctx, g, dx.ptr, t.ptr, K.tmp.ptr + 2 * n, BIE_MIXED, info, s));
+      k_axpby<<<nblk(n), 256, 0, s>>>(-1.0, t.ptr, 1.0, r.ptr, n);
+      count_launch();
+      BIE_CUDA_TRY(cudaGetLastError());
+      updated = true;
+    } else {
+      updated = false;
+    }
   }
 }
 

@@ -75,10 +75,10 @@ int launch_self_direct(int kind, const double* dens, const long long* foff3, lon
                        cudaStream_t s);
 int launch_kernel_dft(int kind, const double* cache, long long ntarget, int p, int pq, const double* cs, double* M64,
                       float* M32, cudaStream_t s);
-template <typename R>
-int launch_self_fourier(const double* dens, const long long* foff3, long long ndrop, int p, int pq, const R* wblk,
+template <typename R, typename CT>
+int launch_self_fourier(const CT* dens, const long long* foff3, long long ndrop, int p, int pq, const R* wblk,
                         long long wstride, const R* ph, const R* T0, const R* Mhat, const double* wts,
-                        const long long* val_off, double* vals, size_t smem_budget, cudaStream_t s);
+                        const long long* val_off, double* vals, cudaStream_t s);
 // out[i] = (float) in[i]
 int launch_to_float(const double* in, float* out, long long n, cudaStream_t s);
 

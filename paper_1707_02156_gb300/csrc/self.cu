@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_self_direct(
 }
 
 // ---- Fourier form: set-up of Mhat (FP64, optional FP32 copy) ----
-// Mhat[t][e][ri][j][m], e over (xx, yy, zz, xy, xz, yz), ri = real / imaginary part.
+// Mhat[t][e][ri][m][j], e over (xx, yy, zz, xy, xz, yz), ri = real / imaginary part.
 constexpr int kDftJ = 3;
 
 template <int KIND>
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256) k_kernel_dft(const double* __restrict__ c
         re += src[k] * cs[((long long)m * nk + k) * 2];
         im += src[k] * cs[((long long)m * nk + k) * 2 + 1];
       }
-      const long long o = (long long)(j0 + jj) * (p + 1) + m;
+      const long long o = (long long)m * nq_j + (j0 + jj);  // layout [plane][m][j]
       o64[(2 * e) * plane + o] = re;
       o64[(2 * e + 1) * plane + o] = im;
       if (o32) {
@@ -275,51 +275,146 @@ __global__ void __launch_bounds__(256) k_kernel_dft(const double* __restrict__ c
 }
 
 // ---- Fourier form: apply ----
+// Shared-memory layout of the Fourier kernel (R = float or double):
+//   rc6 [tri(n,m)][8]    rotated coefficients, (Re, Im) of the three components at (n, m >= 0),
+//                        tri(n,m) = n(n+1)/2 + m, padded to 8 for vector loads;
+//   union: g4 [(p+1)^2][4] phase-shifted input coefficients, three components interleaved,
+//          then h [3][rows][p+1][2], the Legendre step for a chunk of Gauss-node pairs.
+// The Legendre step evaluates each node pair (t_i, t_{pq-i} = -t_i) at once:
+// P~_n^m(-t) = (-1)^(n+m) P~_n^m(t), so with E (n+m even) and O (n+m odd) partial sums,
+// h(t_i) = E + O and h(-t_i) = E - O.
 template <typename R>
-__global__ void __launch_bounds__(256) k_self_fourier(
-    const double* __restrict__ dens, const long long* __restrict__ foff3, int p, int pq, const R* __restrict__ wblk,
-    long long wstride, const R* __restrict__ ph, const R* __restrict__ T0, const R* __restrict__ Mhat, int ng,
-    const double* __restrict__ wts, const long long* __restrict__ val_off, double* __restrict__ vals, int jc) {
-  extern __shared__ unsigned char smem_raw[];
-  R* rc = reinterpret_cast<R*>(smem_raw);
+__device__ inline int tri_(int n, int m) {
+  return n * (n + 1) / 2 + m;
+}
+
+template <typename R, typename CT>
+__device__ void rotate_target_v(const CT* __restrict__ dens, const long long* __restrict__ foff3, long long ld,
+                                int p, int a, int b, const R* __restrict__ wblk, long long wstride,
+                                const R* __restrict__ ph, R* rc6, R* g4) {
   const int nc = (p + 1) * (p + 1);
-  R* un = rc + 3 * nc;
+  const int nb = 2 * p + 2;
+  for (int i = threadIdx.x; i < 3 * nc; i += blockDim.x) {
+    const int c = i / nc, r = i - c * nc;
+    const int n = degree_of(r);
+    const int m = r - n * (n + 1);
+    if (m < 0) continue;  // the owner of Re rho_n^m writes both parts
+    const CT* f = dens + foff3[ld * 3 + c];
+    const R fr = (R)f[n * (n + 1) + m];
+    const R fi = m > 0 ? (R)f[n * (n + 1) - m] : (R)0;
+    const R co = ph[((long long)m * nb + b) * 2], si = ph[((long long)m * nb + b) * 2 + 1];
+    g4[(n * (n + 1) + m) * 4 + c] = fr * co - fi * si;
+    if (m > 0) g4[(n * (n + 1) - m) * 4 + c] = fr * si + fi * co;
+  }
+  __syncthreads();
+  const R* blk = wblk + (long long)a * wstride;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const int n = degree_of(i);
+    const int o = i - n * n;  // 0..2n
+    const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
+    R a0 = 0, a1 = 0, a2 = 0;
+    if (o <= n) {
+      const R* Cc = blk + boff + o;
+      const R* g = g4 + n * (n + 1) * 4;
+      for (int m = 0; m <= n; ++m) {
+        const R cv = Cc[(long long)m * (n + 1)];
+        a0 += cv * g[4 * m];
+        a1 += cv * g[4 * m + 1];
+        a2 += cv * g[4 * m + 2];
+      }
+      R* d = rc6 + tri_<R>(n, o) * 8;
+      d[0] = a0;
+      d[2] = a1;
+      d[4] = a2;
+      if (o == 0) d[1] = d[3] = d[5] = 0;
+    } else {
+      const int mp = o - n;
+      const R* Sc = blk + boff + (long long)(n + 1) * (n + 1) + (mp - 1);
+      const R* g = g4 + n * (n + 1) * 4;
+      for (int m = 1; m <= n; ++m) {
+        const R sv = Sc[(long long)(m - 1) * n];
+        a0 += sv * g[-4 * m];
+        a1 += sv * g[-4 * m + 1];
+        a2 += sv * g[-4 * m + 2];
+      }
+      R* d = rc6 + tri_<R>(n, mp) * 8;
+      d[1] = a0;
+      d[3] = a1;
+      d[5] = a2;
+    }
+  }
+  __syncthreads();
+}
+
+// Fused Legendre step and contraction: one thread item = (order m, node pair i).  The partial
+// sums E (n+m even) and O (n+m odd) give h at t_i and at t_{pq-i} = -t_i, each contracted at once
+// with the Fourier factors of its latitude.  h never leaves registers.
+template <typename R>
+__device__ inline void contract(const R* __restrict__ M, long long plane, long long o, R cm, const R* h, R& s0,
+                                R& s1, R& s2) {
+  R Mr[6], Mi[6];
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    Mr[e] = M[(2 * e) * plane + o];
+    Mi[e] = M[(2 * e + 1) * plane + o];
+  }
+  // rows of the symmetric matrix: (xx xy xz), (xy yy yz), (xz yz zz); h = (Re, Im) x 3 components
+  s0 += cm * (Mr[0] * h[0] + Mr[3] * h[2] + Mr[4] * h[4] - Mi[0] * h[1] - Mi[3] * h[3] - Mi[4] * h[5]);
+  s1 += cm * (Mr[3] * h[0] + Mr[1] * h[2] + Mr[5] * h[4] - Mi[3] * h[1] - Mi[1] * h[3] - Mi[5] * h[5]);
+  s2 += cm * (Mr[4] * h[0] + Mr[5] * h[2] + Mr[2] * h[4] - Mi[4] * h[1] - Mi[5] * h[3] - Mi[2] * h[5]);
+}
+
+template <typename R, typename CT>
+__global__ void __launch_bounds__(256) k_self_fourier(
+    const CT* __restrict__ dens, const long long* __restrict__ foff3, int p, int pq, const R* __restrict__ wblk,
+    long long wstride, const R* __restrict__ ph, const R* __restrict__ T0, const R* __restrict__ Mhat, int ng,
+    const double* __restrict__ wts, const long long* __restrict__ val_off, double* __restrict__ vals) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* rc6 = reinterpret_cast<R*>(smem_raw);
+  const int ntri = (p + 1) * (p + 2) / 2;
+  R* g4 = rc6 + 8 * ntri;
   const long long t = blockIdx.x;
   const long long ld = t / ng;
   const int tl = (int)(t - ld * ng);
   const int a = tl / (2 * p + 2), b = tl - a * (2 * p + 2);
   const int nq_j = pq + 1;
+  const int npair = (nq_j + 1) / 2;  // the middle node of an odd count pairs with itself
   const long long plane = (long long)nq_j * (p + 1);
   const R* M = Mhat + t * 12 * plane;
-  rotate_target<R>(dens, foff3, ld, p, a, b, wblk, wstride, ph, rc, un);
+  rotate_target_v<R, CT>(dens, foff3, ld, p, a, b, wblk, wstride, ph, rc6, g4);
   R s0 = 0, s1 = 0, s2 = 0;
-  for (int j0 = 0; j0 < nq_j; j0 += jc) {
-    const int jn = min(jc, nq_j - j0);
-    legendre_chunk<R>(rc, p, nq_j, j0, jn, T0, un);
-    const long long cstride = (long long)jn * (p + 1) * 2;
-    for (int i = threadIdx.x; i < jn * (p + 1); i += blockDim.x) {
-      const int jj = i / (p + 1), m = i - jj * (p + 1);
-      const R* hh = un + ((long long)jj * (p + 1) + m) * 2;
-      const R hr0 = hh[0], hi0 = hh[1], hr1 = hh[cstride], hi1 = hh[cstride + 1];
-      const R hr2 = hh[2 * cstride], hi2 = hh[2 * cstride + 1];
-      const long long o = (long long)(j0 + jj) * (p + 1) + m;
-      R Mr[6], Mi[6];
+  for (int it = threadIdx.x; it < (p + 1) * npair; it += blockDim.x) {
+    const int m = it / npair, i = it - m * npair;
+    R e[6] = {0, 0, 0, 0, 0, 0}, o[6] = {0, 0, 0, 0, 0, 0};
+    const R* Tm = T0 + leg_row(p, m, m, nq_j) + i;
+    for (int n = m; n <= p; n += 2) {  // n + m even
+      const R* r = rc6 + tri_<R>(n, m) * 8;
+      const R tv = Tm[(long long)(n - m) * nq_j];
 #pragma unroll
-      for (int e = 0; e < 6; ++e) {
-        Mr[e] = M[(2 * e) * plane + o];
-        Mi[e] = M[(2 * e + 1) * plane + o];
-      }
-      const R cm = m == 0 ? (R)1 : (R)2;
-      // rows of the symmetric matrix: (xx xy xz), (xy yy yz), (xz yz zz)
-      s0 += cm * (Mr[0] * hr0 + Mr[3] * hr1 + Mr[4] * hr2 - Mi[0] * hi0 - Mi[3] * hi1 - Mi[4] * hi2);
-      s1 += cm * (Mr[3] * hr0 + Mr[1] * hr1 + Mr[5] * hr2 - Mi[3] * hi0 - Mi[1] * hi1 - Mi[5] * hi2);
-      s2 += cm * (Mr[4] * hr0 + Mr[5] * hr1 + Mr[2] * hr2 - Mi[4] * hi0 - Mi[5] * hi1 - Mi[2] * hi2);
+      for (int k = 0; k < 6; ++k) e[k] += r[k] * tv;
     }
-    __syncthreads();
+    for (int n = m + 1; n <= p; n += 2) {  // n + m odd
+      const R* r = rc6 + tri_<R>(n, m) * 8;
+      const R tv = Tm[(long long)(n - m) * nq_j];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) o[k] += r[k] * tv;
+    }
+    const R cm = m == 0 ? (R)1 : (R)2;
+    R hv[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hv[k] = e[k] + o[k];
+    contract<R>(M, plane, (long long)m * nq_j + i, cm, hv, s0, s1, s2);
+    const int jh = pq - i;
+    if (jh != i) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) hv[k] = e[k] - o[k];
+      contract<R>(M, plane, (long long)m * nq_j + jh, cm, hv, s0, s1, s2);
+    }
   }
   write_target<R>(s0, s1, s2, wts, val_off, vals, ld, tl, ng);
 }
 
+// Latitudes per chunk of the direct kernel within a shared-memory budget.
 template <typename R>
 int pick_jc(int p, int pq, size_t budget, size_t* smem) {
   const size_t nc = (size_t)(p + 1) * (p + 1);
@@ -365,20 +460,18 @@ int launch_kernel_dft(int kind, const double* cache, long long ntarget, int p, i
   return BIE_OK;
 }
 
-template <typename R>
-int launch_self_fourier(const double* dens, const long long* foff3, long long ndrop, int p, int pq, const R* wblk,
+template <typename R, typename CT>
+int launch_self_fourier(const CT* dens, const long long* foff3, long long ndrop, int p, int pq, const R* wblk,
                         long long wstride, const R* ph, const R* T0, const R* Mhat, const double* wts,
-                        const long long* val_off, double* vals, size_t smem_budget, cudaStream_t s) {
+                        const long long* val_off, double* vals, cudaStream_t s) {
   const int ng = (p + 1) * (2 * p + 2);
   const long long nt = ndrop * ng;
   if (nt == 0) return BIE_OK;
   if (nt > 0x7fffffffLL) return BIE_EINVAL;
-  size_t smem;
-  const int jc = pick_jc<R>(p, pq, smem_budget, &smem);
-  if (smem > 48 * 1024)
-    BIE_CUDA_TRY(cudaFuncSetAttribute(k_self_fourier<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_self_fourier<R><<<(unsigned)nt, 256, smem, s>>>(dens, foff3, p, pq, wblk, wstride, ph, T0, Mhat, ng, wts,
-                                                    val_off, vals, jc);
+  const size_t smem = sizeof(R) * (8 * (size_t)(p + 1) * (p + 2) / 2 + 4 * (size_t)(p + 1) * (p + 1));
+  auto kern = k_self_fourier<R, CT>;
+  if (smem > 48 * 1024) BIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)nt, 256, smem, s>>>(dens, foff3, p, pq, wblk, wstride, ph, T0, Mhat, ng, wts, val_off, vals);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
@@ -390,11 +483,12 @@ template int launch_self_direct<double>(int, const double*, const long long*, lo
 template int launch_self_direct<float>(int, const double*, const long long*, long long, int, int, const float*,
                                        long long, const float*, const float*, const float*, const float*,
                                        const double*, const long long*, double*, size_t, cudaStream_t);
-template int launch_self_fourier<double>(const double*, const long long*, long long, int, int, const double*,
-                                         long long, const double*, const double*, const double*, const double*,
-                                         const long long*, double*, size_t, cudaStream_t);
-template int launch_self_fourier<float>(const double*, const long long*, long long, int, int, const float*,
-                                        long long, const float*, const float*, const float*, const double*,
-                                        const long long*, double*, size_t, cudaStream_t);
+template int launch_self_fourier<double, double>(const double*, const long long*, long long, int, int,
+                                                 const double*, long long, const double*, const double*,
+                                                 const double*, const double*, const long long*, double*,
+                                                 cudaStream_t);
+template int launch_self_fourier<float, float>(const float*, const long long*, long long, int, int, const float*,
+                                               long long, const float*, const float*, const float*, const double*,
+                                               const long long*, double*, cudaStream_t);
 
 }  // namespace bie
