@@ -150,7 +150,9 @@ int bie_geometry_info(const bie_geom* geom, bie_geom_info* info);
 /* Interfacial force f = -2 sigma K n - grad_gamma sigma (Sec. 1, Table 2), computed on the grid of
  * degree 2p+1 and truncated to degree p (Sec. 1.3).  gammacoef: [drop][1][(p+1)^2] device surfactant
  * coefficients; sigma = 1 + E ln(1 - x_s Gamma) (Eq. langmuir) when x_s > 0, else 1 - E Gamma.
- * fcoef: [drop][3][(p+1)^2] device output. */
+ * K is the mean curvature (E N - 2 F M + G L)/(2 W^2) of Table 2 (whose curvature labels are swapped)
+ * with the outward normal, so K = -1/R on a sphere and f = 2 sigma/R n there.  Requires 0 <= x_s < 1.
+ * fcoef: [drop][3][(p+1)^2] device output.  Synchronous. */
 int bie_interfacial_force(bie_ctx* ctx, const bie_geom* geom, const double* gammacoef, double elasticity,
                           double x_s, double* fcoef, void* stream);
 

@@ -1476,9 +1476,46 @@ int bie_geometry_info(const bie_geom* g, bie_geom_info* info) {
   return BIE_OK;
 }
 
-int bie_interfacial_force(bie_ctx*, const bie_geom*, const double*, double, double, double*, void*) {
-  set_error("interfacial force not available in this build");
-  return BIE_ENOTSUP;
+int bie_interfacial_force(bie_ctx* ctx, const bie_geom* g, const double* gammacoef, double elasticity, double x_s,
+                          double* fcoef, void* stream) {
+  if (!ctx || !g || !gammacoef || !fcoef) return BIE_EINVAL;
+  if (x_s < 0.0 || x_s >= 1.0) {
+    set_error("surface coverage x_s must satisfy 0 <= x_s < 1");
+    return BIE_EINVAL;
+  }
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  Phase phz(ctx, "force", s);
+  long long go = 0;  // offset of drop d's Gamma coefficients (one scalar per drop)
+  for (int d = 0; d < g->ndrop; ++d) {
+    const int p = g->p[d], P = 2 * p + 1;  // nonlinear terms on the grid of degree 2p+1 (Sec. 1.3)
+    Plan* pl;
+    BIE_TRY(get_plan(ctx, p, P, &pl));
+    const long long N = ngrid(P), nc = ncoef(p);
+    DevBuf<double> tmp;
+    BIE_TRY(tmp.alloc(3 * (p + 1) * (size_t)(P + 1) * 2 + 18 * N + 3 * N + 3 * N + 3 * (p + 1) * (size_t)(P + 1) * 2));
+    double* H = tmp.ptr;
+    double* X = H + 3 * (p + 1) * (long long)(P + 1) * 2;  // [6][3][N]
+    double* Gm = X + 18 * N;                                // [3][N]
+    double* f = Gm + 3 * N;                                 // [3][N]
+    double* F = f + 3 * N;
+    const double* xc = g->xcoef.ptr + g->coef_off[d];
+    const double* T[6] = {pl->T0.ptr, pl->T1.ptr, pl->T0.ptr, pl->T2.ptr, pl->T1.ptr, pl->T0.ptr};
+    const int dphi[6] = {0, 0, 1, 0, 1, 2};
+    for (int k = 0; k < 6; ++k) {
+      BIE_TRY((launch_leg_synth<double, double>(xc, nullptr, nc, 3, p, T[k], P + 1, H, dphi[k], s)));
+      BIE_TRY((launch_phi_synth<double, double>(H, 3, p, P, pl->cs.ptr, X + k * 3 * N, nullptr, N, s)));
+    }
+    for (int k = 0; k < 3; ++k) {
+      BIE_TRY((launch_leg_synth<double, double>(gammacoef + go, nullptr, nc, 1, p, T[k], P + 1, H, dphi[k], s)));
+      BIE_TRY((launch_phi_synth<double, double>(H, 1, p, P, pl->cs.ptr, Gm + k * N, nullptr, N, s)));
+    }
+    BIE_TRY(launch_force(X, Gm, N, elasticity, x_s, f, s));
+    BIE_TRY(launch_analyze(f, nullptr, N, 3, P, p, pl->cs.ptr, pl->A.ptr, F, fcoef + g->coef_off[d], nullptr, nc, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));  // the temporaries are released per drop
+    go += nc;
+  }
+  return BIE_OK;
 }
 
 int bie_apply_single(bie_ctx* ctx, const bie_geom* g, const double* fcoef, double* out, int precision,

@@ -79,6 +79,8 @@ template <typename R, typename CT>
 int launch_self_fourier(const CT* dens, const long long* foff3, long long ndrop, int p, int pq, const R* wblk,
                         long long wstride, const R* ph, const R* T0, const R* Mhat, const double* wts,
                         const long long* val_off, double* vals, cudaStream_t s);
+// interfacial force at N grid points from x derivatives [6][3][N] and Gamma derivatives [3][N]
+int launch_force(const double* X, const double* Gm, long long N, double es, double xs, double* f, cudaStream_t s);
 // out[i] = (float) in[i]
 int launch_to_float(const double* in, float* out, long long n, cudaStream_t s);
 

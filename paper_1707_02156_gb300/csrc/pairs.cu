@@ -77,6 +77,48 @@ __global__ void k_rotgeo(const double* __restrict__ X, const double* __restrict_
   o[6 * nq + q] = (R)(wsq[j] * W);
 }
 
+// Interfacial force f = -2 sigma K n - grad_gamma sigma at grid points (Sec. 1, Table 2), from the
+// six derivative fields of x ([3][N] each, order: f, t, p, tt, tp, pp) and of Gamma (f, t, p).
+// K = (E N - 2 F M + G L) / (2 W^2) with E = x_p.x_p, F = x_p.x_t, G = x_t.x_t, L = x_pp.n,
+// M = x_tp.n, N = x_tt.n, outward n = x_t x x_p / W; sigma = 1 + E_s ln(1 - x_s Gamma) (x_s > 0)
+// or 1 - E_s Gamma; grad sigma = [(G s_p - F s_t) x_p + (E s_t - F s_p) x_t] / W^2.
+__global__ void k_force(const double* __restrict__ X, const double* __restrict__ Gm, long long N, double es,
+                        double xs, double* __restrict__ f) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  double xt[3], xp[3], xtt[3], xtp[3], xpp[3], n[3];
+  for (int c = 0; c < 3; ++c) {
+    xt[c] = X[(1 * 3 + c) * N + q];
+    xp[c] = X[(2 * 3 + c) * N + q];
+    xtt[c] = X[(3 * 3 + c) * N + q];
+    xtp[c] = X[(4 * 3 + c) * N + q];
+    xpp[c] = X[(5 * 3 + c) * N + q];
+  }
+  cross3(xt, xp, n);
+  const double W = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  for (int c = 0; c < 3; ++c) n[c] /= W;
+  const double E = xp[0] * xp[0] + xp[1] * xp[1] + xp[2] * xp[2];
+  const double F = xp[0] * xt[0] + xp[1] * xt[1] + xp[2] * xt[2];
+  const double G = xt[0] * xt[0] + xt[1] * xt[1] + xt[2] * xt[2];
+  const double L = xpp[0] * n[0] + xpp[1] * n[1] + xpp[2] * n[2];
+  const double M = xtp[0] * n[0] + xtp[1] * n[1] + xtp[2] * n[2];
+  const double Nn = xtt[0] * n[0] + xtt[1] * n[1] + xtt[2] * n[2];
+  const double W2 = W * W;
+  const double K = (E * Nn - 2.0 * F * M + G * L) / (2.0 * W2);
+  const double gam = Gm[q], gt = Gm[N + q], gp = Gm[2 * N + q];
+  double sigma, ds;
+  if (xs > 0.0) {
+    sigma = 1.0 + es * log(1.0 - xs * gam);
+    ds = -es * xs / (1.0 - xs * gam);
+  } else {
+    sigma = 1.0 - es * gam;
+    ds = -es;
+  }
+  const double st = ds * gt, sp = ds * gp;
+  const double a = (G * sp - F * st) / W2, b = (E * st - F * sp) / W2;
+  for (int c = 0; c < 3; ++c) f[c * N + q] = -2.0 * sigma * K * n[c] - (a * xp[c] + b * xt[c]);
+}
+
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
@@ -87,6 +129,14 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
 int launch_to_float(const double* in, float* out, long long n, cudaStream_t s) {
   if (n == 0) return BIE_OK;
   k_to_float<<<blocks_for(n), kThreads, 0, s>>>(in, out, n);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+int launch_force(const double* X, const double* Gm, long long N, double es, double xs, double* f, cudaStream_t s) {
+  if (N == 0) return BIE_OK;
+  k_force<<<blocks_for(N), kThreads, 0, s>>>(X, Gm, N, es, xs, f);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;

@@ -1,0 +1,142 @@
+"""Full-size parity on sampled targets: the near-contact pair (p = 32, U = 4, all three regions), the
+64-drop batch of uneven degree (p in {16, 24, 32, 48}) and the 512 deformed drops (p = 24), in the
+configurations bench.py uses.  The GPU returns the values at every grid target (BIE_GRID_OUT); the
+oracle evaluates the same sums at one or a few latitudes of one drop, built from its own pieces
+(singular rule of that drop, regular / upsampled / near-singular rules of every other drop)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import geometry, layer, near
+from paper_1707_02156_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 2e-5
+
+
+def _relerr(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return max(np.linalg.norm(a - b) / np.linalg.norm(b), np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _split(w, arr):
+    out, o = [], 0
+    for p in w.p:
+        k = 3 * (p + 1) ** 2
+        out.append(arr[o:o + k].reshape(3, -1))
+        o += k
+    return out
+
+
+def _weight(w, kind, j):
+    return -1.0 / (4 * math.pi) if kind == "S" else (w.lam[j] - 1.0) / (4 * math.pi)
+
+
+def _gpu_grid(w, kind, prec):
+    from paper_1707_02156_gb300 import api, build
+    build.build()
+    ctx = api.Context(0, upsample=w.up)
+    geo = ctx.geometry(w.p, w.pq, torch.tensor(w.xcoef, device="cuda"), w.lam)
+    f = torch.tensor(w.density, device="cuda")
+    out = torch.zeros(sum(3 * (p + 1) * (2 * p + 2) for p in w.p), dtype=torch.float64, device="cuda")
+    res = {}
+    for pr in prec:
+        (geo.apply_single if kind == "S" else geo.apply_double)(f, out, precision=pr, grid_out=True)
+        torch.cuda.synchronize()
+        res[pr] = out.cpu().numpy().copy()
+    geo.close()
+    ctx.close()
+    return res
+
+
+def _drop_block(w, grid, i, lats):
+    o = sum(3 * (p + 1) * (2 * p + 2) for p in w.p[:i])
+    p = w.p[i]
+    return grid[o:o + 3 * (p + 1) * (2 * p + 2)].reshape(3, p + 1, 2 * p + 2)[:, lats, :]
+
+
+def _far_only_oracle(w, kind, i, lats):
+    """Sampled values for workloads without near-singular targets (regions 0 and 1 only)."""
+    xs, ds = _split(w, w.xcoef), _split(w, w.density)
+    p = w.p[i]
+    sq = layer.SelfQuadrature(xs[i], p, w.pq[i], cache=False)
+    val = _weight(w, kind, i) * sq.apply(ds[i], kind, lats=lats)[:, lats, :].reshape(3, -1)
+    pts = layer.DropGrid(xs[i], p, p).x.reshape(3, p + 1, 2 * p + 2)[:, lats, :].reshape(3, -1)
+    for j in range(len(w.p)):
+        if j == i:
+            continue
+        pj = w.p[j]
+        c = xs[j][:, 0] / math.sqrt(4 * math.pi)
+        dev = xs[j].copy()
+        dev[:, 0] = 0.0
+        bound = math.sqrt(sum(inputs.supnorm_bound(dev[k], pj) ** 2 for k in range(3)))
+        dist = np.linalg.norm(pts - c[:, None], axis=0)
+        std = layer.DropGrid(xs[j], pj, pj)
+        rho = std.density(ds[j])
+        if np.all(dist - bound > 5.0 * math.pi * bound / (pj + 1)):  # surely beyond 5 h_j
+            val += _weight(w, kind, j) * layer.regular_sum(pts, std, rho, kind)
+            continue
+        h = geometry.mean_radius(xs[j], pj) * math.pi / (pj + 1)
+        ups = layer.DropGrid(xs[j], pj, w.up * (pj + 1) - 1)
+        d = np.array([np.sqrt(np.min(np.sum((ups.x - pts[:, k:k + 1]) ** 2, axis=0))) for k in range(pts.shape[1])])
+        reg = np.where(d <= h, 2, np.where(d <= 5.0 * h, 1, 0))
+        assert not np.any(reg == 2)
+        for r, src, rr in ((0, std, rho), (1, ups, None)):
+            sel = np.nonzero(reg == r)[0]
+            if len(sel):
+                rr = rr if rr is not None else src.density(ds[j])
+                val[:, sel] += _weight(w, kind, j) * layer.regular_sum(pts[:, sel], src, rr, kind)
+    return val.reshape(3, len(lats), 2 * p + 2)
+
+
+@pytest.fixture(scope="module")
+def cuda_ok():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("kind", ["S", "D"])
+def test_near_contact_pair_full_size(cuda_ok, kind):
+    w = inputs.config("c3")
+    xs, ds = _split(w, w.xcoef), _split(w, w.density)
+    drops = layer.Drops(xs, w.p, w.pq, w.lam, up=w.up)
+    i, j, lats = 0, 1, [0, 4, 16]  # latitude 0 faces the other drop (theta = pi side): regions 2, 1, 0
+    p = w.p[i]
+    self_j = drops.selfq[j].apply(ds[j], kind)                 # the anchor expansion needs all of drop j
+    val = _weight(w, kind, i) * drops.selfq[i].apply(ds[i], kind, lats=lats)[:, lats, :].reshape(3, -1)
+    tgt = np.concatenate([np.arange(a * (2 * p + 2), (a + 1) * (2 * p + 2)) for a in lats])
+    reg = drops.region[(i, j)][tgt]
+    assert set(np.unique(reg)) == {0, 1, 2}
+    std_rho, up_rho = drops.std[j].density(ds[j]), drops.ups[j].density(ds[j])
+    for r, src, rho in ((0, drops.std[j], std_rho), (1, drops.ups[j], up_rho)):
+        sel = np.nonzero(reg == r)[0]
+        val[:, sel] += _weight(w, kind, j) * layer.regular_sum(drops.targets[i][:, tgt[sel]], src, rho, kind)
+    sel = np.nonzero(reg == 2)[0]
+    val[:, sel] += _weight(w, kind, j) * near.near_values(drops, i, j, tgt[sel], ds[j], kind, self_j)
+    ref = val.reshape(3, len(lats), 2 * p + 2)
+    g = _gpu_grid(w, kind, (0, 1))
+    assert _relerr(_drop_block(w, g[0], i, lats), ref) < FP64_TOL
+    assert _relerr(_drop_block(w, g[1], i, lats), ref) < MIXED_TOL
+
+
+def test_batch_of_64_uneven_degree_drops_full_size(cuda_ok):
+    w = inputs.config("c4")
+    i = int(np.argmax(w.p))  # a p = 48 drop
+    lats = [7]
+    g = _gpu_grid(w, "D", (0, 1))
+    ref = _far_only_oracle(w, "D", i, lats)
+    assert _relerr(_drop_block(w, g[0], i, lats), ref) < FP64_TOL
+    assert _relerr(_drop_block(w, g[1], i, lats), ref) < MIXED_TOL
+
+
+def test_512_deformed_drops_full_size(cuda_ok):
+    w = inputs.config("c5")
+    i, lats = 137, [3]
+    g = _gpu_grid(w, "D", (1,))
+    ref = _far_only_oracle(w, "D", i, lats)
+    assert _relerr(_drop_block(w, g[1], i, lats), ref) < MIXED_TOL
