@@ -266,6 +266,7 @@ struct bie_geom {
     bie::DevBuf<double> wS, wD, wSraw, wDraw;
     bie::DevBuf<double> cache64;            // [gdrop][N_g][7][nq] rotated geometry (Sec. 2.2)
     bie::DevBuf<float> cache32;             // FP32 copy, made on the first direct-form mixed apply
+    bie::DevBuf<long long> src_off_std, src_off_up;  // first source of each drop on the two grids
     bie::DevBuf<double> mhat64[2];          // phi transforms of the kernel weights, S and D (Fourier form)
     bie::DevBuf<float> mhat32[2];
   };
@@ -309,8 +310,7 @@ static int analyze_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, const do
   long long nf = (long long)G.drops.size() * 3;
   BIE_TRY(g->anaF.alloc(nf * (G.p + 1) * (G.p + 1) * 2));
   Phase ph(ctx, "analyze", s);
-  return launch_analyze(vals, G.goff3.ptr, 0, nf, G.p, G.p, pl->cs.ptr, pl->A.ptr, g->anaF.ptr, out, G.foff3.ptr,
-                        0, s);
+  return launch_analyze_fused(vals, G.goff3.ptr, nf, G.p, pl->cs.ptr, pl->A.ptr, out, G.foff3.ptr, s);
 }
 
 // Fourier-form operator factors of one group, built on first use from the FP64 geometry cache.
@@ -762,6 +762,15 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   g->info.near_targets = (long long)g->near.size();
   BIE_TRY(g->up_off_d.upload(g->up_off));
   BIE_TRY(g->up_n_d.upload(g->up_n));
+  for (auto& G : g->groups) {
+    std::vector<long long> so, uo2;
+    for (int d : G->drops) {
+      so.push_back(g->tgt_off[d]);
+      uo2.push_back(g->up_off[d]);
+    }
+    BIE_TRY(G->src_off_std.upload(so));
+    BIE_TRY(G->src_off_up.upload(uo2));
+  }
   if (!g->near.empty()) BIE_TRY(setup_near(ctx, g, s));
   return BIE_OK;
 }
@@ -794,15 +803,10 @@ static int source_densities(bie_geom* g, const double* dens, R* Qs, R* Qu, cudaS
       R* grid = H + nd * 3 * (long long)(p + 1) * (P + 1) * 2;
       BIE_TRY((launch_leg_synth<double, R>(dens, G.foff3.ptr, 0, nd * 3, p, pl->T0_<R>(), P + 1, H, 0, s)));
       BIE_TRY((launch_phi_synth<R, R>(H, nd * 3, p, P, pl->cs_<R>(), grid, nullptr, N, s)));
-      for (long long i = 0; i < nd; ++i) {
-        const int d = G.drops[i];
-        if (gridk == 0)
-          BIE_TRY(launch_weight_sources<R>(grid + i * 3 * N, g->rec_std.ptr + 7 * g->tgt_off[d], N, Qs + g->tgt_off[d],
-                                           g->ntarget, s));
-        else
-          BIE_TRY(launch_weight_sources<R>(grid + i * 3 * N, g->rec_up.ptr + 7 * g->up_off[d], N, Qu + g->up_off[d],
-                                           g->nup_total, s));
-      }
+      if (gridk == 0)
+        BIE_TRY(launch_weight_sources<R>(grid, g->rec_std.ptr, G.src_off_std.ptr, N, nd, Qs, g->ntarget, s));
+      else
+        BIE_TRY(launch_weight_sources<R>(grid, g->rec_up.ptr, G.src_off_up.ptr, N, nd, Qu, g->nup_total, s));
     }
   }
   return BIE_OK;
@@ -1104,7 +1108,31 @@ struct Krylov {
   long long n = 0;
   int m = 0;
   DevBuf<double> V, w, tmp, partial, hdev, r, dx, t;
+  double* hpin = nullptr;  // pinned host copy of the Arnoldi coefficients
+  int hpin_n = 0;
+  ~Krylov() {
+    if (hpin) cudaFreeHost(hpin);
+  }
 };
+
+// hout[i] = V_i . w for i < k (and hout[k] = w . w with with_norm), reduced on the device
+static int dots_dev(Krylov& K, const double* V, int k, const double* w, double* hout, bool with_norm,
+                    cudaStream_t s) {
+  dim3 grid(kRedBlocks, k);
+  k_multidot<<<grid, kRedThreads, 0, s>>>(V, K.n, w, K.n, k, K.partial.ptr);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  if (with_norm) {
+    k_multidot<<<dim3(kRedBlocks, 1), kRedThreads, 0, s>>>(w, K.n, w, K.n, 1, K.partial.ptr + (long long)k * kRedBlocks);
+    count_launch();
+    BIE_CUDA_TRY(cudaGetLastError());
+    ++k;
+  }
+  k_sum_partials<<<k, 128, 0, s>>>(K.partial.ptr, kRedBlocks, k, hout);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
 
 // out[i] = V_i . w for i < k; with with_norm, out[k] = w . w as well (one synchronisation)
 static int dots(Krylov& K, const double* V, int k, const double* w, std::vector<double>& out, cudaStream_t s,
@@ -1171,7 +1199,7 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
     x_is_zero = xn == 0.0;
   }
   int it = 0;
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol, h2;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1);
   while (true) {
     // r = b - A x
     if (x_is_zero) {
@@ -1197,25 +1225,30 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
     for (int k = 0; k < m; ++k) {
       double* vk1 = V + (long long)(k + 1) * n;
       BIE_TRY(sys_matvec(ctx, g, V + (long long)k * n, vk1, t2, prec, info, s));
-      // CGS with one re-orthogonalisation
-      BIE_TRY(dots(K, V, k + 1, vk1, hcol, s));
-      BIE_CUDA_TRY(cudaMemcpyAsync(K.hdev.ptr, hcol.data(), (k + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
-      k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, K.hdev.ptr, k + 1, n);
+      // CGS with one re-orthogonalisation; both coefficient vectors stay on the device for the
+      // updates and come to the host together (one synchronisation per Arnoldi step)
+      double* h1 = K.hdev.ptr;
+      double* h2d = K.hdev.ptr + (m + 2);
+      BIE_TRY(dots_dev(K, V, k + 1, vk1, h1, false, s));
+      k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, h1, k + 1, n);
       count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
+      BIE_CUDA_TRY(cudaGetLastError());
       // second pass with the squared norm: |w - V h2|^2 = |w|^2 - |h2|^2 for orthonormal V
-      BIE_TRY(dots(K, V, k + 1, vk1, h2, s, true));
-      BIE_CUDA_TRY(cudaMemcpyAsync(K.hdev.ptr, h2.data(), (k + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
-      k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, K.hdev.ptr, k + 1, n);
+      BIE_TRY(dots_dev(K, V, k + 1, vk1, h2d, true, s));
+      k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, h2d, k + 1, n);
       count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
-      double hsq = h2[k + 1];
+      BIE_CUDA_TRY(cudaGetLastError());
+      BIE_CUDA_TRY(cudaMemcpyAsync(K.hpin, K.hdev.ptr, 2 * (m + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+      BIE_CUDA_TRY(cudaStreamSynchronize(s));
+      const double* hc = K.hpin;
+      const double* hh2 = K.hpin + (m + 2);
+      double hsq = hh2[k + 1];
       for (int i = 0; i <= k; ++i) {
-        H[(size_t)i * m + k] = hcol[i] + h2[i];
-        hsq -= h2[i] * h2[i];
+        H[(size_t)i * m + k] = hc[i] + hh2[i];
+        hsq -= hh2[i] * hh2[i];
       }
       double hn;
-      if (hsq > 1e-8 * h2[k + 1]) {
+      if (hsq > 1e-8 * hh2[k + 1]) {
         hn = std::sqrt(hsq);
       } else {  // heavy cancellation: measure the norm directly
         BIE_TRY(norm2(K, vk1, &hn, s));
@@ -1576,7 +1609,13 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
   BIE_TRY(K.V.alloc((size_t)(opts->restart + 1) * n));
   BIE_TRY(K.tmp.alloc(3 * n));
   BIE_TRY(K.partial.alloc((size_t)kRedBlocks * (opts->restart + 2)));
-  BIE_TRY(K.hdev.alloc(opts->restart + 2));
+  BIE_TRY(K.hdev.alloc(2 * (opts->restart + 2)));
+  if (K.hpin_n < 2 * (opts->restart + 2)) {
+    if (K.hpin) cudaFreeHost(K.hpin);
+    K.hpin = nullptr;
+    BIE_CUDA_TRY(cudaMallocHost(&K.hpin, 2 * (opts->restart + 2) * sizeof(double)));
+    K.hpin_n = 2 * (opts->restart + 2);
+  }
   double rel = 0;
   int st;
   if ((opts->precision & 0xff) == BIE_FP64) {

@@ -59,10 +59,13 @@ __global__ void k_classify(const double* __restrict__ rec_std, long long ntarget
   region[idx] = code;
 }
 
-constexpr int kChunk = 128;  // sources staged per pass
+constexpr int kChunk = 128;               // sources staged per pass
+constexpr int kPairThreads = kTile / 2;  // two targets per thread
 
+// One block per work-list block: the tile's 128 targets (two per thread, tid and tid + 64)
+// against the sources of its items, staged through shared memory.
 template <typename R, int KIND>
-__global__ void __launch_bounds__(kTile) k_interdrop(
+__global__ void __launch_bounds__(kPairThreads) k_interdrop(
     const PairItem* __restrict__ items, const int* __restrict__ blk_item, const long long* __restrict__ tile_t0,
     const int* __restrict__ tile_n, const int* __restrict__ tile_drop, const long long* __restrict__ tgt_loc,
     const long long* __restrict__ toff_std, const int* __restrict__ ngd, const double* __restrict__ rec_std,
@@ -77,75 +80,103 @@ __global__ void __launch_bounds__(kTile) k_interdrop(
   const int tid = threadIdx.x;
   const int nt = tile_n[tile];
   const int di = tile_drop[tile];
-  double tx = 0, ty = 0, tz = 0;
-  if (tid < nt) {
-    const long long t = tile_t0[tile] + tid;
-    const long long ng = ngd[di];
-    const double* ri = rec_std + 7 * toff_std[di];
-    const long long l = tgt_loc[t];
-    tx = ri[l];
-    ty = ri[ng + l];
-    tz = ri[2 * ng + l];
+  double tx[2] = {0, 0}, ty[2] = {0, 0}, tz[2] = {0, 0};
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int k = tid + u * kPairThreads;
+    if (k < nt) {
+      const long long t = tile_t0[tile] + k;
+      const long long ng = ngd[di];
+      const double* ri = rec_std + 7 * toff_std[di];
+      const long long l = tgt_loc[t];
+      tx[u] = ri[l];
+      ty[u] = ri[ng + l];
+      tz[u] = ri[2 * ng + l];
+    }
   }
-  double a0 = 0, a1 = 0, a2 = 0;
+  double a00 = 0, a01 = 0, a02 = 0, a10 = 0, a11 = 0, a12 = 0;
   for (int it = it0; it < it1; ++it) {
     const PairItem item = items[it];
     const int j = item.src_drop;
-    const bool active = tid < nt && ((item.mask[tid >> 5] >> (tid & 31)) & 1u);
+    bool act[2];
+    R px[2], py[2], pz[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int k = tid + u * kPairThreads;
+      act[u] = k < nt && ((item.mask[k >> 5] >> (k & 31)) & 1u);
+      px[u] = (R)(tx[u] - centre[3 * j]);
+      py[u] = (R)(ty[u] - centre[3 * j + 1]);
+      pz[u] = (R)(tz[u] - centre[3 * j + 2]);
+    }
     const R* X = item.grid ? Xu : Xs;
     const R* N = item.grid ? Nu : Ns;
     const R* Q = item.grid ? Qu : Qs;
     const long long ld = item.grid ? nup : nstd;
-    const R px = (R)(tx - centre[3 * j]), py = (R)(ty - centre[3 * j + 1]), pz = (R)(tz - centre[3 * j + 2]);
-    R s0 = 0, s1 = 0, s2 = 0;
+    R s[2][3] = {{0, 0, 0}, {0, 0, 0}};
     for (long long c0 = item.s0; c0 < item.s1; c0 += kChunk) {
       const int cn = (int)min((long long)kChunk, item.s1 - c0);
-      if (tid < cn) {
-        const long long s = c0 + tid;
-        sx[tid] = X[s];
-        sy[tid] = X[ld + s];
-        sz[tid] = X[2 * ld + s];
-        sq0[tid] = Q[s];
-        sq1[tid] = Q[ld + s];
-        sq2[tid] = Q[2 * ld + s];
+      for (int k = tid; k < cn; k += kPairThreads) {
+        const long long sidx = c0 + k;
+        sx[k] = X[sidx];
+        sy[k] = X[ld + sidx];
+        sz[k] = X[2 * ld + sidx];
+        sq0[k] = Q[sidx];
+        sq1[k] = Q[ld + sidx];
+        sq2[k] = Q[2 * ld + sidx];
         if (KIND) {
-          sn0[tid] = N[s];
-          sn1[tid] = N[ld + s];
-          sn2[tid] = N[2 * ld + s];
+          sn0[k] = N[sidx];
+          sn1[k] = N[ld + sidx];
+          sn2[k] = N[2 * ld + sidx];
         }
       }
       __syncthreads();
-      if (active) {
+      if (act[0] || act[1]) {
         for (int k = 0; k < cn; ++k) {
-          const R dx = px - sx[k], dy = py - sy[k], dz = pz - sz[k];
-          const R ri = rsqrt_<R>(dx * dx + dy * dy + dz * dz);
-          const R xq = dx * sq0[k] + dy * sq1[k] + dz * sq2[k];
-          if (KIND == 0) {  // Stokeslet
-            const R c = xq * ri * ri * ri;
-            s0 += sq0[k] * ri + c * dx;
-            s1 += sq1[k] * ri + c * dy;
-            s2 += sq2[k] * ri + c * dz;
-          } else {  // stresslet
-            const R xn = dx * sn0[k] + dy * sn1[k] + dz * sn2[k];
-            const R ri2 = ri * ri;
-            const R c = (R)(-6) * xq * xn * ri2 * ri2 * ri;
-            s0 += c * dx;
-            s1 += c * dy;
-            s2 += c * dz;
+          const R xs_ = sx[k], ys_ = sy[k], zs_ = sz[k], q0 = sq0[k], q1 = sq1[k], q2 = sq2[k];
+          R n0 = 0, n1 = 0, n2 = 0;
+          if (KIND) {
+            n0 = sn0[k];
+            n1 = sn1[k];
+            n2 = sn2[k];
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const R dx = px[u] - xs_, dy = py[u] - ys_, dz = pz[u] - zs_;
+            const R ri = rsqrt_<R>(dx * dx + dy * dy + dz * dz);
+            const R xq = dx * q0 + dy * q1 + dz * q2;
+            if (KIND == 0) {  // Stokeslet
+              const R c = xq * ri * ri * ri;
+              s[u][0] += q0 * ri + c * dx;
+              s[u][1] += q1 * ri + c * dy;
+              s[u][2] += q2 * ri + c * dz;
+            } else {  // stresslet
+              const R xn = dx * n0 + dy * n1 + dz * n2;
+              const R ri2 = ri * ri;
+              const R c = (R)(-6) * xq * xn * ri2 * ri2 * ri;
+              s[u][0] += c * dx;
+              s[u][1] += c * dy;
+              s[u][2] += c * dz;
+            }
           }
         }
       }
       __syncthreads();
     }
-    const double wt = wts[j];
-    a0 += wt * (double)s0;
-    a1 += wt * (double)s1;
-    a2 += wt * (double)s2;
+    const double w0 = act[0] ? wts[j] : 0.0, w1 = act[1] ? wts[j] : 0.0;
+    a00 += w0 * (double)s[0][0];
+    a01 += w0 * (double)s[0][1];
+    a02 += w0 * (double)s[0][2];
+    a10 += w1 * (double)s[1][0];
+    a11 += w1 * (double)s[1][1];
+    a12 += w1 * (double)s[1][2];
   }
   double* pp = partial + (long long)b * 3 * kTile;
-  pp[tid] = a0;
-  pp[kTile + tid] = a1;
-  pp[2 * kTile + tid] = a2;
+  pp[tid] = a00;
+  pp[kTile + tid] = a01;
+  pp[2 * kTile + tid] = a02;
+  pp[tid + kPairThreads] = a10;
+  pp[kTile + tid + kPairThreads] = a11;
+  pp[2 * kTile + tid + kPairThreads] = a12;
 }
 
 // vals += sum of the partials of the tile's blocks, in block order
@@ -176,15 +207,20 @@ __global__ void k_reduce_tiles(const double* __restrict__ partial, const int* __
   v[2 * ng] += a2;
 }
 
-// Q[c][s] = wJ[s] * grid[c][s] for one drop, source records rec [7][N] (weight in row 6)
+// Q[c][off_d + s] = wJ[s] * grid[d][c][s] for the nd drops of one degree group, whose source records
+// rec [7][N] start at 7 * off_d (weight in row 6).
 template <typename R>
-__global__ void k_weight_sources(const R* __restrict__ grid, const double* __restrict__ rec, long long N,
-                                 R* __restrict__ Q, long long ldq) {
+__global__ void k_weight_sources(const R* __restrict__ grid, const double* __restrict__ rec,
+                                 const long long* __restrict__ off, long long N, long long nd, R* __restrict__ Q,
+                                 long long ldq) {
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 3 * N) return;
-  const int c = (int)(idx / N);
-  const long long s = idx - c * N;
-  Q[c * ldq + s] = (R)rec[6 * N + s] * grid[c * N + s];
+  if (idx >= nd * 3 * N) return;
+  const long long d = idx / (3 * N);
+  const long long r = idx - d * 3 * N;
+  const int c = (int)(r / N);
+  const long long s = r - c * N;
+  const long long o = off[d];
+  Q[c * ldq + o + s] = (R)rec[7 * o + 6 * N + s] * grid[idx];
 }
 
 // sum_s x.n wJ over one drop's records (for the volume), and max_s |x - c|, via atomics on doubles
@@ -251,10 +287,10 @@ int launch_interdrop(int kind, int nblk, const PairItem* items, const int* blk_i
                      const double* wts, double* partial, cudaStream_t s) {
   if (nblk == 0) return BIE_OK;
   if (kind == 0)
-    k_interdrop<R, 0><<<nblk, kTile, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
+    k_interdrop<R, 0><<<nblk, kPairThreads, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
                                              rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial);
   else
-    k_interdrop<R, 1><<<nblk, kTile, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
+    k_interdrop<R, 1><<<nblk, kPairThreads, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
                                              rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
@@ -274,9 +310,10 @@ int launch_reduce_tiles(const double* partial, const int* tile_blk, const long l
 }
 
 template <typename R>
-int launch_weight_sources(const R* grid, const double* rec, long long N, R* Q, long long ldq, cudaStream_t s) {
-  if (N == 0) return BIE_OK;
-  k_weight_sources<R><<<blocks_for(3 * N), kThreads, 0, s>>>(grid, rec, N, Q, ldq);
+int launch_weight_sources(const R* grid, const double* rec, const long long* off, long long N, long long nd, R* Q,
+                          long long ldq, cudaStream_t s) {
+  if (N == 0 || nd == 0) return BIE_OK;
+  k_weight_sources<R><<<blocks_for(nd * 3 * N), kThreads, 0, s>>>(grid, rec, off, N, nd, Q, ldq);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
@@ -308,8 +345,10 @@ template int launch_interdrop<float>(int, int, const PairItem*, const int*, cons
                                      const long long*, const long long*, const int*, const double*, const double*,
                                      const float*, const float*, const float*, long long, const float*, const float*,
                                      const float*, long long, const double*, double*, cudaStream_t);
-template int launch_weight_sources<double>(const double*, const double*, long long, double*, long long, cudaStream_t);
-template int launch_weight_sources<float>(const float*, const double*, long long, float*, long long, cudaStream_t);
+template int launch_weight_sources<double>(const double*, const double*, const long long*, long long, long long,
+                                           double*, long long, cudaStream_t);
+template int launch_weight_sources<float>(const float*, const double*, const long long*, long long, long long, float*,
+                                          long long, cudaStream_t);
 template int launch_source_geometry<double>(const double*, long long, const double*, double*, double*, long long,
                                             cudaStream_t);
 template int launch_source_geometry<float>(const double*, long long, const double*, float*, float*, long long,

@@ -31,7 +31,8 @@ int launch_reduce_tiles(const double* partial, const int* tile_blk, const long l
                         const int* tile_drop, const long long* tgt_loc, const long long* val_off, const int* ngd,
                         int ntile, double* vals, cudaStream_t s);
 template <typename R>
-int launch_weight_sources(const R* grid, const double* rec, long long N, R* Q, long long ldq, cudaStream_t s);
+int launch_weight_sources(const R* grid, const double* rec, const long long* off, long long N, long long nd, R* Q,
+                          long long ldq, cudaStream_t s);
 int launch_drop_stats(const double* rec, long long N, const double* c, double* out2x64, cudaStream_t s);
 template <typename R>
 int launch_source_geometry(const double* rec, long long N, const double* c, R* X, R* Nn, long long ld,

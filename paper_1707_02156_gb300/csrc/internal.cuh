@@ -48,6 +48,9 @@ int launch_phi_synth(const R* H, long long nfield, int p, int P, const R* cs, OT
 int launch_analyze(const double* grid, const long long* grid_off, long long grid_stride, long long nfield, int P,
                    int p_out, const double* cs, const double* A, double* F, double* coef,
                    const long long* coef_off, long long coef_stride, cudaStream_t s);
+// analysis of nfield fields on their own degree-p grids, one block per field (grid_off, coef_off per field)
+int launch_analyze_fused(const double* grid, const long long* grid_off, long long nfield, int p, const double* cs,
+                         const double* A, double* coef, const long long* coef_off, cudaStream_t s);
 // rotation (App. B): out[ld][a*nb+b][c] = blocks(a) applied to e^{i m alpha_b} coef[ld][c]
 template <typename CT, typename R>
 int launch_rotate(const CT* coef, const long long* field_off, int ncomp, long long ndrop, int p, const R* blocks,

@@ -275,12 +275,10 @@ __global__ void __launch_bounds__(256) k_kernel_dft(const double* __restrict__ c
 }
 
 // ---- Fourier form: apply ----
-// Shared-memory layout of the Fourier kernel (R = float or double):
-//   rc6 [tri(n,m)][8]    rotated coefficients, (Re, Im) of the three components at (n, m >= 0),
-//                        tri(n,m) = n(n+1)/2 + m, padded to 8 for vector loads;
-//   union: g4 [(p+1)^2][4] phase-shifted input coefficients, three components interleaved,
-//          then h [3][rows][p+1][2], the Legendre step for a chunk of Gauss-node pairs.
-// The Legendre step evaluates each node pair (t_i, t_{pq-i} = -t_i) at once:
+// Shared memory (R = float or double): rcA, rcB [tri(n,m)][6], the rotated coefficients of the two
+// targets of a pair, (Re, Im) x 3 components at (n, m >= 0) with tri(n,m) = n(n+1)/2 + m; g4
+// [(p+1)^2][4], the phase-shifted input coefficients with the three components interleaved.
+// The Legendre step evaluates each Gauss-node pair (t_i, t_{pq-i} = -t_i) at once:
 // P~_n^m(-t) = (-1)^(n+m) P~_n^m(t), so with E (n+m even) and O (n+m odd) partial sums,
 // h(t_i) = E + O and h(-t_i) = E - O.
 template <typename R>
@@ -288,67 +286,7 @@ __device__ inline int tri_(int n, int m) {
   return n * (n + 1) / 2 + m;
 }
 
-template <typename R, typename CT>
-__device__ void rotate_target_v(const CT* __restrict__ dens, const long long* __restrict__ foff3, long long ld,
-                                int p, int a, int b, const R* __restrict__ wblk, long long wstride,
-                                const R* __restrict__ ph, R* rc6, R* g4) {
-  const int nc = (p + 1) * (p + 1);
-  const int nb = 2 * p + 2;
-  for (int i = threadIdx.x; i < 3 * nc; i += blockDim.x) {
-    const int c = i / nc, r = i - c * nc;
-    const int n = degree_of(r);
-    const int m = r - n * (n + 1);
-    if (m < 0) continue;  // the owner of Re rho_n^m writes both parts
-    const CT* f = dens + foff3[ld * 3 + c];
-    const R fr = (R)f[n * (n + 1) + m];
-    const R fi = m > 0 ? (R)f[n * (n + 1) - m] : (R)0;
-    const R co = ph[((long long)m * nb + b) * 2], si = ph[((long long)m * nb + b) * 2 + 1];
-    g4[(n * (n + 1) + m) * 4 + c] = fr * co - fi * si;
-    if (m > 0) g4[(n * (n + 1) - m) * 4 + c] = fr * si + fi * co;
-  }
-  __syncthreads();
-  const R* blk = wblk + (long long)a * wstride;
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    const int n = degree_of(i);
-    const int o = i - n * n;  // 0..2n
-    const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
-    R a0 = 0, a1 = 0, a2 = 0;
-    if (o <= n) {
-      const R* Cc = blk + boff + o;
-      const R* g = g4 + n * (n + 1) * 4;
-      for (int m = 0; m <= n; ++m) {
-        const R cv = Cc[(long long)m * (n + 1)];
-        a0 += cv * g[4 * m];
-        a1 += cv * g[4 * m + 1];
-        a2 += cv * g[4 * m + 2];
-      }
-      R* d = rc6 + tri_<R>(n, o) * 8;
-      d[0] = a0;
-      d[2] = a1;
-      d[4] = a2;
-      if (o == 0) d[1] = d[3] = d[5] = 0;
-    } else {
-      const int mp = o - n;
-      const R* Sc = blk + boff + (long long)(n + 1) * (n + 1) + (mp - 1);
-      const R* g = g4 + n * (n + 1) * 4;
-      for (int m = 1; m <= n; ++m) {
-        const R sv = Sc[(long long)(m - 1) * n];
-        a0 += sv * g[-4 * m];
-        a1 += sv * g[-4 * m + 1];
-        a2 += sv * g[-4 * m + 2];
-      }
-      R* d = rc6 + tri_<R>(n, mp) * 8;
-      d[1] = a0;
-      d[3] = a1;
-      d[5] = a2;
-    }
-  }
-  __syncthreads();
-}
-
-// Fused Legendre step and contraction: one thread item = (order m, node pair i).  The partial
-// sums E (n+m even) and O (n+m odd) give h at t_i and at t_{pq-i} = -t_i, each contracted at once
-// with the Fourier factors of its latitude.  h never leaves registers.
+// Contraction of h_m(theta_j) (Re, Im x 3 components) with the Fourier factors at (m, j).
 template <typename R>
 __device__ inline void contract(const R* __restrict__ M, long long plane, long long o, R cm, const R* h, R& s0,
                                 R& s1, R& s2) {
@@ -364,54 +302,142 @@ __device__ inline void contract(const R* __restrict__ M, long long plane, long l
   s2 += cm * (Mr[4] * h[0] + Mr[5] * h[2] + Mr[2] * h[4] - Mi[4] * h[1] - Mi[5] * h[3] - Mi[2] * h[5]);
 }
 
+// Target pairs: the targets (theta_a, phi_b) and (theta_a, phi_b + pi) share the latitude's Wigner
+// blocks, and e^{i m (phi + pi)} = (-1)^m e^{i m phi}, so even-m and odd-m partial sums E, O of one
+// pass over the blocks give the rotated coefficients of both (E + O and E - O).  The pair also
+// shares every Legendre table load.  rc is stored with 6 entries per (n, m): (Re, Im) x 3 components.
 template <typename R, typename CT>
 __global__ void __launch_bounds__(256) k_self_fourier(
     const CT* __restrict__ dens, const long long* __restrict__ foff3, int p, int pq, const R* __restrict__ wblk,
     long long wstride, const R* __restrict__ ph, const R* __restrict__ T0, const R* __restrict__ Mhat, int ng,
     const double* __restrict__ wts, const long long* __restrict__ val_off, double* __restrict__ vals) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* rc6 = reinterpret_cast<R*>(smem_raw);
   const int ntri = (p + 1) * (p + 2) / 2;
-  R* g4 = rc6 + 8 * ntri;
-  const long long t = blockIdx.x;
-  const long long ld = t / ng;
-  const int tl = (int)(t - ld * ng);
-  const int a = tl / (2 * p + 2), b = tl - a * (2 * p + 2);
-  const int nq_j = pq + 1;
-  const int npair = (nq_j + 1) / 2;  // the middle node of an odd count pairs with itself
-  const long long plane = (long long)nq_j * (p + 1);
-  const R* M = Mhat + t * 12 * plane;
-  rotate_target_v<R, CT>(dens, foff3, ld, p, a, b, wblk, wstride, ph, rc6, g4);
-  R s0 = 0, s1 = 0, s2 = 0;
-  for (int it = threadIdx.x; it < (p + 1) * npair; it += blockDim.x) {
-    const int m = it / npair, i = it - m * npair;
-    R e[6] = {0, 0, 0, 0, 0, 0}, o[6] = {0, 0, 0, 0, 0, 0};
-    const R* Tm = T0 + leg_row(p, m, m, nq_j) + i;
-    for (int n = m; n <= p; n += 2) {  // n + m even
-      const R* r = rc6 + tri_<R>(n, m) * 8;
-      const R tv = Tm[(long long)(n - m) * nq_j];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) e[k] += r[k] * tv;
-    }
-    for (int n = m + 1; n <= p; n += 2) {  // n + m odd
-      const R* r = rc6 + tri_<R>(n, m) * 8;
-      const R tv = Tm[(long long)(n - m) * nq_j];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) o[k] += r[k] * tv;
-    }
-    const R cm = m == 0 ? (R)1 : (R)2;
-    R hv[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) hv[k] = e[k] + o[k];
-    contract<R>(M, plane, (long long)m * nq_j + i, cm, hv, s0, s1, s2);
-    const int jh = pq - i;
-    if (jh != i) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) hv[k] = e[k] - o[k];
-      contract<R>(M, plane, (long long)m * nq_j + jh, cm, hv, s0, s1, s2);
+  const int nc = (p + 1) * (p + 1);
+  R* rcA = reinterpret_cast<R*>(smem_raw);
+  R* rcB = rcA + 6 * ntri;
+  R* g4 = rcB + 6 * ntri;
+  const int half_b = p + 1;                 // targets per latitude pair group
+  const long long tp = blockIdx.x;          // target pair
+  const long long ld = tp / (ng / 2);
+  const int r = (int)(tp - ld * (ng / 2));
+  const int a = r / half_b, b = r - a * half_b;
+  const int nb = 2 * p + 2;
+  const int tlA = a * nb + b, tlB = tlA + half_b;
+  const long long tA = ld * ng + tlA, tB = ld * ng + tlB;
+  // stage 0: g = e^{i m phi_b} rho_n^m
+  for (int i = threadIdx.x; i < 3 * nc; i += blockDim.x) {
+    const int c = i / nc, rr = i - c * nc;
+    const int n = degree_of(rr);
+    const int m = rr - n * (n + 1);
+    if (m < 0) continue;
+    const CT* f = dens + foff3[ld * 3 + c];
+    const R fr = (R)f[n * (n + 1) + m];
+    const R fi = m > 0 ? (R)f[n * (n + 1) - m] : (R)0;
+    const R co = ph[((long long)m * nb + b) * 2], si = ph[((long long)m * nb + b) * 2 + 1];
+    g4[(n * (n + 1) + m) * 4 + c] = fr * co - fi * si;
+    if (m > 0) g4[(n * (n + 1) - m) * 4 + c] = fr * si + fi * co;
+  }
+  __syncthreads();
+  // stage 1: rotation of both targets in one pass (even / odd orders)
+  const R* blk = wblk + (long long)a * wstride;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const int n = degree_of(i);
+    const int o = i - n * n;
+    const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
+    const R* g = g4 + n * (n + 1) * 4;
+    R e0 = 0, e1 = 0, e2 = 0, d0 = 0, d1 = 0, d2 = 0;
+    if (o <= n) {
+      const R* Cc = blk + boff + o;
+      for (int m = 0; m <= n; m += 2) {
+        const R cv = Cc[(long long)m * (n + 1)];
+        e0 += cv * g[4 * m];
+        e1 += cv * g[4 * m + 1];
+        e2 += cv * g[4 * m + 2];
+      }
+      for (int m = 1; m <= n; m += 2) {
+        const R cv = Cc[(long long)m * (n + 1)];
+        d0 += cv * g[4 * m];
+        d1 += cv * g[4 * m + 1];
+        d2 += cv * g[4 * m + 2];
+      }
+      R* A = rcA + tri_<R>(n, o) * 6;
+      R* B = rcB + tri_<R>(n, o) * 6;
+      A[0] = e0 + d0, A[2] = e1 + d1, A[4] = e2 + d2;
+      B[0] = e0 - d0, B[2] = e1 - d1, B[4] = e2 - d2;
+      if (o == 0) A[1] = A[3] = A[5] = B[1] = B[3] = B[5] = 0;
+    } else {
+      const int mp = o - n;
+      const R* Sc = blk + boff + (long long)(n + 1) * (n + 1) + (mp - 1);
+      for (int m = 2; m <= n; m += 2) {
+        const R sv = Sc[(long long)(m - 1) * n];
+        e0 += sv * g[-4 * m];
+        e1 += sv * g[-4 * m + 1];
+        e2 += sv * g[-4 * m + 2];
+      }
+      for (int m = 1; m <= n; m += 2) {
+        const R sv = Sc[(long long)(m - 1) * n];
+        d0 += sv * g[-4 * m];
+        d1 += sv * g[-4 * m + 1];
+        d2 += sv * g[-4 * m + 2];
+      }
+      R* A = rcA + tri_<R>(n, mp) * 6;
+      R* B = rcB + tri_<R>(n, mp) * 6;
+      A[1] = e0 + d0, A[3] = e1 + d1, A[5] = e2 + d2;
+      B[1] = e0 - d0, B[3] = e1 - d1, B[5] = e2 - d2;
     }
   }
-  write_target<R>(s0, s1, s2, wts, val_off, vals, ld, tl, ng);
+  __syncthreads();
+  // stages 2-3: Legendre step per (order m, node pair i) for both targets, contracted at once
+  const int nq_j = pq + 1;
+  const int npair = (nq_j + 1) / 2;
+  const long long plane = (long long)nq_j * (p + 1);
+  const R* MA = Mhat + tA * 12 * plane;
+  const R* MB = Mhat + tB * 12 * plane;
+  R sa0 = 0, sa1 = 0, sa2 = 0, sb0 = 0, sb1 = 0, sb2 = 0;
+  for (int it = threadIdx.x; it < (p + 1) * npair; it += blockDim.x) {
+    const int m = it / npair, i = it - m * npair;
+    R eA[6] = {0, 0, 0, 0, 0, 0}, oA[6] = {0, 0, 0, 0, 0, 0}, eB[6] = {0, 0, 0, 0, 0, 0}, oB[6] = {0, 0, 0, 0, 0, 0};
+    const R* Tm = T0 + leg_row(p, m, m, nq_j) + i;
+    for (int n = m; n <= p; n += 2) {
+      const int q = tri_<R>(n, m) * 6;
+      const R tv = Tm[(long long)(n - m) * nq_j];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        eA[k] += rcA[q + k] * tv;
+        eB[k] += rcB[q + k] * tv;
+      }
+    }
+    for (int n = m + 1; n <= p; n += 2) {
+      const int q = tri_<R>(n, m) * 6;
+      const R tv = Tm[(long long)(n - m) * nq_j];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        oA[k] += rcA[q + k] * tv;
+        oB[k] += rcB[q + k] * tv;
+      }
+    }
+    const R cm = m == 0 ? (R)1 : (R)2;
+    const int jh = pq - i;
+    R hv[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hv[k] = eA[k] + oA[k];
+    contract<R>(MA, plane, (long long)m * nq_j + i, cm, hv, sa0, sa1, sa2);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hv[k] = eB[k] + oB[k];
+    contract<R>(MB, plane, (long long)m * nq_j + i, cm, hv, sb0, sb1, sb2);
+    if (jh != i) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) hv[k] = eA[k] - oA[k];
+      contract<R>(MA, plane, (long long)m * nq_j + jh, cm, hv, sa0, sa1, sa2);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) hv[k] = eB[k] - oB[k];
+      contract<R>(MB, plane, (long long)m * nq_j + jh, cm, hv, sb0, sb1, sb2);
+    }
+  }
+  write_target<R>(sa0, sa1, sa2, wts, val_off, vals, ld, tlA, ng);
+  __syncthreads();
+  write_target<R>(sb0, sb1, sb2, wts, val_off, vals, ld, tlB, ng);
 }
 
 // Latitudes per chunk of the direct kernel within a shared-memory budget.
@@ -468,10 +494,10 @@ int launch_self_fourier(const CT* dens, const long long* foff3, long long ndrop,
   const long long nt = ndrop * ng;
   if (nt == 0) return BIE_OK;
   if (nt > 0x7fffffffLL) return BIE_EINVAL;
-  const size_t smem = sizeof(R) * (8 * (size_t)(p + 1) * (p + 2) / 2 + 4 * (size_t)(p + 1) * (p + 1));
+  const size_t smem = sizeof(R) * (12 * (size_t)(p + 1) * (p + 2) / 2 + 4 * (size_t)(p + 1) * (p + 1));
   auto kern = k_self_fourier<R, CT>;
   if (smem > 48 * 1024) BIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<(unsigned)nt, 256, smem, s>>>(dens, foff3, p, pq, wblk, wstride, ph, T0, Mhat, ng, wts, val_off, vals);
+  kern<<<(unsigned)(nt / 2), 256, smem, s>>>(dens, foff3, p, pq, wblk, wstride, ph, T0, Mhat, ng, wts, val_off, vals);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;

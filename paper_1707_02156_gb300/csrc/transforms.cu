@@ -129,6 +129,43 @@ __global__ void k_leg_analyze(const double* __restrict__ F, long long nfield, in
   if (m > 0) c[n * (n + 1) - m] = im;
 }
 
+// Analysis on the field's own grid (degree p), one block per (field, order m): the phi transform
+// F_m(theta_j) of the block's order is formed in shared memory, then contracted with the weighted
+// Legendre table for n = m..p.
+__global__ void k_analyze_fused(const double* __restrict__ grid, const long long* __restrict__ grid_off, int p,
+                                const double* __restrict__ cs, const double* __restrict__ A,
+                                double* __restrict__ coef, const long long* __restrict__ coef_off) {
+  __shared__ double F[2 * (BIE_MAX_P + 1)];
+  const int nj = p + 1, nk = 2 * p + 2;
+  const long long f = blockIdx.x / (p + 1);
+  const int m = (int)(blockIdx.x - f * (p + 1));
+  const double* src = grid + grid_off[f];
+  const double* c = cs + (long long)m * nk * 2;
+  for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+    const double* row = src + (long long)j * nk;
+    double re = 0, im = 0;
+    for (int k = 0; k < nk; ++k) {
+      const double v = row[k];
+      re += v * c[2 * k];
+      im -= v * c[2 * k + 1];
+    }
+    F[2 * j] = re;
+    F[2 * j + 1] = im;
+  }
+  __syncthreads();
+  double* out = coef + coef_off[f];
+  for (int n = m + threadIdx.x; n <= p; n += blockDim.x) {
+    const double* a = A + leg_row(p, m, n, nj);
+    double re = 0, im = 0;
+    for (int j = 0; j < nj; ++j) {
+      re += a[j] * F[2 * j];
+      im += a[j] * F[2 * j + 1];
+    }
+    out[n * (n + 1) + m] = re;
+    if (m > 0) out[n * (n + 1) - m] = im;
+  }
+}
+
 constexpr int kRotB = 16;  // targets (longitudes) per rotation block
 
 // One block per (drop, latitude a, degree n, chunk of kRotB longitudes b).
@@ -250,6 +287,17 @@ int launch_analyze(const double* grid, const long long* grid_off, long long grid
   BIE_CUDA_TRY(cudaGetLastError());
   long long n2 = nfield * (long long)(p_out + 1) * (p_out + 2) / 2;
   k_leg_analyze<<<blocks_for(n2), kThreads, 0, s>>>(F, nfield, P, p_out, A, coef, coef_off, coef_stride);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+int launch_analyze_fused(const double* grid, const long long* grid_off, long long nfield, int p, const double* cs,
+                         const double* A, double* coef, const long long* coef_off, cudaStream_t s) {
+  if (nfield == 0) return BIE_OK;
+  const long long nblk = nfield * (p + 1);
+  if (p > BIE_MAX_P || nblk > 0x7fffffffLL) return BIE_EINVAL;
+  k_analyze_fused<<<(unsigned)nblk, 64, 0, s>>>(grid, grid_off, p, cs, A, coef, coef_off);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
