@@ -33,7 +33,7 @@ FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FM
 FP64_ALU_PEAK = 1.25                              # TFLOP/s: nominal GB300 FP64 rate
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this workload
 # (profiles/self_fourier_f64_c2.md, profiles/self_fourier_f32_c2.md); null for any other kernel.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {"self_fourier_f64": 463.808512e6 + 3.089664e6, "self_fourier_f32": 233.705984e6 + 4.323072e6}
 
 
 def parse():
@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-aux", action="store_true", help="skip the many-drop apply measurements in the main line")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c4s", "c5"],
                     help="c2 (default): the solve step below; the others time one operator apply per step")
     return ap.parse_args()
@@ -116,14 +117,16 @@ class ClockSampler:
 def self_work_per_target(name: str, p: int, pq: int, kind: str = "D"):
     """(flops, bytes) of one target of the self kernel `name` (self_fourier_* or self_direct_*).
 
-    Counts the arithmetic the kernel's algorithm performs: the Fourier form evaluates the Legendre
-    step once per Gauss-node pair (t, -t) through the parity of n + m.
+    Counts the arithmetic the kernel's algorithm performs: the Fourier form rotates the two targets
+    phi_b and phi_b + pi of a latitude in one pass (even/odd orders) and evaluates the Legendre step
+    once per Gauss-node pair (t, -t) through the parity of n + m.
     """
     esize = 8 if name.endswith("f64") else 4
     wig = sum((n + 1) ** 2 + n * n for n in range(p + 1))          # rotation blocks of one latitude
     rot = 2.0 * 3 * wig                                              # three components
     nq = (pq + 1) * (2 * pq + 2)
     if "fourier" in name:
+        rot /= 2.0  # one pass over the blocks rotates the target pair (phi_b, phi_b + pi)
         npair = (pq + 2) // 2
         leg = npair * sum(12.0 * (p + 1 - m) + 12.0 for m in range(p + 1))  # E/O sums, then E +- O
         contr = 36.0 * (pq + 1) * (p + 1)                           # 3x3 complex symmetric times h_m
@@ -262,6 +265,19 @@ def run_ours(args):
             "peak_source": ("nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64 peak available)" if f64 else
                             "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz")}
 
+    # the inter-drop rows (regions, regular and upsampled pair sums) on the many-drop workloads
+    also = {}
+    if not args.no_aux:
+        geo.close()
+        for name in ("c4", "c5"):
+            info_a, pairs_a, res_a = time_apply(name, local, 3, 2)
+            ma = res_a[1]
+            also[name] = {"workload": APPLY_WORKLOADS[name], "step": "one mixed double-layer apply",
+                          "ms_per_apply": ma["ms"], "pairs": pairs_a, "value": pairs_a / (ma["ms"] / 1e3),
+                          "unit": UNIT, "far_pairs": info_a["far_pairs"], "up_pairs": info_a["up_pairs"],
+                          "roofline": interdrop_roofline(info_a, ma["phases"], 3),
+                          "phases_ms": {k: {"ms": v[0], "calls": v[1]} for k, v in ma["phases"].items()}}
+
     cpu = cpu_baseline_sample(w, budget_s=15.0) if rank == 0 else None
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -284,6 +300,7 @@ def run_ours(args):
                    "pairs_per_s_mixed": pairs_per_apply / (mv[1] / 1e3)},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "also": also,
     }
     if rank == 0:
         print(json.dumps(res))
@@ -346,26 +363,22 @@ APPLY_WORKLOADS = {
 }
 
 
-def run_apply(args):
-    """Auxiliary mode: time one double-layer apply per step (mixed, then FP64) on a multi-drop workload."""
+def time_apply(name, local, steps, warmup, precisions=(1,)):
+    """Time double-layer applies of a multi-drop workload; returns per-precision timings and phases."""
     import torch
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     from paper_1707_02156_gb300 import api, build, inputs
     build.build()
-    w = inputs.config(args.workload)
+    w = inputs.config(name)
     ctx = api.Context(local, upsample=w.up)
     geo = ctx.geometry(w.p, w.pq, torch.tensor(w.xcoef, device="cuda"), w.lam)
-    info = geo.info
+    info = dict(geo.info)
     pairs = info["self_pairs"] + info["far_pairs"] + info["up_pairs"] + info["near_pairs"]
     f = torch.tensor(w.density, device="cuda")
     out = torch.zeros_like(f)
     stream = torch.cuda.current_stream()
     res = {}
-    for prec in (1, 0):
-        if prec == 0 and args.workload in ("c4", "c5"):
-            continue  # FP64 applies of the many-drop workloads take seconds each
-        for _ in range(args.warmup):
+    for prec in precisions:
+        for _ in range(warmup):
             geo.apply_double(f, out, precision=prec)
         torch.cuda.synchronize()
         ctx.profile(True)
@@ -373,14 +386,40 @@ def run_apply(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 geo.apply_double(f, out, precision=prec)
             e1.record(stream)
             torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        res[prec] = {"ms": ms, "phases": ctx.profile_read(), "launches": api.launch_count() - launches0,
-                     "clocks": clk.summary()}
+        res[prec] = {"ms": e0.elapsed_time(e1) / steps, "phases": ctx.profile_read(),
+                     "launches": api.launch_count() - launches0, "clocks": clk.summary()}
         ctx.profile(False)
+    geo.close()
+    ctx.close()
+    del f, out
+    torch.cuda.empty_cache()
+    return info, pairs, res
+
+
+def interdrop_roofline(info, phases, steps):
+    """Roofline entry of the inter-drop pair kernel: 32 flops per stresslet pair (FP32 FMA pipe)."""
+    ms, calls = phases.get("interdrop_f32", (0.0, 0))
+    if not calls:
+        return None
+    flops = 32.0 * (info["far_pairs"] + info["up_pairs"])
+    avg = ms / 1e3 / calls
+    ach = flops / avg / 1e12
+    return {"bound": "alu", "kernel": "interdrop_f32", "achieved": ach, "peak": FP32_ALU_PEAK, "unit": "TFLOP/s",
+            "frac": ach / FP32_ALU_PEAK, "traffic": None, "algorithmic_flops_per_launch": flops,
+            "avg_launch_ms": avg * 1e3, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
+
+
+def run_apply(args):
+    """Auxiliary mode: time one double-layer apply per step (mixed, then FP64) on a multi-drop workload."""
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    precs = (1,) if args.workload in ("c4", "c5") else (1, 0)  # FP64 applies of the many-drop sets take seconds
+    info, pairs, res = time_apply(args.workload, local, args.steps, args.warmup, precs)
     m = res[1]
     print(json.dumps({
         "metric": METRIC, "value": pairs / (m["ms"] / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -390,6 +429,7 @@ def run_apply(args):
                    "pairs": pairs, **{k: info[k] for k in ("ntarget", "self_pairs", "far_pairs", "up_pairs",
                                                                "near_targets", "near_pairs")}},
         "gpu_launches": m["launches"], "clocks": m["clocks"],
+        "roofline": interdrop_roofline(info, m["phases"], args.steps),
         "phases_ms": {k: {"ms": v[0], "calls": v[1]} for k, v in m["phases"].items()},
         "fp64": ({"ms_per_apply": res[0]["ms"], "phases_ms": {k: {"ms": v[0], "calls": v[1]}
                                                               for k, v in res[0]["phases"].items()}}

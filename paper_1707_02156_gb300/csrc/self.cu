@@ -286,6 +286,20 @@ __device__ inline int tri_(int n, int m) {
   return n * (n + 1) / 2 + m;
 }
 
+// 128-bit vector of R for shared-memory loads (float4 / double2).
+template <typename R>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  typedef float4 T;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec4<double> {
+  typedef double2 T;
+  static constexpr int n = 2;
+};
+
 // Contraction of h_m(theta_j) (Re, Im x 3 components) with the Fourier factors at (m, j).
 template <typename R>
 __device__ inline void contract(const R* __restrict__ M, long long plane, long long o, R cm, const R* h, R& s0,
@@ -307,16 +321,16 @@ __device__ inline void contract(const R* __restrict__ M, long long plane, long l
 // pass over the blocks give the rotated coefficients of both (E + O and E - O).  The pair also
 // shares every Legendre table load.  rc is stored with 6 entries per (n, m): (Re, Im) x 3 components.
 template <typename R, typename CT>
-__global__ void __launch_bounds__(256) k_self_fourier(
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_self_fourier(
     const CT* __restrict__ dens, const long long* __restrict__ foff3, int p, int pq, const R* __restrict__ wblk,
     long long wstride, const R* __restrict__ ph, const R* __restrict__ T0, const R* __restrict__ Mhat, int ng,
     const double* __restrict__ wts, const long long* __restrict__ val_off, double* __restrict__ vals) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ntri = (p + 1) * (p + 2) / 2;
   const int nc = (p + 1) * (p + 1);
-  R* rcA = reinterpret_cast<R*>(smem_raw);
-  R* rcB = rcA + 6 * ntri;
-  R* g4 = rcB + 6 * ntri;
+  // rc [tri(n,m)][12]: target A (Re, Im) x 3 components, then target B, 16-byte aligned records
+  R* rc = reinterpret_cast<R*>(smem_raw);
+  R* g4 = rc + 12 * ntri;                   // [(p+1)^2][4]: three components interleaved, padded
   const int half_b = p + 1;                 // targets per latitude pair group
   const long long tp = blockIdx.x;          // target pair
   const long long ld = tp / (ng / 2);
@@ -325,6 +339,7 @@ __global__ void __launch_bounds__(256) k_self_fourier(
   const int nb = 2 * p + 2;
   const int tlA = a * nb + b, tlB = tlA + half_b;
   const long long tA = ld * ng + tlA, tB = ld * ng + tlB;
+  typedef typename Vec4<R>::T V4;
   // stage 0: g = e^{i m phi_b} rho_n^m
   for (int i = threadIdx.x; i < 3 * nc; i += blockDim.x) {
     const int c = i / nc, rr = i - c * nc;
@@ -351,40 +366,42 @@ __global__ void __launch_bounds__(256) k_self_fourier(
       const R* Cc = blk + boff + o;
       for (int m = 0; m <= n; m += 2) {
         const R cv = Cc[(long long)m * (n + 1)];
-        e0 += cv * g[4 * m];
-        e1 += cv * g[4 * m + 1];
-        e2 += cv * g[4 * m + 2];
+        const R* gm = g + 4 * m;
+        e0 += cv * gm[0];
+        e1 += cv * gm[1];
+        e2 += cv * gm[2];
       }
       for (int m = 1; m <= n; m += 2) {
         const R cv = Cc[(long long)m * (n + 1)];
-        d0 += cv * g[4 * m];
-        d1 += cv * g[4 * m + 1];
-        d2 += cv * g[4 * m + 2];
+        const R* gm = g + 4 * m;
+        d0 += cv * gm[0];
+        d1 += cv * gm[1];
+        d2 += cv * gm[2];
       }
-      R* A = rcA + tri_<R>(n, o) * 6;
-      R* B = rcB + tri_<R>(n, o) * 6;
-      A[0] = e0 + d0, A[2] = e1 + d1, A[4] = e2 + d2;
-      B[0] = e0 - d0, B[2] = e1 - d1, B[4] = e2 - d2;
-      if (o == 0) A[1] = A[3] = A[5] = B[1] = B[3] = B[5] = 0;
+      R* q = rc + tri_<R>(n, o) * 12;
+      q[0] = e0 + d0, q[2] = e1 + d1, q[4] = e2 + d2;
+      q[6] = e0 - d0, q[8] = e1 - d1, q[10] = e2 - d2;
+      if (o == 0) q[1] = q[3] = q[5] = q[7] = q[9] = q[11] = 0;
     } else {
       const int mp = o - n;
       const R* Sc = blk + boff + (long long)(n + 1) * (n + 1) + (mp - 1);
       for (int m = 2; m <= n; m += 2) {
         const R sv = Sc[(long long)(m - 1) * n];
-        e0 += sv * g[-4 * m];
-        e1 += sv * g[-4 * m + 1];
-        e2 += sv * g[-4 * m + 2];
+        const R* gm = g - 4 * m;
+        e0 += sv * gm[0];
+        e1 += sv * gm[1];
+        e2 += sv * gm[2];
       }
       for (int m = 1; m <= n; m += 2) {
         const R sv = Sc[(long long)(m - 1) * n];
-        d0 += sv * g[-4 * m];
-        d1 += sv * g[-4 * m + 1];
-        d2 += sv * g[-4 * m + 2];
+        const R* gm = g - 4 * m;
+        d0 += sv * gm[0];
+        d1 += sv * gm[1];
+        d2 += sv * gm[2];
       }
-      R* A = rcA + tri_<R>(n, mp) * 6;
-      R* B = rcB + tri_<R>(n, mp) * 6;
-      A[1] = e0 + d0, A[3] = e1 + d1, A[5] = e2 + d2;
-      B[1] = e0 - d0, B[3] = e1 - d1, B[5] = e2 - d2;
+      R* q = rc + tri_<R>(n, mp) * 12;
+      q[1] = e0 + d0, q[3] = e1 + d1, q[5] = e2 + d2;
+      q[7] = e0 - d0, q[9] = e1 - d1, q[11] = e2 - d2;
     }
   }
   __syncthreads();
@@ -395,43 +412,47 @@ __global__ void __launch_bounds__(256) k_self_fourier(
   const R* MA = Mhat + tA * 12 * plane;
   const R* MB = Mhat + tB * 12 * plane;
   R sa0 = 0, sa1 = 0, sa2 = 0, sb0 = 0, sb1 = 0, sb2 = 0;
-  for (int it = threadIdx.x; it < (p + 1) * npair; it += blockDim.x) {
+  const int nitem = (p + 1) * npair;
+  constexpr int NV = 12 / Vec4<R>::n;  // vector loads per rc record
+  for (int it = threadIdx.x; it < nitem; it += blockDim.x) {
     const int m = it / npair, i = it - m * npair;
-    R eA[6] = {0, 0, 0, 0, 0, 0}, oA[6] = {0, 0, 0, 0, 0, 0}, eB[6] = {0, 0, 0, 0, 0, 0}, oB[6] = {0, 0, 0, 0, 0, 0};
+    R e[12], o[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) e[k] = o[k] = 0;
     const R* Tm = T0 + leg_row(p, m, m, nq_j) + i;
-    for (int n = m; n <= p; n += 2) {
-      const int q = tri_<R>(n, m) * 6;
+    for (int n = m; n <= p; n += 2) {  // n + m even
+      const V4* q = reinterpret_cast<const V4*>(rc + tri_<R>(n, m) * 12);
       const R tv = Tm[(long long)(n - m) * nq_j];
+      R v[12];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        eA[k] += rcA[q + k] * tv;
-        eB[k] += rcB[q + k] * tv;
-      }
+      for (int u = 0; u < NV; ++u) *reinterpret_cast<V4*>(v + u * Vec4<R>::n) = q[u];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) e[k] += v[k] * tv;
     }
-    for (int n = m + 1; n <= p; n += 2) {
-      const int q = tri_<R>(n, m) * 6;
+    for (int n = m + 1; n <= p; n += 2) {  // n + m odd
+      const V4* q = reinterpret_cast<const V4*>(rc + tri_<R>(n, m) * 12);
       const R tv = Tm[(long long)(n - m) * nq_j];
+      R v[12];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        oA[k] += rcA[q + k] * tv;
-        oB[k] += rcB[q + k] * tv;
-      }
+      for (int u = 0; u < NV; ++u) *reinterpret_cast<V4*>(v + u * Vec4<R>::n) = q[u];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) o[k] += v[k] * tv;
     }
     const R cm = m == 0 ? (R)1 : (R)2;
     const int jh = pq - i;
     R hv[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) hv[k] = eA[k] + oA[k];
+    for (int k = 0; k < 6; ++k) hv[k] = e[k] + o[k];
     contract<R>(MA, plane, (long long)m * nq_j + i, cm, hv, sa0, sa1, sa2);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) hv[k] = eB[k] + oB[k];
+    for (int k = 0; k < 6; ++k) hv[k] = e[6 + k] + o[6 + k];
     contract<R>(MB, plane, (long long)m * nq_j + i, cm, hv, sb0, sb1, sb2);
     if (jh != i) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) hv[k] = eA[k] - oA[k];
+      for (int k = 0; k < 6; ++k) hv[k] = e[k] - o[k];
       contract<R>(MA, plane, (long long)m * nq_j + jh, cm, hv, sa0, sa1, sa2);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) hv[k] = eB[k] - oB[k];
+      for (int k = 0; k < 6; ++k) hv[k] = e[6 + k] - o[6 + k];
       contract<R>(MB, plane, (long long)m * nq_j + jh, cm, hv, sb0, sb1, sb2);
     }
   }
