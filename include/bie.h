@@ -68,9 +68,12 @@ typedef struct bie_config {
   int self_direct;   /* 0: singular self term in Fourier form (phi transform of the kernel weights built
                         once per geometry, the default); 1: direct form (phi synthesis and kernel
                         evaluation at every quadrature point on every apply) */
+  int use_graphs;    /* 1: an apply (kind, flags) is captured into a CUDA graph at its second call and
+                        replayed afterwards (input and output pass through fixed internal buffers);
+                        0: every apply launches its kernels one by one */
 } bie_config;
 
-/* Fill a config with the paper's defaults: device 0, U = 4, A = 5, L = 8, Fourier form. */
+/* Fill a config with the paper's defaults: device 0, U = 4, A = 5, L = 8, Fourier form, graphs on. */
 void bie_config_default(bie_config* cfg);
 
 /* Create a context on cfg->device.  Plan tables are built lazily per degree and cached. */
@@ -204,7 +207,8 @@ int bie_solve(bie_ctx* ctx, const bie_geom* geom, const double* rhs, double* u, 
  * library's work (on the stream each phase is launched on); bie_profile(ctx, 0) stops and discards.
  * bie_profile_read synchronises on the recorded events, returns per-phase totals (milliseconds and
  * number of timed calls, at most cap entries, *count = number of phases) and clears the record.
- * Phases: "self_fourier_f64/f32" and "self_direct_f64/f32" (rotation + Legendre step + the
+ * While profiling is on, applies launch their kernels one by one (no graph replay), so every phase
+ * is timed.  Phases: "self_fourier_f64/f32" and "self_direct_f64/f32" (rotation + Legendre step + the
  * singular pair sum of Thm 1), "kernel_dft" (Fourier-form factors, once per geometry), "analyze" (Galerkin
  * projection), "interdrop" (regular and upsampled pair sums), "near" (near-singular step),
  * "source_synth" (source densities on the standard/upsampled grids), "gmres_vec". */

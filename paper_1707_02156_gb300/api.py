@@ -23,7 +23,7 @@ STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIME
 
 class bie_config(ctypes.Structure):
     _fields_ = [("device", c_int), ("upsample", c_int), ("a_tilde", c_double), ("n_interp", c_int),
-                ("self_direct", c_int)]
+                ("self_direct", c_int), ("use_graphs", c_int)]
 
 
 class bie_geom_info(ctypes.Structure):
@@ -135,12 +135,13 @@ class Context:
     """A library context on one CUDA device (plan tables cached per degree)."""
 
     def __init__(self, device: int = 0, upsample: int = 4, a_tilde: float = 5.0, n_interp: int = 8,
-                 self_direct: bool = False):
+                 self_direct: bool = False, use_graphs: bool = True):
         L = lib()
         cfg = bie_config()
         L.bie_config_default(ctypes.byref(cfg))
         cfg.device, cfg.upsample, cfg.a_tilde, cfg.n_interp = device, upsample, a_tilde, n_interp
         cfg.self_direct = 1 if self_direct else 0
+        cfg.use_graphs = 1 if use_graphs else 0
         h = c_void()
         _check(L.bie_create(ctypes.byref(h), ctypes.byref(cfg)), "bie_create")
         self.h = h

@@ -273,6 +273,14 @@ struct bie_geom {
   std::vector<std::unique_ptr<Group>> groups;
   bie::DevBuf<double> anaF;   // analysis workspace
   bie::DevBuf<float> dens32;  // FP32 copy of the density (mixed applies)
+  struct GraphSlot {
+    bool warm = false;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+  };
+  std::map<int, GraphSlot> graphs;       // captured applies by (flags, kind)
+  bie::DevBuf<double> gin, gout;          // fixed input / output of the captured applies
+  cudaStream_t cap_stream = nullptr;
   bie::Krylov* kry = nullptr;  // solve workspace, kept between solves
   bie_geom_info info{};
   // inter-drop data (ndrop > 1), Sec. 2.3
@@ -374,8 +382,8 @@ static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, 
 static int near_apply(bie_geom* g, int kind, bool raw, int prec, const double* dens, cudaStream_t s);
 static int near_snapshot(bie_geom* g, cudaStream_t s);
 
-static int layer_apply(bie_ctx* ctx, const bie_geom* gc, int kind, const double* dens, double* out, int precision,
-                       cudaStream_t s) {
+static int layer_apply_eager(bie_ctx* ctx, const bie_geom* gc, int kind, const double* dens, double* out,
+                             int precision, cudaStream_t s) {
   bie_geom* g = const_cast<bie_geom*>(gc);
   if (!ctx || !g || !dens || !out) {
     set_error("null argument");
@@ -404,6 +412,66 @@ static int layer_apply(bie_ctx* ctx, const bie_geom* gc, int kind, const double*
     return BIE_OK;
   }
   for (auto& G : g->groups) BIE_TRY(analyze_group(ctx, g, *G, g->vals.ptr, out, s));
+  return BIE_OK;
+}
+
+// An apply (kind, flags) that has run once eagerly is captured into a CUDA graph on an internal
+// stream, reading and writing fixed internal buffers; later calls copy the input in, replay the graph
+// on the caller's stream and copy the result out.  The eager run performs every lazy allocation, so
+// nothing allocates or synchronises inside the capture.
+static int layer_apply(bie_ctx* ctx, const bie_geom* gc, int kind, const double* dens, double* out, int precision,
+                       cudaStream_t s) {
+  bie_geom* g = const_cast<bie_geom*>(gc);
+  if (!ctx || !g || !dens || !out) {
+    set_error("null argument");
+    return BIE_EINVAL;
+  }
+  // per-phase profiling needs the kernels launched one by one
+  if (!ctx->cfg.use_graphs || ctx->prof.on) return layer_apply_eager(ctx, g, kind, dens, out, precision, s);
+  const int key = (precision & 0x3ff) * 2 + kind;
+  auto& slot = g->graphs[key];
+  const size_t nin = g->ncoef_total;
+  const size_t nout = (precision & BIE_GRID_OUT) ? 3 * g->ntarget : g->ncoef_total;
+  if (!slot.exec) {
+    if (!slot.warm) {  // first call with this key: eager, performs the lazy allocations
+      BIE_TRY(layer_apply_eager(ctx, g, kind, dens, out, precision, s));
+      slot.warm = true;
+      return BIE_OK;
+    }
+    BIE_TRY(g->gin.alloc(std::max(g->ncoef_total, 3 * g->ntarget)));
+    BIE_TRY(g->gout.alloc(std::max(g->ncoef_total, 3 * g->ntarget)));
+    if (!g->cap_stream) BIE_CUDA_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+    const bool prof = ctx->prof.on;
+    ctx->prof.on = false;  // no event records inside the graph
+    const long long l0 = bie_launch_count();
+    BIE_CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed));
+    const int st = layer_apply_eager(ctx, g, kind, g->gin.ptr, g->gout.ptr, precision, g->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(g->cap_stream, &graph);
+    ctx->prof.on = prof;
+    if (st != BIE_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess) {
+      set_error(std::string("graph capture: ") + cudaGetErrorString(ce));
+      return BIE_ECUDA;
+    }
+    slot.launches = bie_launch_count() - l0;
+    const cudaError_t ie = cudaGraphInstantiate(&slot.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      slot.exec = nullptr;
+      set_error(std::string("graph instantiate: ") + cudaGetErrorString(ie));
+      return BIE_ECUDA;
+    }
+  }
+  Phase ph(ctx, "apply_graph", s);
+  BIE_CUDA_TRY(cudaMemcpyAsync(g->gin.ptr, dens, nin * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  BIE_CUDA_TRY(cudaGraphLaunch(slot.exec, s));
+  count_launch((int)slot.launches);
+  BIE_CUDA_TRY(cudaMemcpyAsync(out, g->gout.ptr, nout * sizeof(double), cudaMemcpyDeviceToDevice, s));
   return BIE_OK;
 }
 
@@ -1307,6 +1375,7 @@ void bie_config_default(bie_config* cfg) {
   cfg->a_tilde = 5.0;
   cfg->n_interp = 8;
   cfg->self_direct = 0;
+  cfg->use_graphs = 1;
 }
 
 const char* bie_strerror(int st) {
@@ -1499,6 +1568,9 @@ int bie_geometry_setup(bie_ctx* ctx, int ndrop, const int* p, const int* pq, con
 
 void bie_geometry_destroy(bie_geom* g) {
   if (!g) return;
+  for (auto& kv : g->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   delete g->kry;
   delete g;
 }

@@ -115,3 +115,29 @@ def test_overlapping_drops_are_rejected(ctx):
     with pytest.raises(api.BIEError) as e:
         ctx.geometry([p, p], [p, p], torch.tensor(inputs.pack_drops(xs), device="cuda"), [1.0, 1.0])
     assert e.value.status == 6
+
+
+def test_graph_replay_matches_eager_launches_bit_for_bit():
+    # an apply captured into a CUDA graph (second call onwards) must give the eager result exactly
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_02156_gb300 import api
+    ps, xs, fs, lam = _batch(seed=9)
+    x = torch.tensor(inputs.pack_drops(xs), device="cuda")
+    f = torch.tensor(inputs.pack_drops(fs), device="cuda")
+    outs = {}
+    for graphs in (False, True):
+        ctx = api.Context(0, upsample=3, use_graphs=graphs)
+        geo = ctx.geometry(ps, ps, x, lam)
+        res = []
+        for prec in (0, 1):
+            for call in range(3):  # eager, captured, replayed
+                out = torch.zeros_like(f)
+                geo.apply_double(f * (1.0 + 0.5 * call), out, precision=prec)
+                torch.cuda.synchronize()
+                res.append(out.cpu().numpy())
+        outs[graphs] = res
+        geo.close()
+        ctx.close()
+    for a, b in zip(outs[False], outs[True]):
+        assert np.array_equal(a, b)
