@@ -147,6 +147,7 @@ typedef struct bie_geom_info {
   long long near_targets; /* (target, drop) pairs in Omega_2 */
   long long near_pairs;   /* pairs evaluated at Omega_2 check points */
   double cache_bytes;     /* device bytes held by the geometry */
+  int interdrop_tpt;      /* targets per thread chosen by the pair-kernel autotuner (FP32) */
 } bie_geom_info;
 int bie_geometry_info(const bie_geom* geom, bie_geom_info* info);
 

@@ -28,7 +28,8 @@ class bie_config(ctypes.Structure):
 
 class bie_geom_info(ctypes.Structure):
     _fields_ = [("ndrop", c_int), ("ncoef", c_ll), ("ntarget", c_ll), ("self_pairs", c_ll), ("far_pairs", c_ll),
-                ("up_pairs", c_ll), ("near_targets", c_ll), ("near_pairs", c_ll), ("cache_bytes", c_double)]
+                ("up_pairs", c_ll), ("near_targets", c_ll), ("near_pairs", c_ll), ("cache_bytes", c_double),
+                ("interdrop_tpt", c_int)]
 
 
 class bie_solve_opts(ctypes.Structure):

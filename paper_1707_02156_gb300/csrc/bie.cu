@@ -298,6 +298,7 @@ struct bie_geom {
   bie::DevBuf<long long> tile_t0, tgt_loc, toff, val_off_all;
   bie::DevBuf<double> centre_d, partial, wS_all, wD_all, wSr_all, wDr_all;
   int nblk = 0, ntile = 0;
+  int tpt32 = 2, tpt64 = 2;                         // targets per thread of the pair kernel (autotuned FP32)
   std::vector<std::pair<long long, int>> near;      // (target, source drop) pairs in Omega_2
   // near-singular step (Omega_2), Sec. 2.3
   int nnear_tgt = 0;
@@ -608,6 +609,49 @@ static int drop_stats(const double* rec, long long N, const double* c, double* v
 
 static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s);
 
+// Autotuner of the FP32 pair kernel: for large work lists, time the targets-per-thread variants
+// (1, 2, 4) once on this geometry's work list (double layer, zero densities: the cost does not
+// depend on the values) and keep the fastest.
+static int autotune_interdrop(bie_geom* g, cudaStream_t s) {
+  const long long pairs = g->info.far_pairs + g->info.up_pairs;
+  g->info.interdrop_tpt = g->tpt32;
+  if (pairs < 500000000LL || g->nblk == 0) return BIE_OK;
+  BIE_TRY(g->sQ32.alloc(3 * g->ntarget));
+  BIE_TRY(g->uQ32.alloc(3 * g->nup_total));
+  BIE_CUDA_TRY(cudaMemsetAsync(g->sQ32.ptr, 0, 3 * g->ntarget * sizeof(float), s));
+  BIE_CUDA_TRY(cudaMemsetAsync(g->uQ32.ptr, 0, 3 * g->nup_total * sizeof(float), s));
+  cudaEvent_t e0, e1;
+  BIE_CUDA_TRY(cudaEventCreate(&e0));
+  BIE_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  const int cand[3] = {1, 2, 4};
+  for (int ci = 0; ci < 3; ++ci) {
+    cudaEventRecord(e0, s);
+    int st = launch_interdrop<float>(1, cand[ci], g->nblk, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr,
+                                     g->tile_n.ptr, g->tile_drop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr,
+                                     g->rec_std.ptr, g->centre_d.ptr, g->sX32.ptr, g->sN32.ptr, g->sQ32.ptr,
+                                     g->ntarget, g->uX32.ptr, g->uN32.ptr, g->uQ32.ptr, g->nup_total, g->wD_all.ptr,
+                                     g->partial.ptr, s);
+    cudaEventRecord(e1, s);
+    if (st != BIE_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return st;
+    }
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      g->tpt32 = cand[ci];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->info.interdrop_tpt = g->tpt32;
+  return BIE_OK;
+}
+
 static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   const int nd = g->ndrop;
   const int U = ctx->cfg.upsample;
@@ -830,6 +874,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   g->info.near_targets = (long long)g->near.size();
   BIE_TRY(g->up_off_d.upload(g->up_off));
   BIE_TRY(g->up_n_d.upload(g->up_n));
+  BIE_TRY(autotune_interdrop(g, s));
   for (auto& G : g->groups) {
     std::vector<long long> so, uo2;
     for (int d : G->drops) {
@@ -1080,7 +1125,7 @@ static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, 
   const double* wts = kind == 0 ? (raw ? g->wSr_all.ptr : g->wS_all.ptr) : (raw ? g->wDr_all.ptr : g->wD_all.ptr);
   {
     Phase ph(ctx, sizeof(R) == 8 ? "interdrop_f64" : "interdrop_f32", s);
-    BIE_TRY(launch_interdrop<R>(kind, g->nblk, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr, g->tile_n.ptr,
+    BIE_TRY(launch_interdrop<R>(kind, sizeof(R) == 8 ? g->tpt64 : g->tpt32, g->nblk, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr, g->tile_n.ptr,
                                 g->tile_drop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr, g->rec_std.ptr,
                                 g->centre_d.ptr, Xs, Ns, Qs, g->ntarget, Xu, Nu, Qu, g->nup_total, wts,
                                 g->partial.ptr, s));

@@ -59,19 +59,19 @@ __global__ void k_classify(const double* __restrict__ rec_std, long long ntarget
   region[idx] = code;
 }
 
-constexpr int kChunk = 128;               // sources staged per pass
-constexpr int kPairThreads = kTile / 2;  // two targets per thread
+constexpr int kChunk = 128;  // sources staged per pass
 
-// One block per work-list block: the tile's 128 targets (two per thread, tid and tid + 64)
+// One block per work-list block: the tile's 128 targets, TPT per thread (targets tid + u * 128/TPT),
 // against the sources of its items, staged through shared memory.
-template <typename R, int KIND>
-__global__ void __launch_bounds__(kPairThreads) k_interdrop(
+template <typename R, int KIND, int TPT>
+__global__ void __launch_bounds__(kTile / TPT) k_interdrop(
     const PairItem* __restrict__ items, const int* __restrict__ blk_item, const long long* __restrict__ tile_t0,
     const int* __restrict__ tile_n, const int* __restrict__ tile_drop, const long long* __restrict__ tgt_loc,
     const long long* __restrict__ toff_std, const int* __restrict__ ngd, const double* __restrict__ rec_std,
     const double* __restrict__ centre, const R* __restrict__ Xs, const R* __restrict__ Ns, const R* __restrict__ Qs,
     long long nstd, const R* __restrict__ Xu, const R* __restrict__ Nu, const R* __restrict__ Qu, long long nup,
     const double* __restrict__ wts, double* __restrict__ partial) {
+  constexpr int NT = kTile / TPT;  // threads per block
   __shared__ R sx[kChunk], sy[kChunk], sz[kChunk], sq0[kChunk], sq1[kChunk], sq2[kChunk];
   __shared__ R sn0[KIND ? kChunk : 1], sn1[KIND ? kChunk : 1], sn2[KIND ? kChunk : 1];
   const int b = blockIdx.x;
@@ -80,10 +80,12 @@ __global__ void __launch_bounds__(kPairThreads) k_interdrop(
   const int tid = threadIdx.x;
   const int nt = tile_n[tile];
   const int di = tile_drop[tile];
-  double tx[2] = {0, 0}, ty[2] = {0, 0}, tz[2] = {0, 0};
+  double tx[TPT], ty[TPT], tz[TPT], acc[TPT][3];
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int k = tid + u * kPairThreads;
+  for (int u = 0; u < TPT; ++u) {
+    const int k = tid + u * NT;
+    tx[u] = ty[u] = tz[u] = 0;
+    acc[u][0] = acc[u][1] = acc[u][2] = 0;
     if (k < nt) {
       const long long t = tile_t0[tile] + k;
       const long long ng = ngd[di];
@@ -94,16 +96,16 @@ __global__ void __launch_bounds__(kPairThreads) k_interdrop(
       tz[u] = ri[2 * ng + l];
     }
   }
-  double a00 = 0, a01 = 0, a02 = 0, a10 = 0, a11 = 0, a12 = 0;
   for (int it = it0; it < it1; ++it) {
     const PairItem item = items[it];
     const int j = item.src_drop;
-    bool act[2];
-    R px[2], py[2], pz[2];
+    bool act[TPT], any = false;
+    R px[TPT], py[TPT], pz[TPT];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int k = tid + u * kPairThreads;
+    for (int u = 0; u < TPT; ++u) {
+      const int k = tid + u * NT;
       act[u] = k < nt && ((item.mask[k >> 5] >> (k & 31)) & 1u);
+      any = any || act[u];
       px[u] = (R)(tx[u] - centre[3 * j]);
       py[u] = (R)(ty[u] - centre[3 * j + 1]);
       pz[u] = (R)(tz[u] - centre[3 * j + 2]);
@@ -112,10 +114,12 @@ __global__ void __launch_bounds__(kPairThreads) k_interdrop(
     const R* N = item.grid ? Nu : Ns;
     const R* Q = item.grid ? Qu : Qs;
     const long long ld = item.grid ? nup : nstd;
-    R s[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    R s[TPT][3];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) s[u][0] = s[u][1] = s[u][2] = 0;
     for (long long c0 = item.s0; c0 < item.s1; c0 += kChunk) {
       const int cn = (int)min((long long)kChunk, item.s1 - c0);
-      for (int k = tid; k < cn; k += kPairThreads) {
+      for (int k = tid; k < cn; k += NT) {
         const long long sidx = c0 + k;
         sx[k] = X[sidx];
         sy[k] = X[ld + sidx];
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(kPairThreads) k_interdrop(
         }
       }
       __syncthreads();
-      if (act[0] || act[1]) {
+      if (any) {
         for (int k = 0; k < cn; ++k) {
           const R xs_ = sx[k], ys_ = sy[k], zs_ = sz[k], q0 = sq0[k], q1 = sq1[k], q2 = sq2[k];
           R n0 = 0, n1 = 0, n2 = 0;
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(kPairThreads) k_interdrop(
             n2 = sn2[k];
           }
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+          for (int u = 0; u < TPT; ++u) {
             const R dx = px[u] - xs_, dy = py[u] - ys_, dz = pz[u] - zs_;
             const R ri = rsqrt_<R>(dx * dx + dy * dy + dz * dz);
             const R xq = dx * q0 + dy * q1 + dz * q2;
@@ -162,21 +166,23 @@ __global__ void __launch_bounds__(kPairThreads) k_interdrop(
       }
       __syncthreads();
     }
-    const double w0 = act[0] ? wts[j] : 0.0, w1 = act[1] ? wts[j] : 0.0;
-    a00 += w0 * (double)s[0][0];
-    a01 += w0 * (double)s[0][1];
-    a02 += w0 * (double)s[0][2];
-    a10 += w1 * (double)s[1][0];
-    a11 += w1 * (double)s[1][1];
-    a12 += w1 * (double)s[1][2];
+    const double wj = wts[j];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const double w = act[u] ? wj : 0.0;
+      acc[u][0] += w * (double)s[u][0];
+      acc[u][1] += w * (double)s[u][1];
+      acc[u][2] += w * (double)s[u][2];
+    }
   }
   double* pp = partial + (long long)b * 3 * kTile;
-  pp[tid] = a00;
-  pp[kTile + tid] = a01;
-  pp[2 * kTile + tid] = a02;
-  pp[tid + kPairThreads] = a10;
-  pp[kTile + tid + kPairThreads] = a11;
-  pp[2 * kTile + tid + kPairThreads] = a12;
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int k = tid + u * NT;
+    pp[k] = acc[u][0];
+    pp[kTile + k] = acc[u][1];
+    pp[2 * kTile + k] = acc[u][2];
+  }
 }
 
 // vals += sum of the partials of the tile's blocks, in block order
@@ -279,19 +285,38 @@ int launch_classify(const double* rec_std, long long ntarget, const int* tdrop, 
   return BIE_OK;
 }
 
+template <typename R, int TPT>
+static void interdrop_kernel(int kind, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
+                             const int* tile_n, const int* tile_drop, const long long* tgt_loc,
+                             const long long* toff_std, const int* ngd, const double* rec_std, const double* centre,
+                             const R* Xs, const R* Ns, const R* Qs, long long nstd, const R* Xu, const R* Nu,
+                             const R* Qu, long long nup, const double* wts, double* partial, cudaStream_t s) {
+  if (kind == 0)
+    k_interdrop<R, 0, TPT><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
+                                                        toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu,
+                                                        nup, wts, partial);
+  else
+    k_interdrop<R, 1, TPT><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
+                                                        toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu,
+                                                        nup, wts, partial);
+}
+
 template <typename R>
-int launch_interdrop(int kind, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
+int launch_interdrop(int kind, int tpt, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
                      const int* tile_n, const int* tile_drop, const long long* tgt_loc, const long long* toff_std,
                      const int* ngd, const double* rec_std, const double* centre, const R* Xs, const R* Ns,
                      const R* Qs, long long nstd, const R* Xu, const R* Nu, const R* Qu, long long nup,
                      const double* wts, double* partial, cudaStream_t s) {
   if (nblk == 0) return BIE_OK;
-  if (kind == 0)
-    k_interdrop<R, 0><<<nblk, kPairThreads, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
-                                             rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial);
+  if (tpt == 1)
+    interdrop_kernel<R, 1>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd, rec_std,
+                           centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);
+  else if (tpt == 4)
+    interdrop_kernel<R, 4>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd, rec_std,
+                           centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);
   else
-    k_interdrop<R, 1><<<nblk, kPairThreads, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
-                                             rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial);
+    interdrop_kernel<R, 2>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd, rec_std,
+                           centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
@@ -336,12 +361,12 @@ int launch_source_geometry(const double* rec, long long N, const double* c, R* X
   return BIE_OK;
 }
 
-template int launch_interdrop<double>(int, int, const PairItem*, const int*, const long long*, const int*,
+template int launch_interdrop<double>(int, int, int, const PairItem*, const int*, const long long*, const int*,
                                       const int*, const long long*, const long long*, const int*, const double*,
                                       const double*, const double*, const double*, const double*, long long,
                                       const double*, const double*, const double*, long long, const double*, double*,
                                       cudaStream_t);
-template int launch_interdrop<float>(int, int, const PairItem*, const int*, const long long*, const int*, const int*,
+template int launch_interdrop<float>(int, int, int, const PairItem*, const int*, const long long*, const int*, const int*,
                                      const long long*, const long long*, const int*, const double*, const double*,
                                      const float*, const float*, const float*, long long, const float*, const float*,
                                      const float*, long long, const double*, double*, cudaStream_t);

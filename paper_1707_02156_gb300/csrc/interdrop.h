@@ -21,8 +21,9 @@ int launch_classify(const double* rec_std, long long ntarget, const int* tdrop, 
                     const long long* toff_std, const int* ngd, int ndrop, const double* centre, const double* bound,
                     const double* h, double a_tilde, const double* rec_up, const long long* up_off,
                     const long long* up_n, unsigned char* region, cudaStream_t s);
+// tpt: targets per thread (1, 2 or 4; chosen per geometry by timing, see setup_interdrop)
 template <typename R>
-int launch_interdrop(int kind, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
+int launch_interdrop(int kind, int tpt, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
                      const int* tile_n, const int* tile_drop, const long long* tgt_loc, const long long* toff_std,
                      const int* ngd, const double* rec_std, const double* centre, const R* Xs, const R* Ns,
                      const R* Qs, long long nstd, const R* Xu, const R* Nu, const R* Qu, long long nup,
