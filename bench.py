@@ -32,8 +32,8 @@ WORKLOAD = "one drop p=32 (sphere + 0.05 SH perturbation, n<=6), lambda=5, shear
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
 FP64_ALU_PEAK = 1.25                              # TFLOP/s: nominal GB300 FP64 rate
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this workload
-# (profiles/self_fourier_f64_c2.md, profiles/self_fourier_f32_c2.md); null for any other kernel.
-PROFILED_TRAFFIC = {"self_fourier_f64": 463.808512e6 + 3.089664e6, "self_fourier_f32": 233.705984e6 + 4.323072e6}
+# (profiles/self_proj_f64_c2.md, profiles/self_proj_f32_c2.md); null for any other kernel.
+PROFILED_TRAFFIC = {}
 
 
 def parse():
@@ -115,26 +115,58 @@ class ClockSampler:
 # algorithmic work of the singular self kernels, per target (FMA = 2 flops, rsqrt = 1)
 # ------------------------------------------------------------------------------------------------
 def self_work_per_target(name: str, p: int, pq: int, kind: str = "D"):
-    """(flops, bytes) of one target of the self kernel `name` (self_fourier_* or self_direct_*).
+    """(flops, bytes) of one target of the self kernel `name` (self_proj_* or self_direct_*).
 
-    Counts the arithmetic the kernel's algorithm performs: the Fourier form rotates the two targets
-    phi_b and phi_b + pi of a latitude in one pass (even/odd orders) and evaluates the Legendre step
-    once per Gauss-node pair (t, -t) through the parity of n + m.
+    Counts the arithmetic the kernel's algorithm performs: the projected form rotates the four
+    targets (theta, phi_b), (theta, phi_b + pi), (pi - theta, phi_b), (pi - theta, phi_b + pi) in one
+    pass over latitude theta's Wigner blocks (even/odd orders), then contracts each rotated
+    coefficient (n, m >= 0; Re, Im x 3 components) with the target's 6 complex projected kernel
+    factors.
     """
     esize = 8 if name.endswith("f64") else 4
     wig = sum((n + 1) ** 2 + n * n for n in range(p + 1))          # rotation blocks of one latitude
     rot = 2.0 * 3 * wig                                              # three components
     nq = (pq + 1) * (2 * pq + 2)
-    if "fourier" in name:
-        rot /= 2.0  # one pass over the blocks rotates the target pair (phi_b, phi_b + pi)
-        npair = (pq + 2) // 2
-        leg = npair * sum(12.0 * (p + 1 - m) + 12.0 for m in range(p + 1))  # E/O sums, then E +- O
-        contr = 36.0 * (pq + 1) * (p + 1)                           # 3x3 complex symmetric times h_m
-        return rot + leg + contr, 12.0 * (pq + 1) * (p + 1) * esize  # Mhat read once per apply
+    if "proj" in name:
+        ng = (p + 1) * (2 * p + 2)
+        rot *= ((p + 2) // 2) * (p + 1) / ng  # one pass over the blocks per target quadruple
+        ntri = (p + 1) * (p + 2) // 2
+        contr = 36.0 * ntri                                          # 3x3 complex symmetric times rho'_n^m
+        return rot + contr, 12.0 * ntri * esize                      # Q read once per apply
     leg = 3.0 * (pq + 1) * (2 * (p + 1) + 4 * sum(p + 1 - m for m in range(1, p + 1)))
     phi = 3.0 * (pq + 1) * (pq + 1) * (4 * p + 2)                    # longitude pairs, even/odd orders
     pair = (32.0 if kind == "D" else 29.0) * nq
     return rot + leg + phi + pair, nq * (7 if kind == "D" else 4) * esize
+
+
+class Scrub:
+    """Writes a buffer larger than L2 (129 MB) between timed intervals, so that no timed step starts
+    with a warm L2; the write itself sits outside every timed event pair."""
+
+    def __init__(self, nbytes=512 << 20):
+        import torch
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.k = 0
+
+    def __call__(self):
+        self.k = (self.k + 1) & 255
+        self.buf.fill_(self.k)
+
+
+def timed_steps(fn, n, stream, scrub):
+    """Total milliseconds of n calls of fn, each timed with its own CUDA events on `stream`, with an
+    L2 scrub before each (outside the events)."""
+    import torch
+    evs = []
+    for _ in range(n):
+        scrub()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs)
 
 
 def run_ours(args):
@@ -152,7 +184,11 @@ def run_ours(args):
     w = inputs.perturbed_drop()
     p, pq = w.p[0], w.pq[0]
     x = torch.tensor(w.xcoef, device="cuda")
+    torch.cuda.synchronize()
+    t_geo = time.perf_counter()
     geo = ctx.geometry(w.p, w.pq, x, w.lam)
+    torch.cuda.synchronize()
+    geometry_ms = 1e3 * (time.perf_counter() - t_geo)
     nco = geo.info["ncoef"]
     pairs_per_apply = geo.info["self_pairs"]
     f = torch.tensor(w.density, device="cuda")
@@ -168,29 +204,38 @@ def run_ours(args):
         info = geo.solve(rhs_out, uvec, precision=precision, tol=1e-10, inner_tol=1e-5)
         return info
 
-    # warm-up
+    scrub = Scrub()
+    # warm-up; the first step builds the per-geometry projected kernel factors (timed as set-up)
+    ctx.profile(True)
+    step(1, u, rhs)
+    step(0, u, rhs)
+    setup_phases = ctx.profile_read()
+    ctx.profile(False)
     for _ in range(args.warmup):
         info = step(1, u, rhs)
     torch.cuda.synchronize()
 
     # timed region: K mixed solves, default library behaviour (applies replayed as CUDA graphs)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = api.launch_count()
     applies = 0
+    last = {}
+
+    def mixed_step():
+        last["info"] = step(1, u, rhs)
+
     with ClockSampler(local) as clk:
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        ev0.record(stream)
+        ms_total = 0.0
         for _ in range(args.steps):
-            info = step(1, u, rhs)
+            ms_total += timed_steps(mixed_step, 1, stream, scrub)
+            info = last["info"]
             applies += 1 + info["applies_fp64"] + info["applies_mixed"]
-        ev1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
     launches = api.launch_count() - launches0
-    ms_total = ev0.elapsed_time(ev1)
     t_local = ms_total / 1e3
     if world > 1:
         t = torch.tensor([t_local], device="cuda")
@@ -202,28 +247,22 @@ def run_ours(args):
     value = world * applies * pairs_per_apply / t_max
     # the same K steps again with the library's per-phase CUDA events on (kernels launched one by one)
     ctx.profile(True)
-    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    pe0.record(stream)
-    for _ in range(args.steps):
-        step(1, u, rhs)
-    pe1.record(stream)
-    torch.cuda.synchronize()
+    ms_step_profiled = timed_steps(lambda: step(1, u, rhs), args.steps, stream, scrub) / args.steps
     phases = ctx.profile_read()
     ctx.profile(False)
-    ms_step_profiled = pe0.elapsed_time(pe1) / args.steps
     u_mixed = u.clone()
     mixed_info = info
 
     # FP64 reference solve on the GPU (same step, plain FP64 path), and the accuracy of mixed vs FP64
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     u64 = torch.zeros_like(u)
     step(0, u64, rhs)
     torch.cuda.synchronize()
-    e0.record(stream)
-    info64 = step(0, u64, rhs)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    fp64_ms = e0.elapsed_time(e1)
+
+    def fp64_step():
+        last["info64"] = step(0, u64, rhs)
+
+    fp64_ms = timed_steps(fp64_step, 1, stream, scrub)
+    info64 = last["info64"]
     rel = float(torch.linalg.norm(u_mixed - u64) / torch.linalg.norm(u64))
 
     # matvec times (double layer) at each precision
@@ -232,28 +271,21 @@ def run_ours(args):
     for prec in (0, 1):
         for _ in range(3):
             geo.apply_double(u64, out, precision=prec)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(10):
-            geo.apply_double(u64, out, precision=prec)
-        b.record(stream)
-        torch.cuda.synchronize()
-        mv[prec] = a.elapsed_time(b) / 10
+        mv[prec] = timed_steps(lambda: geo.apply_double(u64, out, precision=prec), 10, stream, scrub) / 10
 
     # end to end through the public API with host buffers: H2D of (f, u_inf), step, D2H of u
     f_h = torch.tensor(w.density).pin_memory()
     uinf_h = uinf.cpu().pin_memory()
     u_h = torch.zeros(nco, dtype=torch.float64).pin_memory()
-    e0.record(stream)
     n_e2e = max(3, args.steps // 2)
-    for _ in range(n_e2e):
+
+    def e2e_step():
         f.copy_(f_h, non_blocking=True)
         uinf.copy_(uinf_h, non_blocking=True)
         step(1, u, rhs)
         u_h.copy_(u, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3 / n_e2e
+
+    e2e_s = timed_steps(e2e_step, n_e2e, stream, scrub) / 1e3 / n_e2e
     e2e_value = world * (applies / args.steps) * pairs_per_apply / e2e_s
 
     # roofline of the dominant kernel (the self kernel with the largest total time in the profiled steps)
@@ -294,7 +326,10 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "p": p, "p_q": pq, "targets": ntarget,
                    "pairs_per_apply": pairs_per_apply, "step": "rhs (FP64 S apply) + mixed GMRES solve, tol 1e-10",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2: rotated-geometry cache 0.53 GB FP32 + 1.06 GB FP64 read per apply"},
+                   "l2": "L2 flushed (512 MB write) before every timed step; within a step the applies re-read "
+                         "the projected kernel factors (FP32 59 MB, FP64 117 MB)"},
+        "setup_ms": {"geometry": geometry_ms,
+                     "kernel_proj": setup_phases.get("kernel_proj", (None, 0))[0]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * nco * 8, "d2h_bytes_per_step": nco * 8},
         "gpu_launches": launches,
         "roofline": roof,
@@ -385,6 +420,7 @@ def time_apply(name, local, steps, warmup, precisions=(1,)):
     f = torch.tensor(w.density, device="cuda")
     out = torch.zeros_like(f)
     stream = torch.cuda.current_stream()
+    scrub = Scrub()
     res = {}
     for prec in precisions:
         for _ in range(warmup):
@@ -392,14 +428,9 @@ def time_apply(name, local, steps, warmup, precisions=(1,)):
         torch.cuda.synchronize()
         ctx.profile(True)
         launches0 = api.launch_count()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
-            e0.record(stream)
-            for _ in range(steps):
-                geo.apply_double(f, out, precision=prec)
-            e1.record(stream)
-            torch.cuda.synchronize()
-        res[prec] = {"ms": e0.elapsed_time(e1) / steps, "phases": ctx.profile_read(),
+            ms = timed_steps(lambda: geo.apply_double(f, out, precision=prec), steps, stream, scrub)
+        res[prec] = {"ms": ms / steps, "phases": ctx.profile_read(),
                      "launches": api.launch_count() - launches0, "clocks": clk.summary()}
         ctx.profile(False)
     geo.close()

@@ -65,9 +65,11 @@ typedef struct bie_config {
   int upsample;      /* U: the intermediate region uses the grid of degree U(p+1)-1 (Sec. 2.3), >= 1 */
   double a_tilde;    /* A: Omega_0 / Omega_1 boundary at distance A*h (Sec. 2.3; the paper uses 5) */
   int n_interp;      /* L: check points of the near-singular interpolation (Sec. 2.3; 8) */
-  int self_direct;   /* 0: singular self term in Fourier form (phi transform of the kernel weights built
-                        once per geometry, the default); 1: direct form (phi synthesis and kernel
-                        evaluation at every quadrature point on every apply) */
+  int self_direct;   /* 0: singular self term in projected form (the kernel weights of each target's
+                        rotated grid, phi-transformed and projected onto the associated Legendre
+                        functions once per geometry; an apply rotates the density and contracts it
+                        with them; the default); 1: direct form (synthesis on the rotated grid and
+                        kernel evaluation at every quadrature point on every apply) */
   int use_graphs;    /* 1: an apply (kind, flags) is captured into a CUDA graph at its second call and
                         replayed afterwards (input and output pass through fixed internal buffers);
                         0: every apply launches its kernels one by one */
@@ -209,8 +211,9 @@ int bie_solve(bie_ctx* ctx, const bie_geom* geom, const double* rhs, double* u, 
  * bie_profile_read synchronises on the recorded events, returns per-phase totals (milliseconds and
  * number of timed calls, at most cap entries, *count = number of phases) and clears the record.
  * While profiling is on, applies launch their kernels one by one (no graph replay), so every phase
- * is timed.  Phases: "self_fourier_f64/f32" and "self_direct_f64/f32" (rotation + Legendre step + the
- * singular pair sum of Thm 1), "kernel_dft" (Fourier-form factors, once per geometry), "analyze" (Galerkin
+ * is timed.  Phases: "self_proj_f64/f32" (rotation + contraction with the projected kernel factors) and
+ * "self_direct_f64/f32" (rotation + synthesis + the singular pair sum of Thm 1), "kernel_proj"
+ * (projected kernel factors, once per geometry and kind), "analyze" (Galerkin
  * projection), "interdrop" (regular and upsampled pair sums), "near" (near-singular step),
  * "source_synth" (source densities on the standard/upsampled grids), "gmres_vec". */
 typedef struct bie_phase_stat {

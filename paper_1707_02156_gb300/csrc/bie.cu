@@ -267,8 +267,8 @@ struct bie_geom {
     bie::DevBuf<double> cache64;            // [gdrop][N_g][7][nq] rotated geometry (Sec. 2.2)
     bie::DevBuf<float> cache32;             // FP32 copy, made on the first direct-form mixed apply
     bie::DevBuf<long long> src_off_std, src_off_up;  // first source of each drop on the two grids
-    bie::DevBuf<double> mhat64[2];          // phi transforms of the kernel weights, S and D (Fourier form)
-    bie::DevBuf<float> mhat32[2];
+    bie::DevBuf<double> qk64[2];            // projected kernel factors of every target, S and D
+    bie::DevBuf<float> qk32[2];
   };
   std::vector<std::unique_ptr<Group>> groups;
   bie::DevBuf<double> anaF;   // analysis workspace
@@ -322,31 +322,39 @@ static int analyze_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, const do
   return launch_analyze_fused(vals, G.goff3.ptr, nf, G.p, pl->cs.ptr, pl->A.ptr, out, G.foff3.ptr, s);
 }
 
-// Fourier-form operator factors of one group, built on first use from the FP64 geometry cache.
-static int ensure_mhat(bie_ctx* ctx, bie_geom::Group& G, int kind, cudaStream_t s) {
-  if (G.mhat64[kind].ptr) return BIE_OK;
+// Projected-form kernel factors of one group, built on first use from the FP64 geometry cache.
+static int ensure_qk(bie_ctx* ctx, bie_geom::Group& G, int kind, cudaStream_t s) {
+  if (G.qk64[kind].ptr) return BIE_OK;
   Plan* pl;
   BIE_TRY(get_plan(ctx, G.p, G.pq, &pl));
   const long long nt = (long long)G.drops.size() * ngrid(G.p);
-  const long long n = nt * 12 * (long long)(G.pq + 1) * (G.p + 1);
-  BIE_TRY(G.mhat64[kind].alloc(n));
-  BIE_TRY(G.mhat32[kind].alloc(n));
-  Phase ph(ctx, "kernel_dft", s);
-  return launch_kernel_dft(kind, G.cache64.ptr, nt, G.p, G.pq, pl->cs.ptr, G.mhat64[kind].ptr, G.mhat32[kind].ptr, s);
+  const long long n = nt * 6 * (long long)(G.p + 1) * (G.p + 2);
+  BIE_TRY(G.qk64[kind].alloc(n));
+  BIE_TRY(G.qk32[kind].alloc(n));
+  Phase ph(ctx, "kernel_proj", s);
+  return launch_kernel_proj(kind, G.cache64.ptr, nt, G.p, G.pq, pl->cs.ptr, pl->T0.ptr, G.qk64[kind].ptr,
+                            G.qk32[kind].ptr, s);
 }
 
 // Singular self part of every drop (Sec. 2.2): one launch per degree group.
 template <typename R>
 static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s) {
   bie_ctx* ctx = g->ctx;
-  const bool direct = ctx->cfg.self_direct != 0;
-  if (sizeof(R) == 4 && !direct) {  // the FP32 kernels read an FP32 copy of the density
+  // the projected form keeps its per-target factors in shared memory while they are built; groups
+  // whose factors do not fit there use the direct form
+  auto use_direct = [&](const bie_geom::Group& G) {
+    return ctx->cfg.self_direct != 0 || kernel_proj_smem(G.p, G.pq) > 227 * 1024;
+  };
+  bool any_proj = false;
+  for (auto& Gp : g->groups) any_proj = any_proj || !use_direct(*Gp);
+  if (sizeof(R) == 4 && any_proj) {  // the FP32 projected kernel reads an FP32 copy of the density
     BIE_TRY(g->dens32.alloc(g->ncoef_total));
     BIE_TRY(launch_to_float(dens, g->dens32.ptr, g->ncoef_total, s));
   }
   for (auto& Gp : g->groups) {
     auto& G = *Gp;
     const int p = G.p, pq = G.pq;
+    const bool direct = use_direct(G);
     Plan *pl, *pp;
     WigPlan* wp;
     BIE_TRY(get_plan(ctx, p, pq, &pl));
@@ -366,13 +374,13 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
                                     pl->T0_<R>(), pl->cs_<R>(), cache, wts, G.val_off.ptr, g->vals.ptr,
                                     sizeof(R) == 8 ? 96 * 1024 : 40 * 1024, s));
     } else {
-      BIE_TRY(ensure_mhat(ctx, G, kind, s));
-      const R* M = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.mhat64[kind].ptr)
-                                  : reinterpret_cast<const R*>(G.mhat32[kind].ptr);
+      BIE_TRY(ensure_qk(ctx, G, kind, s));
+      const R* Q = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.qk64[kind].ptr)
+                                  : reinterpret_cast<const R*>(G.qk32[kind].ptr);
       const R* dR = sizeof(R) == 8 ? reinterpret_cast<const R*>(dens) : reinterpret_cast<const R*>(g->dens32.ptr);
-      Phase ph(ctx, sizeof(R) == 8 ? "self_fourier_f64" : "self_fourier_f32", s);
-      BIE_TRY((launch_self_fourier<R, R>(dR, G.foff3.ptr, nd, p, pq, wp->blk_<R>(), wp->stride, pp->cs_<R>(),
-                                         pl->T0_<R>(), M, wts, G.val_off.ptr, g->vals.ptr, s)));
+      Phase ph(ctx, sizeof(R) == 8 ? "self_proj_f64" : "self_proj_f32", s);
+      BIE_TRY((launch_self_proj<R, R>(dR, G.foff3.ptr, nd, p, wp->blk_<R>(), wp->stride, pp->cs_<R>(), Q, wts,
+                                      G.val_off.ptr, g->vals.ptr, s)));
     }
   }
   return BIE_OK;

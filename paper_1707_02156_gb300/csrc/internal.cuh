@@ -70,18 +70,21 @@ template <typename R>
 int launch_rotgeo(const double* X, const double* Xt, const double* Xp, long long ndrop, int ng, int pq,
                   const double* rec_std, const double* wsq, R* cache, cudaStream_t s);
 // Singular self interaction (Thm 1, Sec. 2.2), one block per target of ndrop drops of degree p:
-// direct form against the rotated-geometry cache, or Fourier form against Mhat (see self.cu).
+// direct form against the rotated-geometry cache, or projected form against Q (see self.cu).
 template <typename R>
 int launch_self_direct(int kind, const double* dens, const long long* foff3, long long ndrop, int p, int pq,
                        const R* wblk, long long wstride, const R* ph, const R* T0, const R* cs, const R* cache,
                        const double* wts, const long long* val_off, double* vals, size_t smem_budget,
                        cudaStream_t s);
-int launch_kernel_dft(int kind, const double* cache, long long ntarget, int p, int pq, const double* cs, double* M64,
-                      float* M32, cudaStream_t s);
+// Projected kernel factors Q[t][12][tri(n,m)] of ntarget targets (see self.cu), from the FP64
+// rotated-geometry cache and the degree-pq grid's Legendre table T0 (degrees <= p, all nodes).
+size_t kernel_proj_smem(int p, int pq);
+int launch_kernel_proj(int kind, const double* cache, long long ntarget, int p, int pq, const double* cs,
+                       const double* T0, double* Q64, float* Q32, cudaStream_t s);
 template <typename R, typename CT>
-int launch_self_fourier(const CT* dens, const long long* foff3, long long ndrop, int p, int pq, const R* wblk,
-                        long long wstride, const R* ph, const R* T0, const R* Mhat, const double* wts,
-                        const long long* val_off, double* vals, cudaStream_t s);
+int launch_self_proj(const CT* dens, const long long* foff3, long long ndrop, int p, const R* wblk, long long wstride,
+                     const R* ph, const R* Q, const double* wts, const long long* val_off, double* vals,
+                     cudaStream_t s);
 // interfacial force at N grid points from x derivatives [6][3][N] and Gamma derivatives [3][N]
 int launch_force(const double* X, const double* Gm, long long N, double es, double xs, double* f, cudaStream_t s);
 // out[i] = (float) in[i]

@@ -1,16 +1,19 @@
 // Singular self interaction of every drop (Thm 1, Sec. 2.2, App. B): one block per target.
 //
 // Both forms rotate the density so that the target sits at the pole (App. B, real blocks of the
-// latitude's Wigner matrices applied to e^{i m phi_b} rho_n^m) and run the Legendre step of the
-// synthesis on the degree-pq grid, h_m(theta_j) = sum_n rho'_n^m P~_n^m(cos theta_j), in shared memory.
+// latitude's Wigner matrices applied to e^{i m phi_b} rho_n^m).
 //
-//  * direct form: the phi step rho'(theta_j, phi_k) = h_0 + 2 Re sum_m h_m e^{i m phi_k} is evaluated
+//  * direct form: the Legendre step of the synthesis on the degree-pq grid,
+//    h_m(theta_j) = sum_n rho'_n^m P~_n^m(cos theta_j), runs in shared memory; the phi step rho'(theta_j, phi_k) = h_0 + 2 Re sum_m h_m e^{i m phi_k} is evaluated
 //    for the longitude pair (k, k + pq + 1) from the even and odd orders, and the Stokeslet or
 //    stresslet pair sum of Thm 1 is accumulated against the cached rotated geometry;
-//  * Fourier form: the same double sum reassociated exactly,
-//        sum_{j,k} M_jk rho'_jk = sum_j sum_m c_m Re[ Mhat_jm h_m(theta_j) ],   c_0 = 1, c_m = 2,
-//    with M_jk the 3x3 kernel weight of the quadrature point (w^s_j K(x0 - x') W'/sin theta_j, geometry
-//    only) and Mhat_jm = sum_k M_jk e^{i m phi_k} its phi transform, built once per geometry.
+//  * projected form: the same double sum reassociated exactly,
+//        sum_{j,k} M_jk rho'_jk = sum_j sum_m c_m Re[ Mhat_jm h_m(theta_j) ]
+//                               = sum_{n, m >= 0} Re[ Q_nm rho'_n^m ],   Q_nm = c_m sum_j Mhat_jm P~_n^m(cos theta_j),
+//    with c_0 = 1, c_m = 2, M_jk the 3x3 kernel weight of the quadrature point
+//    (w^s_j K(x0 - x') W'/sin theta_j, geometry only) and Mhat_jm = sum_k M_jk e^{i m phi_k} its phi
+//    transform.  Q (6 complex entries per (n, m) and target) is built once per geometry; an apply
+//    then rotates the density and contracts it with Q, without the Legendre step.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -202,22 +205,35 @@ __global__ void __launch_bounds__(256) k_self_direct(
   write_target<R>(s0, s1, s2, wts, val_off, vals, ld, tl, ng);
 }
 
-// ---- Fourier form: set-up of Mhat (FP64, optional FP32 copy) ----
-// Mhat[t][e][ri][m][j], e over (xx, yy, zz, xy, xz, yz), ri = real / imaginary part.
+// ---- projected form: set-up of Q (FP64, optional FP32 copy) ----
+// For each target, Q[t][e][ri][tri(n,m)] = c_m sum_j Mhat_{e,jm} P~_n^m(cos theta_j), with
+// Mhat_{e,jm} = sum_k M_{e,jk} e^{i m phi_k} the phi transform of entry e of the 3x3 kernel weight
+// over (xx, yy, zz, xy, xz, yz), ri = real / imaginary part, c_0 = 1 and c_m = 2.  Latitudes are
+// processed kDftJ at a time: kernel weights, their phi transform, then the Legendre projection,
+// accumulated in shared memory.
 constexpr int kDftJ = 3;
 
+__device__ inline int tri_index_degree(int it) {
+  int n = (int)((sqrt(8.0 * it + 1.0) - 1.0) * 0.5);
+  while ((n + 1) * (n + 2) / 2 <= it) ++n;
+  while (n * (n + 1) / 2 > it) --n;
+  return n;
+}
+
 template <int KIND>
-__global__ void __launch_bounds__(256) k_kernel_dft(const double* __restrict__ cache, int pq, int p,
-                                                    const double* __restrict__ cs, double* __restrict__ M64,
-                                                    float* __restrict__ M32) {
-  __shared__ double sm[kDftJ * 6 * 2 * 132];  // [jj][e][S/D][k < half] for half <= 132
+__global__ void __launch_bounds__(256) k_kernel_proj(const double* __restrict__ cache, int pq, int p,
+                                                     const double* __restrict__ cs, const double* __restrict__ T0,
+                                                     double* __restrict__ Q64, float* __restrict__ Q32) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long t = blockIdx.x;
   const int nq_j = pq + 1, nk = 2 * pq + 2, half = pq + 1;
+  const int ntri = (p + 1) * (p + 2) / 2;
+  double* sg = reinterpret_cast<double*>(smem_raw);  // [jj][e][even/odd][k < half]
+  double* sm = sg + kDftJ * 12 * half;               // [jj][12][m]
+  double* sq = sm + kDftJ * 12 * (p + 1);            // [12][tri]
   const long long nq = (long long)nq_j * nk;
   const double* geo = cache + t * 7 * nq;
-  const long long plane = (long long)nq_j * (p + 1);
-  double* o64 = M64 + t * 12 * plane;
-  float* o32 = M32 ? M32 + t * 12 * plane : nullptr;
+  for (int i = threadIdx.x; i < 12 * ntri; i += blockDim.x) sq[i] = 0.0;
   for (int j0 = 0; j0 < nq_j; j0 += kDftJ) {
     const int jn = min(kDftJ, nq_j - j0);
     for (int i = threadIdx.x; i < jn * half; i += blockDim.x) {
@@ -247,8 +263,8 @@ __global__ void __launch_bounds__(256) k_kernel_dft(const double* __restrict__ c
       }
 #pragma unroll
       for (int e = 0; e < 6; ++e) {
-        sm[((jj * 6 + e) * 2 + 0) * 132 + k] = Mv[0][e] + Mv[1][e];  // even orders
-        sm[((jj * 6 + e) * 2 + 1) * 132 + k] = Mv[0][e] - Mv[1][e];  // odd orders
+        sg[((jj * 6 + e) * 2 + 0) * half + k] = Mv[0][e] + Mv[1][e];  // even orders
+        sg[((jj * 6 + e) * 2 + 1) * half + k] = Mv[0][e] - Mv[1][e];  // odd orders
       }
     }
     __syncthreads();
@@ -256,90 +272,85 @@ __global__ void __launch_bounds__(256) k_kernel_dft(const double* __restrict__ c
       const int m = i % (p + 1);
       const int r = i / (p + 1);
       const int e = r % 6, jj = r / 6;
-      const double* src = sm + ((jj * 6 + e) * 2 + (m & 1)) * 132;
+      const double* src = sg + ((jj * 6 + e) * 2 + (m & 1)) * half;
       double re = 0, im = 0;
       for (int k = 0; k < half; ++k) {
         re += src[k] * cs[((long long)m * nk + k) * 2];
         im += src[k] * cs[((long long)m * nk + k) * 2 + 1];
       }
-      const long long o = (long long)m * nq_j + (j0 + jj);  // layout [plane][m][j]
-      o64[(2 * e) * plane + o] = re;
-      o64[(2 * e + 1) * plane + o] = im;
-      if (o32) {
-        o32[(2 * e) * plane + o] = (float)re;
-        o32[(2 * e + 1) * plane + o] = (float)im;
+      sm[(jj * 12 + 2 * e) * (p + 1) + m] = re;
+      sm[(jj * 12 + 2 * e + 1) * (p + 1) + m] = im;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < ntri; it += blockDim.x) {
+      const int n = tri_index_degree(it);
+      const int m = it - n * (n + 1) / 2;
+      const double* Tn = T0 + leg_row(p, m, n, nq_j) + j0;
+      double acc[12];
+#pragma unroll
+      for (int e = 0; e < 12; ++e) acc[e] = sq[e * ntri + it];
+      for (int jj = 0; jj < jn; ++jj) {
+        const double P = Tn[jj];
+#pragma unroll
+        for (int e = 0; e < 12; ++e) acc[e] += sm[(jj * 12 + e) * (p + 1) + m] * P;
       }
+#pragma unroll
+      for (int e = 0; e < 12; ++e) sq[e * ntri + it] = acc[e];
     }
     __syncthreads();
   }
-}
-
-// ---- Fourier form: apply ----
-// Shared memory (R = float or double): rcA, rcB [tri(n,m)][6], the rotated coefficients of the two
-// targets of a pair, (Re, Im) x 3 components at (n, m >= 0) with tri(n,m) = n(n+1)/2 + m; g4
-// [(p+1)^2][4], the phase-shifted input coefficients with the three components interleaved.
-// The Legendre step evaluates each Gauss-node pair (t_i, t_{pq-i} = -t_i) at once:
-// P~_n^m(-t) = (-1)^(n+m) P~_n^m(t), so with E (n+m even) and O (n+m odd) partial sums,
-// h(t_i) = E + O and h(-t_i) = E - O.
-template <typename R>
-__device__ inline int tri_(int n, int m) {
-  return n * (n + 1) / 2 + m;
-}
-
-// 128-bit vector of R for shared-memory loads (float4 / double2).
-template <typename R>
-struct Vec4;
-template <>
-struct Vec4<float> {
-  typedef float4 T;
-  static constexpr int n = 4;
-};
-template <>
-struct Vec4<double> {
-  typedef double2 T;
-  static constexpr int n = 2;
-};
-
-// Contraction of h_m(theta_j) (Re, Im x 3 components) with the Fourier factors at (m, j).
-template <typename R>
-__device__ inline void contract(const R* __restrict__ M, long long plane, long long o, R cm, const R* h, R& s0,
-                                R& s1, R& s2) {
-  R Mr[6], Mi[6];
-#pragma unroll
-  for (int e = 0; e < 6; ++e) {
-    Mr[e] = M[(2 * e) * plane + o];
-    Mi[e] = M[(2 * e + 1) * plane + o];
+  double* o64 = Q64 + t * 12 * ntri;
+  float* o32 = Q32 ? Q32 + t * 12 * ntri : nullptr;
+  for (int i = threadIdx.x; i < 12 * ntri; i += blockDim.x) {
+    const int it = i % ntri;
+    const int n = tri_index_degree(it);
+    const double v = (it == n * (n + 1) / 2 ? 1.0 : 2.0) * sq[i];  // c_m: m = 0 at the start of degree n
+    o64[i] = v;
+    if (o32) o32[i] = (float)v;
   }
-  // rows of the symmetric matrix: (xx xy xz), (xy yy yz), (xz yz zz); h = (Re, Im) x 3 components
-  s0 += cm * (Mr[0] * h[0] + Mr[3] * h[2] + Mr[4] * h[4] - Mi[0] * h[1] - Mi[3] * h[3] - Mi[4] * h[5]);
-  s1 += cm * (Mr[3] * h[0] + Mr[1] * h[2] + Mr[5] * h[4] - Mi[3] * h[1] - Mi[1] * h[3] - Mi[5] * h[5]);
-  s2 += cm * (Mr[4] * h[0] + Mr[5] * h[2] + Mr[2] * h[4] - Mi[4] * h[1] - Mi[5] * h[3] - Mi[2] * h[5]);
 }
 
-// Target pairs: the targets (theta_a, phi_b) and (theta_a, phi_b + pi) share the latitude's Wigner
-// blocks, and e^{i m (phi + pi)} = (-1)^m e^{i m phi}, so even-m and odd-m partial sums E, O of one
-// pass over the blocks give the rotated coefficients of both (E + O and E - O).  The pair also
-// shares every Legendre table load.  rc is stored with 6 entries per (n, m): (Re, Im) x 3 components.
+// ---- projected form: apply ----
+// One block per target quadruple: the latitudes theta_a and pi - theta_a (Gauss nodes t and -t) at the
+// longitudes phi_b and phi_b + pi.  One pass over latitude a's real Wigner blocks (C for the real
+// parts, S for the imaginary parts, column m the input order) gives the even-m and odd-m partial sums
+// E and O of every rotated coefficient (n, m'), and the four targets follow exactly:
+//   phi_b + pi:     e^{i m (phi + pi)} = (-1)^m e^{i m phi}                    -> E - O
+//   pi - theta_a:   d^n_{m m'}(pi - beta) = (-1)^(n + m') d^n_{-m m'}(beta), so
+//                   C' = (-1)^(n + m' + m) C and S' = -(-1)^(n + m' + m) S      -> +-(-1)^(n + m') (E -+ O)
+// Each rotated coefficient is contracted at once with the targets' projected kernel factors Q
+// (real parts with the real planes, imaginary parts with minus the imaginary planes), so rotated
+// coefficients never leave registers.  The middle latitude of an odd node count (t = 0) pairs with
+// itself and its block has two targets.  Shared memory: g4 [(p+1)^2][4], the phase-shifted input
+// coefficients e^{i m phi_b} rho_n^m with the three components interleaved.
+constexpr int kSelfThreads = 256;
+
+// acc += S v for the symmetric 3x3 matrix S with entries (xx, yy, zz, xy, xz, yz) at planes q[0..5]
+template <typename R>
+__device__ inline void sym_mul_add(const R* q, const R* v, R sgn, R* acc) {
+  acc[0] += sgn * (q[0] * v[0] + q[3] * v[1] + q[4] * v[2]);
+  acc[1] += sgn * (q[3] * v[0] + q[1] * v[1] + q[5] * v[2]);
+  acc[2] += sgn * (q[4] * v[0] + q[5] * v[1] + q[2] * v[2]);
+}
+
 template <typename R, typename CT>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_self_fourier(
-    const CT* __restrict__ dens, const long long* __restrict__ foff3, int p, int pq, const R* __restrict__ wblk,
-    long long wstride, const R* __restrict__ ph, const R* __restrict__ T0, const R* __restrict__ Mhat, int ng,
-    const double* __restrict__ wts, const long long* __restrict__ val_off, double* __restrict__ vals) {
+__global__ void __launch_bounds__(kSelfThreads, 2) k_self_proj(
+    const CT* __restrict__ dens, const long long* __restrict__ foff3, int p, const R* __restrict__ wblk,
+    long long wstride, const R* __restrict__ ph, const R* __restrict__ Q, int ng, const double* __restrict__ wts,
+    const long long* __restrict__ val_off, double* __restrict__ vals) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ R red[kSelfThreads / 32][12];
   const int ntri = (p + 1) * (p + 2) / 2;
   const int nc = (p + 1) * (p + 1);
-  // rc [tri(n,m)][12]: target A (Re, Im) x 3 components, then target B, 16-byte aligned records
-  R* rc = reinterpret_cast<R*>(smem_raw);
-  R* g4 = rc + 12 * ntri;                   // [(p+1)^2][4]: three components interleaved, padded
-  const int half_b = p + 1;                 // targets per latitude pair group
-  const long long tp = blockIdx.x;          // target pair
-  const long long ld = tp / (ng / 2);
-  const int r = (int)(tp - ld * (ng / 2));
-  const int a = r / half_b, b = r - a * half_b;
-  const int nb = 2 * p + 2;
-  const int tlA = a * nb + b, tlB = tlA + half_b;
-  const long long tA = ld * ng + tlA, tB = ld * ng + tlB;
-  typedef typename Vec4<R>::T V4;
+  R* g4 = reinterpret_cast<R*>(smem_raw);  // [(p+1)^2][4]
+  const int hb = p + 1, nb = 2 * p + 2, na2 = (p + 2) / 2;
+  const long long bid = blockIdx.x;
+  const long long ld = bid / ((long long)na2 * hb);
+  const int r = (int)(bid - ld * na2 * hb);
+  const int a = r / hb, b = r - a * hb;
+  const int a2 = p - a;
+  const bool quad = a2 != a;
+  const int tlA = a * nb + b, tlC = a2 * nb + b;  // targets A, B = A + hb, C, D = C + hb
   // stage 0: g = e^{i m phi_b} rho_n^m
   for (int i = threadIdx.x; i < 3 * nc; i += blockDim.x) {
     const int c = i / nc, rr = i - c * nc;
@@ -354,111 +365,106 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_self_fourier(
     if (m > 0) g4[(n * (n + 1) - m) * 4 + c] = fr * si + fi * co;
   }
   __syncthreads();
-  // stage 1: rotation of both targets in one pass (even / odd orders)
+  // stages 1-2: rotation (even / odd input orders) and contraction, per rotated coefficient
   const R* blk = wblk + (long long)a * wstride;
+  const long long qstride = 12 * (long long)ntri;
+  const R* QA = Q + (ld * ng + tlA) * qstride;
+  const R* QC = Q + (ld * ng + tlC) * qstride;
+  const R* Qk_[4] = {QA, QA + hb * qstride, QC, QC + hb * qstride};
+  R acc[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0;
   for (int i = threadIdx.x; i < nc; i += blockDim.x) {
     const int n = degree_of(i);
     const int o = i - n * n;
     const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
     const R* g = g4 + n * (n + 1) * 4;
-    R e0 = 0, e1 = 0, e2 = 0, d0 = 0, d1 = 0, d2 = 0;
-    if (o <= n) {
+    const bool re = o <= n;
+    const int mo = re ? o : o - n;  // output order m'
+    const int t = n * (n + 1) / 2 + mo;
+    const int ri = re ? 0 : 1;      // real or imaginary planes of Q
+    R q[4][6];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k < 2 || quad) {
+        const R* Qk = Qk_[k] + t;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) q[k][e] = Qk[(2 * e + ri) * (long long)ntri];
+      }
+    }
+    R E[3] = {0, 0, 0}, O[3] = {0, 0, 0};
+    if (re) {
       const R* Cc = blk + boff + o;
       for (int m = 0; m <= n; m += 2) {
         const R cv = Cc[(long long)m * (n + 1)];
         const R* gm = g + 4 * m;
-        e0 += cv * gm[0];
-        e1 += cv * gm[1];
-        e2 += cv * gm[2];
+        E[0] += cv * gm[0];
+        E[1] += cv * gm[1];
+        E[2] += cv * gm[2];
       }
       for (int m = 1; m <= n; m += 2) {
         const R cv = Cc[(long long)m * (n + 1)];
         const R* gm = g + 4 * m;
-        d0 += cv * gm[0];
-        d1 += cv * gm[1];
-        d2 += cv * gm[2];
+        O[0] += cv * gm[0];
+        O[1] += cv * gm[1];
+        O[2] += cv * gm[2];
       }
-      R* q = rc + tri_<R>(n, o) * 12;
-      q[0] = e0 + d0, q[2] = e1 + d1, q[4] = e2 + d2;
-      q[6] = e0 - d0, q[8] = e1 - d1, q[10] = e2 - d2;
-      if (o == 0) q[1] = q[3] = q[5] = q[7] = q[9] = q[11] = 0;
     } else {
-      const int mp = o - n;
-      const R* Sc = blk + boff + (long long)(n + 1) * (n + 1) + (mp - 1);
+      const R* Sc = blk + boff + (long long)(n + 1) * (n + 1) + (mo - 1);
       for (int m = 2; m <= n; m += 2) {
         const R sv = Sc[(long long)(m - 1) * n];
         const R* gm = g - 4 * m;
-        e0 += sv * gm[0];
-        e1 += sv * gm[1];
-        e2 += sv * gm[2];
+        E[0] += sv * gm[0];
+        E[1] += sv * gm[1];
+        E[2] += sv * gm[2];
       }
       for (int m = 1; m <= n; m += 2) {
         const R sv = Sc[(long long)(m - 1) * n];
         const R* gm = g - 4 * m;
-        d0 += sv * gm[0];
-        d1 += sv * gm[1];
-        d2 += sv * gm[2];
+        O[0] += sv * gm[0];
+        O[1] += sv * gm[1];
+        O[2] += sv * gm[2];
       }
-      R* q = rc + tri_<R>(n, mp) * 12;
-      q[1] = e0 + d0, q[3] = e1 + d1, q[5] = e2 + d2;
-      q[7] = e0 - d0, q[9] = e1 - d1, q[11] = e2 - d2;
+    }
+    R vp[3], vm[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      vp[c] = E[c] + O[c];
+      vm[c] = E[c] - O[c];
+    }
+    // real parts enter with +Q_re, imaginary parts with -Q_im.  Latitude pi - theta_a carries
+    // (-1)^(n + m') on the real and -(-1)^(n + m') on the imaginary parts, so its sign is
+    // (-1)^(n + m') in both cases.
+    const R s0 = re ? (R)1 : (R)-1;
+    const R s2 = ((n + mo) & 1) ? (R)-1 : (R)1;
+    sym_mul_add<R>(q[0], vp, s0, acc[0]);
+    sym_mul_add<R>(q[1], vm, s0, acc[1]);
+    if (quad) {
+      sym_mul_add<R>(q[2], vm, s2, acc[2]);
+      sym_mul_add<R>(q[3], vp, s2, acc[3]);
     }
   }
+  // block reduction of the 12 sums
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      for (int off = 16; off > 0; off >>= 1) acc[k][c] += __shfl_down_sync(0xffffffffu, acc[k][c], off);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) red[w][k * 3 + c] = acc[k][c];
   __syncthreads();
-  // stages 2-3: Legendre step per (order m, node pair i) for both targets, contracted at once
-  const int nq_j = pq + 1;
-  const int npair = (nq_j + 1) / 2;
-  const long long plane = (long long)nq_j * (p + 1);
-  const R* MA = Mhat + tA * 12 * plane;
-  const R* MB = Mhat + tB * 12 * plane;
-  R sa0 = 0, sa1 = 0, sa2 = 0, sb0 = 0, sb1 = 0, sb2 = 0;
-  const int nitem = (p + 1) * npair;
-  constexpr int NV = 12 / Vec4<R>::n;  // vector loads per rc record
-  for (int it = threadIdx.x; it < nitem; it += blockDim.x) {
-    const int m = it / npair, i = it - m * npair;
-    R e[12], o[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) e[k] = o[k] = 0;
-    const R* Tm = T0 + leg_row(p, m, m, nq_j) + i;
-    for (int n = m; n <= p; n += 2) {  // n + m even
-      const V4* q = reinterpret_cast<const V4*>(rc + tri_<R>(n, m) * 12);
-      const R tv = Tm[(long long)(n - m) * nq_j];
-      R v[12];
-#pragma unroll
-      for (int u = 0; u < NV; ++u) *reinterpret_cast<V4*>(v + u * Vec4<R>::n) = q[u];
-#pragma unroll
-      for (int k = 0; k < 12; ++k) e[k] += v[k] * tv;
-    }
-    for (int n = m + 1; n <= p; n += 2) {  // n + m odd
-      const V4* q = reinterpret_cast<const V4*>(rc + tri_<R>(n, m) * 12);
-      const R tv = Tm[(long long)(n - m) * nq_j];
-      R v[12];
-#pragma unroll
-      for (int u = 0; u < NV; ++u) *reinterpret_cast<V4*>(v + u * Vec4<R>::n) = q[u];
-#pragma unroll
-      for (int k = 0; k < 12; ++k) o[k] += v[k] * tv;
-    }
-    const R cm = m == 0 ? (R)1 : (R)2;
-    const int jh = pq - i;
-    R hv[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) hv[k] = e[k] + o[k];
-    contract<R>(MA, plane, (long long)m * nq_j + i, cm, hv, sa0, sa1, sa2);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) hv[k] = e[6 + k] + o[6 + k];
-    contract<R>(MB, plane, (long long)m * nq_j + i, cm, hv, sb0, sb1, sb2);
-    if (jh != i) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) hv[k] = e[k] - o[k];
-      contract<R>(MA, plane, (long long)m * nq_j + jh, cm, hv, sa0, sa1, sa2);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) hv[k] = e[6 + k] - o[6 + k];
-      contract<R>(MB, plane, (long long)m * nq_j + jh, cm, hv, sb0, sb1, sb2);
-    }
+  const int nt = quad ? 4 : 2;
+  if (threadIdx.x < 3 * nt) {
+    R v = 0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) v += red[ww][threadIdx.x];
+    const int k = threadIdx.x / 3, c = threadIdx.x - 3 * k;
+    const int tl = (k < 2 ? tlA : tlC) + (k & 1) * hb;
+    vals[val_off[ld] + (long long)c * ng + tl] = wts[ld] * (double)v;
   }
-  write_target<R>(sa0, sa1, sa2, wts, val_off, vals, ld, tlA, ng);
-  __syncthreads();
-  write_target<R>(sb0, sb1, sb2, wts, val_off, vals, ld, tlB, ng);
 }
 
 // Latitudes per chunk of the direct kernel within a shared-memory budget.
@@ -494,31 +500,39 @@ int launch_self_direct(int kind, const double* dens, const long long* foff3, lon
   return BIE_OK;
 }
 
-int launch_kernel_dft(int kind, const double* cache, long long ntarget, int p, int pq, const double* cs, double* M64,
-                      float* M32, cudaStream_t s) {
+size_t kernel_proj_smem(int p, int pq) {
+  return sizeof(double) * ((size_t)kDftJ * 12 * (pq + 1) + (size_t)kDftJ * 12 * (p + 1) + 6 * (size_t)(p + 1) * (p + 2));
+}
+
+int launch_kernel_proj(int kind, const double* cache, long long ntarget, int p, int pq, const double* cs,
+                       const double* T0, double* Q64, float* Q32, cudaStream_t s) {
   if (ntarget == 0) return BIE_OK;
-  if (pq + 1 > 132 || ntarget > 0x7fffffffLL) return BIE_EINVAL;
-  if (kind == 0)
-    k_kernel_dft<0><<<(unsigned)ntarget, 256, 0, s>>>(cache, pq, p, cs, M64, M32);
-  else
-    k_kernel_dft<1><<<(unsigned)ntarget, 256, 0, s>>>(cache, pq, p, cs, M64, M32);
+  if (ntarget > 0x7fffffffLL) return BIE_EINVAL;
+  const size_t smem = kernel_proj_smem(p, pq);
+  if (smem > 227 * 1024) {
+    set_error("degree too large for the projected self form (shared memory)");
+    return BIE_ENOTSUP;
+  }
+  auto kern = kind == 0 ? k_kernel_proj<0> : k_kernel_proj<1>;
+  if (smem > 48 * 1024) BIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(unsigned)ntarget, 256, smem, s>>>(cache, pq, p, cs, T0, Q64, Q32);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
 
 template <typename R, typename CT>
-int launch_self_fourier(const CT* dens, const long long* foff3, long long ndrop, int p, int pq, const R* wblk,
-                        long long wstride, const R* ph, const R* T0, const R* Mhat, const double* wts,
-                        const long long* val_off, double* vals, cudaStream_t s) {
+int launch_self_proj(const CT* dens, const long long* foff3, long long ndrop, int p, const R* wblk, long long wstride,
+                     const R* ph, const R* Q, const double* wts, const long long* val_off, double* vals,
+                     cudaStream_t s) {
   const int ng = (p + 1) * (2 * p + 2);
-  const long long nt = ndrop * ng;
-  if (nt == 0) return BIE_OK;
-  if (nt > 0x7fffffffLL) return BIE_EINVAL;
-  const size_t smem = sizeof(R) * (12 * (size_t)(p + 1) * (p + 2) / 2 + 4 * (size_t)(p + 1) * (p + 1));
-  auto kern = k_self_fourier<R, CT>;
+  const long long nblk = ndrop * ((p + 2) / 2) * (p + 1);
+  if (nblk == 0) return BIE_OK;
+  if (nblk > 0x7fffffffLL) return BIE_EINVAL;
+  const size_t smem = sizeof(R) * 4 * (size_t)(p + 1) * (p + 1);
+  auto kern = k_self_proj<R, CT>;
   if (smem > 48 * 1024) BIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<(unsigned)(nt / 2), 256, smem, s>>>(dens, foff3, p, pq, wblk, wstride, ph, T0, Mhat, ng, wts, val_off, vals);
+  kern<<<(unsigned)nblk, kSelfThreads, smem, s>>>(dens, foff3, p, wblk, wstride, ph, Q, ng, wts, val_off, vals);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
@@ -530,12 +544,11 @@ template int launch_self_direct<double>(int, const double*, const long long*, lo
 template int launch_self_direct<float>(int, const double*, const long long*, long long, int, int, const float*,
                                        long long, const float*, const float*, const float*, const float*,
                                        const double*, const long long*, double*, size_t, cudaStream_t);
-template int launch_self_fourier<double, double>(const double*, const long long*, long long, int, int,
-                                                 const double*, long long, const double*, const double*,
-                                                 const double*, const double*, const long long*, double*,
-                                                 cudaStream_t);
-template int launch_self_fourier<float, float>(const float*, const long long*, long long, int, int, const float*,
-                                               long long, const float*, const float*, const float*, const double*,
-                                               const long long*, double*, cudaStream_t);
+template int launch_self_proj<double, double>(const double*, const long long*, long long, int, const double*,
+                                              long long, const double*, const double*, const double*,
+                                              const long long*, double*, cudaStream_t);
+template int launch_self_proj<float, float>(const float*, const long long*, long long, int, const float*, long long,
+                                            const float*, const float*, const double*, const long long*, double*,
+                                            cudaStream_t);
 
 }  // namespace bie

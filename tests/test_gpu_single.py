@@ -17,7 +17,7 @@ FP64_TOL = 1e-12
 MIXED_TOL = 2e-5
 
 
-@pytest.fixture(scope="module", params=[False, True], ids=["fourier", "direct"])
+@pytest.fixture(scope="module", params=[False, True], ids=["projected", "direct"])
 def ctx(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
