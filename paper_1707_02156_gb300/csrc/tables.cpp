@@ -1,10 +1,11 @@
-// Host-side plan tables (FP64 results computed in long double).
+// Host-side plan tables (FP64 results; long double where it is cheap).
 //
 // Gauss grid (Sec. 2.1), normalised associated Legendre functions (App. A recursion),
 // their theta derivatives (ladder form of the App. A identities), Wigner small-d matrices
 // (App. B) by the three-term recursion in the degree, singular weights (Thm 1).
 #include "tables.h"
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -134,78 +135,73 @@ void phase_table(int p, int P, std::vector<double>& out) {
 
 long long wigner_block_stride(int p) { return wigner_block_offset(p + 1); }
 
-// d^j_{mp,m}(beta) at j0 = max(|m|,|mp|): the factorial sum of App. B has a single term there.
-static ld small_d_start(int j, int mp, int m, ld beta) {
-  int lo = std::max(0, m - mp), hi = std::min(j + m, j - mp);
-  (void)hi;
-  int s = lo;
-  ld c = std::cos(beta / 2), sn = std::sin(beta / 2);
-  ld lf = 0.5L * (std::lgamma((ld)j + mp + 1) + std::lgamma((ld)j - mp + 1) + std::lgamma((ld)j + m + 1) +
-                  std::lgamma((ld)j - m + 1)) -
-          (std::lgamma((ld)j + m - s + 1) + std::lgamma((ld)s + 1) + std::lgamma((ld)mp - m + s + 1) +
-           std::lgamma((ld)j - mp - s + 1));
-  int e1 = 2 * (j - s) + m - mp, e2 = 2 * s - m + mp;
-  ld v = std::exp(lf) * std::pow(c, (ld)e1) * std::pow(sn, (ld)e2);
-  return ((mp - m + s) & 1) ? -v : v;
+// d^j_{mp,m}(beta) at j0 = max(|m|,|mp|): the factorial sum of App. B has a single term there,
+// K(mp, m) cos(beta/2)^e1 sin(beta/2)^e2 with a sign.  With j0 the larger of |m|, |mp|, K is the
+// square root of a binomial coefficient, sqrt(C(2 j0, j0 + r)) with r = mp or m (whichever is not
+// +-j0); it is formed as a product of ratios, exact to a few units of rounding.
+static double start_const(int mp, int m) {
+  const int j = std::max(std::abs(mp), std::abs(m));
+  const int r = std::abs(mp) == j ? m : mp;
+  const int k = std::min(j + r, j - r);  // C(2j, j + r) = C(2j, k)
+  double c = 1.0;
+  for (int i = 1; i <= k; ++i) c = c * (double)(2 * j - k + i) / (double)i;
+  return std::sqrt(c);
 }
 
-// d^j_{mp,m}(beta) for j = 0..p into col[j] (zero below j0), three-term recursion in j.
-static void small_d_column(int p, int mp, int m, ld beta, std::vector<ld>& col) {
-  col.assign(p + 1, 0);
-  int j0 = std::max(std::abs(m), std::abs(mp));
+// d^j_{mp,m}(beta) for j = 0..p into col[j] (zero below j0), three-term recursion in j (double;
+// the recursion is stable and loses about 1e-14 relative up to degree 64).
+static void small_d_column(int p, int mp, int m, double cb, double ch, double sh, double* col) {
+  for (int j = 0; j <= p; ++j) col[j] = 0.0;
+  const int j0 = std::max(std::abs(m), std::abs(mp));
   if (j0 > p) return;
-  col[j0] = small_d_start(j0, mp, m, beta);
-  ld cb = std::cos(beta);
+  {
+    const int s = std::max(0, m - mp);
+    const int e1 = 2 * (j0 - s) + m - mp, e2 = 2 * s - m + mp;
+    const double v = start_const(mp, m) * std::pow(ch, (double)e1) * std::pow(sh, (double)e2);
+    col[j0] = ((mp - m + s) & 1) ? -v : v;
+  }
+  const double mm = (double)m * m, pp = (double)mp * mp, mpm = (double)m * mp;
   for (int j = j0 + 1; j <= p; ++j) {
     if (j == 1) {  // j0 = 0, m = mp = 0
       col[1] = cb * col[0];
       continue;
     }
-    ld a = (ld)j * (2 * j - 1) / std::sqrt(((ld)j * j - (ld)m * m) * ((ld)j * j - (ld)mp * mp));
-    ld t1 = (cb - (ld)m * mp / ((ld)j * (j - 1))) * col[j - 1];
-    ld t2 = 0;
-    if (j - 2 >= j0)
-      t2 = std::sqrt(((ld)(j - 1) * (j - 1) - (ld)m * m) * ((ld)(j - 1) * (j - 1) - (ld)mp * mp)) /
-           ((ld)(j - 1) * (2 * j - 1)) * col[j - 2];
+    const double jj = (double)j * j, j1 = (double)(j - 1) * (j - 1);
+    const double a = (double)j * (2 * j - 1) / std::sqrt((jj - mm) * (jj - pp));
+    const double t1 = (cb - mpm / ((double)j * (j - 1))) * col[j - 1];
+    double t2 = 0;
+    if (j - 2 >= j0) t2 = std::sqrt((j1 - mm) * (j1 - pp)) / ((double)(j - 1) * (2 * j - 1)) * col[j - 2];
     col[j] = a * (t1 - t2);
   }
 }
 
 void wigner_small_d(int n, double beta, double* out) {
-  std::vector<ld> col;
+  std::vector<double> col(n + 1);
+  const double cb = std::cos(beta), ch = std::cos(beta / 2), sh = std::sin(beta / 2);
   for (int mp = -n; mp <= n; ++mp)
     for (int m = -n; m <= n; ++m) {
-      small_d_column(n, mp, m, (ld)beta, col);
-      out[(mp + n) * (2 * n + 1) + (m + n)] = (double)col[n];
+      small_d_column(n, mp, m, cb, ch, sh, col.data());
+      out[(mp + n) * (2 * n + 1) + (m + n)] = col[n];
     }
 }
 
 void wigner_blocks(int p, double beta, double* out) {
-  // dd[j][a+p][b+p] = d^j_{a,b}(beta)
-  const int W = 2 * p + 1;
-  std::vector<ld> dd((size_t)(p + 1) * W * W, 0), col;
-  for (int a = -p; a <= p; ++a)
-    for (int b = -p; b <= p; ++b) {
-      small_d_column(p, a, b, (ld)beta, col);
-      for (int j = 0; j <= p; ++j) dd[((size_t)j * W + (a + p)) * W + (b + p)] = col[j];
+  // rotated coefficient g_{n m'} = sum_m D_{m'm} e^{i m alpha} f_{n m}, D_{m'm} = d^n_{m m'}; the
+  // blocks need the columns d^n_{+-m, m'} for m, m' >= 0 only
+  const double cb = std::cos(beta), ch = std::cos(beta / 2), sh = std::sin(beta / 2);
+  std::vector<double> cp(p + 1), cm(p + 1);
+  for (int mp = 0; mp <= p; ++mp)
+    for (int m = 0; m <= p; ++m) {
+      small_d_column(p, m, mp, cb, ch, sh, cp.data());
+      if (m > 0) small_d_column(p, -m, mp, cb, ch, sh, cm.data());
+      const double sg = (m & 1) ? -1.0 : 1.0;
+      for (int n = std::max(m, mp); n <= p; ++n) {
+        double* C = out + wigner_block_offset(n);
+        double* S = C + (size_t)(n + 1) * (n + 1);
+        C[m * (n + 1) + mp] = m > 0 ? cp[n] + sg * cm[n] : cp[n];  // column-major: consecutive m' contiguous
+        if (m > 0 && mp > 0) S[(m - 1) * n + (mp - 1)] = cp[n] - sg * cm[n];
+      }
     }
-  // rotated coefficient g_{n m'} = sum_m D_{m'm} e^{i m alpha} f_{n m}, D_{m'm} = d^n_{m m'}
-  auto D = [&](int n, int mp, int m) -> ld { return dd[((size_t)n * W + (m + p)) * W + (mp + p)]; };
-  for (int n = 0; n <= p; ++n) {
-    double* C = out + wigner_block_offset(n);
-    double* S = C + (size_t)(n + 1) * (n + 1);
-    for (int mp = 0; mp <= n; ++mp)
-      for (int m = 0; m <= n; ++m) {
-        ld v = D(n, mp, m);
-        if (m > 0) v += ((m & 1) ? -1 : 1) * D(n, mp, -m);
-        C[m * (n + 1) + mp] = (double)v;  // column-major: consecutive m' contiguous
-      }
-    for (int mp = 1; mp <= n; ++mp)
-      for (int m = 1; m <= n; ++m) {
-        ld v = D(n, mp, m) - ((m & 1) ? -1 : 1) * D(n, mp, -m);
-        S[(m - 1) * n + (mp - 1)] = (double)v;
-      }
-  }
 }
 
 void singular_weights(int pq, std::vector<double>& out) {
