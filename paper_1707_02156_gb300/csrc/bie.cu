@@ -1221,6 +1221,177 @@ __global__ void k_add_comb(double* __restrict__ x, const double* __restrict__ V,
   x[i] = t;
 }
 
+// ---- fused Krylov kernels: each block owns one contiguous slice of the vectors; dot products are
+// reduced per block, then the last block to finish (threadfence + counter) adds the per-block sums
+// in block order, so every result is deterministic.
+constexpr int kKryThreads = 256;
+constexpr int kKryGroup = 4;  // vectors reduced together
+
+__device__ inline void kry_slice(long long n, long long* x0, long long* x1) {
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  *x0 = (long long)blockIdx.x * chunk;
+  *x1 = min(n, *x0 + chunk);
+}
+
+// partial[i][block] = V_i . w over the block's slice for i < nv (V_nv = w itself when with_norm)
+__device__ void kry_block_dots(const double* __restrict__ V, long long ldv, const double* __restrict__ w, int nv,
+                               bool with_norm, long long x0, long long x1, double* __restrict__ partial) {
+  __shared__ double sh[kKryThreads / 32][kKryGroup];
+  const int nt = nv + (with_norm ? 1 : 0);
+  for (int i0 = 0; i0 < nt; i0 += kKryGroup) {
+    double a[kKryGroup];
+#pragma unroll
+    for (int g = 0; g < kKryGroup; ++g) a[g] = 0;
+    for (long long x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+      const double wx = w[x];
+#pragma unroll
+      for (int g = 0; g < kKryGroup; ++g) {
+        const int i = i0 + g;
+        if (i < nv) a[g] += V[(long long)i * ldv + x] * wx;
+        else if (i == nv && with_norm) a[g] += wx * wx;
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < kKryGroup; ++g)
+      for (int o = 16; o > 0; o >>= 1) a[g] += __shfl_down_sync(0xffffffffu, a[g], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+      for (int g = 0; g < kKryGroup; ++g) sh[threadIdx.x >> 5][g] = a[g];
+    __syncthreads();
+    if (threadIdx.x < kKryGroup && i0 + (int)threadIdx.x < nt) {
+      double t = 0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q][threadIdx.x];
+      partial[(long long)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// true in the last block to finish; the counter is reset for the next launch
+__device__ inline bool kry_last_block(unsigned* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(counter, 1u);
+    last = t == gridDim.x - 1;
+    if (last) *counter = 0;
+  }
+  __syncthreads();
+  return last;
+}
+
+// out[i] = sum over blocks of partial[i][b], b in order (i < nt), by the last block
+__device__ inline void kry_finish(const double* partial, int nt, double* out) {
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+    double t = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(partial + (long long)i * gridDim.x + b);
+    out[i] = t;
+  }
+}
+
+// w = (lambda + 1) u - d (system operator of Eq. main_eq), then h = V_i . w for i <= k
+__global__ void __launch_bounds__(kKryThreads) k_kry_sysop_dots(const double* __restrict__ lam,
+                                                                const double* __restrict__ u,
+                                                                const double* __restrict__ d, double* __restrict__ w,
+                                                                const double* __restrict__ V, long long n, int k,
+                                                                double* __restrict__ partial, unsigned* counter,
+                                                                double* __restrict__ h) {
+  long long x0, x1;
+  kry_slice(n, &x0, &x1);
+  for (long long x = x0 + threadIdx.x; x < x1; x += blockDim.x) w[x] = (lam[x] + 1.0) * u[x] - d[x];
+  __syncthreads();
+  kry_block_dots(V, n, w, k + 1, false, x0, x1, partial);
+  if (kry_last_block(counter)) kry_finish(partial, k + 1, h);
+}
+
+// w -= V h_prev (i <= k), then h = V_i . w for i <= k and h[k+1] = w . w
+__global__ void __launch_bounds__(kKryThreads) k_kry_sub_dots(double* __restrict__ w, const double* __restrict__ V,
+                                                              long long n, int k, const double* __restrict__ hprev,
+                                                              double* __restrict__ partial, unsigned* counter,
+                                                              double* __restrict__ h) {
+  long long x0, x1;
+  kry_slice(n, &x0, &x1);
+  for (long long x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+    double t = w[x];
+    for (int i = 0; i <= k; ++i) t -= hprev[i] * V[(long long)i * n + x];
+    w[x] = t;
+  }
+  __syncthreads();
+  kry_block_dots(V, n, w, k + 1, true, x0, x1, partial);
+  if (kry_last_block(counter)) kry_finish(partial, k + 2, h);
+}
+
+// w -= V h2 (i <= k); |w| by a direct sum; then, in the last block, the end of Arnoldi step k: the
+// Hessenberg column h1 + h2 with subdiagonal |w|, the previous Givens rotations, the new one, the
+// least-squares right-hand side gv, the residual estimate res[k] = |gv[k+1]| and scale = 1/|w|
+// (applied to w at the start of the next step).
+__global__ void __launch_bounds__(kKryThreads) k_kry_sub_tail(double* __restrict__ w, const double* __restrict__ V,
+                                                              long long n, int k, int m,
+                                                              const double* __restrict__ h1,
+                                                              const double* __restrict__ h2,
+                                                              double* __restrict__ partial, unsigned* counter,
+                                                              double* __restrict__ H, double* __restrict__ cs,
+                                                              double* __restrict__ sn, double* __restrict__ gv,
+                                                              double* __restrict__ scale, double* __restrict__ res) {
+  long long x0, x1;
+  kry_slice(n, &x0, &x1);
+  for (long long x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+    double t = w[x];
+    for (int i = 0; i <= k; ++i) t -= h2[i] * V[(long long)i * n + x];
+    w[x] = t;
+  }
+  __syncthreads();
+  kry_block_dots(V, n, w, 0, true, x0, x1, partial);
+  if (!kry_last_block(counter)) return;
+  if (threadIdx.x != 0) return;
+  double wn2 = 0;
+  for (int b = 0; b < (int)gridDim.x; ++b) wn2 += __ldcg(partial + b);
+  const double hn = sqrt(wn2);
+  for (int i = 0; i <= k; ++i) H[(long long)i * m + k] = h1[i] + h2[i];
+  for (int i = 0; i < k; ++i) {
+    const double a = H[(long long)i * m + k], b = H[(long long)(i + 1) * m + k];
+    H[(long long)i * m + k] = cs[i] * a + sn[i] * b;
+    H[(long long)(i + 1) * m + k] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = H[(long long)k * m + k];
+  const double den = hypot(a, hn);
+  cs[k] = den > 0 ? a / den : 1.0;
+  sn[k] = den > 0 ? hn / den : 0.0;
+  H[(long long)k * m + k] = den;
+  gv[k + 1] = -sn[k] * gv[k];
+  gv[k] = cs[k] * gv[k];
+  scale[0] = hn > 0 ? 1.0 / hn : 0.0;
+  res[k] = fabs(gv[k + 1]);
+}
+
+inline int kry_blocks(long long n) { return (int)std::max(1LL, std::min<long long>(120, (n + 255) / 256)); }
+
+// y = s * y with the scale read from the device
+__global__ void k_scale_dev(double* __restrict__ y, const double* __restrict__ scale, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] *= scale[0];
+}
+
+// start of a cycle: gv = (beta, 0, ..., 0), V_0 = r / beta
+__global__ void k_cycle_start(const double* __restrict__ r, double beta, double* __restrict__ v0, long long n,
+                              double* __restrict__ gv, int m) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v0[i] = r[i] / beta;
+  if (i <= m) gv[i] = i == 0 ? beta : 0.0;
+}
+
+// back substitution y = H^-1 gv on the leading k x k triangle (one thread)
+__global__ void k_backsub(const double* __restrict__ H, const double* __restrict__ gv, int k, int m,
+                          double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double t = gv[i];
+    for (int q = i + 1; q < k; ++q) t -= H[(long long)i * m + q] * y[q];
+    y[i] = t / H[(long long)i * m + i];
+  }
+}
+
 inline unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
@@ -1229,31 +1400,16 @@ struct Krylov {
   long long n = 0;
   int m = 0;
   DevBuf<double> V, w, tmp, partial, hdev, r, dx, t;
-  double* hpin = nullptr;  // pinned host copy of the Arnoldi coefficients
+  DevBuf<double> Hd, csd, snd, gvd, scale, resd, yd;  // Hessenberg, rotations, rhs, residual estimates
+  DevBuf<unsigned> counter;                              // last-block counter of the fused kernels
+  double* hpin = nullptr;  // pinned host copy of the residual estimates
   int hpin_n = 0;
+  std::vector<cudaEvent_t> ev;  // end of each Arnoldi step
   ~Krylov() {
     if (hpin) cudaFreeHost(hpin);
+    for (auto e : ev) cudaEventDestroy(e);
   }
 };
-
-// hout[i] = V_i . w for i < k (and hout[k] = w . w with with_norm), reduced on the device
-static int dots_dev(Krylov& K, const double* V, int k, const double* w, double* hout, bool with_norm,
-                    cudaStream_t s) {
-  dim3 grid(kRedBlocks, k);
-  k_multidot<<<grid, kRedThreads, 0, s>>>(V, K.n, w, K.n, k, K.partial.ptr);
-  count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
-  if (with_norm) {
-    k_multidot<<<dim3(kRedBlocks, 1), kRedThreads, 0, s>>>(w, K.n, w, K.n, 1, K.partial.ptr + (long long)k * kRedBlocks);
-    count_launch();
-    BIE_CUDA_TRY(cudaGetLastError());
-    ++k;
-  }
-  k_sum_partials<<<k, 128, 0, s>>>(K.partial.ptr, kRedBlocks, k, hout);
-  count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
-  return BIE_OK;
-}
 
 // out[i] = V_i . w for i < k; with with_norm, out[k] = w . w as well (one synchronisation)
 static int dots(Krylov& K, const double* V, int k, const double* w, std::vector<double>& out, cudaStream_t s,
@@ -1301,6 +1457,10 @@ static int sys_matvec(bie_ctx* ctx, const bie_geom* g, const double* u, double* 
 
 // Restarted GMRES (Sec. 7) with classical Gram-Schmidt and one re-orthogonalisation, FP64 Krylov
 // basis; the operator is applied at precision prec.  x holds the initial guess (zero if x_is_zero).
+// Each Arnoldi step runs as the operator apply and three fused kernels that end on the device
+// (k_kry_sub_tail); the host reads the residual estimate of step k - 1 after it has queued step k,
+// so the device never waits for the host between steps.  A cycle that converges at step k - 1 has
+// computed one more step than it uses.
 static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, double* x, bool x_is_zero, double tol,
                  int restart, int max_iter, Krylov& K, bie_solve_info* info, double* relres, cudaStream_t s) {
   const long long n = g->ncoef_total;
@@ -1320,7 +1480,6 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
     x_is_zero = xn == 0.0;
   }
   int it = 0;
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1);
   while (true) {
     // r = b - A x
     if (x_is_zero) {
@@ -1329,85 +1488,85 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
       BIE_TRY(sys_matvec(ctx, g, x, r, t2, prec, info, s));
       k_axpby<<<nblk(n), 256, 0, s>>>(1.0, b, -1.0, r, n);
       count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
+      BIE_CUDA_TRY(cudaGetLastError());
     }
     double beta;
     BIE_TRY(norm2(K, r, &beta, s));
     *relres = beta / bnorm;
     if (beta / bnorm <= tol || it >= max_iter) return beta / bnorm <= tol ? BIE_OK : BIE_ENOCONV;
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(gv.begin(), gv.end(), 0.0);
-    gv[0] = beta;
     double* V = K.V.ptr;
-    k_axpby<<<nblk(n), 256, 0, s>>>(1.0 / beta, r, 0.0, V, n);
+    k_cycle_start<<<nblk(std::max<long long>(n, m + 1)), 256, 0, s>>>(r, beta, V, n, K.gvd.ptr, m);
     count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
-    int k_used = 0;
-    for (int k = 0; k < m; ++k) {
+    BIE_CUDA_TRY(cudaGetLastError());
+    const int kmax = std::min(m, max_iter - it);
+    int k_used = -1;
+    double est = beta / bnorm;
+    for (int k = 0; k < kmax; ++k) {
+      double* vk = V + (long long)k * n;
       double* vk1 = V + (long long)(k + 1) * n;
-      BIE_TRY(sys_matvec(ctx, g, V + (long long)k * n, vk1, t2, prec, info, s));
-      // CGS with one re-orthogonalisation; both coefficient vectors stay on the device for the
-      // updates and come to the host together (one synchronisation per Arnoldi step)
+      if (k > 0) {  // normalisation of V_k, deferred from the previous step
+        k_scale_dev<<<nblk(n), 256, 0, s>>>(vk, K.scale.ptr, n);
+        count_launch();
+        BIE_CUDA_TRY(cudaGetLastError());
+      }
+      BIE_TRY(layer_apply(ctx, g, 1, vk, t2, prec, s));
+      if (prec == BIE_FP64)
+        info->applies_fp64++;
+      else
+        info->applies_mixed++;
+      // classical Gram-Schmidt with one re-orthogonalisation, three fused kernels
       double* h1 = K.hdev.ptr;
       double* h2d = K.hdev.ptr + (m + 2);
-      BIE_TRY(dots_dev(K, V, k + 1, vk1, h1, false, s));
-      k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, h1, k + 1, n);
+      const int nbk = kry_blocks(n);
+      k_kry_sysop_dots<<<nbk, kKryThreads, 0, s>>>(g->lamc.ptr, vk, t2, vk1, V, n, k, K.partial.ptr,
+                                                   K.counter.ptr, h1);
       count_launch();
       BIE_CUDA_TRY(cudaGetLastError());
-      // second pass with the squared norm: |w - V h2|^2 = |w|^2 - |h2|^2 for orthonormal V
-      BIE_TRY(dots_dev(K, V, k + 1, vk1, h2d, true, s));
-      k_sub_comb<<<nblk(n), 256, 0, s>>>(vk1, V, n, h2d, k + 1, n);
+      k_kry_sub_dots<<<nbk, kKryThreads, 0, s>>>(vk1, V, n, k, h1, K.partial.ptr, K.counter.ptr, h2d);
       count_launch();
       BIE_CUDA_TRY(cudaGetLastError());
-      BIE_CUDA_TRY(cudaMemcpyAsync(K.hpin, K.hdev.ptr, 2 * (m + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
-      BIE_CUDA_TRY(cudaStreamSynchronize(s));
-      const double* hc = K.hpin;
-      const double* hh2 = K.hpin + (m + 2);
-      double hsq = hh2[k + 1];
-      for (int i = 0; i <= k; ++i) {
-        H[(size_t)i * m + k] = hc[i] + hh2[i];
-        hsq -= hh2[i] * hh2[i];
+      k_kry_sub_tail<<<nbk, kKryThreads, 0, s>>>(vk1, V, n, k, m, h1, h2d, K.partial.ptr, K.counter.ptr,
+                                                 K.Hd.ptr, K.csd.ptr, K.snd.ptr, K.gvd.ptr, K.scale.ptr,
+                                                 K.resd.ptr);
+      count_launch();
+      BIE_CUDA_TRY(cudaGetLastError());
+      BIE_CUDA_TRY(cudaMemcpyAsync(K.hpin + k, K.resd.ptr + k, sizeof(double), cudaMemcpyDeviceToHost, s));
+      BIE_CUDA_TRY(cudaEventRecord(K.ev[k], s));
+      if (k >= 1) {  // step k - 1, read while step k runs
+        BIE_CUDA_TRY(cudaEventSynchronize(K.ev[k - 1]));
+        const double prev = est;
+        est = K.hpin[k - 1] / bnorm;
+        if (est <= tol) {
+          k_used = k;
+          break;
+        }
+        // when the residual's trend says step k is likely the last one, wait for it before
+        // queueing step k + 1 (instead of computing a step that would not be used)
+        const double rate = prev > 0 ? est / prev : 1.0;
+        if (k + 1 < kmax && est * rate <= 2.0 * tol) {
+          BIE_CUDA_TRY(cudaEventSynchronize(K.ev[k]));
+          est = K.hpin[k] / bnorm;
+          if (est <= tol) {
+            k_used = k + 1;
+            break;
+          }
+        }
       }
-      double hn;
-      if (hsq > 1e-8 * hh2[k + 1]) {
-        hn = std::sqrt(hsq);
-      } else {  // heavy cancellation: measure the norm directly
-        BIE_TRY(norm2(K, vk1, &hn, s));
-      }
-      H[(size_t)(k + 1) * m + k] = hn;
-      if (hn > 0) {
-        k_axpby<<<nblk(n), 256, 0, s>>>(1.0 / hn, vk1, 0.0, vk1, n);
-        count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
-      }
-      for (int i = 0; i < k; ++i) {
-        double a = H[(size_t)i * m + k], bb = H[(size_t)(i + 1) * m + k];
-        H[(size_t)i * m + k] = cs[i] * a + sn[i] * bb;
-        H[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * bb;
-      }
-      double a = H[(size_t)k * m + k], bb = H[(size_t)(k + 1) * m + k];
-      double den = std::hypot(a, bb);
-      cs[k] = a / den;
-      sn[k] = bb / den;
-      H[(size_t)k * m + k] = den;
-      H[(size_t)(k + 1) * m + k] = 0;
-      gv[k + 1] = -sn[k] * gv[k];
-      gv[k] = cs[k] * gv[k];
-      ++it;
-      info->iterations++;
-      k_used = k + 1;
-      if (std::fabs(gv[k + 1]) / bnorm <= tol || it >= max_iter || hn == 0) break;
     }
-    std::vector<double> y(k_used);
-    for (int i = k_used - 1; i >= 0; --i) {
-      double t = gv[i];
-      for (int q = i + 1; q < k_used; ++q) t -= H[(size_t)i * m + q] * y[q];
-      y[i] = t / H[(size_t)i * m + i];
+    if (k_used < 0) {
+      BIE_CUDA_TRY(cudaEventSynchronize(K.ev[kmax - 1]));
+      est = K.hpin[kmax - 1] / bnorm;
+      k_used = kmax;
     }
-    BIE_CUDA_TRY(cudaMemcpyAsync(K.hdev.ptr, y.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, s));
-    k_add_comb<<<nblk(n), 256, 0, s>>>(x, V, n, K.hdev.ptr, k_used, n);
+    (void)est;
+    it += k_used;
+    info->iterations += k_used;
+    k_backsub<<<1, 32, 0, s>>>(K.Hd.ptr, K.gvd.ptr, k_used, m, K.yd.ptr);
     count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
+    BIE_CUDA_TRY(cudaGetLastError());
+    k_add_comb<<<nblk(n), 256, 0, s>>>(x, V, n, K.yd.ptr, k_used, n);
+    count_launch();
+    BIE_CUDA_TRY(cudaGetLastError());
     x_is_zero = false;
   }
 }
@@ -1735,11 +1894,28 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
   BIE_TRY(K.tmp.alloc(3 * n));
   BIE_TRY(K.partial.alloc((size_t)kRedBlocks * (opts->restart + 2)));
   BIE_TRY(K.hdev.alloc(2 * (opts->restart + 2)));
-  if (K.hpin_n < 2 * (opts->restart + 2)) {
+  const int mr = opts->restart;
+  BIE_TRY(K.Hd.alloc((size_t)(mr + 1) * mr));
+  BIE_TRY(K.csd.alloc(mr));
+  BIE_TRY(K.snd.alloc(mr));
+  BIE_TRY(K.gvd.alloc(mr + 1));
+  BIE_TRY(K.scale.alloc(1));
+  BIE_TRY(K.resd.alloc(mr));
+  BIE_TRY(K.yd.alloc(mr));
+  if (!K.counter.ptr) {
+    BIE_TRY(K.counter.alloc(1));
+    BIE_CUDA_TRY(cudaMemset(K.counter.ptr, 0, sizeof(unsigned)));
+  }
+  if (K.hpin_n < mr) {
     if (K.hpin) cudaFreeHost(K.hpin);
     K.hpin = nullptr;
-    BIE_CUDA_TRY(cudaMallocHost(&K.hpin, 2 * (opts->restart + 2) * sizeof(double)));
-    K.hpin_n = 2 * (opts->restart + 2);
+    BIE_CUDA_TRY(cudaMallocHost(&K.hpin, mr * sizeof(double)));
+    K.hpin_n = mr;
+  }
+  while ((int)K.ev.size() < mr) {
+    cudaEvent_t e;
+    BIE_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    K.ev.push_back(e);
   }
   double rel = 0;
   int st;
