@@ -272,7 +272,6 @@ struct bie_geom {
   };
   std::vector<std::unique_ptr<Group>> groups;
   bie::DevBuf<double> anaF;   // analysis workspace
-  bie::DevBuf<float> dens32;  // FP32 copy of the density (mixed applies)
   struct GraphSlot {
     bool warm = false;
     cudaGraphExec_t exec = nullptr;
@@ -345,12 +344,6 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
   auto use_direct = [&](const bie_geom::Group& G) {
     return ctx->cfg.self_direct != 0 || kernel_proj_smem(G.p, G.pq) > 227 * 1024;
   };
-  bool any_proj = false;
-  for (auto& Gp : g->groups) any_proj = any_proj || !use_direct(*Gp);
-  if (sizeof(R) == 4 && any_proj) {  // the FP32 projected kernel reads an FP32 copy of the density
-    BIE_TRY(g->dens32.alloc(g->ncoef_total));
-    BIE_TRY(launch_to_float(dens, g->dens32.ptr, g->ncoef_total, s));
-  }
   for (auto& Gp : g->groups) {
     auto& G = *Gp;
     const int p = G.p, pq = G.pq;
@@ -377,10 +370,10 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
       BIE_TRY(ensure_qk(ctx, G, kind, s));
       const R* Q = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.qk64[kind].ptr)
                                   : reinterpret_cast<const R*>(G.qk32[kind].ptr);
-      const R* dR = sizeof(R) == 8 ? reinterpret_cast<const R*>(dens) : reinterpret_cast<const R*>(g->dens32.ptr);
+      // the kernel reads the FP64 density and rounds it as it loads it
       Phase ph(ctx, sizeof(R) == 8 ? "self_proj_f64" : "self_proj_f32", s);
-      BIE_TRY((launch_self_proj<R, R>(dR, G.foff3.ptr, nd, p, wp->blk_<R>(), wp->stride, pp->cs_<R>(), Q, wts,
-                                      G.val_off.ptr, g->vals.ptr, s)));
+      BIE_TRY((launch_self_proj<R, double>(dens, G.foff3.ptr, nd, p, wp->blk_<R>(), wp->stride, pp->cs_<R>(), Q, wts,
+                                           G.val_off.ptr, g->vals.ptr, s)));
     }
   }
   return BIE_OK;
@@ -1433,6 +1426,24 @@ static int dots(Krylov& K, const double* V, int k, const double* w, std::vector<
   return BIE_OK;
 }
 
+// |a| and |b| with one synchronisation
+static int norm2_pair(Krylov& K, const double* a, const double* b, double* na, double* nb, cudaStream_t s) {
+  k_multidot<<<dim3(kRedBlocks, 1), kRedThreads, 0, s>>>(a, K.n, a, K.n, 1, K.partial.ptr);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  k_multidot<<<dim3(kRedBlocks, 1), kRedThreads, 0, s>>>(b, K.n, b, K.n, 1, K.partial.ptr + kRedBlocks);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  k_sum_partials<<<2, 128, 0, s>>>(K.partial.ptr, kRedBlocks, 2, K.hdev.ptr);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  BIE_CUDA_TRY(cudaMemcpyAsync(K.hpin, K.hdev.ptr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  *na = std::sqrt(std::max(0.0, K.hpin[0]));
+  *nb = std::sqrt(std::max(0.0, K.hpin[1]));
+  return BIE_OK;
+}
+
 static int norm2(Krylov& K, const double* x, double* out, cudaStream_t s) {
   std::vector<double> h;
   BIE_TRY(dots(K, x, 1, x, h, s));
@@ -1461,14 +1472,19 @@ static int sys_matvec(bie_ctx* ctx, const bie_geom* g, const double* u, double* 
 // (k_kry_sub_tail); the host reads the residual estimate of step k - 1 after it has queued step k,
 // so the device never waits for the host between steps.  A cycle that converges at step k - 1 has
 // computed one more step than it uses.
+//
+// bnorm_in >= 0 is |b| when the caller knows it.  With trust_estimate (the inner solve of the mixed
+// refinement, whose true residual the caller recomputes), a cycle that reaches tol by the Givens
+// residual estimate returns without recomputing b - A x.
 static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, double* x, bool x_is_zero, double tol,
-                 int restart, int max_iter, Krylov& K, bie_solve_info* info, double* relres, cudaStream_t s) {
+                 int restart, int max_iter, Krylov& K, bie_solve_info* info, double* relres, cudaStream_t s,
+                 double bnorm_in = -1.0, bool trust_estimate = false) {
   const long long n = g->ncoef_total;
   const int m = restart;
   double* r = K.tmp.ptr;            // residual
   double* t2 = K.tmp.ptr + n;       // apply temporary
-  double bnorm;
-  BIE_TRY(norm2(K, b, &bnorm, s));
+  double bnorm = bnorm_in;
+  if (bnorm < 0) BIE_TRY(norm2(K, b, &bnorm, s));
   if (bnorm == 0.0) {
     BIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
     *relres = 0;
@@ -1491,7 +1507,10 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
       BIE_CUDA_TRY(cudaGetLastError());
     }
     double beta;
-    BIE_TRY(norm2(K, r, &beta, s));
+    if (x_is_zero)
+      beta = bnorm;
+    else
+      BIE_TRY(norm2(K, r, &beta, s));
     *relres = beta / bnorm;
     if (beta / bnorm <= tol || it >= max_iter) return beta / bnorm <= tol ? BIE_OK : BIE_ENOCONV;
     double* V = K.V.ptr;
@@ -1558,7 +1577,6 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
       est = K.hpin[kmax - 1] / bnorm;
       k_used = kmax;
     }
-    (void)est;
     it += k_used;
     info->iterations += k_used;
     k_backsub<<<1, 32, 0, s>>>(K.Hd.ptr, K.gvd.ptr, k_used, m, K.yd.ptr);
@@ -1568,6 +1586,10 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
     count_launch();
     BIE_CUDA_TRY(cudaGetLastError());
     x_is_zero = false;
+    if (trust_estimate && est <= tol) {
+      *relres = est;
+      return BIE_OK;
+    }
   }
 }
 
@@ -1906,11 +1928,11 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
     BIE_TRY(K.counter.alloc(1));
     BIE_CUDA_TRY(cudaMemset(K.counter.ptr, 0, sizeof(unsigned)));
   }
-  if (K.hpin_n < mr) {
+  if (K.hpin_n < std::max(mr, 2)) {
     if (K.hpin) cudaFreeHost(K.hpin);
     K.hpin = nullptr;
-    BIE_CUDA_TRY(cudaMallocHost(&K.hpin, mr * sizeof(double)));
-    K.hpin_n = mr;
+    BIE_CUDA_TRY(cudaMallocHost(&K.hpin, std::max(mr, 2) * sizeof(double)));
+    K.hpin_n = std::max(mr, 2);
   }
   while ((int)K.ev.size() < mr) {
     cudaEvent_t e;
@@ -1931,8 +1953,7 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
   BIE_TRY(dx.alloc(n));
   BIE_TRY(t.alloc(n));
   double bnorm, unorm;
-  BIE_TRY(norm2(K, rhs, &bnorm, s));
-  BIE_TRY(norm2(K, u, &unorm, s));
+  BIE_TRY(norm2_pair(K, rhs, u, &bnorm, &unorm, s));
   int left = opts->max_iter;
   bool updated = false;
   for (int outer = 0;; ++outer) {
@@ -1945,7 +1966,10 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
       BIE_CUDA_TRY(cudaGetLastError());
     }
     double rn;
-    BIE_TRY(norm2(K, r.ptr, &rn, s));
+    if (outer == 0 && unorm == 0.0)
+      rn = bnorm;
+    else
+      BIE_TRY(norm2(K, r.ptr, &rn, s));
     rel = bnorm > 0 ? rn / bnorm : 0.0;
     info->residual = rel;
     if (rel <= opts->tol) {
@@ -1957,7 +1981,8 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
     int before = info->iterations;
     double inner_rel;
     BIE_CUDA_TRY(cudaMemsetAsync(dx.ptr, 0, n * sizeof(double), s));
-    st = gmres(ctx, g, BIE_MIXED, r.ptr, dx.ptr, true, opts->inner_tol, opts->restart, left, K, info, &inner_rel, s);
+    st = gmres(ctx, g, BIE_MIXED, r.ptr, dx.ptr, true, opts->inner_tol, opts->restart, left, K, info, &inner_rel, s,
+               rn, true);
     if (st != BIE_OK && st != BIE_ENOCONV) return st;
     left -= info->iterations - before;
     k_axpby<<<nblk(n), 256, 0, s>>>(1.0, dx.ptr, 1.0, u, n);
@@ -1966,8 +1991,7 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
     // Next residual.  Once the correction is small against u, r <- r - A dx with the mixed operator
     // is accurate to ~eps_32 |A| |dx|, far below the tolerance; otherwise recompute b - A u in FP64.
     double dxn;
-    BIE_TRY(norm2(K, dx.ptr, &dxn, s));
-    BIE_TRY(norm2(K, u, &unorm, s));
+    BIE_TRY(norm2_pair(K, dx.ptr, u, &dxn, &unorm, s));
     if (dxn <= 1e-4 * unorm) {
       BIE_TRY(sys_matvec(ctx, g, dx.ptr, t.ptr, K.tmp.ptr + 2 * n, BIE_MIXED, info, s));
       k_axpby<<<nblk(n), 256, 0, s>>>(-1.0, t.ptr, 1.0, r.ptr, n);

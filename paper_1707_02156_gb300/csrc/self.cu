@@ -547,8 +547,8 @@ template int launch_self_direct<float>(int, const double*, const long long*, lon
 template int launch_self_proj<double, double>(const double*, const long long*, long long, int, const double*,
                                               long long, const double*, const double*, const double*,
                                               const long long*, double*, cudaStream_t);
-template int launch_self_proj<float, float>(const float*, const long long*, long long, int, const float*, long long,
-                                            const float*, const float*, const double*, const long long*, double*,
-                                            cudaStream_t);
+template int launch_self_proj<float, double>(const double*, const long long*, long long, int, const float*,
+                                             long long, const float*, const float*, const double*, const long long*,
+                                             double*, cudaStream_t);
 
 }  // namespace bie

@@ -130,39 +130,59 @@ __global__ void k_leg_analyze(const double* __restrict__ F, long long nfield, in
 }
 
 // Analysis on the field's own grid (degree p), one block per (field, order m): the phi transform
-// F_m(theta_j) of the block's order is formed in shared memory, then contracted with the weighted
-// Legendre table for n = m..p.
-__global__ void k_analyze_fused(const double* __restrict__ grid, const long long* __restrict__ grid_off, int p,
-                                const double* __restrict__ cs, const double* __restrict__ A,
-                                double* __restrict__ coef, const long long* __restrict__ coef_off) {
+// F_m(theta_j) of the block's order, one warp per latitude with the lanes across the longitudes
+// (coalesced loads, shuffle reduction), then the contraction with the weighted Legendre table for
+// n = m..p, one warp per degree with the lanes across the latitudes.
+constexpr int kAnaThreads = 128;
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kAnaThreads) k_analyze_fused(const double* __restrict__ grid,
+                                                               const long long* __restrict__ grid_off, int p,
+                                                               const double* __restrict__ cs,
+                                                               const double* __restrict__ A,
+                                                               double* __restrict__ coef,
+                                                               const long long* __restrict__ coef_off) {
   __shared__ double F[2 * (BIE_MAX_P + 1)];
   const int nj = p + 1, nk = 2 * p + 2;
   const long long f = blockIdx.x / (p + 1);
   const int m = (int)(blockIdx.x - f * (p + 1));
   const double* src = grid + grid_off[f];
   const double* c = cs + (long long)m * nk * 2;
-  for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < nj; j += nw) {
     const double* row = src + (long long)j * nk;
     double re = 0, im = 0;
-    for (int k = 0; k < nk; ++k) {
+    for (int k = lane; k < nk; k += 32) {
       const double v = row[k];
       re += v * c[2 * k];
       im -= v * c[2 * k + 1];
     }
-    F[2 * j] = re;
-    F[2 * j + 1] = im;
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) {
+      F[2 * j] = re;
+      F[2 * j + 1] = im;
+    }
   }
   __syncthreads();
   double* out = coef + coef_off[f];
-  for (int n = m + threadIdx.x; n <= p; n += blockDim.x) {
+  for (int n = m + warp; n <= p; n += nw) {
     const double* a = A + leg_row(p, m, n, nj);
     double re = 0, im = 0;
-    for (int j = 0; j < nj; ++j) {
+    for (int j = lane; j < nj; j += 32) {
       re += a[j] * F[2 * j];
       im += a[j] * F[2 * j + 1];
     }
-    out[n * (n + 1) + m] = re;
-    if (m > 0) out[n * (n + 1) - m] = im;
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) {
+      out[n * (n + 1) + m] = re;
+      if (m > 0) out[n * (n + 1) - m] = im;
+    }
   }
 }
 
@@ -297,7 +317,7 @@ int launch_analyze_fused(const double* grid, const long long* grid_off, long lon
   if (nfield == 0) return BIE_OK;
   const long long nblk = nfield * (p + 1);
   if (p > BIE_MAX_P || nblk > 0x7fffffffLL) return BIE_EINVAL;
-  k_analyze_fused<<<(unsigned)nblk, 64, 0, s>>>(grid, grid_off, p, cs, A, coef, coef_off);
+  k_analyze_fused<<<(unsigned)nblk, kAnaThreads, 0, s>>>(grid, grid_off, p, cs, A, coef, coef_off);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
