@@ -310,13 +310,21 @@ def run_ours(args):
     if not args.no_aux:
         geo.close()
         for name in ("c4", "c5"):
-            info_a, pairs_a, res_a = time_apply(name, local, 3, 2)
+            runs = ((1, 3, 2), (2, 2, 1), (0, 1, 0))
+            info_a, pairs_a, res_a, sol = time_apply(name, local, runs, solve=(name == "c4"))
             ma = res_a[1]
             also[name] = {"workload": APPLY_WORKLOADS[name], "step": "one mixed double-layer apply",
                           "ms_per_apply": ma["ms"], "pairs": pairs_a, "value": pairs_a / (ma["ms"] / 1e3),
                           "unit": UNIT, "far_pairs": info_a["far_pairs"], "up_pairs": info_a["up_pairs"],
                           "roofline": interdrop_roofline(info_a, ma["phases"], 3),
-                          "phases_ms": {k: {"ms": v[0], "calls": v[1]} for k, v in ma["phases"].items()}}
+                          "precisions": apply_summary(res_a)}
+            if sol:
+                rel_a = float(torch.linalg.norm(sol["mixed"]["u"] - sol["fp64"]["u"]) / torch.linalg.norm(sol["fp64"]["u"]))
+                also[name]["solve"] = {
+                    "step": "rhs + solve to 1e-10: mixed GMRES with double-float refinement residuals vs FP64 GMRES",
+                    "mixed": {k: v for k, v in sol["mixed"].items() if k != "u"},
+                    "fp64": {k: v for k, v in sol["fp64"].items() if k != "u"},
+                    "speedup_vs_fp64": sol["fp64"]["ms"] / sol["mixed"]["ms"], "rel_err_mixed_vs_fp64": rel_a}
 
     cpu = cpu_baseline_sample(w, budget_s=15.0) if rank == 0 else None
     res = {
@@ -407,8 +415,10 @@ APPLY_WORKLOADS = {
 }
 
 
-def time_apply(name, local, steps, warmup, precisions=(1,)):
-    """Time double-layer applies of a multi-drop workload; returns per-precision timings and phases."""
+def time_apply(name, local, runs=((1, 3, 2),), solve=False):
+    """Double-layer applies of a multi-drop workload at the precisions of `runs` = ((prec, steps,
+    warm-up), ...); returns the geometry info, the pairs per apply, per-precision timings, phases and
+    outputs, and (with solve) a mixed solve with double-float residuals next to the plain FP64 solve."""
     import torch
     from paper_1707_02156_gb300 import api, build, inputs
     build.build()
@@ -422,7 +432,7 @@ def time_apply(name, local, steps, warmup, precisions=(1,)):
     stream = torch.cuda.current_stream()
     scrub = Scrub()
     res = {}
-    for prec in precisions:
+    for prec, steps, warmup in runs:
         for _ in range(warmup):
             geo.apply_double(f, out, precision=prec)
         torch.cuda.synchronize()
@@ -431,13 +441,37 @@ def time_apply(name, local, steps, warmup, precisions=(1,)):
         with ClockSampler(local) as clk:
             ms = timed_steps(lambda: geo.apply_double(f, out, precision=prec), steps, stream, scrub)
         res[prec] = {"ms": ms / steps, "phases": ctx.profile_read(),
-                     "launches": api.launch_count() - launches0, "clocks": clk.summary()}
+                     "launches": api.launch_count() - launches0, "clocks": clk.summary(), "out": out.clone()}
         ctx.profile(False)
+    sol = None
+    if solve:
+        # b = 2 u_inf + S[f] with u_inf = (z, 0, 0), then the solve: mixed GMRES inside refinement with
+        # double-float residuals, against FP64 GMRES (both to 1e-10)
+        uinf = torch.zeros_like(f)
+        o = 0
+        for p in w.p:
+            k = (p + 1) ** 2
+            uinf[o:o + k] = torch.tensor(w.xcoef[o + 2 * k:o + 3 * k], device="cuda")
+            o += 3 * k
+        sol = {}
+        for label, prec, rprec in (("mixed", 1, 2), ("fp64", 0, 0)):
+            b = torch.zeros_like(f)
+            u = torch.zeros_like(f)
+            last = {}
+
+            def run():
+                geo.rhs(uinf, f, b, precision=rprec)
+                u.zero_()
+                last["info"] = geo.solve(b, u, precision=prec, tol=1e-10, residual_precision=2)
+
+            ms = timed_steps(run, 1, stream, scrub)
+            sol[label] = {"ms": ms, **{k: last["info"][k] for k in ("iterations", "refinements", "applies_fp64",
+                                                                     "applies_mixed", "residual")}, "u": u.clone()}
     geo.close()
     ctx.close()
     del f, out
     torch.cuda.empty_cache()
-    return info, pairs, res
+    return info, pairs, res, sol
 
 
 def interdrop_roofline(info, phases, steps):
@@ -454,12 +488,13 @@ def interdrop_roofline(info, phases, steps):
 
 
 def run_apply(args):
-    """Auxiliary mode: time one double-layer apply per step (mixed, then FP64) on a multi-drop workload."""
+    """Auxiliary mode: time one double-layer apply per step (mixed, then double-float and FP64) on a
+    multi-drop workload."""
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)
-    precs = (1,) if args.workload in ("c4", "c5") else (1, 0)  # FP64 applies of the many-drop sets take seconds
-    info, pairs, res = time_apply(args.workload, local, args.steps, args.warmup, precs)
+    runs = ((1, args.steps, args.warmup), (2, 1, 1), (0, 1, 0))
+    info, pairs, res, _ = time_apply(args.workload, local, runs)
     m = res[1]
     print(json.dumps({
         "metric": METRIC, "value": pairs / (m["ms"] / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -471,10 +506,25 @@ def run_apply(args):
         "gpu_launches": m["launches"], "clocks": m["clocks"],
         "roofline": interdrop_roofline(info, m["phases"], args.steps),
         "phases_ms": {k: {"ms": v[0], "calls": v[1]} for k, v in m["phases"].items()},
-        "fp64": ({"ms_per_apply": res[0]["ms"], "phases_ms": {k: {"ms": v[0], "calls": v[1]}
-                                                              for k, v in res[0]["phases"].items()}}
-                 if 0 in res else None),
+        "precisions": apply_summary(res),
     }))
+
+
+def apply_summary(res):
+    """Per-precision apply times and relative errors against the FP64 apply."""
+    import torch
+    ref = res[0]["out"] if 0 in res else None
+    out = {}
+    for prec, name in ((1, "mixed"), (2, "df"), (0, "fp64")):
+        if prec not in res:
+            continue
+        r = res[prec]
+        e = {"ms_per_apply": r["ms"], "phases_ms": {k: {"ms": v[0], "calls": v[1]} for k, v in r["phases"].items()}}
+        if ref is not None and prec != 0:
+            e["rel_err_vs_fp64"] = float(torch.linalg.norm(r["out"] - ref) / torch.linalg.norm(ref))
+            e["speedup_vs_fp64"] = res[0]["ms"] / r["ms"]
+        out[name] = e
+    return out
 
 
 if __name__ == "__main__":

@@ -53,6 +53,10 @@ enum bie_status {
 /* precision flags (the low byte), OR-able with BIE_RAW */
 #define BIE_FP64 0   /* every step in double precision */
 #define BIE_MIXED 1  /* rotation, synthesis and pair sums in FP32; geometry, analysis in FP64 */
+#define BIE_DF 2     /* FP64 everywhere except the inter-drop pair sums (Omega_0, Omega_1), which run in
+                        double-float arithmetic (pairs of FP32 numbers, about 44 significant bits) on
+                        the FP32 pipes: FP64-grade results (relative error ~1e-13) at a fraction of the
+                        FP64 pipe's cost.  With a single drop it is BIE_FP64. */
 #define BIE_RAW 0x100
 #define BIE_GRID_OUT 0x200  /* applies: write the values at the grid targets, [drop][3][j][k], instead
                                of their Galerkin projection (for sampled checks against a reference) */
@@ -164,7 +168,7 @@ int bie_interfacial_force(bie_ctx* ctx, const bie_geom* geom, const double* gamm
 
 /* Single-layer apply (Eq. main_eq, Sec. 2.2-2.3, Galerkin projection of Sec. 1.2):
  * out = coefficients of S[f] at every drop's grid targets.  fcoef: [drop][3][(p+1)^2] (device);
- * precision: BIE_FP64 or BIE_MIXED, optionally | BIE_RAW. */
+ * precision: BIE_FP64, BIE_MIXED or BIE_DF, optionally | BIE_RAW. */
 int bie_apply_single(bie_ctx* ctx, const bie_geom* geom, const double* fcoef, double* out_coef, int precision,
                      void* stream);
 
@@ -172,12 +176,12 @@ int bie_apply_single(bie_ctx* ctx, const bie_geom* geom, const double* fcoef, do
 int bie_apply_double(bie_ctx* ctx, const bie_geom* geom, const double* ucoef, double* out_coef, int precision,
                      void* stream);
 
-/* Right-hand side of Eq. main_eq in coefficient space: rhs = 2 u_inf + S[f] with the FP64 single
- * layer.  uinf: [drop][3][(p+1)^2] device coefficients of the far field at the drop surfaces (a
+/* Right-hand side of Eq. main_eq in coefficient space: rhs = 2 u_inf + S[f] with the single layer at
+ * precision BIE_FP64 or BIE_DF (both FP64-grade).  uinf: [drop][3][(p+1)^2] device coefficients of the far field at the drop surfaces (a
  * linear flow is exactly band-limited: u_inf = (z, 0, 0) has the z coefficients of x in its first
  * component); fcoef: interfacial force coefficients; rhs: device output (must not alias the inputs). */
 int bie_rhs(bie_ctx* ctx, const bie_geom* geom, const double* uinf, const double* fcoef, double* rhs,
-            void* stream);
+            int precision, void* stream);
 
 typedef struct bie_solve_opts {
   int precision;      /* BIE_FP64: FP64 GMRES; BIE_MIXED: mixed GMRES inside FP64 iterative refinement */
@@ -186,12 +190,14 @@ typedef struct bie_solve_opts {
   int max_iter;       /* total GMRES iterations allowed */
   double inner_tol;   /* mixed only: relative tolerance of each inner solve */
   int max_refine;     /* mixed only: outer refinement steps allowed */
+  int residual_precision; /* mixed only: precision of the refinement residual b - A u, BIE_FP64 or
+                             BIE_DF (the default: FP64-grade, inter-drop pairs on the FP32 pipes) */
 } bie_solve_opts;
 
 typedef struct bie_solve_info {
   int iterations;        /* GMRES iterations (all inner solves) */
   int refinements;       /* outer refinement steps (mixed) */
-  int applies_fp64;      /* FP64 double-layer applies */
+  int applies_fp64;      /* FP64-grade double-layer applies (BIE_FP64 or BIE_DF) */
   int applies_mixed;     /* mixed double-layer applies */
   double residual;       /* final FP64 relative residual */
   int converged;

@@ -17,7 +17,7 @@ c_int, c_double, c_ll, c_void = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
 P_int = ctypes.POINTER(ctypes.c_int)
 P_double = ctypes.POINTER(ctypes.c_double)
 
-BIE_FP64, BIE_MIXED, BIE_RAW, BIE_GRID_OUT = 0, 1, 0x100, 0x200
+BIE_FP64, BIE_MIXED, BIE_DF, BIE_RAW, BIE_GRID_OUT = 0, 1, 2, 0x100, 0x200
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT", 6: "EOVERLAP", 7: "ENOTSUP"}
 
 
@@ -34,7 +34,7 @@ class bie_geom_info(ctypes.Structure):
 
 class bie_solve_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("tol", c_double), ("restart", c_int), ("max_iter", c_int),
-                ("inner_tol", c_double), ("max_refine", c_int)]
+                ("inner_tol", c_double), ("max_refine", c_int), ("residual_precision", c_int)]
 
 
 class bie_solve_info(ctypes.Structure):
@@ -62,7 +62,7 @@ EXPORTS = {
     "bie_interfacial_force": (c_int, [c_void, c_void, c_void, c_double, c_double, c_void, c_void]),
     "bie_apply_single": (c_int, [c_void, c_void, c_void, c_void, c_int, c_void]),
     "bie_apply_double": (c_int, [c_void, c_void, c_void, c_void, c_int, c_void]),
-    "bie_rhs": (c_int, [c_void, c_void, c_void, c_void, c_void, c_void]),
+    "bie_rhs": (c_int, [c_void, c_void, c_void, c_void, c_void, c_int, c_void]),
     "bie_solve_opts_default": (None, [ctypes.POINTER(bie_solve_opts)]),
     "bie_solve": (c_int, [c_void, c_void, c_void, c_void, ctypes.POINTER(bie_solve_opts),
                           ctypes.POINTER(bie_solve_info), c_void]),
@@ -239,18 +239,19 @@ class Geometry:
                "bie_interfacial_force")
         return out
 
-    def rhs(self, uinf: torch.Tensor, f: torch.Tensor, out: torch.Tensor):
-        """out = 2 u_inf + S[f] (FP64), the right-hand side of the boundary integral equation."""
-        _check(lib().bie_rhs(self.ctx.h, self.h, _ptr(uinf), _ptr(f), _ptr(out), _stream()), "bie_rhs")
+    def rhs(self, uinf: torch.Tensor, f: torch.Tensor, out: torch.Tensor, precision: int = BIE_FP64):
+        """out = 2 u_inf + S[f], the right-hand side of the boundary integral equation (S at BIE_FP64
+        or BIE_DF, both FP64-grade)."""
+        _check(lib().bie_rhs(self.ctx.h, self.h, _ptr(uinf), _ptr(f), _ptr(out), precision, _stream()), "bie_rhs")
         return out
 
     def solve(self, rhs: torch.Tensor, u: torch.Tensor, precision: int = BIE_FP64, tol: float = 1e-10,
               restart: int = 30, max_iter: int = 300, inner_tol: float = 1e-5, max_refine: int = 10,
-              raise_on_noconv: bool = True) -> dict:
+              residual_precision: int = BIE_DF, raise_on_noconv: bool = True) -> dict:
         o = bie_solve_opts()
         lib().bie_solve_opts_default(ctypes.byref(o))
-        o.precision, o.tol, o.restart, o.max_iter, o.inner_tol, o.max_refine = (
-            precision, tol, restart, max_iter, inner_tol, max_refine)
+        o.precision, o.tol, o.restart, o.max_iter, o.inner_tol, o.max_refine, o.residual_precision = (
+            precision, tol, restart, max_iter, inner_tol, max_refine, residual_precision)
         info = bie_solve_info()
         st = lib().bie_solve(self.ctx.h, self.h, _ptr(rhs), _ptr(u), ctypes.byref(o), ctypes.byref(info), _stream())
         res = {k: getattr(info, k) for k, _ in bie_solve_info._fields_}

@@ -380,7 +380,7 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
 }
 
 template <typename R>
-static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s);
+static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s, bool df = false);
 static int near_apply(bie_geom* g, int kind, bool raw, int prec, const double* dens, cudaStream_t s);
 static int near_snapshot(bie_geom* g, cudaStream_t s);
 
@@ -393,21 +393,22 @@ static int layer_apply_eager(bie_ctx* ctx, const bie_geom* gc, int kind, const d
   }
   const bool raw = (precision & BIE_RAW) != 0;
   const int prec = precision & 0xff;
-  if (prec != BIE_FP64 && prec != BIE_MIXED) {
-    set_error("precision must be BIE_FP64 or BIE_MIXED");
+  if (prec != BIE_FP64 && prec != BIE_MIXED && prec != BIE_DF) {
+    set_error("precision must be BIE_FP64, BIE_MIXED or BIE_DF");
     return BIE_EINVAL;
   }
-  if (prec == BIE_FP64)
-    BIE_TRY(self_apply<double>(g, kind, raw, dens, s));
-  else
+  if (prec == BIE_MIXED)
     BIE_TRY(self_apply<float>(g, kind, raw, dens, s));
+  else
+    BIE_TRY(self_apply<double>(g, kind, raw, dens, s));
   if (g->ndrop > 1) {
     if (!g->near.empty()) BIE_TRY(near_snapshot(g, s));
-    if (prec == BIE_FP64)
-      BIE_TRY(interdrop_apply<double>(g, kind, raw, dens, s));
-    else
+    if (prec == BIE_MIXED)
       BIE_TRY(interdrop_apply<float>(g, kind, raw, dens, s));
-    BIE_TRY(near_apply(g, kind, raw, prec, dens, s));
+    else
+      BIE_TRY(interdrop_apply<double>(g, kind, raw, dens, s, prec == BIE_DF));
+    // the FP64 source densities of BIE_DF are already in place
+    BIE_TRY(near_apply(g, kind, raw, prec == BIE_DF ? BIE_FP64 : prec, dens, s));
   }
   if (precision & BIE_GRID_OUT) {
     BIE_CUDA_TRY(cudaMemcpyAsync(out, g->vals.ptr, 3 * g->ntarget * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1099,7 +1100,7 @@ static int near_apply(bie_geom* g, int kind, bool raw, int prec, const double* d
 }
 
 template <typename R>
-static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s) {
+static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s, bool df) {
   bie_ctx* ctx = g->ctx;
   R *Qs, *Qu;
   const R *Xs, *Ns, *Xu, *Nu;
@@ -1124,7 +1125,13 @@ static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, 
   }
   BIE_TRY(source_densities<R>(g, dens, Qs, Qu, s));
   const double* wts = kind == 0 ? (raw ? g->wSr_all.ptr : g->wS_all.ptr) : (raw ? g->wDr_all.ptr : g->wD_all.ptr);
-  {
+  if (df) {
+    Phase ph(ctx, "interdrop_df", s);
+    BIE_TRY(launch_interdrop_df(kind, g->nblk, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr, g->tile_n.ptr,
+                                g->tile_drop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr, g->rec_std.ptr,
+                                g->centre_d.ptr, g->sX64.ptr, g->sN64.ptr, g->sQ64.ptr, g->ntarget, g->uX64.ptr,
+                                g->uN64.ptr, g->uQ64.ptr, g->nup_total, wts, g->partial.ptr, s));
+  } else {
     Phase ph(ctx, sizeof(R) == 8 ? "interdrop_f64" : "interdrop_f32", s);
     BIE_TRY(launch_interdrop<R>(kind, sizeof(R) == 8 ? g->tpt64 : g->tpt32, g->nblk, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr, g->tile_n.ptr,
                                 g->tile_drop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr, g->rec_std.ptr,
@@ -1455,10 +1462,10 @@ static int norm2(Krylov& K, const double* x, double* out, cudaStream_t s) {
 static int sys_matvec(bie_ctx* ctx, const bie_geom* g, const double* u, double* y, double* tmp, int prec,
                       bie_solve_info* info, cudaStream_t s) {
   BIE_TRY(layer_apply(ctx, g, 1, u, tmp, prec, s));
-  if (prec == BIE_FP64)
-    info->applies_fp64++;
-  else
+  if (prec == BIE_MIXED)
     info->applies_mixed++;
+  else
+    info->applies_fp64++;
   Phase ph(ctx, "gmres_vec", s);
   k_sysop<<<nblk(g->ncoef_total), 256, 0, s>>>(g->lamc.ptr, u, tmp, y, g->ncoef_total);
   count_launch();
@@ -1529,10 +1536,10 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
         BIE_CUDA_TRY(cudaGetLastError());
       }
       BIE_TRY(layer_apply(ctx, g, 1, vk, t2, prec, s));
-      if (prec == BIE_FP64)
-        info->applies_fp64++;
-      else
+      if (prec == BIE_MIXED)
         info->applies_mixed++;
+      else
+        info->applies_fp64++;
       // classical Gram-Schmidt with one re-orthogonalisation, three fused kernels
       double* h1 = K.hdev.ptr;
       double* h2d = K.hdev.ptr + (m + 2);
@@ -1871,11 +1878,16 @@ int bie_apply_double(bie_ctx* ctx, const bie_geom* g, const double* ucoef, doubl
   return layer_apply(ctx, g, 1, ucoef, out, precision, (cudaStream_t)stream);
 }
 
-int bie_rhs(bie_ctx* ctx, const bie_geom* g, const double* uinf, const double* fcoef, double* rhs, void* stream) {
+int bie_rhs(bie_ctx* ctx, const bie_geom* g, const double* uinf, const double* fcoef, double* rhs, int precision,
+            void* stream) {
   if (!ctx || !g || !uinf || !fcoef || !rhs) return BIE_EINVAL;
+  if (precision != BIE_FP64 && precision != BIE_DF) {
+    set_error("bie_rhs: precision must be BIE_FP64 or BIE_DF");
+    return BIE_EINVAL;
+  }
   BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
   cudaStream_t s = (cudaStream_t)stream;
-  BIE_TRY(layer_apply(ctx, g, 0, fcoef, rhs, BIE_FP64, s));
+  BIE_TRY(layer_apply(ctx, g, 0, fcoef, rhs, precision, s));
   Phase ph(ctx, "gmres_vec", s);
   k_axpby<<<nblk(g->ncoef_total), 256, 0, s>>>(2.0, uinf, 1.0, rhs, g->ncoef_total);
   count_launch();
@@ -1891,12 +1903,14 @@ void bie_solve_opts_default(bie_solve_opts* o) {
   o->max_iter = 300;
   o->inner_tol = 1e-5;
   o->max_refine = 10;
+  o->residual_precision = BIE_DF;
 }
 
 int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, const bie_solve_opts* opts,
               bie_solve_info* info, void* stream) {
   if (!ctx || !g || !rhs || !u || !opts || !info) return BIE_EINVAL;
-  if (opts->restart < 1 || opts->restart > 64 || opts->tol <= 0 || opts->max_iter < 1) {
+  if (opts->restart < 1 || opts->restart > 64 || opts->tol <= 0 || opts->max_iter < 1 ||
+      (opts->residual_precision != BIE_FP64 && opts->residual_precision != BIE_DF)) {
     set_error("bad solve options");
     return BIE_EINVAL;
   }
@@ -1960,7 +1974,7 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
     if (outer == 0 && unorm == 0.0) {  // r = b for a zero initial guess
       BIE_CUDA_TRY(cudaMemcpyAsync(r.ptr, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     } else if (!updated) {
-      BIE_TRY(sys_matvec(ctx, g, u, r.ptr, t.ptr, BIE_FP64, info, s));
+      BIE_TRY(sys_matvec(ctx, g, u, r.ptr, t.ptr, opts->residual_precision, info, s));
       k_axpby<<<nblk(n), 256, 0, s>>>(1.0, rhs, -1.0, r.ptr, n);
       count_launch();
       BIE_CUDA_TRY(cudaGetLastError());

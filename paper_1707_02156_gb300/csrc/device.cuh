@@ -6,9 +6,18 @@ namespace bie {
 
 template <typename R>
 __device__ inline R rsqrt_(R v);
+// 1/sqrt(v) in FP64 by Newton's method on f(y) = 1/y^2 - v, y <- y (3 - v y^2)/2, started from the
+// FP32 hardware estimate: each step squares the relative error, so two steps take its 2^-23 below
+// FP64 rounding (a few ulp).  Outside the FP32 exponent range the estimate is unusable and the
+// quotient of the IEEE square root is returned instead.
 template <>
 __device__ inline double rsqrt_<double>(double v) {
-  return 1.0 / sqrt(v);
+  if (!(v > 1e-30 && v < 1e30)) return 1.0 / sqrt(v);
+  const double h = 0.5 * v;
+  double y = (double)rsqrtf((float)v);
+  y = y * fma(-h, y * y, 1.5);
+  y = y * fma(-h, y * y, 1.5);
+  return y;
 }
 template <>
 __device__ inline float rsqrt_<float>(float v) {

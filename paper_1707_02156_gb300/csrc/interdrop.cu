@@ -185,6 +185,175 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop(
   }
 }
 
+// ---- double-float pair sums ----
+// A double-float value is an unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2
+// (about 44 significant bits).  Sums use Knuth's TwoSum and products the FMA-based TwoProduct (both
+// error-free transformations), renormalised by Dekker's Fast2Sum; 1/sqrt starts from the FP32
+// estimate and takes one Newton step in double-float.  Every operation runs on the FP32 pipes.
+struct df2 {
+  float h, l;
+};
+
+__device__ inline df2 df_from(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ inline df2 fast2sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ inline df2 df_add(df2 a, df2 b) {
+  const float s = a.h + b.h;
+  const float v = s - a.h;
+  const float e = (a.h - (s - v)) + (b.h - v) + a.l + b.l;
+  return fast2sum(s, e);
+}
+__device__ inline df2 df_neg(df2 a) { return {-a.h, -a.l}; }
+__device__ inline df2 df_mul(df2 a, df2 b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return fast2sum(p, e);
+}
+__device__ inline df2 df_sqr(df2 a) {
+  const float p = a.h * a.h;
+  float e = fmaf(a.h, a.h, -p);
+  e = fmaf(2.0f * a.h, a.l, e);
+  return fast2sum(p, e);
+}
+__device__ inline df2 df_mulf(df2 a, float b) {
+  const float p = a.h * b;
+  float e = fmaf(a.h, b, -p);
+  e = fmaf(a.l, b, e);
+  return fast2sum(p, e);
+}
+__device__ inline df2 df_rsqrt(df2 a) {
+  const float y = rsqrtf(a.h);
+  const float y2 = y * y;
+  const df2 ay2 = df_mul(a, {y2, fmaf(y, y, -y2)});
+  const float e = (1.0f - ay2.h) - ay2.l;  // 1 - a y^2, of the order of the estimate's error
+  return fast2sum(y, 0.5f * y * e);
+}
+
+// Same work list and layout as k_interdrop; sources are read in FP64 and split into double-float
+// pairs as they are staged through shared memory, targets are split once per item.
+template <int KIND, int TPT>
+__global__ void __launch_bounds__(kTile / TPT) k_interdrop_df(
+    const PairItem* __restrict__ items, const int* __restrict__ blk_item, const long long* __restrict__ tile_t0,
+    const int* __restrict__ tile_n, const int* __restrict__ tile_drop, const long long* __restrict__ tgt_loc,
+    const long long* __restrict__ toff_std, const int* __restrict__ ngd, const double* __restrict__ rec_std,
+    const double* __restrict__ centre, const double* __restrict__ Xs, const double* __restrict__ Ns,
+    const double* __restrict__ Qs, long long nstd, const double* __restrict__ Xu, const double* __restrict__ Nu,
+    const double* __restrict__ Qu, long long nup, const double* __restrict__ wts, double* __restrict__ partial) {
+  constexpr int NT = kTile / TPT;
+  constexpr int NV = KIND ? 9 : 6;  // staged values per source: x, q (and n)
+  __shared__ df2 sv[NV][kChunk];
+  const int b = blockIdx.x;
+  const int it0 = blk_item[b], it1 = blk_item[b + 1];
+  const int tile = items[it0].tile;
+  const int tid = threadIdx.x;
+  const int nt = tile_n[tile];
+  const int di = tile_drop[tile];
+  double tx[TPT], ty[TPT], tz[TPT], acc[TPT][3];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int k = tid + u * NT;
+    tx[u] = ty[u] = tz[u] = 0;
+    acc[u][0] = acc[u][1] = acc[u][2] = 0;
+    if (k < nt) {
+      const long long t = tile_t0[tile] + k;
+      const long long ng = ngd[di];
+      const double* ri = rec_std + 7 * toff_std[di];
+      const long long l = tgt_loc[t];
+      tx[u] = ri[l];
+      ty[u] = ri[ng + l];
+      tz[u] = ri[2 * ng + l];
+    }
+  }
+  for (int it = it0; it < it1; ++it) {
+    const PairItem item = items[it];
+    const int j = item.src_drop;
+    bool act[TPT], any = false;
+    df2 px[TPT], py[TPT], pz[TPT];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const int k = tid + u * NT;
+      act[u] = k < nt && ((item.mask[k >> 5] >> (k & 31)) & 1u);
+      any = any || act[u];
+      px[u] = df_from(tx[u] - centre[3 * j]);
+      py[u] = df_from(ty[u] - centre[3 * j + 1]);
+      pz[u] = df_from(tz[u] - centre[3 * j + 2]);
+    }
+    const double* X = item.grid ? Xu : Xs;
+    const double* N = item.grid ? Nu : Ns;
+    const double* Q = item.grid ? Qu : Qs;
+    const long long ld = item.grid ? nup : nstd;
+    df2 s[TPT][3];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) s[u][0] = s[u][1] = s[u][2] = {0.0f, 0.0f};
+    for (long long c0 = item.s0; c0 < item.s1; c0 += kChunk) {
+      const int cn = (int)min((long long)kChunk, item.s1 - c0);
+      for (int k = tid; k < cn; k += NT) {
+        const long long sidx = c0 + k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          sv[c][k] = df_from(X[c * ld + sidx]);
+          sv[3 + c][k] = df_from(Q[c * ld + sidx]);
+          if (KIND) sv[6 + c][k] = df_from(N[c * ld + sidx]);
+        }
+      }
+      __syncthreads();
+      if (any) {
+        for (int k = 0; k < cn; ++k) {
+          const df2 xs_ = sv[0][k], ys_ = sv[1][k], zs_ = sv[2][k];
+          const df2 q0 = sv[3][k], q1 = sv[4][k], q2 = sv[5][k];
+#pragma unroll
+          for (int u = 0; u < TPT; ++u) {
+            const df2 dx = df_add(px[u], df_neg(xs_)), dy = df_add(py[u], df_neg(ys_)),
+                      dz = df_add(pz[u], df_neg(zs_));
+            const df2 r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+            const df2 ri = df_rsqrt(r2);
+            const df2 xq = df_add(df_add(df_mul(dx, q0), df_mul(dy, q1)), df_mul(dz, q2));
+            if (KIND == 0) {  // Stokeslet
+              const df2 ri3 = df_mul(df_sqr(ri), ri);
+              const df2 c = df_mul(xq, ri3);
+              s[u][0] = df_add(s[u][0], df_add(df_mul(q0, ri), df_mul(c, dx)));
+              s[u][1] = df_add(s[u][1], df_add(df_mul(q1, ri), df_mul(c, dy)));
+              s[u][2] = df_add(s[u][2], df_add(df_mul(q2, ri), df_mul(c, dz)));
+            } else {  // stresslet
+              const df2 n0 = sv[6][k], n1 = sv[7][k], n2 = sv[8][k];
+              const df2 xn = df_add(df_add(df_mul(dx, n0), df_mul(dy, n1)), df_mul(dz, n2));
+              const df2 ri2 = df_sqr(ri);
+              const df2 ri5 = df_mul(df_sqr(ri2), ri);
+              const df2 c = df_mulf(df_mul(df_mul(xq, xn), ri5), -6.0f);
+              s[u][0] = df_add(s[u][0], df_mul(c, dx));
+              s[u][1] = df_add(s[u][1], df_mul(c, dy));
+              s[u][2] = df_add(s[u][2], df_mul(c, dz));
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const double wj = wts[j];
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const double w = act[u] ? wj : 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[u][c] += w * ((double)s[u][c].h + (double)s[u][c].l);
+    }
+  }
+  double* pp = partial + (long long)b * 3 * kTile;
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int k = tid + u * NT;
+    pp[k] = acc[u][0];
+    pp[kTile + k] = acc[u][1];
+    pp[2 * kTile + k] = acc[u][2];
+  }
+}
+
 // vals += sum of the partials of the tile's blocks, in block order
 __global__ void k_reduce_tiles(const double* __restrict__ partial, const int* __restrict__ tile_blk,
                                const long long* __restrict__ tile_t0, const int* __restrict__ tile_n,
@@ -317,6 +486,21 @@ int launch_interdrop(int kind, int tpt, int nblk, const PairItem* items, const i
   else
     interdrop_kernel<R, 2>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd, rec_std,
                            centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+int launch_interdrop_df(int kind, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
+                        const int* tile_n, const int* tile_drop, const long long* tgt_loc, const long long* toff_std,
+                        const int* ngd, const double* rec_std, const double* centre, const double* Xs,
+                        const double* Ns, const double* Qs, long long nstd, const double* Xu, const double* Nu,
+                        const double* Qu, long long nup, const double* wts, double* partial, cudaStream_t s) {
+  if (nblk == 0) return BIE_OK;
+  constexpr int TPT = 2;
+  auto kern = kind == 0 ? k_interdrop_df<0, TPT> : k_interdrop_df<1, TPT>;
+  kern<<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd, rec_std,
+                                    centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;

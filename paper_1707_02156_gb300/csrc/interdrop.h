@@ -28,6 +28,12 @@ int launch_interdrop(int kind, int tpt, int nblk, const PairItem* items, const i
                      const int* ngd, const double* rec_std, const double* centre, const R* Xs, const R* Ns,
                      const R* Qs, long long nstd, const R* Xu, const R* Nu, const R* Qu, long long nup,
                      const double* wts, double* partial, cudaStream_t s);
+// the same pair sums in double-float arithmetic (FP32 pipes, about 44 bits) from FP64 sources
+int launch_interdrop_df(int kind, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
+                        const int* tile_n, const int* tile_drop, const long long* tgt_loc, const long long* toff_std,
+                        const int* ngd, const double* rec_std, const double* centre, const double* Xs,
+                        const double* Ns, const double* Qs, long long nstd, const double* Xu, const double* Nu,
+                        const double* Qu, long long nup, const double* wts, double* partial, cudaStream_t s);
 int launch_reduce_tiles(const double* partial, const int* tile_blk, const long long* tile_t0, const int* tile_n,
                         const int* tile_drop, const long long* tgt_loc, const long long* val_off, const int* ngd,
                         int ntile, double* vals, cudaStream_t s);

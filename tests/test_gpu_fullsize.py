@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 MIXED_TOL = 2e-5
+DF_TOL = 1e-11  # double-float inter-drop pair sums (about 44 bits per operation)
 
 
 def _relerr(a, b):
@@ -119,24 +120,27 @@ def test_near_contact_pair_full_size(cuda_ok, kind):
     sel = np.nonzero(reg == 2)[0]
     val[:, sel] += _weight(w, kind, j) * near.near_values(drops, i, j, tgt[sel], ds[j], kind, self_j)
     ref = val.reshape(3, len(lats), 2 * p + 2)
-    g = _gpu_grid(w, kind, (0, 1))
+    g = _gpu_grid(w, kind, (0, 1, 2))
     assert _relerr(_drop_block(w, g[0], i, lats), ref) < FP64_TOL
     assert _relerr(_drop_block(w, g[1], i, lats), ref) < MIXED_TOL
+    assert _relerr(_drop_block(w, g[2], i, lats), ref) < DF_TOL
 
 
 def test_batch_of_64_uneven_degree_drops_full_size(cuda_ok):
     w = inputs.config("c4")
     i = int(np.argmax(w.p))  # a p = 48 drop
     lats = [7]
-    g = _gpu_grid(w, "D", (0, 1))
+    g = _gpu_grid(w, "D", (0, 1, 2))
     ref = _far_only_oracle(w, "D", i, lats)
     assert _relerr(_drop_block(w, g[0], i, lats), ref) < FP64_TOL
     assert _relerr(_drop_block(w, g[1], i, lats), ref) < MIXED_TOL
+    assert _relerr(_drop_block(w, g[2], i, lats), ref) < DF_TOL
 
 
 def test_512_deformed_drops_full_size(cuda_ok):
     w = inputs.config("c5")
     i, lats = 137, [3]
-    g = _gpu_grid(w, "D", (1,))
+    g = _gpu_grid(w, "D", (1, 2))
     ref = _far_only_oracle(w, "D", i, lats)
     assert _relerr(_drop_block(w, g[1], i, lats), ref) < MIXED_TOL
+    assert _relerr(_drop_block(w, g[2], i, lats), ref) < DF_TOL

@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 MIXED_TOL = 2e-5
+DF_TOL = 1e-11  # 2^-44 per operation, grown over ~10^4-term sums with magnitudes up to the 1/r peak
 
 
 @pytest.fixture(scope="module")
@@ -78,7 +79,8 @@ def test_multidrop_apply_matches_oracle(batch, kind):
     f = torch.tensor(inputs.pack_drops(fs), device="cuda")
     out = torch.zeros_like(f)
     fn = geo.apply_single if kind == "S" else geo.apply_double
-    for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
+    # BIE_DF: inter-drop pair sums in double-float (about 44 bits), everything else FP64
+    for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL), (2, DF_TOL)):
         fn(f, out, precision=prec)
         torch.cuda.synchronize()
         assert _relerr(out.cpu().numpy(), ref) < tol, (kind, prec)
@@ -100,12 +102,13 @@ def test_multidrop_solve_matches_oracle(batch):
     u_ref, info = gmres.gmres(drops.system_matvec, b, tol=1e-13)
     assert info["converged"]
     rhs = torch.tensor(b, device="cuda")
-    for prec, tol in ((0, 1e-11), (1, 1e-8)):
+    # FP64 GMRES; mixed with double-float residuals (the default); mixed with FP64 residuals
+    for prec, resid, tol in ((0, 2, 1e-11), (1, 2, 1e-8), (1, 0, 1e-8)):
         u = torch.zeros_like(rhs)
-        res = geo.solve(rhs, u, precision=prec, tol=1e-12 if prec == 0 else 1e-10)
+        res = geo.solve(rhs, u, precision=prec, tol=1e-12 if prec == 0 else 1e-10, residual_precision=resid)
         assert res["converged"]
         torch.cuda.synchronize()
-        assert _relerr(u.cpu().numpy(), u_ref) < tol, (prec, res)
+        assert _relerr(u.cpu().numpy(), u_ref) < tol, (prec, resid, res)
 
 
 def test_overlapping_drops_are_rejected(ctx):
