@@ -31,9 +31,18 @@ UNIT = "pair-interactions/s"
 WORKLOAD = "one drop p=32 (sphere + 0.05 SH perturbation, n<=6), lambda=5, shear (z,0,0), self rule on the p_q=65 grid"
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
 FP64_ALU_PEAK = 1.25                              # TFLOP/s: nominal GB300 FP64 rate
+
+
+def hbm_peak():
+    """Measured copy bandwidth (GB/s) of the GB300s, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this workload
 # (profiles/self_proj_f64_c2.md, profiles/self_proj_f32_c2.md); null for any other kernel.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {"self_proj_f64": 120.655872e6 + 3.2e6, "self_proj_f32": 60.348416e6 + 0.530176e6}
 
 
 def parse():
@@ -296,14 +305,23 @@ def run_ours(args):
     flops, nbytes = fl * ntarget, by * ntarget
     avg_s = dom_ms / 1e3 / max(1, dom_calls)
     f64 = dom_name.endswith("f64")
-    peak = FP64_ALU_PEAK if f64 else FP32_ALU_PEAK
-    achieved = flops / avg_s / 1e12
-    roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": PROFILED_TRAFFIC.get(dom_name), "algorithmic_flops_per_launch": flops,
-            "algorithmic_bytes_per_launch": nbytes, "hbm_gbs_achieved": nbytes / avg_s / 1e9,
-            "avg_launch_ms": avg_s * 1e3,
-            "peak_source": ("nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64 peak available)" if f64 else
-                            "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz")}
+    alu_peak = FP64_ALU_PEAK if f64 else FP32_ALU_PEAK
+    bw_peak, bw_src = hbm_peak()
+    # the roofline that bounds the kernel: the larger of its algorithmic times at the two peaks
+    t_alu, t_hbm = flops / (alu_peak * 1e12), nbytes / (bw_peak * 1e9)
+    if t_hbm > t_alu:
+        achieved = nbytes / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": bw_peak, "unit": "GB/s",
+                "frac": achieved / bw_peak, "peak_source": bw_src}
+    else:
+        achieved = flops / avg_s / 1e12
+        roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak,
+                "peak_source": ("nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64 peak available)" if f64 else
+                                "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz")}
+    roof.update({"traffic": PROFILED_TRAFFIC.get(dom_name), "algorithmic_flops_per_launch": flops,
+                 "algorithmic_bytes_per_launch": nbytes, "tflops_achieved": flops / avg_s / 1e12,
+                 "hbm_gbs_achieved": nbytes / avg_s / 1e9, "avg_launch_ms": avg_s * 1e3})
 
     # the inter-drop rows (regions, regular and upsampled pair sums) on the many-drop workloads
     also = {}
