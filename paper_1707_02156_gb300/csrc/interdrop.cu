@@ -4,6 +4,8 @@
 // source range, target mask) items.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device.cuh"
 #include "interdrop.h"
 #include "internal.cuh"
@@ -61,8 +63,16 @@ __global__ void k_classify(const double* __restrict__ rec_std, long long ntarget
 
 constexpr int kChunk = 128;  // sources staged per pass
 
+// Staged source record: (x, y, z, q0), (q1, q2, n0, n1), (n2, -, -, -) so that the inner loop reads
+// it with 128-bit shared-memory loads (two for the single layer, three for the double layer).
+template <typename R>
+struct alignas(16) SrcRec {
+  R v[12];
+};
+
 // One block per work-list block: the tile's 128 targets, TPT per thread (targets tid + u * 128/TPT),
-// against the sources of its items, staged through shared memory.
+// against the sources of its items, staged through shared memory.  The stresslet's factor -6 is
+// applied with the item's weight.
 template <typename R, int KIND, int TPT>
 __global__ void __launch_bounds__(kTile / TPT) k_interdrop(
     const PairItem* __restrict__ items, const int* __restrict__ blk_item, const long long* __restrict__ tile_t0,
@@ -72,8 +82,8 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop(
     long long nstd, const R* __restrict__ Xu, const R* __restrict__ Nu, const R* __restrict__ Qu, long long nup,
     const double* __restrict__ wts, double* __restrict__ partial) {
   constexpr int NT = kTile / TPT;  // threads per block
-  __shared__ R sx[kChunk], sy[kChunk], sz[kChunk], sq0[kChunk], sq1[kChunk], sq2[kChunk];
-  __shared__ R sn0[KIND ? kChunk : 1], sn1[KIND ? kChunk : 1], sn2[KIND ? kChunk : 1];
+  constexpr int NR = KIND ? 9 : 6;  // values used per source
+  __shared__ SrcRec<R> src[kChunk];
   const int b = blockIdx.x;
   const int it0 = blk_item[b], it1 = blk_item[b + 1];
   const int tile = items[it0].tile;
@@ -121,28 +131,34 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop(
       const int cn = (int)min((long long)kChunk, item.s1 - c0);
       for (int k = tid; k < cn; k += NT) {
         const long long sidx = c0 + k;
-        sx[k] = X[sidx];
-        sy[k] = X[ld + sidx];
-        sz[k] = X[2 * ld + sidx];
-        sq0[k] = Q[sidx];
-        sq1[k] = Q[ld + sidx];
-        sq2[k] = Q[2 * ld + sidx];
+        SrcRec<R> r;
+        r.v[0] = X[sidx];
+        r.v[1] = X[ld + sidx];
+        r.v[2] = X[2 * ld + sidx];
+        r.v[3] = Q[sidx];
+        r.v[4] = Q[ld + sidx];
+        r.v[5] = Q[2 * ld + sidx];
         if (KIND) {
-          sn0[k] = N[sidx];
-          sn1[k] = N[ld + sidx];
-          sn2[k] = N[2 * ld + sidx];
+          r.v[6] = N[sidx];
+          r.v[7] = N[ld + sidx];
+          r.v[8] = N[2 * ld + sidx];
+        } else {
+          r.v[6] = r.v[7] = r.v[8] = 0;
         }
+        r.v[9] = r.v[10] = r.v[11] = 0;
+        src[k] = r;
       }
       __syncthreads();
       if (any) {
         for (int k = 0; k < cn; ++k) {
-          const R xs_ = sx[k], ys_ = sy[k], zs_ = sz[k], q0 = sq0[k], q1 = sq1[k], q2 = sq2[k];
-          R n0 = 0, n1 = 0, n2 = 0;
-          if (KIND) {
-            n0 = sn0[k];
-            n1 = sn1[k];
-            n2 = sn2[k];
-          }
+          R v[12];
+          // 128-bit shared-memory loads of the record (the double-layer record needs all three)
+          typedef typename std::conditional<sizeof(R) == 4, float4, double2>::type V;
+          constexpr int per = 16 / sizeof(R);
+          constexpr int nv = (NR + per - 1) / per;
+#pragma unroll
+          for (int q = 0; q < nv; ++q) *reinterpret_cast<V*>(v + q * per) = reinterpret_cast<const V*>(&src[k])[q];
+          const R xs_ = v[0], ys_ = v[1], zs_ = v[2], q0 = v[3], q1 = v[4], q2 = v[5];
 #pragma unroll
           for (int u = 0; u < TPT; ++u) {
             const R dx = px[u] - xs_, dy = py[u] - ys_, dz = pz[u] - zs_;
@@ -153,10 +169,10 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop(
               s[u][0] += q0 * ri + c * dx;
               s[u][1] += q1 * ri + c * dy;
               s[u][2] += q2 * ri + c * dz;
-            } else {  // stresslet
-              const R xn = dx * n0 + dy * n1 + dz * n2;
+            } else {  // stresslet, without its factor -6
+              const R xn = dx * v[6] + dy * v[7] + dz * v[8];
               const R ri2 = ri * ri;
-              const R c = (R)(-6) * xq * xn * ri2 * ri2 * ri;
+              const R c = xq * xn * ri2 * ri2 * ri;
               s[u][0] += c * dx;
               s[u][1] += c * dy;
               s[u][2] += c * dz;
@@ -166,7 +182,7 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop(
       }
       __syncthreads();
     }
-    const double wj = wts[j];
+    const double wj = KIND ? -6.0 * wts[j] : wts[j];
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
       const double w = act[u] ? wj : 0.0;
