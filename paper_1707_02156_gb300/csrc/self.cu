@@ -334,7 +334,7 @@ __device__ inline void sym_mul_add(const R* q, const R* v, R sgn, R* acc) {
 }
 
 template <typename R, typename CT>
-__global__ void __launch_bounds__(kSelfThreads, 2) k_self_proj(
+__global__ void __launch_bounds__(kSelfThreads, sizeof(R) == 4 ? 4 : 2) k_self_proj(
     const CT* __restrict__ dens, const long long* __restrict__ foff3, int p, const R* __restrict__ wblk,
     long long wstride, const R* __restrict__ ph, const R* __restrict__ Q, int ng, const double* __restrict__ wts,
     const long long* __restrict__ val_off, double* __restrict__ vals) {
@@ -395,30 +395,40 @@ __global__ void __launch_bounds__(kSelfThreads, 2) k_self_proj(
     R E[3] = {0, 0, 0}, O[3] = {0, 0, 0};
     if (re) {
       const R* Cc = blk + boff + o;
-      for (int m = 0; m <= n; m += 2) {
+      int m = 0;
+#pragma unroll 2
+      for (; m + 1 <= n; m += 2) {
+        const R cv = Cc[(long long)m * (n + 1)], cw = Cc[(long long)(m + 1) * (n + 1)];
+        const R* gm = g + 4 * m;
+        E[0] += cv * gm[0];
+        E[1] += cv * gm[1];
+        E[2] += cv * gm[2];
+        O[0] += cw * gm[4];
+        O[1] += cw * gm[5];
+        O[2] += cw * gm[6];
+      }
+      if (m <= n) {
         const R cv = Cc[(long long)m * (n + 1)];
         const R* gm = g + 4 * m;
         E[0] += cv * gm[0];
         E[1] += cv * gm[1];
         E[2] += cv * gm[2];
       }
-      for (int m = 1; m <= n; m += 2) {
-        const R cv = Cc[(long long)m * (n + 1)];
-        const R* gm = g + 4 * m;
-        O[0] += cv * gm[0];
-        O[1] += cv * gm[1];
-        O[2] += cv * gm[2];
-      }
     } else {
       const R* Sc = blk + boff + (long long)(n + 1) * (n + 1) + (mo - 1);
-      for (int m = 2; m <= n; m += 2) {
-        const R sv = Sc[(long long)(m - 1) * n];
+      int m = 1;
+#pragma unroll 2
+      for (; m + 1 <= n; m += 2) {
+        const R sv = Sc[(long long)(m - 1) * n], sw = Sc[(long long)m * n];
         const R* gm = g - 4 * m;
-        E[0] += sv * gm[0];
-        E[1] += sv * gm[1];
-        E[2] += sv * gm[2];
+        O[0] += sv * gm[0];
+        O[1] += sv * gm[1];
+        O[2] += sv * gm[2];
+        E[0] += sw * gm[-4];
+        E[1] += sw * gm[-3];
+        E[2] += sw * gm[-2];
       }
-      for (int m = 1; m <= n; m += 2) {
+      if (m <= n) {
         const R sv = Sc[(long long)(m - 1) * n];
         const R* gm = g - 4 * m;
         O[0] += sv * gm[0];
