@@ -271,7 +271,6 @@ struct bie_geom {
     bie::DevBuf<float> qk32[2];
   };
   std::vector<std::unique_ptr<Group>> groups;
-  bie::DevBuf<double> anaF;   // analysis workspace
   struct GraphSlot {
     bool warm = false;
     cudaGraphExec_t exec = nullptr;
@@ -311,14 +310,25 @@ namespace bie {
 
 static const long long kWorkBudget = 3LL << 30;  // bytes of set-up temporaries per chunk
 
-static int analyze_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, const double* vals, double* out,
-                         cudaStream_t s) {
-  Plan* pl;
-  BIE_TRY(get_plan(ctx, G.p, G.p, &pl));
-  long long nf = (long long)G.drops.size() * 3;
-  BIE_TRY(g->anaF.alloc(nf * (G.p + 1) * (G.p + 1) * 2));
+// Galerkin projection of the values of every degree group, one launch.
+static int analyze_groups(bie_ctx* ctx, bie_geom* g, const double* vals, double* out, cudaStream_t s) {
+  std::vector<AnaGroup> ag;
+  for (auto& Gp : g->groups) {
+    auto& G = *Gp;
+    Plan* pl;
+    BIE_TRY(get_plan(ctx, G.p, G.p, &pl));
+    AnaGroup a{};
+    a.nfield = (long long)G.drops.size() * 3;
+    a.grid_off = G.goff3.ptr;
+    a.coef_off = G.foff3.ptr;
+    a.cs = pl->cs.ptr;
+    a.A = pl->A.ptr;
+    a.p = G.p;
+    ag.push_back(a);
+  }
+  std::sort(ag.begin(), ag.end(), [](const AnaGroup& x, const AnaGroup& y) { return x.p > y.p; });
   Phase ph(ctx, "analyze", s);
-  return launch_analyze_fused(vals, G.goff3.ptr, nf, G.p, pl->cs.ptr, pl->A.ptr, out, G.foff3.ptr, s);
+  return launch_analyze_fused(ag, vals, out, s);
 }
 
 // Projected-form kernel factors of one group, built on first use from the FP64 geometry cache.
@@ -344,6 +354,7 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
   auto use_direct = [&](const bie_geom::Group& G) {
     return ctx->cfg.self_direct != 0 || kernel_proj_smem(G.p, G.pq) > 227 * 1024;
   };
+  std::vector<SelfGroup<R>> proj;
   for (auto& Gp : g->groups) {
     auto& G = *Gp;
     const int p = G.p, pq = G.pq;
@@ -368,13 +379,23 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
                                     sizeof(R) == 8 ? 96 * 1024 : 40 * 1024, s));
     } else {
       BIE_TRY(ensure_qk(ctx, G, kind, s));
-      const R* Q = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.qk64[kind].ptr)
-                                  : reinterpret_cast<const R*>(G.qk32[kind].ptr);
-      // the kernel reads the FP64 density and rounds it as it loads it
-      Phase ph(ctx, sizeof(R) == 8 ? "self_proj_f64" : "self_proj_f32", s);
-      BIE_TRY((launch_self_proj<R, double>(dens, G.foff3.ptr, nd, p, wp->blk_<R>(), wp->stride, pp->cs_<R>(), Q, wts,
-                                           G.val_off.ptr, g->vals.ptr, s)));
+      SelfGroup<R> sg{};
+      sg.ndrop = nd;
+      sg.foff3 = G.foff3.ptr;
+      sg.wblk = wp->blk_<R>();
+      sg.wstride = wp->stride;
+      sg.ph = pp->cs_<R>();
+      sg.Q = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.qk64[kind].ptr)
+                            : reinterpret_cast<const R*>(G.qk32[kind].ptr);
+      sg.wts = wts;
+      sg.val_off = G.val_off.ptr;
+      sg.p = p;
+      proj.push_back(sg);
     }
+  }
+  if (!proj.empty()) {  // every projected-form group in one launch; it reads the FP64 density directly
+    Phase ph(ctx, sizeof(R) == 8 ? "self_proj_f64" : "self_proj_f32", s);
+    BIE_TRY((launch_self_proj<R, double>(proj, dens, g->vals.ptr, s)));
   }
   return BIE_OK;
 }
@@ -414,7 +435,7 @@ static int layer_apply_eager(bie_ctx* ctx, const bie_geom* gc, int kind, const d
     BIE_CUDA_TRY(cudaMemcpyAsync(out, g->vals.ptr, 3 * g->ntarget * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return BIE_OK;
   }
-  for (auto& G : g->groups) BIE_TRY(analyze_group(ctx, g, *G, g->vals.ptr, out, s));
+  BIE_TRY(analyze_groups(ctx, g, g->vals.ptr, out, s));
   return BIE_OK;
 }
 
@@ -1073,7 +1094,7 @@ static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
 static int near_snapshot(bie_geom* g, cudaStream_t s) {
   BIE_CUDA_TRY(cudaMemcpyAsync(g->selfvals.ptr, g->vals.ptr, 3 * g->ntarget * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
-  for (auto& G : g->groups) BIE_TRY(analyze_group(g->ctx, g, *G, g->selfvals.ptr, g->selfcoef.ptr, s));
+  BIE_TRY(analyze_groups(g->ctx, g, g->selfvals.ptr, g->selfcoef.ptr, s));
   return BIE_OK;
 }
 

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/bie.h"
 
@@ -48,9 +49,22 @@ int launch_phi_synth(const R* H, long long nfield, int p, int P, const R* cs, OT
 int launch_analyze(const double* grid, const long long* grid_off, long long grid_stride, long long nfield, int P,
                    int p_out, const double* cs, const double* A, double* F, double* coef,
                    const long long* coef_off, long long coef_stride, cudaStream_t s);
-// analysis of nfield fields on their own degree-p grids, one block per field (grid_off, coef_off per field)
-int launch_analyze_fused(const double* grid, const long long* grid_off, long long nfield, int p, const double* cs,
-                         const double* A, double* coef, const long long* coef_off, cudaStream_t s);
+// analysis of nfield fields on their own degree-p grids, for several degree groups in one launch
+// (grid_off, coef_off per field; begin is set by the launcher)
+struct AnaGroup {
+  long long begin, nfield;
+  const long long* grid_off;
+  const long long* coef_off;
+  const double* cs;
+  const double* A;
+  int p;
+};
+constexpr int kMaxAnaGroups = 8;
+struct AnaGroups {
+  int n;
+  AnaGroup g[kMaxAnaGroups];
+};
+int launch_analyze_fused(const std::vector<AnaGroup>& groups, const double* grid, double* coef, cudaStream_t s);
 // rotation (App. B): out[ld][a*nb+b][c] = blocks(a) applied to e^{i m alpha_b} coef[ld][c]
 template <typename CT, typename R>
 int launch_rotate(const CT* coef, const long long* field_off, int ncomp, long long ndrop, int p, const R* blocks,
@@ -81,10 +95,29 @@ int launch_self_direct(int kind, const double* dens, const long long* foff3, lon
 size_t kernel_proj_smem(int p, int pq);
 int launch_kernel_proj(int kind, const double* cache, long long ntarget, int p, int pq, const double* cs,
                        const double* T0, double* Q64, float* Q32, cudaStream_t s);
+// One degree group of the projected-form apply (device pointers; begin is set by the launcher).
+template <typename R>
+struct SelfGroup {
+  long long begin;          // first block of the group
+  long long ndrop;          // drops of the group
+  const long long* foff3;   // [drop][3] offsets of the density coefficients
+  const R* wblk;            // Wigner blocks of the group's latitudes, wstride apart
+  long long wstride;
+  const R* ph;              // cos, sin (m phi_b) of the degree-p grid
+  const R* Q;               // projected kernel factors
+  const double* wts;        // per-drop weight
+  const long long* val_off; // per-drop offset into vals
+  int p;
+};
+constexpr int kMaxSelfGroups = 8;
+template <typename R>
+struct SelfGroups {
+  int n;
+  SelfGroup<R> g[kMaxSelfGroups];
+};
+// All projected-form groups in one launch (eight groups per launch at most).
 template <typename R, typename CT>
-int launch_self_proj(const CT* dens, const long long* foff3, long long ndrop, int p, const R* wblk, long long wstride,
-                     const R* ph, const R* Q, const double* wts, const long long* val_off, double* vals,
-                     cudaStream_t s);
+int launch_self_proj(std::vector<SelfGroup<R>> groups, const CT* dens, double* vals, cudaStream_t s);
 // interfacial force at N grid points from x derivatives [6][3][N] and Gamma derivatives [3][N]
 int launch_force(const double* X, const double* Gm, long long N, double es, double xs, double* f, cudaStream_t s);
 // out[i] = (float) in[i]

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "device.cuh"
 #include "internal.cuh"
@@ -333,18 +334,31 @@ __device__ inline void sym_mul_add(const R* q, const R* v, R sgn, R* acc) {
   acc[2] += sgn * (q[4] * v[0] + q[5] * v[1] + q[2] * v[2]);
 }
 
+// One launch covers every degree group (a persistent batch over drops of uneven degree): the groups'
+// arguments travel by value, block ranges in descending degree so that the longest blocks start first.
 template <typename R, typename CT>
 __global__ void __launch_bounds__(kSelfThreads, sizeof(R) == 4 ? 4 : 2) k_self_proj(
-    const CT* __restrict__ dens, const long long* __restrict__ foff3, int p, const R* __restrict__ wblk,
-    long long wstride, const R* __restrict__ ph, const R* __restrict__ Q, int ng, const double* __restrict__ wts,
-    const long long* __restrict__ val_off, double* __restrict__ vals) {
+    SelfGroups<R> G, const CT* __restrict__ dens, double* __restrict__ vals) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ R red[kSelfThreads / 32][12];
+  SelfGroup<R> A = G.g[0];
+#pragma unroll
+  for (int i = 1; i < kMaxSelfGroups; ++i)
+    if (i < G.n && (long long)blockIdx.x >= G.g[i].begin) A = G.g[i];
+  const int p = A.p;
+  const long long* __restrict__ foff3 = A.foff3;
+  const R* __restrict__ wblk = A.wblk;
+  const long long wstride = A.wstride;
+  const R* __restrict__ ph = A.ph;
+  const R* __restrict__ Q = A.Q;
+  const double* __restrict__ wts = A.wts;
+  const long long* __restrict__ val_off = A.val_off;
   const int ntri = (p + 1) * (p + 2) / 2;
   const int nc = (p + 1) * (p + 1);
+  const int ng = (p + 1) * (2 * p + 2);
   R* g4 = reinterpret_cast<R*>(smem_raw);  // [(p+1)^2][4]
   const int hb = p + 1, nb = 2 * p + 2, na2 = (p + 2) / 2;
-  const long long bid = blockIdx.x;
+  const long long bid = (long long)blockIdx.x - A.begin;
   const long long ld = bid / ((long long)na2 * hb);
   const int r = (int)(bid - ld * na2 * hb);
   const int a = r / hb, b = r - a * hb;
@@ -532,19 +546,29 @@ int launch_kernel_proj(int kind, const double* cache, long long ntarget, int p, 
 }
 
 template <typename R, typename CT>
-int launch_self_proj(const CT* dens, const long long* foff3, long long ndrop, int p, const R* wblk, long long wstride,
-                     const R* ph, const R* Q, const double* wts, const long long* val_off, double* vals,
-                     cudaStream_t s) {
-  const int ng = (p + 1) * (2 * p + 2);
-  const long long nblk = ndrop * ((p + 2) / 2) * (p + 1);
-  if (nblk == 0) return BIE_OK;
-  if (nblk > 0x7fffffffLL) return BIE_EINVAL;
-  const size_t smem = sizeof(R) * 4 * (size_t)(p + 1) * (p + 1);
-  auto kern = k_self_proj<R, CT>;
-  if (smem > 48 * 1024) BIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<(unsigned)nblk, kSelfThreads, smem, s>>>(dens, foff3, p, wblk, wstride, ph, Q, ng, wts, val_off, vals);
-  count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
+int launch_self_proj(std::vector<SelfGroup<R>> groups, const CT* dens, double* vals, cudaStream_t s) {
+  std::sort(groups.begin(), groups.end(), [](const SelfGroup<R>& x, const SelfGroup<R>& y) { return x.p > y.p; });
+  for (size_t g0 = 0; g0 < groups.size(); g0 += kMaxSelfGroups) {
+    SelfGroups<R> G{};
+    G.n = (int)std::min<size_t>(kMaxSelfGroups, groups.size() - g0);
+    long long nblk = 0;
+    size_t smem = 0;
+    for (int i = 0; i < G.n; ++i) {
+      G.g[i] = groups[g0 + i];
+      const int p = G.g[i].p;
+      G.g[i].begin = nblk;
+      nblk += G.g[i].ndrop * ((p + 2) / 2) * (p + 1);
+      smem = std::max(smem, sizeof(R) * 4 * (size_t)(p + 1) * (p + 1));
+      if (G.g[i].ndrop * (long long)(p + 1) * (2 * p + 2) > 0x7fffffffLL) return BIE_EINVAL;
+    }
+    if (nblk == 0) continue;
+    if (nblk > 0x7fffffffLL) return BIE_EINVAL;
+    auto kern = k_self_proj<R, CT>;
+    if (smem > 48 * 1024) BIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)nblk, kSelfThreads, smem, s>>>(G, dens, vals);
+    count_launch();
+    BIE_CUDA_TRY(cudaGetLastError());
+  }
   return BIE_OK;
 }
 
@@ -554,11 +578,7 @@ template int launch_self_direct<double>(int, const double*, const long long*, lo
 template int launch_self_direct<float>(int, const double*, const long long*, long long, int, int, const float*,
                                        long long, const float*, const float*, const float*, const float*,
                                        const double*, const long long*, double*, size_t, cudaStream_t);
-template int launch_self_proj<double, double>(const double*, const long long*, long long, int, const double*,
-                                              long long, const double*, const double*, const double*,
-                                              const long long*, double*, cudaStream_t);
-template int launch_self_proj<float, double>(const double*, const long long*, long long, int, const float*,
-                                             long long, const float*, const float*, const double*, const long long*,
-                                             double*, cudaStream_t);
+template int launch_self_proj<double, double>(std::vector<SelfGroup<double>>, const double*, double*, cudaStream_t);
+template int launch_self_proj<float, double>(std::vector<SelfGroup<float>>, const double*, double*, cudaStream_t);
 
 }  // namespace bie

@@ -6,6 +6,9 @@
 // longitudes).  Analysis runs the same two steps in the opposite order with the weighted table.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace bie {
@@ -140,16 +143,23 @@ __device__ inline double warp_sum(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kAnaThreads) k_analyze_fused(const double* __restrict__ grid,
-                                                               const long long* __restrict__ grid_off, int p,
-                                                               const double* __restrict__ cs,
-                                                               const double* __restrict__ A,
-                                                               double* __restrict__ coef,
-                                                               const long long* __restrict__ coef_off) {
+// Several degree groups in one launch: block ranges per group, arguments by value.
+__global__ void __launch_bounds__(kAnaThreads) k_analyze_fused(AnaGroups G, const double* __restrict__ grid,
+                                                               double* __restrict__ coef) {
   __shared__ double F[2 * (BIE_MAX_P + 1)];
+  AnaGroup Gr = G.g[0];
+#pragma unroll
+  for (int i = 1; i < kMaxAnaGroups; ++i)
+    if (i < G.n && (long long)blockIdx.x >= G.g[i].begin) Gr = G.g[i];
+  const int p = Gr.p;
+  const long long* __restrict__ grid_off = Gr.grid_off;
+  const long long* __restrict__ coef_off = Gr.coef_off;
+  const double* __restrict__ cs = Gr.cs;
+  const double* __restrict__ A = Gr.A;
   const int nj = p + 1, nk = 2 * p + 2;
-  const long long f = blockIdx.x / (p + 1);
-  const int m = (int)(blockIdx.x - f * (p + 1));
+  const long long bl = (long long)blockIdx.x - Gr.begin;
+  const long long f = bl / (p + 1);
+  const int m = (int)(bl - f * (p + 1));
   const double* src = grid + grid_off[f];
   const double* c = cs + (long long)m * nk * 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -312,14 +322,23 @@ int launch_analyze(const double* grid, const long long* grid_off, long long grid
   return BIE_OK;
 }
 
-int launch_analyze_fused(const double* grid, const long long* grid_off, long long nfield, int p, const double* cs,
-                         const double* A, double* coef, const long long* coef_off, cudaStream_t s) {
-  if (nfield == 0) return BIE_OK;
-  const long long nblk = nfield * (p + 1);
-  if (p > BIE_MAX_P || nblk > 0x7fffffffLL) return BIE_EINVAL;
-  k_analyze_fused<<<(unsigned)nblk, kAnaThreads, 0, s>>>(grid, grid_off, p, cs, A, coef, coef_off);
-  count_launch();
-  BIE_CUDA_TRY(cudaGetLastError());
+int launch_analyze_fused(const std::vector<AnaGroup>& groups, const double* grid, double* coef, cudaStream_t s) {
+  for (size_t g0 = 0; g0 < groups.size(); g0 += kMaxAnaGroups) {
+    AnaGroups G{};
+    G.n = (int)std::min<size_t>(kMaxAnaGroups, groups.size() - g0);
+    long long nblk = 0;
+    for (int i = 0; i < G.n; ++i) {
+      G.g[i] = groups[g0 + i];
+      if (G.g[i].p > BIE_MAX_P) return BIE_EINVAL;
+      G.g[i].begin = nblk;
+      nblk += G.g[i].nfield * (G.g[i].p + 1);
+    }
+    if (nblk == 0) continue;
+    if (nblk > 0x7fffffffLL) return BIE_EINVAL;
+    k_analyze_fused<<<(unsigned)nblk, kAnaThreads, 0, s>>>(G, grid, coef);
+    count_launch();
+    BIE_CUDA_TRY(cudaGetLastError());
+  }
   return BIE_OK;
 }
 
