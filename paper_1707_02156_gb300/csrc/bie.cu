@@ -547,6 +547,7 @@ static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream
 
   // standard grid: targets and regular-rule sources, one drop at a time
   {
+    Phase ph(ctx, "setup_surface", s);
     Plan* pl;
     BIE_TRY(get_plan(ctx, p, p, &pl));
     DevBuf<double> tmp;
@@ -563,6 +564,7 @@ static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream
   }
 
   // rotated-grid cache of the singular rule (Sec. 2.2), chunked over drops
+  Phase ph(ctx, "setup_rotcache", s);
   Plan *pl, *pp;
   WigPlan* wp;
   BIE_TRY(get_plan(ctx, p, pq, &pl));
@@ -648,9 +650,13 @@ static int autotune_interdrop(bie_geom* g, cudaStream_t s) {
   BIE_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
   const int cand[3] = {1, 2, 4};
+  // time a leading part of the work list of about 5e10 pairs (at least 32 blocks per SM); blocks carry
+  // similar work, so its ranking is the full list's
+  const int nsample = (int)std::min<long long>(
+      g->nblk, std::max<long long>(32LL * 152, (long long)((double)g->nblk * std::min(1.0, 5e10 / (double)pairs))));
   for (int ci = 0; ci < 3; ++ci) {
     cudaEventRecord(e0, s);
-    int st = launch_interdrop<float>(1, cand[ci], g->nblk, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr,
+    int st = launch_interdrop<float>(1, cand[ci], nsample, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr,
                                      g->tile_n.ptr, g->tile_drop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr,
                                      g->rec_std.ptr, g->centre_d.ptr, g->sX32.ptr, g->sN32.ptr, g->sQ32.ptr,
                                      g->ntarget, g->uX32.ptr, g->uN32.ptr, g->uQ32.ptr, g->nup_total, g->wD_all.ptr,
@@ -699,6 +705,8 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   g->nup_total = uo;
   BIE_TRY(g->rec_up.alloc(7 * uo));
   BIE_TRY(g->centre_d.upload(g->centre));
+  // set-up stages are timed as phases when profiling is on
+  std::unique_ptr<Phase> stage(new Phase(ctx, "setup_records", s));
   for (int d = 0; d < nd; ++d) {
     const int p = g->p[d];
     // volume by the regular rule on the grid of degree 2p+1, mean radius, h = R pi/(p+1)
@@ -718,6 +726,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
     BIE_TRY(drop_stats(ru, g->up_n[d], &g->centre[3 * d], &v2, &g->bound[d], s));
   }
   // per-target bookkeeping
+  stage.reset(new Phase(ctx, "setup_sources", s));
   const long long nt = g->ntarget;
   std::vector<int> tdrop(nt), ngd(nd);
   std::vector<long long> tloc(nt), voff(nd);
@@ -757,24 +766,8 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
     BIE_TRY(launch_source_geometry<float>(ru, g->up_n[d], c, g->uX32.ptr + g->up_off[d], g->uN32.ptr + g->up_off[d],
                                           uo, s));
   }
-  // region classification on the device, work list on the host
-  std::vector<unsigned char> region;
-  {
-    DevBuf<unsigned char> reg;
-    DevBuf<double> bnd, hh;
-    DevBuf<long long> uoff, un;
-    BIE_TRY(reg.alloc((size_t)nt * nd));
-    BIE_TRY(bnd.upload(g->bound));
-    BIE_TRY(hh.upload(g->hdrop));
-    BIE_TRY(uoff.upload(g->up_off));
-    BIE_TRY(un.upload(g->up_n));
-    BIE_TRY(launch_classify(g->rec_std.ptr, nt, g->tdrop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr, nd,
-                            g->centre_d.ptr, bnd.ptr, hh.ptr, ctx->cfg.a_tilde, g->rec_up.ptr, uoff.ptr, un.ptr,
-                            reg.ptr, s));
-    region.resize((size_t)nt * nd);
-    BIE_CUDA_TRY(cudaMemcpyAsync(region.data(), reg.ptr, region.size(), cudaMemcpyDeviceToHost, s));
-    BIE_CUDA_TRY(cudaStreamSynchronize(s));
-  }
+  // region classification on the device, per-(tile, drop) masks on the device, work list on the host
+  stage.reset(new Phase(ctx, "setup_classify", s));
   std::vector<long long> tile_t0;
   std::vector<int> tile_n, tile_drop;
   for (int d = 0; d < nd; ++d)
@@ -784,18 +777,40 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
       tile_drop.push_back(d);
     }
   const int ntile = (int)tile_t0.size();
+  BIE_TRY(g->tile_t0.upload(tile_t0));
+  BIE_TRY(g->tile_n.upload(tile_n));
+  std::vector<TileMask> tmask((size_t)ntile * nd);
+  {
+    DevBuf<unsigned char> reg;
+    DevBuf<double> bnd, hh;
+    DevBuf<long long> uoff, un;
+    DevBuf<TileMask> tm;
+    BIE_TRY(reg.alloc((size_t)nt * nd));
+    BIE_TRY(bnd.upload(g->bound));
+    BIE_TRY(hh.upload(g->hdrop));
+    BIE_TRY(uoff.upload(g->up_off));
+    BIE_TRY(un.upload(g->up_n));
+    BIE_TRY(tm.alloc(tmask.size()));
+    BIE_TRY(launch_classify(g->rec_std.ptr, nt, g->tdrop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr, nd,
+                            g->centre_d.ptr, bnd.ptr, hh.ptr, ctx->cfg.a_tilde, g->rec_up.ptr, uoff.ptr, un.ptr,
+                            reg.ptr, s));
+    BIE_TRY(launch_tile_masks(reg.ptr, nd, g->tile_t0.ptr, g->tile_n.ptr, ntile, tm.ptr, s));
+    BIE_CUDA_TRY(cudaMemcpyAsync(tmask.data(), tm.ptr, tmask.size() * sizeof(TileMask), cudaMemcpyDeviceToHost, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  stage.reset(new Phase(ctx, "setup_worklist", s));
+  auto popc = [](const unsigned* m) {
+    int c = 0;
+    for (int q = 0; q < 4; ++q) c += __builtin_popcount(m[q]);
+    return c;
+  };
   // total sources over all tiles, to aim at >= 8 blocks per SM overall
   long long all_sources = 0;
   for (int ti = 0; ti < ntile; ++ti)
     for (int j = 0; j < nd; ++j) {
       if (j == tile_drop[ti]) continue;
-      bool any0 = false, any1 = false;
-      for (int k = 0; k < tile_n[ti]; ++k) {
-        const unsigned char r = region[(size_t)(tile_t0[ti] + k) * nd + j];
-        any0 |= r == 0;
-        any1 |= r == 1;
-      }
-      all_sources += (any0 ? ngd[j] : 0) + (any1 ? g->up_n[j] : 0);
+      const TileMask& tmj = tmask[(size_t)ti * nd + j];
+      all_sources += (popc(tmj.m[0]) ? ngd[j] : 0) + (popc(tmj.m[1]) ? g->up_n[j] : 0);
     }
   const long long cap_global = std::max<long long>(2048, std::min<long long>(65536, all_sources / (8 * 152)));
   std::vector<PairItem> items;
@@ -808,25 +823,19 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
     for (int j = 0; j < nd; ++j) {
       if (j == tile_drop[ti]) continue;
       PairItem a{}, b{};
-      int n0 = 0, n1 = 0;
-      for (int k = 0; k < tile_n[ti]; ++k) {
-        const long long t = tile_t0[ti] + k;
-        const unsigned char r = region[(size_t)t * nd + j];
-        if (r == 3) {
-          set_error("drops overlap: a grid point of drop " + std::to_string(tile_drop[ti]) + " lies inside drop " +
-                    std::to_string(j));
-          return BIE_EOVERLAP;
-        }
-        if (r == 0) {
-          a.mask[k >> 5] |= 1u << (k & 31);
-          ++n0;
-        } else if (r == 1) {
-          b.mask[k >> 5] |= 1u << (k & 31);
-          ++n1;
-        } else if (r == 2) {
-          g->near.emplace_back(t, j);
-        }
+      const TileMask& tmj = tmask[(size_t)ti * nd + j];
+      if (tmj.inside) {
+        set_error("drops overlap: a grid point of drop " + std::to_string(tile_drop[ti]) + " lies inside drop " +
+                  std::to_string(j));
+        return BIE_EOVERLAP;
       }
+      for (int q = 0; q < 4; ++q) {
+        a.mask[q] = tmj.m[0][q];
+        b.mask[q] = tmj.m[1][q];
+      }
+      const int n0 = popc(tmj.m[0]), n1 = popc(tmj.m[1]);
+      for (int k = 0; k < tile_n[ti]; ++k)
+        if ((tmj.m[2][k >> 5] >> (k & 31)) & 1u) g->near.emplace_back(tile_t0[ti] + k, j);
       if (n0) {
         a.tile = ti;
         a.src_drop = j;
@@ -877,8 +886,6 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   if (!items.empty()) BIE_TRY(g->items.upload(items));
   BIE_TRY(g->blk_item.upload(blk_item));
   BIE_TRY(g->tile_blk.upload(tile_blk));
-  BIE_TRY(g->tile_t0.upload(tile_t0));
-  BIE_TRY(g->tile_n.upload(tile_n));
   BIE_TRY(g->tile_drop.upload(tile_drop));
   BIE_TRY(g->partial.alloc((size_t)std::max(1, nblk) * 3 * kTile));
   std::vector<double> wS(nd), wD(nd), wSr(nd), wDr(nd);
@@ -897,7 +904,9 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   g->info.near_targets = (long long)g->near.size();
   BIE_TRY(g->up_off_d.upload(g->up_off));
   BIE_TRY(g->up_n_d.upload(g->up_n));
+  stage.reset(new Phase(ctx, "setup_autotune", s));
   BIE_TRY(autotune_interdrop(g, s));
+  stage.reset();
   for (auto& G : g->groups) {
     std::vector<long long> so, uo2;
     for (int d : G->drops) {
@@ -907,7 +916,10 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
     BIE_TRY(G->src_off_std.upload(so));
     BIE_TRY(G->src_off_up.upload(uo2));
   }
-  if (!g->near.empty()) BIE_TRY(setup_near(ctx, g, s));
+  if (!g->near.empty()) {
+    Phase ph(ctx, "setup_near", s);
+    BIE_TRY(setup_near(ctx, g, s));
+  }
   return BIE_OK;
 }
 

@@ -370,6 +370,26 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_df(
   }
 }
 
+// Per (tile, source drop j): the tile's targets in Omega_0, Omega_1 and Omega_2 of drop j as 128-bit
+// masks, and whether any target lies inside drop j.  Consecutive threads take consecutive j, so the
+// region reads of one target are coalesced.
+__global__ void k_tile_masks(const unsigned char* __restrict__ region, int nd, const long long* __restrict__ tile_t0,
+                             const int* __restrict__ tile_n, long long ntile, TileMask* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ntile * nd) return;
+  const long long ti = idx / nd;
+  const int j = (int)(idx - ti * nd);
+  TileMask m{};
+  const long long t0 = tile_t0[ti];
+  const int n = tile_n[ti];
+  for (int k = 0; k < n; ++k) {
+    const unsigned char r = region[(t0 + k) * nd + j];
+    if (r < 3) m.m[r][k >> 5] |= 1u << (k & 31);
+    else if (r == 3) m.inside = 1;
+  }
+  out[idx] = m;
+}
+
 // vals += sum of the partials of the tile's blocks, in block order
 __global__ void k_reduce_tiles(const double* __restrict__ partial, const int* __restrict__ tile_blk,
                                const long long* __restrict__ tile_t0, const int* __restrict__ tile_n,
@@ -517,6 +537,16 @@ int launch_interdrop_df(int kind, int nblk, const PairItem* items, const int* bl
   auto kern = kind == 0 ? k_interdrop_df<0, TPT> : k_interdrop_df<1, TPT>;
   kern<<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd, rec_std,
                                     centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
+int launch_tile_masks(const unsigned char* region, int nd, const long long* tile_t0, const int* tile_n,
+                      long long ntile, TileMask* out, cudaStream_t s) {
+  const long long n = ntile * nd;
+  if (n == 0) return BIE_OK;
+  k_tile_masks<<<blocks_for(n), kThreads, 0, s>>>(region, nd, tile_t0, tile_n, ntile, out);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;

@@ -17,6 +17,13 @@ struct PairItem {
   unsigned mask[4];
 };
 
+// targets of a tile per region of one source drop (bit k of m[r] = target k in region r)
+struct TileMask {
+  unsigned m[3][4];
+  int inside;  // some target lies inside the source drop
+};
+int launch_tile_masks(const unsigned char* region, int nd, const long long* tile_t0, const int* tile_n,
+                      long long ntile, TileMask* out, cudaStream_t s);
 int launch_classify(const double* rec_std, long long ntarget, const int* tdrop, const long long* tloc,
                     const long long* toff_std, const int* ngd, int ndrop, const double* centre, const double* bound,
                     const double* h, double a_tilde, const double* rec_up, const long long* up_off,
