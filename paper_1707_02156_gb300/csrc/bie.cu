@@ -795,6 +795,8 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
                             g->centre_d.ptr, bnd.ptr, hh.ptr, ctx->cfg.a_tilde, g->rec_up.ptr, uoff.ptr, un.ptr,
                             reg.ptr, s));
     BIE_TRY(launch_tile_masks(reg.ptr, nd, g->tile_t0.ptr, g->tile_n.ptr, ntile, tm.ptr, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+    stage.reset(new Phase(ctx, "setup_masks_copy", s));
     BIE_CUDA_TRY(cudaMemcpyAsync(tmask.data(), tm.ptr, tmask.size() * sizeof(TileMask), cudaMemcpyDeviceToHost, s));
     BIE_CUDA_TRY(cudaStreamSynchronize(s));
   }
@@ -834,8 +836,9 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
         b.mask[q] = tmj.m[1][q];
       }
       const int n0 = popc(tmj.m[0]), n1 = popc(tmj.m[1]);
-      for (int k = 0; k < tile_n[ti]; ++k)
-        if ((tmj.m[2][k >> 5] >> (k & 31)) & 1u) g->near.emplace_back(tile_t0[ti] + k, j);
+      if (tmj.m[2][0] | tmj.m[2][1] | tmj.m[2][2] | tmj.m[2][3])
+        for (int k = 0; k < tile_n[ti]; ++k)
+          if ((tmj.m[2][k >> 5] >> (k & 31)) & 1u) g->near.emplace_back(tile_t0[ti] + k, j);
       if (n0) {
         a.tile = ti;
         a.src_drop = j;
@@ -879,6 +882,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
     }
   }
   tile_blk[ntile] = (int)blk_item.size();
+  stage.reset(new Phase(ctx, "setup_worklist_upload", s));
   const int nblk = (int)blk_item.size();
   blk_item.push_back((int)items.size());
   g->ntile = ntile;

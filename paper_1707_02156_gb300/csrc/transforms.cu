@@ -136,7 +136,7 @@ __global__ void k_leg_analyze(const double* __restrict__ F, long long nfield, in
 // F_m(theta_j) of the block's order, one warp per latitude with the lanes across the longitudes
 // (coalesced loads, shuffle reduction), then the contraction with the weighted Legendre table for
 // n = m..p, one warp per degree with the lanes across the latitudes.
-constexpr int kAnaThreads = 128;
+constexpr int kAnaThreads = 512;  // 16 warps: about two latitudes, then two degrees, per warp at p = 32
 
 __device__ inline double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -144,3 +144,33 @@ def test_graph_replay_matches_eager_launches_bit_for_bit():
         ctx.close()
     for a, b in zip(outs[False], outs[True]):
         assert np.array_equal(a, b)
+
+
+def test_more_degree_groups_than_one_launch_holds():
+    # ten drops of ten different degrees: the self term and the Galerkin projection of all groups run
+    # as one launch of at most eight groups, so this takes two launches of each
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_02156_gb300 import api
+    rng = np.random.default_rng(21)
+    ps = list(range(3, 13))
+    xs, fs = [], []
+    for i, p in enumerate(ps):
+        c = (3.0 * (i % 4), 3.0 * ((i // 4) % 3), 3.0 * (i // 12))
+        x = inputs.sphere_coef(p, centre=c, axes=(1.0, 0.9, 1.1), rot=inputs.random_rotation(rng))
+        xs.append(x + inputs.perturbation(rng, p, 1, 3, 0.03))
+        fs.append(inputs.random_bandlimited(rng, p, 3))
+    lam = np.linspace(0.5, 3.0, len(ps))
+    drops = layer.Drops(xs, ps, ps, lam, up=3)
+    ctx = api.Context(0, upsample=3)
+    geo = ctx.geometry(ps, ps, torch.tensor(inputs.pack_drops(xs), device="cuda"), lam)
+    f = torch.tensor(inputs.pack_drops(fs), device="cuda")
+    out = torch.zeros_like(f)
+    for kind in ("S", "D"):
+        ref = np.concatenate([r.ravel() for r in (drops.apply_single if kind == "S" else drops.apply_double)(fs)])
+        for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
+            (geo.apply_single if kind == "S" else geo.apply_double)(f, out, precision=prec)
+            torch.cuda.synchronize()
+            assert _relerr(out.cpu().numpy(), ref) < tol, (kind, prec)
+    geo.close()
+    ctx.close()
