@@ -202,10 +202,12 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop(
 }
 
 // ---- double-float pair sums ----
-// A double-float value is an unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2
-// (about 44 significant bits).  Sums use Knuth's TwoSum and products the FMA-based TwoProduct (both
-// error-free transformations), renormalised by Dekker's Fast2Sum; 1/sqrt starts from the FP32
-// estimate and takes one Newton step in double-float.  Every operation runs on the FP32 pipes.
+// A double-float value is an unevaluated sum hi + lo of two FP32 numbers (about 44 significant
+// bits).  Sums use Knuth's TwoSum and products the FMA-based TwoProduct (both error-free
+// transformations).  Results are left unnormalised (|lo| may exceed ulp(hi)/2 by a few units, which
+// costs no accuracy in the short chains of one pair); the per-target accumulators are renormalised
+// by Dekker's Fast2Sum after every staged chunk of sources.  1/sqrt starts from the FP32 estimate and
+// takes one Newton step in double-float.  Every operation runs on the FP32 pipes.
 struct df2 {
   float h, l;
 };
@@ -221,8 +223,12 @@ __device__ inline df2 fast2sum(float a, float b) {  // |a| >= |b|
 __device__ inline df2 df_add(df2 a, df2 b) {
   const float s = a.h + b.h;
   const float v = s - a.h;
-  const float e = (a.h - (s - v)) + (b.h - v) + a.l + b.l;
-  return fast2sum(s, e);
+  return {s, (a.h - (s - v)) + (b.h - v) + a.l + b.l};
+}
+__device__ inline df2 df_renorm(df2 a) {  // TwoSum of the two parts
+  const float s = a.h + a.l;
+  const float v = s - a.h;
+  return {s, (a.h - (s - v)) + (a.l - v)};
 }
 __device__ inline df2 df_neg(df2 a) { return {-a.h, -a.l}; }
 __device__ inline df2 df_mul(df2 a, df2 b) {
@@ -230,19 +236,13 @@ __device__ inline df2 df_mul(df2 a, df2 b) {
   float e = fmaf(a.h, b.h, -p);
   e = fmaf(a.h, b.l, e);
   e = fmaf(a.l, b.h, e);
-  return fast2sum(p, e);
+  return {p, e};
 }
 __device__ inline df2 df_sqr(df2 a) {
   const float p = a.h * a.h;
   float e = fmaf(a.h, a.h, -p);
   e = fmaf(2.0f * a.h, a.l, e);
-  return fast2sum(p, e);
-}
-__device__ inline df2 df_mulf(df2 a, float b) {
-  const float p = a.h * b;
-  float e = fmaf(a.h, b, -p);
-  e = fmaf(a.l, b, e);
-  return fast2sum(p, e);
+  return {p, e};
 }
 __device__ inline df2 df_rsqrt(df2 a) {
   const float y = rsqrtf(a.h);
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_df(
               const df2 xn = df_add(df_add(df_mul(dx, n0), df_mul(dy, n1)), df_mul(dz, n2));
               const df2 ri2 = df_sqr(ri);
               const df2 ri5 = df_mul(df_sqr(ri2), ri);
-              const df2 c = df_mulf(df_mul(df_mul(xq, xn), ri5), -6.0f);
+              const df2 c = df_mul(df_mul(xq, xn), ri5);  // the factor -6 goes with the weight
               s[u][0] = df_add(s[u][0], df_mul(c, dx));
               s[u][1] = df_add(s[u][1], df_mul(c, dy));
               s[u][2] = df_add(s[u][2], df_mul(c, dz));
@@ -351,8 +351,12 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_df(
         }
       }
       __syncthreads();
+#pragma unroll
+      for (int u = 0; u < TPT; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s[u][c] = df_renorm(s[u][c]);
     }
-    const double wj = wts[j];
+    const double wj = KIND ? -6.0 * wts[j] : wts[j];
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
       const double w = act[u] ? wj : 0.0;
