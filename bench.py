@@ -329,20 +329,29 @@ def run_ours(args):
         geo.close()
         for name in ("c4", "c5"):
             runs = ((1, 3, 2), (2, 2, 1), (0, 1, 0))
-            info_a, pairs_a, res_a, sol = time_apply(name, local, runs, solve=(name == "c4"))
+            info_a, pairs_a, res_a, sol = time_apply(name, local, runs, solve="both" if name == "c4" else "mixed")
             ma = res_a[1]
             also[name] = {"workload": APPLY_WORKLOADS[name], "step": "one mixed double-layer apply",
                           "ms_per_apply": ma["ms"], "pairs": pairs_a, "value": pairs_a / (ma["ms"] / 1e3),
                           "unit": UNIT, "far_pairs": info_a["far_pairs"], "up_pairs": info_a["up_pairs"],
                           "roofline": interdrop_roofline(info_a, ma["phases"], 3),
                           "setup_ms": info_a["setup_ms"], "precisions": apply_summary(res_a)}
-            if sol:
+            if sol and "fp64" in sol:
                 rel_a = float(torch.linalg.norm(sol["mixed"]["u"] - sol["fp64"]["u"]) / torch.linalg.norm(sol["fp64"]["u"]))
                 also[name]["solve"] = {
                     "step": "rhs + solve to 1e-10: mixed GMRES with double-float refinement residuals vs FP64 GMRES",
                     "mixed": {k: v for k, v in sol["mixed"].items() if k != "u"},
                     "fp64": {k: v for k, v in sol["fp64"].items() if k != "u"},
                     "speedup_vs_fp64": sol["fp64"]["ms"] / sol["mixed"]["ms"], "rel_err_mixed_vs_fp64": rel_a}
+            elif sol:
+                # an FP64 GMRES solve here takes minutes: its time is estimated, not measured, as
+                # (iterations of the mixed solve + 1 right-hand side) FP64 applies
+                est = (sol["mixed"]["iterations"] + 1) * res_a[0]["ms"]
+                also[name]["solve"] = {
+                    "step": "rhs + solve to 1e-10: mixed GMRES with double-float refinement residuals",
+                    "mixed": {k: v for k, v in sol["mixed"].items() if k != "u"},
+                    "fp64_estimate_ms": est, "fp64_estimate": "(mixed iterations + 1) x measured FP64 apply; not run",
+                    "speedup_vs_fp64_estimate": est / sol["mixed"]["ms"]}
 
     cpu = cpu_baseline_sample(w, budget_s=15.0) if rank == 0 else None
     res = {
@@ -485,7 +494,8 @@ def time_apply(name, local, runs=((1, 3, 2),), solve=False):
             uinf[o:o + k] = torch.tensor(w.xcoef[o + 2 * k:o + 3 * k], device="cuda")
             o += 3 * k
         sol = {}
-        for label, prec, rprec in (("mixed", 1, 2), ("fp64", 0, 0)):
+        cases = (("mixed", 1, 2), ("fp64", 0, 0)) if solve == "both" else (("mixed", 1, 2),)
+        for label, prec, rprec in cases:
             b = torch.zeros_like(f)
             u = torch.zeros_like(f)
             last = {}
