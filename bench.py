@@ -57,6 +57,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(t_local, device="cuda"):
+    """The job's time: the largest of the ranks' times (t_local itself in a single process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_local
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, t_max):
+    """Units processed by all ranks per second of the job's (slowest rank's) time."""
+    return world * units_per_rank / t_max
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -245,15 +261,9 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
     launches = api.launch_count() - launches0
-    t_local = ms_total / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
+    t_max = max_over_ranks(ms_total / 1e3)
     ms_step = 1e3 * t_max / args.steps
-    value = world * applies * pairs_per_apply / t_max
+    value = whole_job_rate(applies * pairs_per_apply, world, t_max)
     # the same K steps again with the library's per-phase CUDA events on (kernels launched one by one)
     ctx.profile(True)
     ms_step_profiled = timed_steps(lambda: step(1, u, rhs), args.steps, stream, scrub) / args.steps
