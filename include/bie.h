@@ -137,8 +137,11 @@ int bie_rotate_noalloc(bie_ctx* ctx, int ndrop, const int* p, int ncomp, const d
  *          p <= pq <= 2p+1 (pq = 2p+1 is the "upsampled 2x for quadrature" rule);
  *   xcoef  [drop][3][(p+1)^2] device coefficients of x(theta, phi);
  *   lambda host [ndrop] viscosity ratios.
- * Synchronous: returns when the geometry is ready.  BIE_EOVERLAP if a grid point of one drop lies
- * inside another.  The geometry owns its device memory until bie_geometry_destroy. */
+ * Synchronous: returns when the geometry is ready.  With the projected self form (the default) this
+ * includes the projected kernel factors of both layers, after which the rotated-grid cache is
+ * released; with bie_config.self_direct the cache is kept for the per-apply evaluation.
+ * BIE_EOVERLAP if a grid point of one drop lies inside another.  The geometry owns its device
+ * memory until bie_geometry_destroy. */
 int bie_geometry_setup(bie_ctx* ctx, int ndrop, const int* p, const int* pq, const double* xcoef,
                        const double* lambda, bie_geom** geom, void* stream);
 void bie_geometry_destroy(bie_geom* geom);

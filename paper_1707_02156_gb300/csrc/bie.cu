@@ -331,7 +331,13 @@ static int analyze_groups(bie_ctx* ctx, bie_geom* g, const double* vals, double*
   return launch_analyze_fused(ag, vals, out, s);
 }
 
-// Projected-form kernel factors of one group, built on first use from the FP64 geometry cache.
+// The direct form serves a group when the configuration asks for it, or when the projected form's
+// per-target factors would not fit in shared memory while they are built.
+static bool group_uses_direct(const bie_ctx* ctx, const bie_geom::Group& G) {
+  return ctx->cfg.self_direct != 0 || kernel_proj_smem(G.p, G.pq) > 227 * 1024;
+}
+
+// Projected-form kernel factors of one group, built from the FP64 rotated-grid cache.
 static int ensure_qk(bie_ctx* ctx, bie_geom::Group& G, int kind, cudaStream_t s) {
   if (G.qk64[kind].ptr) return BIE_OK;
   Plan* pl;
@@ -351,9 +357,7 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
   bie_ctx* ctx = g->ctx;
   // the projected form keeps its per-target factors in shared memory while they are built; groups
   // whose factors do not fit there use the direct form
-  auto use_direct = [&](const bie_geom::Group& G) {
-    return ctx->cfg.self_direct != 0 || kernel_proj_smem(G.p, G.pq) > 227 * 1024;
-  };
+  auto use_direct = [&](const bie_geom::Group& G) { return group_uses_direct(ctx, G); };
   std::vector<SelfGroup<R>> proj;
   for (auto& Gp : g->groups) {
     auto& G = *Gp;
@@ -1831,13 +1835,22 @@ int bie_geometry_setup(bie_ctx* ctx, int ndrop, const int* p, const int* pq, con
     self_pairs += (long long)G->drops.size() * ngrid(G->p) * ngrid(G->pq);
   }
   if (ndrop > 1) BIE_TRY(setup_interdrop(ctx, g.get(), s));
+  // projected-form groups: both kinds' factors now, then the rotated-grid cache is no longer needed
+  for (auto& G : g->groups) {
+    if (group_uses_direct(ctx, *G)) continue;
+    BIE_TRY(ensure_qk(ctx, *G, 0, s));
+    BIE_TRY(ensure_qk(ctx, *G, 1, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+    G->cache64.release();
+  }
   BIE_CUDA_TRY(cudaStreamSynchronize(s));
   g->info.ndrop = ndrop;
   g->info.ncoef = co;
   g->info.ntarget = to;
   g->info.self_pairs = self_pairs;
   double bytes = 0;
-  for (auto& G : g->groups) bytes += G->cache64.n * 8.0;
+  for (auto& G : g->groups)
+    bytes += G->cache64.n * 8.0 + (G->qk64[0].n + G->qk64[1].n) * 8.0 + (G->qk32[0].n + G->qk32[1].n) * 4.0;
   bytes += g->rec_std.n * 8.0 + g->vals.n * 8.0 + g->xcoef.n * 8.0;
   g->info.cache_bytes = bytes;
   *out = g.release();
