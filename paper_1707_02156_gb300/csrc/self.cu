@@ -300,12 +300,24 @@ __global__ void __launch_bounds__(256) k_kernel_proj(const double* __restrict__ 
     }
     __syncthreads();
   }
+  // The apply adds every product with a plus sign: the imaginary planes of targets on latitudes
+  // a <= p/2 are stored negated (imaginary parts enter as -Q_im), and targets on latitudes a > p/2,
+  // which the apply reaches as the mirror pi - theta of a lower latitude, carry (-1)^(n+m).
   double* o64 = Q64 + t * 12 * ntri;
   float* o32 = Q32 ? Q32 + t * 12 * ntri : nullptr;
+  const int nbl = 2 * p + 2;
+  const int lat = (int)((t % ((long long)(p + 1) * nbl)) / nbl);
+  const bool mirror = 2 * lat > p;
   for (int i = threadIdx.x; i < 12 * ntri; i += blockDim.x) {
-    const int it = i % ntri;
+    const int it = i % ntri, plane = i / ntri;
     const int n = tri_index_degree(it);
-    const double v = (it == n * (n + 1) / 2 ? 1.0 : 2.0) * sq[i];  // c_m: m = 0 at the start of degree n
+    const int m = it - n * (n + 1) / 2;
+    double v = (m == 0 ? 1.0 : 2.0) * sq[i];  // c_m
+    if (mirror) {
+      if ((n + m) & 1) v = -v;
+    } else if (plane & 1) {
+      v = -v;
+    }
     o64[i] = v;
     if (o32) o32[i] = (float)v;
   }
@@ -328,10 +340,10 @@ constexpr int kSelfThreads = 256;
 
 // acc += S v for the symmetric 3x3 matrix S with entries (xx, yy, zz, xy, xz, yz) at planes q[0..5]
 template <typename R>
-__device__ inline void sym_mul_add(const R* q, const R* v, R sgn, R* acc) {
-  acc[0] += sgn * (q[0] * v[0] + q[3] * v[1] + q[4] * v[2]);
-  acc[1] += sgn * (q[3] * v[0] + q[1] * v[1] + q[5] * v[2]);
-  acc[2] += sgn * (q[4] * v[0] + q[5] * v[1] + q[2] * v[2]);
+__device__ inline void sym_mul_add(const R* q, const R* v, R* acc) {
+  acc[0] = fma(q[4], v[2], fma(q[3], v[1], fma(q[0], v[0], acc[0])));
+  acc[1] = fma(q[5], v[2], fma(q[1], v[1], fma(q[3], v[0], acc[1])));
+  acc[2] = fma(q[2], v[2], fma(q[5], v[1], fma(q[4], v[0], acc[2])));
 }
 
 // One launch covers every degree group (a persistent batch over drops of uneven degree): the groups'
@@ -456,16 +468,14 @@ __global__ void __launch_bounds__(kSelfThreads, sizeof(R) == 4 ? 4 : 2) k_self_p
       vp[c] = E[c] + O[c];
       vm[c] = E[c] - O[c];
     }
-    // real parts enter with +Q_re, imaginary parts with -Q_im.  Latitude pi - theta_a carries
-    // (-1)^(n + m') on the real and -(-1)^(n + m') on the imaginary parts, so its sign is
-    // (-1)^(n + m') in both cases.
-    const R s0 = re ? (R)1 : (R)-1;
-    const R s2 = ((n + mo) & 1) ? (R)-1 : (R)1;
-    sym_mul_add<R>(q[0], vp, s0, acc[0]);
-    sym_mul_add<R>(q[1], vm, s0, acc[1]);
+    // Real parts enter with +Q_re, imaginary parts with -Q_im; latitude pi - theta_a carries
+    // (-1)^(n + m') on the real and -(-1)^(n + m') on the imaginary parts.  Both signs are stored in
+    // the factors (see k_kernel_proj), so every product is added.
+    sym_mul_add<R>(q[0], vp, acc[0]);
+    sym_mul_add<R>(q[1], vm, acc[1]);
     if (quad) {
-      sym_mul_add<R>(q[2], vm, s2, acc[2]);
-      sym_mul_add<R>(q[3], vp, s2, acc[3]);
+      sym_mul_add<R>(q[2], vm, acc[2]);
+      sym_mul_add<R>(q[3], vp, acc[3]);
     }
   }
   // block reduction of the 12 sums
