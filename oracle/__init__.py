@@ -12,6 +12,7 @@ Modules, each following the passage of Sorgentone & Tornberg (arXiv 1707.02156) 
   layer     singular self quadrature (Thm 1, Sec. 2.2), regular and upsampled pair sums and the
             region split (Sec. 2.3), near-singular interpolation (Sec. 2.3), Galerkin projection (Sec. 1.2)
   gmres     restarted GMRES with modified Gram-Schmidt (Sec. 7)
+  timestep  midpoint step of the drop shapes with the surfactant held fixed (Sec. 3, Alg. 1)
   brute     adaptive polar quadrature used only to pin the singular rule
 
 Parity unpinned: the absolute accuracy of the near-singular (Omega_2) interpolation on

@@ -174,3 +174,35 @@ def test_more_degree_groups_than_one_launch_holds():
             assert _relerr(out.cpu().numpy(), ref) < tol, (kind, prec)
     geo.close()
     ctx.close()
+
+
+def test_double_float_rhs_matches_fp64(batch):
+    # b = 2 u_inf + S[f] with the single layer in double-float (inter-drop pairs) and in FP64
+    ps, xs, fs, lam, drops, geo = batch
+    f = torch.tensor(inputs.pack_drops(fs), device="cuda")
+    uinf = torch.zeros_like(f)
+    b64, bdf = torch.zeros_like(f), torch.zeros_like(f)
+    geo.rhs(uinf, f, b64, precision=0)
+    geo.rhs(uinf, f, bdf, precision=2)
+    torch.cuda.synchronize()
+    assert _relerr(bdf.cpu().numpy(), b64.cpu().numpy()) < DF_TOL
+
+
+def test_double_float_is_fp64_for_one_drop():
+    # without inter-drop pairs BIE_DF runs the FP64 path: identical results
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_02156_gb300 import api
+    rng = np.random.default_rng(3)
+    p = 9
+    x = inputs.sphere_coef(p) + inputs.perturbation(rng, p, 1, 4, 0.05)
+    f = torch.tensor(inputs.random_bandlimited(rng, p, 3).ravel(), device="cuda")
+    ctx = api.Context(0)
+    geo = ctx.geometry([p], [p], torch.tensor(x.ravel(), device="cuda"), [2.0])
+    a, b = torch.zeros_like(f), torch.zeros_like(f)
+    geo.apply_double(f, a, precision=0)
+    geo.apply_double(f, b, precision=2)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    geo.close()
+    ctx.close()
