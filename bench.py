@@ -363,6 +363,8 @@ def run_ours(args):
                     "fp64_estimate_ms": est, "fp64_estimate": "(mixed iterations + 1) x measured FP64 apply; not run",
                     "speedup_vs_fp64_estimate": est / sol["mixed"]["ms"]}
 
+    if not args.no_aux:
+        also["c4"]["time_step"] = time_midpoint("c4", local)
     cpu = cpu_baseline_sample(w, budget_s=15.0) if rank == 0 else None
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -529,6 +531,31 @@ def time_apply(name, local, runs=((1, 3, 2),), solve=False):
     torch.cuda.empty_cache()
     info["setup_ms"] = setup
     return info, pairs, res, sol
+
+
+def time_midpoint(name, local, nsteps=2, dt=0.01):
+    """Wall time of midpoint steps of the drop shapes (two geometries, two right-hand sides and two
+    mixed solves with double-float residuals per step) on a many-drop workload in shear."""
+    import torch
+    from paper_1707_02156_gb300 import api, build, inputs
+    build.build()
+    w = inputs.config(name)
+    shear = w.shear if w.shear else 1.0
+    ctx = api.Context(local, upsample=w.up)
+    x = torch.tensor(w.xcoef, device="cuda")
+    g = torch.tensor(w.gamma, device="cuda")
+    out = []
+    for _ in range(nsteps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = api.midpoint_step(ctx, w.p, w.pq, x, g, w.elasticity, 0.0, w.lam, shear, dt)
+        torch.cuda.synchronize()
+        out.append({"ms": 1e3 * (time.perf_counter() - t0),
+                    "iterations": [i["iterations"] for i in infos], "residual": [i["residual"] for i in infos]})
+    ctx.close()
+    torch.cuda.empty_cache()
+    return {"step": f"midpoint step dt={dt} in shear {shear}: geometry, force, rhs and mixed solve at x and x+dt/2 u",
+            "first_includes": "the context's per-degree tables", "steps": out}
 
 
 def interdrop_roofline(info, phases, steps):

@@ -233,6 +233,24 @@ typedef struct bie_phase_stat {
 int bie_profile(bie_ctx* ctx, int enable);
 int bie_profile_read(bie_ctx* ctx, bie_phase_stat* stats, int cap, int* count);
 
+/* One midpoint time step of the drop shapes (Sec. 3, the drop update of Alg. 1, with the surfactant
+ * held fixed over the step):
+ *     x^{1/2} = x + (dt/2) u(x),    x^{new} = x + dt u(x^{1/2}),
+ * where u(x) solves Eq. main_eq (bie_solve) for the shapes x, in the linear shear u_inf =
+ * (shear z, 0, 0), with the interfacial force of the surfactant coefficients (bie_interfacial_force).
+ *   p, pq, lambda   host [ndrop], as bie_geometry_setup;
+ *   xcoef           [drop][3][(p+1)^2] device shapes: in at t, out at t + dt;
+ *   gammacoef       [drop][1][(p+1)^2] device surfactant coefficients (not changed);
+ *   elasticity, x_s as bie_interfacial_force;
+ *   opts            options of both solves (zero initial guesses; the right-hand sides are formed at
+ *                   BIE_FP64 for an FP64 solve, else at opts->residual_precision);
+ *   info            NULL or an array of two: the solves at x and at x^{1/2}.
+ * Builds and destroys the two geometries it needs.  Synchronous.  The status of the first failing
+ * call is returned (xcoef unchanged unless both solves succeeded). */
+int bie_step_midpoint(bie_ctx* ctx, int ndrop, const int* p, const int* pq, double* xcoef, const double* gammacoef,
+                      double elasticity, double x_s, const double* lambda, double shear, double dt,
+                      const bie_solve_opts* opts, bie_solve_info* info, void* stream);
+
 /* Number of CUDA kernels the library has launched in this process (all contexts). */
 long long bie_launch_count(void);
 

@@ -69,6 +69,8 @@ EXPORTS = {
     "bie_profile": (c_int, [c_void, c_int]),
     "bie_profile_read": (c_int, [c_void, ctypes.POINTER(bie_phase_stat), c_int, P_int]),
     "bie_launch_count": (c_ll, []),
+    "bie_step_midpoint": (c_int, [c_void, c_int, P_int, P_int, c_void, c_void, c_double, c_double, P_double,
+                                  c_double, c_double, c_void, c_void, c_void]),
     "bie_debug_table": (c_ll, [c_int, c_int, c_int, c_int, c_double, P_double, c_ll]),
 }
 
@@ -259,6 +261,25 @@ class Geometry:
             return res
         _check(st, "bie_solve")
         return res
+
+
+def midpoint_step(ctx: "Context", p, pq, x: torch.Tensor, gamma: torch.Tensor, elasticity: float, x_s: float, lam,
+                  shear: float, dt: float, precision: int = BIE_MIXED, tol: float = 1e-10, restart: int = 30,
+                  max_iter: int = 300, inner_tol: float = 1e-5, max_refine: int = 10,
+                  residual_precision: int = BIE_DF) -> list:
+    """One midpoint step of the drop shapes x (updated in place); returns the infos of the two solves."""
+    n = len(p)
+    P = (ctypes.c_int * n)(*[int(v) for v in p])
+    PQ = (ctypes.c_int * n)(*[int(v) for v in pq])
+    L = (ctypes.c_double * n)(*[float(v) for v in lam])
+    o = bie_solve_opts()
+    lib().bie_solve_opts_default(ctypes.byref(o))
+    o.precision, o.tol, o.restart, o.max_iter, o.inner_tol, o.max_refine, o.residual_precision = (
+        precision, tol, restart, max_iter, inner_tol, max_refine, residual_precision)
+    info = (bie_solve_info * 2)()
+    _check(lib().bie_step_midpoint(ctx.h, n, P, PQ, _ptr(x), _ptr(gamma), elasticity, x_s, L, shear, dt,
+                                   ctypes.byref(o), info, _stream()), "bie_step_midpoint")
+    return [{k: getattr(info[i], k) for k, _ in bie_solve_info._fields_} for i in range(2)]
 
 
 def launch_count() -> int:

@@ -2068,6 +2068,72 @@ int bie_solve(bie_ctx* ctx, const bie_geom* g, const double* rhs, double* u, con
   }
 }
 
+int bie_step_midpoint(bie_ctx* ctx, int ndrop, const int* p, const int* pq, double* xcoef, const double* gammacoef,
+                      double elasticity, double x_s, const double* lambda, double shear, double dt,
+                      const bie_solve_opts* opts, bie_solve_info* info, void* stream) {
+  if (!ctx || !p || !pq || !xcoef || !gammacoef || !lambda || !opts) {
+    set_error("null argument");
+    return BIE_EINVAL;
+  }
+  BIE_TRY(check_degrees(ndrop, p));
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<long long> off(ndrop);
+  long long n = 0;
+  for (int d = 0; d < ndrop; ++d) {
+    off[d] = n;
+    n += 3 * ncoef(p[d]);
+  }
+  DevBuf<double> xh, f, uinf, b, u;
+  BIE_TRY(xh.alloc(n));
+  BIE_TRY(f.alloc(n));
+  BIE_TRY(uinf.alloc(n));
+  BIE_TRY(b.alloc(n));
+  BIE_TRY(u.alloc(n));
+  // the right-hand side at the solve's FP64-grade precision
+  const int rprec = (opts->precision & 0xff) == BIE_FP64 ? BIE_FP64 : opts->residual_precision;
+  // u(x): Eq. main_eq for the shapes x, u_inf = (shear z, 0, 0) (the z coefficients of x, scaled)
+  auto velocity = [&](const double* x, bie_solve_info* inf) -> int {
+    bie_geom* g = nullptr;
+    BIE_TRY(bie_geometry_setup(ctx, ndrop, p, pq, x, lambda, &g, stream));
+    int st = bie_interfacial_force(ctx, g, gammacoef, elasticity, x_s, f.ptr, stream);
+    if (st == BIE_OK) {
+      if (cudaMemsetAsync(uinf.ptr, 0, n * sizeof(double), s) != cudaSuccess) st = BIE_ECUDA;
+      for (int d = 0; d < ndrop && st == BIE_OK; ++d) {
+        const long long nc = ncoef(p[d]);
+        if (cudaMemcpyAsync(uinf.ptr + off[d], x + off[d] + 2 * nc, nc * sizeof(double), cudaMemcpyDeviceToDevice,
+                            s) != cudaSuccess)
+          st = BIE_ECUDA;
+      }
+      if (st == BIE_OK) {
+        k_axpby<<<nblk(n), 256, 0, s>>>(shear, uinf.ptr, 0.0, uinf.ptr, n);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) st = BIE_ECUDA;
+      }
+    }
+    if (st == BIE_OK) st = bie_rhs(ctx, g, uinf.ptr, f.ptr, b.ptr, rprec, stream);
+    if (st == BIE_OK && cudaMemsetAsync(u.ptr, 0, n * sizeof(double), s) != cudaSuccess) st = BIE_ECUDA;
+    if (st == BIE_OK) st = bie_solve(ctx, g, b.ptr, u.ptr, opts, inf, stream);
+    bie_geometry_destroy(g);
+    return st;
+  };
+  bie_solve_info tmp[2];
+  bie_solve_info* inf = info ? info : tmp;
+  BIE_TRY(velocity(xcoef, &inf[0]));
+  // x^{1/2} = x + (dt/2) u(x)
+  BIE_CUDA_TRY(cudaMemcpyAsync(xh.ptr, xcoef, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  k_axpby<<<nblk(n), 256, 0, s>>>(0.5 * dt, u.ptr, 1.0, xh.ptr, n);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  BIE_TRY(velocity(xh.ptr, &inf[1]));
+  // x^{new} = x + dt u(x^{1/2})
+  k_axpby<<<nblk(n), 256, 0, s>>>(dt, u.ptr, 1.0, xcoef, n);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return BIE_OK;
+}
+
 int bie_profile(bie_ctx* ctx, int enable) {
   if (!ctx) return BIE_EINVAL;
   ctx->prof.on = enable != 0;
