@@ -53,10 +53,11 @@ enum bie_status {
 /* precision flags (the low byte), OR-able with BIE_RAW */
 #define BIE_FP64 0   /* every step in double precision */
 #define BIE_MIXED 1  /* rotation, synthesis and pair sums in FP32; geometry, analysis in FP64 */
-#define BIE_DF 2     /* FP64 everywhere except the inter-drop pair sums (Omega_0, Omega_1), which run in
-                        double-float arithmetic (pairs of FP32 numbers, about 44 significant bits) on
-                        the FP32 pipes: FP64-grade results (relative error ~1e-13) at a fraction of the
-                        FP64 pipe's cost.  With a single drop it is BIE_FP64. */
+#define BIE_DF 2     /* the rotation and contraction of the singular self term (projected form) and the
+                        inter-drop pair sums (Omega_0, Omega_1) in double-float arithmetic (pairs of
+                        FP32 numbers, about 44 significant bits) on the FP32 pipes; geometry, the
+                        near-singular step and the analysis in FP64: FP64-grade results (relative
+                        error ~1e-13) at a fraction of the FP64 pipe's cost */
 #define BIE_RAW 0x100
 #define BIE_GRID_OUT 0x200  /* applies: write the values at the grid targets, [drop][3][j][k], instead
                                of their Galerkin projection (for sampled checks against a reference) */

@@ -11,9 +11,11 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "interdrop.h"
 #include "near.h"
 #include "internal.cuh"
@@ -76,6 +78,7 @@ struct Plan {
   int p = 0, P = 0;
   DevBuf<double> T0, T1, T2, A, cs, wsin, wsq;
   DevBuf<float> T0f, csf;
+  DevBuf<dff> csdf;
   template <typename R>
   const R* T0_() const;
   template <typename R>
@@ -97,12 +100,17 @@ template <>
 const float* Plan::cs_<float>() const {
   return csf.ptr;
 }
+template <>
+const dff* Plan::cs_<dff>() const {
+  return csdf.ptr;
+}
 
 struct WigPlan {  // rotation blocks for the p+1 latitudes of the degree-p grid
   int p = 0;
   long long stride = 0;
   DevBuf<double> blk;
   DevBuf<float> blkf;
+  DevBuf<dff> blkdf;
   template <typename R>
   const R* blk_() const;
 };
@@ -113,6 +121,10 @@ const double* WigPlan::blk_<double>() const {
 template <>
 const float* WigPlan::blk_<float>() const {
   return blkf.ptr;
+}
+template <>
+const dff* WigPlan::blk_<dff>() const {
+  return blkdf.ptr;
 }
 
 }  // namespace bie
@@ -185,6 +197,7 @@ static int get_plan(bie_ctx* ctx, int p, int P, Plan** out) {
   phase_table(p, P, v);
   BIE_TRY(pl->cs.upload(v));
   BIE_TRY(upload_as(pl->csf, v));
+  BIE_TRY(upload_as(pl->csdf, v));
   std::vector<double> t, w, ws;
   gauss_legendre(P + 1, t, w);
   singular_weights(P, ws);
@@ -217,6 +230,7 @@ static int get_wig(bie_ctx* ctx, int p, WigPlan** out) {
   for (int a = 0; a <= p; ++a) wigner_blocks(p, std::acos(t[a]), blk.data() + (size_t)a * wp->stride);
   BIE_TRY(wp->blk.upload(blk));
   BIE_TRY(upload_as(wp->blkf, blk));
+  BIE_TRY(upload_as(wp->blkdf, blk));
   *out = wp.get();
   ctx->wigs[p] = std::move(wp);
   return BIE_OK;
@@ -269,6 +283,7 @@ struct bie_geom {
     bie::DevBuf<long long> src_off_std, src_off_up;  // first source of each drop on the two grids
     bie::DevBuf<double> qk64[2];            // projected kernel factors of every target, S and D
     bie::DevBuf<float> qk32[2];
+    bie::DevBuf<bie::dff> qkdf[2];          // double-float copy, made on the first BIE_DF apply
   };
   std::vector<std::unique_ptr<Group>> groups;
   struct GraphSlot {
@@ -351,9 +366,39 @@ static int ensure_qk(bie_ctx* ctx, bie_geom::Group& G, int kind, cudaStream_t s)
                             G.qk32[kind].ptr, s);
 }
 
-// Singular self part of every drop (Sec. 2.2): one launch per degree group.
+// Projected factors of one group in the arithmetic type R (the double-float copy is split from the
+// FP64 factors on first use).
+template <typename R>
+static int qk_of(bie_geom::Group& G, int kind, cudaStream_t s, const R** out);
+template <>
+int qk_of<double>(bie_geom::Group& G, int kind, cudaStream_t, const double** out) {
+  *out = G.qk64[kind].ptr;
+  return BIE_OK;
+}
+template <>
+int qk_of<float>(bie_geom::Group& G, int kind, cudaStream_t, const float** out) {
+  *out = G.qk32[kind].ptr;
+  return BIE_OK;
+}
+template <>
+int qk_of<dff>(bie_geom::Group& G, int kind, cudaStream_t s, const dff** out) {
+  if (!G.qkdf[kind].ptr) {
+    BIE_TRY(G.qkdf[kind].alloc(G.qk64[kind].n));
+    BIE_TRY(launch_split_dff(G.qk64[kind].ptr, G.qkdf[kind].ptr, (long long)G.qk64[kind].n, s));
+  }
+  *out = G.qkdf[kind].ptr;
+  return BIE_OK;
+}
+template <typename R>
+static const char* self_phase_name() {
+  return std::is_same<R, float>::value ? "self_proj_f32" : std::is_same<R, dff>::value ? "self_proj_df" : "self_proj_f64";
+}
+
+// Singular self part of every drop (Sec. 2.2): one launch for every projected-form degree group
+// (direct-form groups one launch each; in double-float arithmetic those run in FP64).
 template <typename R>
 static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaStream_t s) {
+  using RD = typename std::conditional<std::is_same<R, dff>::value, double, R>::type;
   bie_ctx* ctx = g->ctx;
   // the projected form keeps its per-target factors in shared memory while they are built; groups
   // whose factors do not fit there use the direct form
@@ -371,16 +416,16 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
     const double* wts = kind == 0 ? (raw ? G.wSraw.ptr : G.wS.ptr) : (raw ? G.wDraw.ptr : G.wD.ptr);
     const long long nd = (long long)G.drops.size();
     if (direct) {
-      if (sizeof(R) == 4 && !G.cache32.ptr) {
+      if (sizeof(RD) == 4 && !G.cache32.ptr) {
         BIE_TRY(G.cache32.alloc(G.cache64.n));
         BIE_TRY(launch_to_float(G.cache64.ptr, G.cache32.ptr, (long long)G.cache64.n, s));
       }
-      const R* cache = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.cache64.ptr)
-                                      : reinterpret_cast<const R*>(G.cache32.ptr);
-      Phase ph(ctx, sizeof(R) == 8 ? "self_direct_f64" : "self_direct_f32", s);
-      BIE_TRY(launch_self_direct<R>(kind, dens, G.foff3.ptr, nd, p, pq, wp->blk_<R>(), wp->stride, pp->cs_<R>(),
-                                    pl->T0_<R>(), pl->cs_<R>(), cache, wts, G.val_off.ptr, g->vals.ptr,
-                                    sizeof(R) == 8 ? 96 * 1024 : 40 * 1024, s));
+      const RD* cache = sizeof(RD) == 8 ? reinterpret_cast<const RD*>(G.cache64.ptr)
+                                        : reinterpret_cast<const RD*>(G.cache32.ptr);
+      Phase ph(ctx, sizeof(RD) == 8 ? "self_direct_f64" : "self_direct_f32", s);
+      BIE_TRY(launch_self_direct<RD>(kind, dens, G.foff3.ptr, nd, p, pq, wp->blk_<RD>(), wp->stride,
+                                     pp->cs_<RD>(), pl->T0_<RD>(), pl->cs_<RD>(), cache, wts, G.val_off.ptr,
+                                     g->vals.ptr, sizeof(RD) == 8 ? 96 * 1024 : 40 * 1024, s));
     } else {
       BIE_TRY(ensure_qk(ctx, G, kind, s));
       SelfGroup<R> sg{};
@@ -389,8 +434,7 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
       sg.wblk = wp->blk_<R>();
       sg.wstride = wp->stride;
       sg.ph = pp->cs_<R>();
-      sg.Q = sizeof(R) == 8 ? reinterpret_cast<const R*>(G.qk64[kind].ptr)
-                            : reinterpret_cast<const R*>(G.qk32[kind].ptr);
+      BIE_TRY(qk_of<R>(G, kind, s, &sg.Q));
       sg.wts = wts;
       sg.val_off = G.val_off.ptr;
       sg.p = p;
@@ -398,7 +442,7 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
     }
   }
   if (!proj.empty()) {  // every projected-form group in one launch; it reads the FP64 density directly
-    Phase ph(ctx, sizeof(R) == 8 ? "self_proj_f64" : "self_proj_f32", s);
+    Phase ph(ctx, self_phase_name<R>(), s);
     BIE_TRY((launch_self_proj<R, double>(proj, dens, g->vals.ptr, s)));
   }
   return BIE_OK;
@@ -424,6 +468,8 @@ static int layer_apply_eager(bie_ctx* ctx, const bie_geom* gc, int kind, const d
   }
   if (prec == BIE_MIXED)
     BIE_TRY(self_apply<float>(g, kind, raw, dens, s));
+  else if (prec == BIE_DF)
+    BIE_TRY(self_apply<dff>(g, kind, raw, dens, s));
   else
     BIE_TRY(self_apply<double>(g, kind, raw, dens, s));
   if (g->ndrop > 1) {

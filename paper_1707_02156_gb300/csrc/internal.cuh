@@ -115,6 +115,9 @@ struct SelfGroups {
   int n;
   SelfGroup<R> g[kMaxSelfGroups];
 };
+// out[i] = double-float split of in[i] (dff: dfloat.cuh)
+struct dff;
+int launch_split_dff(const double* in, dff* out, long long n, cudaStream_t s);
 // All projected-form groups in one launch (eight groups per launch at most).
 template <typename R, typename CT>
 int launch_self_proj(std::vector<SelfGroup<R>> groups, const CT* dens, double* vals, cudaStream_t s);

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "device.cuh"
 #include "internal.cuh"
 
@@ -341,9 +342,9 @@ constexpr int kSelfThreads = 256;
 // acc += S v for the symmetric 3x3 matrix S with entries (xx, yy, zz, xy, xz, yz) at planes q[0..5]
 template <typename R>
 __device__ inline void sym_mul_add(const R* q, const R* v, R* acc) {
-  acc[0] = fma(q[4], v[2], fma(q[3], v[1], fma(q[0], v[0], acc[0])));
-  acc[1] = fma(q[5], v[2], fma(q[1], v[1], fma(q[3], v[0], acc[1])));
-  acc[2] = fma(q[2], v[2], fma(q[5], v[1], fma(q[4], v[0], acc[2])));
+  acc[0] = fmad(q[4], v[2], fmad(q[3], v[1], fmad(q[0], v[0], acc[0])));
+  acc[1] = fmad(q[5], v[2], fmad(q[1], v[1], fmad(q[3], v[0], acc[1])));
+  acc[2] = fmad(q[2], v[2], fmad(q[5], v[1], fmad(q[4], v[0], acc[2])));
 }
 
 // One launch covers every degree group (a persistent batch over drops of uneven degree): the groups'
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(kSelfThreads, sizeof(R) == 4 ? 4 : 2) k_self_p
   for (int k = 0; k < 4; ++k)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      for (int off = 16; off > 0; off >>= 1) acc[k][c] += __shfl_down_sync(0xffffffffu, acc[k][c], off);
+      for (int off = 16; off > 0; off >>= 1) acc[k][c] += shfl_down(acc[k][c], off);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0)
 #pragma unroll
@@ -512,7 +513,21 @@ int pick_jc(int p, int pq, size_t budget, size_t* smem) {
   return jc;
 }
 
+// out[i] = the double-float split of in[i]
+__global__ void k_split_dff(const double* __restrict__ in, dff* __restrict__ out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = dff(in[i]);
+}
+
 }  // namespace
+
+int launch_split_dff(const double* in, dff* out, long long n, cudaStream_t s) {
+  if (n == 0) return BIE_OK;
+  k_split_dff<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
 
 template <typename R>
 int launch_self_direct(int kind, const double* dens, const long long* foff3, long long ndrop, int p, int pq,
@@ -590,5 +605,6 @@ template int launch_self_direct<float>(int, const double*, const long long*, lon
                                        const double*, const long long*, double*, size_t, cudaStream_t);
 template int launch_self_proj<double, double>(std::vector<SelfGroup<double>>, const double*, double*, cudaStream_t);
 template int launch_self_proj<float, double>(std::vector<SelfGroup<float>>, const double*, double*, cudaStream_t);
+template int launch_self_proj<dff, double>(std::vector<SelfGroup<dff>>, const double*, double*, cudaStream_t);
 
 }  // namespace bie

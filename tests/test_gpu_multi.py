@@ -188,8 +188,8 @@ def test_double_float_rhs_matches_fp64(batch):
     assert _relerr(bdf.cpu().numpy(), b64.cpu().numpy()) < DF_TOL
 
 
-def test_double_float_is_fp64_for_one_drop():
-    # without inter-drop pairs BIE_DF runs the FP64 path: identical results
+def test_double_float_single_drop_matches_fp64():
+    # one drop: the self term alone, in double-float arithmetic against FP64
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1707_02156_gb300 import api
@@ -203,6 +203,6 @@ def test_double_float_is_fp64_for_one_drop():
     geo.apply_double(f, a, precision=0)
     geo.apply_double(f, b, precision=2)
     torch.cuda.synchronize()
-    assert torch.equal(a, b)
+    assert _relerr(b.cpu().numpy(), a.cpu().numpy()) < DF_TOL
     geo.close()
     ctx.close()

@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 MIXED_TOL = 2e-5
+DF_TOL = 1e-11  # double-float: about 44 bits per operation
 
 
 @pytest.fixture(scope="module", params=[False, True], ids=["projected", "direct"])
@@ -117,7 +118,8 @@ def test_self_apply_perturbed_upsampled_quadrature_matches_oracle(ctx, kind):
     f = dev(w.density)
     out = torch.zeros_like(f)
     ref = (drops.apply_single if kind == "S" else drops.apply_double)([w.density])[0].ravel()
-    for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
+    # FP64, mixed, and double-float (the self term's rotation and contraction on the FP32 pipes)
+    for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL), (2, DF_TOL)):
         (geo.apply_single if kind == "S" else geo.apply_double)(f, out, precision=prec)
         assert relerr(host(out), ref) < tol, (kind, prec)
 
