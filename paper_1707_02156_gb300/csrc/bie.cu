@@ -1275,14 +1275,10 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, int k
   if (threadIdx.x == 0) out[i] = sh[0];
 }
 
-// w -= sum_i h[i] V_i
-__global__ void k_sub_comb(double* __restrict__ w, const double* __restrict__ V, long long ldv,
-                           const double* __restrict__ h, int k, long long n) {
-  long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= n) return;
-  double t = w[x];
-  for (int i = 0; i < k; ++i) t -= h[i] * V[(long long)i * ldv + x];
-  w[x] = t;
+// y = a*y
+__global__ void k_scale(double a, double* __restrict__ y, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] *= a;
 }
 
 // y = a*x + b*y
@@ -2152,7 +2148,7 @@ int bie_step_midpoint(bie_ctx* ctx, int ndrop, const int* p, const int* pq, doub
           st = BIE_ECUDA;
       }
       if (st == BIE_OK) {
-        k_axpby<<<nblk(n), 256, 0, s>>>(shear, uinf.ptr, 0.0, uinf.ptr, n);
+        k_scale<<<nblk(n), 256, 0, s>>>(shear, uinf.ptr, n);
         count_launch();
         if (cudaGetLastError() != cudaSuccess) st = BIE_ECUDA;
       }
