@@ -61,3 +61,23 @@ def test_singular_weights_match_oracle(L):
     for pq in (8, 33, 65):
         v = np.array(api.debug_table(3, pq))
         assert np.max(np.abs(v - layer.singular_weights(pq))) < 1e-14
+
+
+def test_null_arguments_are_rejected_before_any_device_work(L):
+    # every entry point checks its handles and pointers first: BIE_EINVAL (1), no CUDA call made
+    import ctypes
+    EINVAL = 1
+    o = api.bie_solve_opts()
+    L.bie_solve_opts_default(ctypes.byref(o))
+    info = api.bie_solve_info()
+    p = (ctypes.c_int * 1)(8)
+    lam = (ctypes.c_double * 1)(1.0)
+    assert L.bie_apply_single(None, None, None, None, 0, None) == EINVAL
+    assert L.bie_apply_double(None, None, None, None, 0, None) == EINVAL
+    assert L.bie_rhs(None, None, None, None, None, 0, None) == EINVAL
+    assert L.bie_solve(None, None, None, None, ctypes.byref(o), ctypes.byref(info), None) == EINVAL
+    assert L.bie_step_midpoint(None, 1, p, p, None, None, 0.2, 0.0, lam, 1.0, 0.01, ctypes.byref(o), None,
+                               None) == EINVAL
+    # status strings
+    assert L.bie_strerror(0) == b"ok"
+    assert L.bie_strerror(EINVAL) == b"invalid argument"
