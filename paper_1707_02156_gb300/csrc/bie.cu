@@ -533,6 +533,7 @@ static int layer_apply(bie_ctx* ctx, const bie_geom* gc, int kind, const double*
       return BIE_ECUDA;
     }
     slot.launches = bie_launch_count() - l0;
+    count_launch(-(int)slot.launches);  // captured, not run
     const cudaError_t ie = cudaGraphInstantiate(&slot.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) {
@@ -1488,9 +1489,18 @@ struct Krylov {
   double* hpin = nullptr;  // pinned host copy of the residual estimates
   int hpin_n = 0;
   std::vector<cudaEvent_t> ev;  // end of each Arnoldi step
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    const void* sig[3] = {nullptr, nullptr, nullptr};  // V, tmp, hpin the graph was captured with
+  };
+  std::map<long long, StepGraph> steps;  // captured Arnoldi steps by (precision, restart, k)
+  bool steps_failed = false;             // a capture failed: step eagerly from then on
   ~Krylov() {
     if (hpin) cudaFreeHost(hpin);
     for (auto e : ev) cudaEventDestroy(e);
+    for (auto& kv : steps)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   }
 };
 
@@ -1556,6 +1566,85 @@ static int sys_matvec(bie_ctx* ctx, const bie_geom* g, const double* u, double* 
   return BIE_OK;
 }
 
+// Arnoldi step k on stream s: normalisation of V_k (deferred from step k - 1), the operator apply
+// into the temporary t2 (its kernels launched one by one when eager_apply), the three fused
+// Gram-Schmidt kernels and the copy of the residual estimate to the pinned host array.
+static int arnoldi_step(bie_ctx* ctx, const bie_geom* g, Krylov& K, int prec, int k, int m, bool eager_apply,
+                        cudaStream_t s) {
+  const long long n = g->ncoef_total;
+  double* V = K.V.ptr;
+  double* t2 = K.tmp.ptr + n;
+  double* vk = V + (long long)k * n;
+  double* vk1 = V + (long long)(k + 1) * n;
+  if (k > 0) {
+    k_scale_dev<<<nblk(n), 256, 0, s>>>(vk, K.scale.ptr, n);
+    count_launch();
+    BIE_CUDA_TRY(cudaGetLastError());
+  }
+  if (eager_apply)
+    BIE_TRY(layer_apply_eager(ctx, g, 1, vk, t2, prec, s));
+  else
+    BIE_TRY(layer_apply(ctx, g, 1, vk, t2, prec, s));
+  double* h1 = K.hdev.ptr;
+  double* h2d = K.hdev.ptr + (m + 2);
+  const int nbk = kry_blocks(n);
+  k_kry_sysop_dots<<<nbk, kKryThreads, 0, s>>>(g->lamc.ptr, vk, t2, vk1, V, n, k, K.partial.ptr, K.counter.ptr, h1);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  k_kry_sub_dots<<<nbk, kKryThreads, 0, s>>>(vk1, V, n, k, h1, K.partial.ptr, K.counter.ptr, h2d);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  k_kry_sub_tail<<<nbk, kKryThreads, 0, s>>>(vk1, V, n, k, m, h1, h2d, K.partial.ptr, K.counter.ptr, K.Hd.ptr,
+                                             K.csd.ptr, K.snd.ptr, K.gvd.ptr, K.scale.ptr, K.resd.ptr);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  BIE_CUDA_TRY(cudaMemcpyAsync(K.hpin + k, K.resd.ptr + k, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return BIE_OK;
+}
+
+// Arnoldi step k as a CUDA graph: captured on the geometry's capture stream at its first use (once
+// the operator apply of this precision has run eagerly, so nothing allocates inside the capture) and
+// replayed on s after that.  Falls back to launching the step's kernels one by one.
+static int arnoldi_step_graph(bie_ctx* ctx, const bie_geom* gc, Krylov& K, int prec, int k, int m,
+                              cudaStream_t s) {
+  bie_geom* g = const_cast<bie_geom*>(gc);
+  const int key_apply = (prec & 0x3ff) * 2 + 1;
+  auto ap = g->graphs.find(key_apply);
+  const bool warm = ap != g->graphs.end() && ap->second.warm;
+  if (!ctx->cfg.use_graphs || ctx->prof.on || !warm || K.steps_failed)
+    return arnoldi_step(ctx, gc, K, prec, k, m, false, s);
+  const long long key = ((long long)prec * 128 + m) * 128 + k;
+  auto& sg = K.steps[key];
+  const void* sig[3] = {K.V.ptr, K.tmp.ptr, K.hpin};
+  if (sg.exec && (sg.sig[0] != sig[0] || sg.sig[1] != sig[1] || sg.sig[2] != sig[2])) {
+    cudaGraphExecDestroy(sg.exec);  // workspace moved since the capture
+    sg.exec = nullptr;
+  }
+  if (!sg.exec) {
+    if (!g->cap_stream) BIE_CUDA_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    const long long l0 = bie_launch_count();
+    BIE_CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed));
+    const int st = arnoldi_step(ctx, gc, K, prec, k, m, true, g->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(g->cap_stream, &graph);
+    cudaError_t ie = cudaErrorUnknown;
+    if (st == BIE_OK && ce == cudaSuccess) ie = cudaGraphInstantiate(&sg.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (st != BIE_OK || ce != cudaSuccess || ie != cudaSuccess) {
+      sg.exec = nullptr;
+      K.steps_failed = true;
+      cudaGetLastError();  // clear the capture's error state
+      return arnoldi_step(ctx, gc, K, prec, k, m, false, s);
+    }
+    sg.launches = bie_launch_count() - l0;
+    count_launch(-(int)sg.launches);  // captured, not run
+    for (int i = 0; i < 3; ++i) sg.sig[i] = sig[i];
+  }
+  BIE_CUDA_TRY(cudaGraphLaunch(sg.exec, s));
+  count_launch((int)sg.launches);
+  return BIE_OK;
+}
+
 // Restarted GMRES (Sec. 7) with classical Gram-Schmidt and one re-orthogonalisation, FP64 Krylov
 // basis; the operator is applied at precision prec.  x holds the initial guess (zero if x_is_zero).
 // Each Arnoldi step runs as the operator apply and three fused kernels that end on the device
@@ -1611,35 +1700,11 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
     int k_used = -1;
     double est = beta / bnorm;
     for (int k = 0; k < kmax; ++k) {
-      double* vk = V + (long long)k * n;
-      double* vk1 = V + (long long)(k + 1) * n;
-      if (k > 0) {  // normalisation of V_k, deferred from the previous step
-        k_scale_dev<<<nblk(n), 256, 0, s>>>(vk, K.scale.ptr, n);
-        count_launch();
-        BIE_CUDA_TRY(cudaGetLastError());
-      }
-      BIE_TRY(layer_apply(ctx, g, 1, vk, t2, prec, s));
+      BIE_TRY(arnoldi_step_graph(ctx, g, K, prec, k, m, s));
       if (prec == BIE_MIXED)
         info->applies_mixed++;
       else
         info->applies_fp64++;
-      // classical Gram-Schmidt with one re-orthogonalisation, three fused kernels
-      double* h1 = K.hdev.ptr;
-      double* h2d = K.hdev.ptr + (m + 2);
-      const int nbk = kry_blocks(n);
-      k_kry_sysop_dots<<<nbk, kKryThreads, 0, s>>>(g->lamc.ptr, vk, t2, vk1, V, n, k, K.partial.ptr,
-                                                   K.counter.ptr, h1);
-      count_launch();
-      BIE_CUDA_TRY(cudaGetLastError());
-      k_kry_sub_dots<<<nbk, kKryThreads, 0, s>>>(vk1, V, n, k, h1, K.partial.ptr, K.counter.ptr, h2d);
-      count_launch();
-      BIE_CUDA_TRY(cudaGetLastError());
-      k_kry_sub_tail<<<nbk, kKryThreads, 0, s>>>(vk1, V, n, k, m, h1, h2d, K.partial.ptr, K.counter.ptr,
-                                                 K.Hd.ptr, K.csd.ptr, K.snd.ptr, K.gvd.ptr, K.scale.ptr,
-                                                 K.resd.ptr);
-      count_launch();
-      BIE_CUDA_TRY(cudaGetLastError());
-      BIE_CUDA_TRY(cudaMemcpyAsync(K.hpin + k, K.resd.ptr + k, sizeof(double), cudaMemcpyDeviceToHost, s));
       BIE_CUDA_TRY(cudaEventRecord(K.ev[k], s));
       if (k >= 1) {  // step k - 1, read while step k runs
         BIE_CUDA_TRY(cudaEventSynchronize(K.ev[k - 1]));
