@@ -154,6 +154,39 @@ def test_two_drops_near_contact_closed_forms_through_all_regions():
     assert np.max(derr[:, reg == 2]) < 1e-6
 
 
+def test_newton_closest_point_is_the_nearest_surface_point():
+    # Sec. 2.3: x* minimises |x(theta, phi) - x0| over the source surface.  At x* the offset x0 - x*
+    # is orthogonal to both tangents, and no point of the surface is closer (checked against 10^4
+    # random surface samples by direct SH evaluation).  Targets sit 0.05 off a deformed drop, some
+    # of them next to a parameter pole.
+    from oracle import near
+    p = 8
+    x, rng = _rand_drop(p, 61, amp=0.12)
+    _, _, theta, phi = sh.gauss_grid(p)
+    T, F = np.meshgrid(theta, phi, indexing="ij")
+    T, F = T.reshape(-1), F.reshape(-1)
+    std_x = np.stack([sh.synthesize(x[c], p, p).reshape(-1) for c in range(3)])
+    ts = np.arccos(rng.uniform(-1.0, 1.0, 10000))
+    fs = rng.uniform(0.0, 2 * np.pi, 10000)
+    samples = np.stack([sh.evaluate(x[c], p, ts, fs) for c in range(3)])
+    for th0, ph0 in ((0.03, 1.0), (1.1, 0.4), (2.0, 4.0), (3.1, 2.5)):
+        d = [sh.evaluate_derivs(x[c], p, np.array([th0]), np.array([ph0])) for c in range(3)]
+        xs0 = np.array([d[c]["f"][0] for c in range(3)])
+        nrm = np.cross([d[c]["t"][0] for c in range(3)], [d[c]["p"][0] for c in range(3)])
+        x0 = xs0 + 0.05 * nrm / np.linalg.norm(nrm) + 0.02 * np.array([0.3, -0.2, 0.1])
+        s = int(np.argmin(np.sum((std_x - x0[:, None]) ** 2, axis=0)))
+        al, be = F[s], T[s] - np.pi / 2
+        xr = np.stack([wigner.rotate(x[c], p, al, be) for c in range(3)])
+        th, ph, xstar = near.newton_closest(xr, p, x0)
+        dr = [sh.evaluate_derivs(xr[c], p, np.array([th]), np.array([ph])) for c in range(3)]
+        xt = np.array([dr[c]["t"][0] for c in range(3)])
+        xp = np.array([dr[c]["p"][0] for c in range(3)])
+        off = x0 - xstar
+        assert abs(off @ xt) < 1e-13 * np.linalg.norm(xt) and abs(off @ xp) < 1e-13 * np.linalg.norm(xp)
+        assert np.linalg.norm(off) <= np.min(np.linalg.norm(samples - x0[:, None], axis=0)) + 1e-15
+        assert np.linalg.norm(off) <= np.min(np.linalg.norm(std_x - x0[:, None], axis=0))
+
+
 def test_gmres_matches_direct_solve():
     rng = np.random.default_rng(0)
     n = 60
@@ -162,6 +195,29 @@ def test_gmres_matches_direct_solve():
     x, info = gmres.gmres(lambda v: A @ v, b, tol=1e-13, restart=12, max_it=300)
     assert info["converged"]
     assert np.max(np.abs(x - np.linalg.solve(A, b))) < 1e-11
+
+
+def test_gmres_iterate_minimises_the_residual_over_the_krylov_space():
+    # GMRES's defining property: after k steps from x = 0, x_k minimises ||b - A x|| over
+    # span{b, A b, ..., A^(k-1) b}; here the minimum is found by least squares on an orthonormal
+    # basis of that space (QR of the Krylov matrix), and the running estimates equal it.
+    rng = np.random.default_rng(5)
+    n = 40
+    A = np.eye(n) * 2 + rng.standard_normal((n, n)) / math.sqrt(n)
+    b = rng.standard_normal(n)
+    for k in (3, 6, 10):
+        K = np.zeros((n, k))
+        v = b.copy()
+        for j in range(k):
+            K[:, j] = v
+            v = A @ v
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(A @ Q, b, rcond=None)
+        best = np.linalg.norm(b - A @ (Q @ y)) / np.linalg.norm(b)
+        x, info = gmres.gmres(lambda v: A @ v, b, tol=1e-15, restart=n, max_it=k)
+        assert info["iterations"] == k
+        assert abs(np.linalg.norm(b - A @ x) / np.linalg.norm(b) - best) < 1e-12
+        assert abs(info["residuals"][-2] - best) < 1e-12   # the last Givens estimate
 
 
 def test_solution_of_rigid_rotation_is_the_flow_for_any_viscosity_ratio():
@@ -176,6 +232,41 @@ def test_solution_of_rigid_rotation_is_the_flow_for_any_viscosity_ratio():
     u, info = gmres.gmres(drops.system_matvec, b, tol=1e-12)
     assert info["converged"]
     assert np.max(np.abs(u - b / 2.0)) < 1e-8
+
+
+def test_force_free_drop_of_matched_viscosity_is_invisible():
+    # A drop with the suspending fluid's viscosity (lambda = 1) and no interfacial force is not
+    # there.  Alone, it moves with the undisturbed shear u_inf = (z, 0, 0).  Next to another drop it
+    # leaves that drop's velocity as it is alone (the double layer of each source drop carries its
+    # own lambda_j - 1, Eq. main_eq).
+    p = 4
+    x0, _ = _rand_drop(p, 51, amp=0.08)
+    zero = np.zeros((3, (p + 1) ** 2))
+    alone = layer.Drops([x0], [p], [p], [1.0])
+    u, info = gmres.gmres(alone.system_matvec, alone.rhs([zero], shear=1.0), tol=1e-13)
+    assert info["converged"]
+    xg = geometry.surface_fields(x0, p, p)["f"]
+    uinf = np.zeros((3, (p + 1) ** 2))
+    uinf[0] = sh.analyze(xg[2], p, p)
+    assert np.max(np.abs(u.reshape(3, -1) - uinf)) < 1e-13
+
+    x1 = inputs.sphere_coef(p, radius=0.8, centre=(2.9, 0.0, 0.3))
+    gam = np.zeros((p + 1) ** 2)
+    gam[0] = math.sqrt(4 * math.pi)
+    f0 = geometry.interfacial_force(x0, p, gam, elasticity=0.2)
+    single = layer.Drops([x0], [p], [p], [3.0])
+    u_single, info = gmres.gmres(single.system_matvec, single.rhs([f0], shear=1.0), tol=1e-13)
+    assert info["converged"]
+    pair = layer.Drops([x0, x1], [p, p], [p, p], [3.0, 1.0], up=2)
+    u_pair, info = gmres.gmres(pair.system_matvec, pair.rhs([f0, zero], shear=1.0), tol=1e-13)
+    assert info["converged"]
+    u0 = pair.split(u_pair)[0].reshape(-1)
+    assert np.max(np.abs(u0 - u_single)) < 1e-11 * np.max(np.abs(u_single))
+    # drop 1 itself moves with the flow that drop 0 disturbs, not with u_inf
+    x1g = geometry.surface_fields(x1, p, p)["f"]
+    uinf1 = np.zeros((3, (p + 1) ** 2))
+    uinf1[0] = sh.analyze(x1g[2], p, p)
+    assert np.max(np.abs(pair.split(u_pair)[1] - uinf1)) > 1e-3
 
 
 def test_volume_conservation_and_relaxation_sign_of_clean_prolate_drop():
