@@ -13,6 +13,9 @@ Modules, each following the passage of Sorgentone & Tornberg (arXiv 1707.02156) 
             region split (Sec. 2.3), near-singular interpolation (Sec. 2.3), Galerkin projection (Sec. 1.2)
   gmres     restarted GMRES with modified Gram-Schmidt (Sec. 7)
   timestep  midpoint step of the drop shapes with the surfactant held fixed (Sec. 3, Alg. 1)
+  surfactant  surface gradient, divergence and Laplacian; the transport terms of Eq. surfactant0;
+            IMEX-2 and IMEX-1 steps with the preconditioned implicit solve; the coupled
+            drop/surfactant step and the adaptive step size of Alg. 1 (Sec. 3)
   brute     adaptive polar quadrature used only to pin the singular rule
 
 Parity unpinned: the absolute accuracy of the near-singular (Omega_2) interpolation on

@@ -11,11 +11,12 @@ import textwrap
 
 import pytest
 
-from oracle import geometry, gmres, layer, near, sh, timestep, wigner
+from oracle import geometry, gmres, layer, near, sh, surfactant, timestep, wigner
 
 import test_oracle_geometry as PG
 import test_oracle_layer as PL
 import test_oracle_sh as PS
+import test_oracle_surfactant as PF
 import test_oracle_timestep as PT
 import test_oracle_wigner as PW
 
@@ -177,6 +178,37 @@ CASES = [
     ("midpoint_at_full_step", timestep, "midpoint_step",
      [("xh = [x + 0.5 * dt * u", "xh = [x + dt * u")],
      PT.test_volume_change_per_step_is_third_order, ()),
+    # surfactant transport and the coupled step (Eq. surfactant0, Sec. 3, Alg. 1)
+    ("stretching_sign_as_printed", surfactant, "f_explicit_grid",
+     [("stretch = 2.0 * S.K * G * un", "stretch = -2.0 * S.K * G * un")],
+     PF.test_stretching_term_of_an_expanding_sphere, ()),
+    ("convection_without_moving_frame_term", surfactant, "f_explicit_grid",
+     [("return -conv + frame + stretch", "return -conv + stretch")],
+     PF.test_rigid_motion_leaves_any_concentration_unchanged, ()),
+    ("laplacian_without_christoffel_term", surfactant, "Surface",
+     [('self.gtt * (s["tt"] - dot(self.d["tt"], gs))', 'self.gtt * s["tt"]')],
+     PF.test_surface_operators_of_the_position_vector_on_a_deformed_drop, ()),
+    ("inverse_metric_cross_term_sign", surfactant, "Surface",
+     [("self.E / W2, -self.F / W2, self.G / W2", "self.E / W2, self.F / W2, self.G / W2")],
+     PF.test_surface_operators_of_the_position_vector_on_a_deformed_drop, ()),
+    ("inverse_metric_diagonal_swapped", surfactant, "Surface",
+     [("self.E / W2, -self.F / W2, self.G / W2", "self.G / W2, -self.F / W2, self.E / W2")],
+     PF.test_laplace_beltrami_on_a_sphere_of_radius_r, ()),
+    ("normal_derivative_operand_order", surfactant, "Surface",
+     [('ct = np.cross(d["tt"], self.xp, axis=0)', 'ct = np.cross(self.xp, d["tt"], axis=0)')],
+     PF.test_rigid_motion_leaves_any_concentration_unchanged, ()),
+    ("imex2_diffusion_at_the_old_level", surfactant, "imex2_full",
+     [("f_implicit(xh, gh, p, pe)", "f_implicit(xh, g0, p, pe)")],
+     PF.test_imex2_step_of_pure_diffusion_on_a_resting_sphere, ()),
+    ("imex2_half_stage_with_full_step", surfactant, "imex2_half",
+     [("g0 + 0.5 * dt * k0", "g0 + dt * k0")],
+     PF.test_expanding_sphere_keeps_gamma_r_squared_to_second_order, ()),
+    ("drop_update_from_the_half_point_as_printed", surfactant, "coupled_step",
+     [("x1 = [x + dt * u for x, u in zip(xs, uh)]", "x1 = [x + dt * u for x, u in zip(xh, uh)]")],
+     PF.test_expanding_sphere_keeps_gamma_r_squared_to_second_order, ()),
+    ("step_size_rule_without_square_root", surfactant, "next_dt",
+     [("dt * math.sqrt(0.9 * tol / err)", "dt * (0.9 * tol / err)")],
+     PF.test_adaptive_run_keeps_every_accepted_step_below_tolerance, ()),
 ]
 
 
