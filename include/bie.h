@@ -252,6 +252,90 @@ int bie_step_midpoint(bie_ctx* ctx, int ndrop, const int* p, const int* pq, doub
                       double elasticity, double x_s, const double* lambda, double shear, double dt,
                       const bie_solve_opts* opts, bie_solve_info* info, void* stream);
 
+/* ---- Insoluble surfactant (Eq. surfactant0, Sec. 1.2, Sec. 3, Alg. 1) ----
+ * The surface points move with the full velocity (dx/dt = u), so Gamma is followed at fixed
+ * parameters, with the rates
+ *     f_E = -div(Gamma u_tan) + u_tan . grad Gamma + 2 K Gamma (u.n)   (= -Gamma div u),
+ *     f_I = (1/Pe) lap Gamma,
+ * K the mean curvature with the outward normal (-1/R on a sphere).  The surface gradient,
+ * divergence and Laplacian are the coordinate forms in (theta, phi).  Every term is formed on the
+ * grid of degree 2p+1 and projected on the degree-p SH basis (Galerkin, Eq. galerkin_surfactant).
+ * Layouts: shapes and velocities [drop][3][(p+1)^2], surfactant [drop][(p+1)^2], device pointers,
+ * per-drop degrees p on the host.  All in FP64. */
+
+/* fe = projection of f_E at (x, u, Gamma); fi (NULL to skip) = projection of inv_pe * lap Gamma.
+ * inv_pe = 1/Pe >= 0 (0: no surface diffusion). */
+int bie_surfactant_rates(bie_ctx* ctx, int ndrop, const int* p, const double* xcoef, const double* ucoef,
+                         const double* gammacoef, double inv_pe, double* fe, double* fi, void* stream);
+
+/* The implicit stage of Sec. 3 (Preconditioning): y with y - a P_p[lap_x y] = b per drop, by GMRES
+ * (restart 60, at most 600 iterations, from y = 0) left-preconditioned with the diagonal the operator
+ * has on the sphere of the drop's mean radius R, 1 + a n(n+1)/R^2; stops at relative residual tol.
+ * a >= 0 (a = 0 copies b).  *iterations (may be NULL) = GMRES iterations.  Synchronous.
+ * BIE_ENOCONV if tol was not reached. */
+int bie_surfactant_implicit(bie_ctx* ctx, int ndrop, const int* p, const double* xcoef, const double* b, double a,
+                            double* y, double tol, int* iterations, void* stream);
+
+/* Surfactant mass int_gamma Gamma dS per drop by the regular rule (Sec. 2.1) on the grid of degree
+ * 2p+1: host mass[ndrop].  Synchronous. */
+int bie_surfactant_mass(bie_ctx* ctx, int ndrop, const int* p, const double* xcoef, const double* gammacoef,
+                        double* mass, void* stream);
+
+typedef struct bie_coupled_info {
+  double err_drop;          /* max over drops of ||dt (u^{t+dt/2} - u^t)||_inf / ||x^{t+dt}||_inf on the
+                               degree-p grid: the embedded Euler estimate of the midpoint rule */
+  double err_conservation;  /* max over drops of |M(t+dt) - M(t)| / |M(t)|, M the surfactant mass
+                               (Eq. err_conservation) */
+  double err_imex1;         /* max over drops of ||Gamma^{t+dt} - Gamma_IMEX1||_inf / ||Gamma^{t+dt}||_inf
+                               (Eq. err_IMEX1), or -1 when not requested */
+  int velocity_solves;      /* 1, or 2 when u^t was computed here */
+  int implicit_iterations;  /* GMRES iterations of the implicit stage */
+  bie_solve_info solve[2];  /* the velocity solves at t (when run) and at t + dt/2 */
+} bie_coupled_info;
+
+/* One step of Alg. 1 (Sec. 3): the midpoint rule for the shapes and the second-order IMEX scheme
+ * (Eqs. systemforgammatpdt2, gammatpiudt) for the surfactant, coupled through the interfacial force:
+ *   u^t = u(x^t, Gamma^t);  x_h = x^t + (dt/2) u^t;
+ *   Gamma_h from (I - (dt/2)(1/Pe) lap_{x_h}) Gamma_h = Gamma^t + (dt/2) f_E(x^t, u^t, Gamma^t);
+ *   u_h = u(x_h, Gamma_h);  x^{t+dt} = x^t + dt u_h;
+ *   Gamma^{t+dt} = Gamma^t + dt (f_E(x_h, u_h, Gamma_h) + f_I(x_h, Gamma_h)),
+ * u(x, Gamma) the solution of Eq. main_eq in the shear u_inf = (shear z, 0, 0) with the interfacial
+ * force of Gamma (as bie_step_midpoint).
+ *   u0         device [drop][3][(p+1)^2]: u^t in when u0_valid (a rejected attempt's), else written;
+ *   x_out, gamma_out  device outputs at t + dt; they must not alias xcoef / gammacoef;
+ *   inv_pe     1/Pe >= 0;  imex1_estimate  nonzero to compute info->err_imex1 (one more implicit solve);
+ *   opts, p, pq, lambda, elasticity, x_s  as bie_step_midpoint.
+ * Synchronous; builds and destroys the geometries it needs. */
+int bie_step_coupled(bie_ctx* ctx, int ndrop, const int* p, const int* pq, const double* xcoef,
+                     const double* gammacoef, double* u0, int u0_valid, double elasticity, double x_s,
+                     const double* lambda, double shear, double inv_pe, double dt, int imex1_estimate,
+                     const bie_solve_opts* opts, double* x_out, double* gamma_out, bie_coupled_info* info,
+                     void* stream);
+
+/* Step-size rule of Alg. 1: min(dt_max, dt (0.9 tol/err)^(1/2)); dt_max when err <= 0. */
+double bie_next_dt(double dt, double err, double tol, double dt_max);
+
+#define BIE_ERR_CONSERVATION 0  /* surfactant error of Alg. 1: the conservation error */
+#define BIE_ERR_IMEX1 1         /* ... or the IMEX-1 estimate */
+
+typedef struct bie_run_info {
+  double t;                 /* time reached */
+  double dt_next;           /* the step size the rule proposes next */
+  double err_max_accepted;  /* largest err = max(err_drop, err_surfactant) of a kept step */
+  int steps_accepted, steps_rejected, velocity_solves;
+} bie_run_info;
+
+/* Alg. 1 from t = 0 to T with adaptive dt: each attempt is bie_step_coupled; it is kept when
+ * err = max(err_drop, err_surfactant) < tol (estimator BIE_ERR_CONSERVATION or BIE_ERR_IMEX1);
+ * after every attempt dt <- bie_next_dt(dt, err, tol, dt_max), the last step cut to end at T;
+ * a rejected attempt reuses u^t.  xcoef, gammacoef: device, in at 0, out at the time reached.
+ * Reparametrisation (Sec. 4) is not part of the run.  BIE_ENOCONV when max_steps attempts end
+ * before T.  Synchronous. */
+int bie_run_coupled(bie_ctx* ctx, int ndrop, const int* p, const int* pq, double* xcoef, double* gammacoef,
+                    double elasticity, double x_s, const double* lambda, double shear, double inv_pe, double T,
+                    double dt0, double tol, double dt_max, int estimator, int max_steps, const bie_solve_opts* opts,
+                    bie_run_info* info, void* stream);
+
 /* Number of CUDA kernels the library has launched in this process (all contexts). */
 long long bie_launch_count(void);
 

@@ -46,6 +46,19 @@ class bie_phase_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("ms", c_double), ("calls", c_ll)]
 
 
+class bie_coupled_info(ctypes.Structure):
+    _fields_ = [("err_drop", c_double), ("err_conservation", c_double), ("err_imex1", c_double),
+                ("velocity_solves", c_int), ("implicit_iterations", c_int), ("solve", bie_solve_info * 2)]
+
+
+class bie_run_info(ctypes.Structure):
+    _fields_ = [("t", c_double), ("dt_next", c_double), ("err_max_accepted", c_double), ("steps_accepted", c_int),
+                ("steps_rejected", c_int), ("velocity_solves", c_int)]
+
+
+BIE_ERR_CONSERVATION, BIE_ERR_IMEX1 = 0, 1
+
+
 EXPORTS = {
     "bie_config_default": (None, [ctypes.POINTER(bie_config)]),
     "bie_create": (c_int, [ctypes.POINTER(c_void), ctypes.POINTER(bie_config)]),
@@ -71,6 +84,17 @@ EXPORTS = {
     "bie_launch_count": (c_ll, []),
     "bie_step_midpoint": (c_int, [c_void, c_int, P_int, P_int, c_void, c_void, c_double, c_double, P_double,
                                   c_double, c_double, c_void, c_void, c_void]),
+    "bie_surfactant_rates": (c_int, [c_void, c_int, P_int, c_void, c_void, c_void, c_double, c_void, c_void, c_void]),
+    "bie_surfactant_implicit": (c_int, [c_void, c_int, P_int, c_void, c_void, c_double, c_void, c_double, P_int,
+                                        c_void]),
+    "bie_surfactant_mass": (c_int, [c_void, c_int, P_int, c_void, c_void, P_double, c_void]),
+    "bie_step_coupled": (c_int, [c_void, c_int, P_int, P_int, c_void, c_void, c_void, c_int, c_double, c_double,
+                                 P_double, c_double, c_double, c_double, c_int, ctypes.POINTER(bie_solve_opts),
+                                 c_void, c_void, ctypes.POINTER(bie_coupled_info), c_void]),
+    "bie_next_dt": (c_double, [c_double, c_double, c_double, c_double]),
+    "bie_run_coupled": (c_int, [c_void, c_int, P_int, P_int, c_void, c_void, c_double, c_double, P_double, c_double,
+                                c_double, c_double, c_double, c_double, c_double, c_int, c_int,
+                                ctypes.POINTER(bie_solve_opts), ctypes.POINTER(bie_run_info), c_void]),
     "bie_debug_table": (c_ll, [c_int, c_int, c_int, c_int, c_double, P_double, c_ll]),
 }
 
@@ -280,6 +304,75 @@ def midpoint_step(ctx: "Context", p, pq, x: torch.Tensor, gamma: torch.Tensor, e
     _check(lib().bie_step_midpoint(ctx.h, n, P, PQ, _ptr(x), _ptr(gamma), elasticity, x_s, L, shear, dt,
                                    ctypes.byref(o), info, _stream()), "bie_step_midpoint")
     return [{k: getattr(info[i], k) for k, _ in bie_solve_info._fields_} for i in range(2)]
+
+
+def _solve_opts(precision, tol, restart, max_iter, inner_tol, max_refine, residual_precision):
+    o = bie_solve_opts()
+    lib().bie_solve_opts_default(ctypes.byref(o))
+    o.precision, o.tol, o.restart, o.max_iter, o.inner_tol, o.max_refine, o.residual_precision = (
+        precision, tol, restart, max_iter, inner_tol, max_refine, residual_precision)
+    return o
+
+
+def surfactant_rates(ctx: "Context", p, x: torch.Tensor, u: torch.Tensor, gamma: torch.Tensor, inv_pe: float,
+                     fe: torch.Tensor, fi: torch.Tensor = None):
+    """fe = projection of f_E(x, u, Gamma); fi (optional) = projection of inv_pe * lap Gamma."""
+    _check(lib().bie_surfactant_rates(ctx.h, len(p), _ints(p), _ptr(x), _ptr(u), _ptr(gamma), inv_pe, _ptr(fe),
+                                      _ptr(fi) if fi is not None else None, _stream()), "bie_surfactant_rates")
+    return fe, fi
+
+
+def surfactant_implicit(ctx: "Context", p, x: torch.Tensor, b: torch.Tensor, a: float, y: torch.Tensor,
+                        tol: float = 1e-13) -> int:
+    """y with y - a P[lap_x y] = b (preconditioned GMRES); returns the iteration count."""
+    it = ctypes.c_int(0)
+    _check(lib().bie_surfactant_implicit(ctx.h, len(p), _ints(p), _ptr(x), _ptr(b), a, _ptr(y), tol,
+                                         ctypes.byref(it), _stream()), "bie_surfactant_implicit")
+    return it.value
+
+
+def surfactant_mass(ctx: "Context", p, x: torch.Tensor, gamma: torch.Tensor) -> list:
+    """Surfactant mass of each drop (regular rule on the grid of degree 2p+1)."""
+    out = (ctypes.c_double * len(p))()
+    _check(lib().bie_surfactant_mass(ctx.h, len(p), _ints(p), _ptr(x), _ptr(gamma), out, _stream()),
+           "bie_surfactant_mass")
+    return list(out)
+
+
+def coupled_step(ctx: "Context", p, pq, x: torch.Tensor, gamma: torch.Tensor, u0: torch.Tensor, u0_valid: bool,
+                 elasticity: float, x_s: float, lam, shear: float, inv_pe: float, dt: float, x_out: torch.Tensor,
+                 gamma_out: torch.Tensor, imex1_estimate: bool = False, precision: int = BIE_MIXED,
+                 tol: float = 1e-10, restart: int = 30, max_iter: int = 300, inner_tol: float = 1e-5,
+                 max_refine: int = 10, residual_precision: int = BIE_DF) -> dict:
+    """One step of Alg. 1 (midpoint shapes, IMEX-2 surfactant) into x_out, gamma_out; u0 holds u^t."""
+    o = _solve_opts(precision, tol, restart, max_iter, inner_tol, max_refine, residual_precision)
+    info = bie_coupled_info()
+    _check(lib().bie_step_coupled(ctx.h, len(p), _ints(p), _ints(pq), _ptr(x), _ptr(gamma), _ptr(u0),
+                                  1 if u0_valid else 0, elasticity, x_s, _doubles(lam), shear, inv_pe, dt,
+                                  1 if imex1_estimate else 0, ctypes.byref(o), _ptr(x_out), _ptr(gamma_out),
+                                  ctypes.byref(info), _stream()), "bie_step_coupled")
+    res = {k: getattr(info, k) for k, _ in bie_coupled_info._fields_ if k != "solve"}
+    res["solve"] = [{k: getattr(info.solve[i], k) for k, _ in bie_solve_info._fields_} for i in range(2)]
+    return res
+
+
+def next_dt(dt: float, err: float, tol: float, dt_max: float) -> float:
+    """Step-size rule of Alg. 1."""
+    return float(lib().bie_next_dt(dt, err, tol, dt_max))
+
+
+def run_coupled(ctx: "Context", p, pq, x: torch.Tensor, gamma: torch.Tensor, elasticity: float, x_s: float, lam,
+                shear: float, inv_pe: float, T: float, dt0: float, tol: float, dt_max: float,
+                estimator: int = BIE_ERR_CONSERVATION, max_steps: int = 1000, precision: int = BIE_MIXED,
+                solve_tol: float = 1e-10, restart: int = 30, max_iter: int = 300, inner_tol: float = 1e-5,
+                max_refine: int = 10, residual_precision: int = BIE_DF) -> dict:
+    """Alg. 1 from 0 to T with adaptive dt; x and gamma are updated in place."""
+    o = _solve_opts(precision, solve_tol, restart, max_iter, inner_tol, max_refine, residual_precision)
+    info = bie_run_info()
+    _check(lib().bie_run_coupled(ctx.h, len(p), _ints(p), _ints(pq), _ptr(x), _ptr(gamma), elasticity, x_s,
+                                 _doubles(lam), shear, inv_pe, T, dt0, tol, dt_max, estimator, max_steps,
+                                 ctypes.byref(o), ctypes.byref(info), _stream()), "bie_run_coupled")
+    return {k: getattr(info, k) for k, _ in bie_run_info._fields_}
 
 
 def launch_count() -> int:

@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -1750,6 +1752,401 @@ static int gmres(bie_ctx* ctx, const bie_geom* g, int prec, const double* b, dou
 
 }  // namespace bie
 
+namespace bie {
+// Velocity of the drop surfaces (Eq. main_eq) for the shapes x and surfactant gamma: geometry,
+// interfacial force, far field u_inf = (shear z, 0, 0) (the z coefficients of x, scaled), the
+// right-hand side at precision rprec and the solve, into u.  f, uinf and b are n-long temporaries.
+static int velocity_solve(bie_ctx* ctx, int ndrop, const int* p, const int* pq, const std::vector<long long>& off,
+                          long long n, const double* x, const double* gammacoef, double elasticity, double x_s,
+                          const double* lambda, double shear, const bie_solve_opts* opts, int rprec, double* f,
+                          double* uinf, double* b, double* u, bie_solve_info* inf, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  bie_geom* g = nullptr;
+  BIE_TRY(bie_geometry_setup(ctx, ndrop, p, pq, x, lambda, &g, stream));
+  int st = bie_interfacial_force(ctx, g, gammacoef, elasticity, x_s, f, stream);
+  if (st == BIE_OK) {
+    if (cudaMemsetAsync(uinf, 0, n * sizeof(double), s) != cudaSuccess) st = BIE_ECUDA;
+    for (int d = 0; d < ndrop && st == BIE_OK; ++d) {
+      const long long nc = ncoef(p[d]);
+      if (cudaMemcpyAsync(uinf + off[d], x + off[d] + 2 * nc, nc * sizeof(double), cudaMemcpyDeviceToDevice, s) !=
+          cudaSuccess)
+        st = BIE_ECUDA;
+    }
+    if (st == BIE_OK) {
+      k_scale<<<nblk(n), 256, 0, s>>>(shear, uinf, n);
+      count_launch();
+      if (cudaGetLastError() != cudaSuccess) st = BIE_ECUDA;
+    }
+  }
+  if (st == BIE_OK) st = bie_rhs(ctx, g, uinf, f, b, rprec, stream);
+  if (st == BIE_OK && cudaMemsetAsync(u, 0, n * sizeof(double), s) != cudaSuccess) st = BIE_ECUDA;
+  if (st == BIE_OK) st = bie_solve(ctx, g, b, u, opts, inf, stream);
+  bie_geometry_destroy(g);
+  return st;
+}
+}  // namespace bie
+
+// ---------------------------------------------------------------------------------------------
+// surfactant transport (Eq. surfactant0, Sec. 1.2, Sec. 3)
+// ---------------------------------------------------------------------------------------------
+namespace bie {
+
+// Drops of one degree p on the grid of degree P: device offsets of their vector coefficient sets
+// (x, u: [drop][3] blocks, one offset per component) and of their scalar sets (Gamma: [drop]).
+struct SurfGroup {
+  int p = 0, P = 0;
+  Plan* pl = nullptr;
+  std::vector<int> drops;
+  DevBuf<long long> voff, soff;
+};
+
+struct SurfLayout {
+  int ndrop = 0;
+  std::vector<int> p;
+  std::vector<long long> voff, soff;  // per drop: start of its vector / scalar coefficients
+  long long nv = 0, ns = 0;           // total lengths
+  std::vector<std::unique_ptr<SurfGroup>> groups;
+};
+
+// P = 2p + 1 (the nonlinear terms of Sec. 1.3) when upsampled, else P = p.
+static int surf_layout(bie_ctx* ctx, int ndrop, const int* p, bool upsampled, SurfLayout& L) {
+  L.ndrop = ndrop;
+  L.p.assign(p, p + ndrop);
+  L.voff.resize(ndrop);
+  L.soff.resize(ndrop);
+  std::map<int, std::vector<int>> byp;
+  for (int d = 0; d < ndrop; ++d) {
+    L.voff[d] = L.nv;
+    L.soff[d] = L.ns;
+    L.nv += 3 * ncoef(p[d]);
+    L.ns += ncoef(p[d]);
+    byp[p[d]].push_back(d);
+  }
+  for (auto& kv : byp) {
+    std::unique_ptr<SurfGroup> G(new SurfGroup());
+    G->p = kv.first;
+    G->P = upsampled ? 2 * kv.first + 1 : kv.first;
+    BIE_TRY(get_plan(ctx, G->p, G->P, &G->pl));
+    G->drops = kv.second;
+    std::vector<long long> vo, so;
+    for (int d : G->drops) {
+      for (int c = 0; c < 3; ++c) vo.push_back(L.voff[d] + c * ncoef(G->p));
+      so.push_back(L.soff[d]);
+    }
+    BIE_TRY(G->voff.upload(vo));
+    BIE_TRY(G->soff.upload(so));
+    L.groups.push_back(std::move(G));
+  }
+  return BIE_OK;
+}
+
+// Derivative fields of nfield coefficient sets (device offsets off) of the group's degree on its
+// grid: kind k (0 f, 1 t, 2 p, 3 tt, 4 tp, 5 pp) is written to out + k * nfield * N.  H holds
+// nfield * (p+1) * (P+1) * 2 doubles.
+static int surf_synth(const SurfGroup& G, const double* coef, const long long* off, long long nfield,
+                      std::initializer_list<int> kinds, double* H, double* out, cudaStream_t s) {
+  const Plan* pl = G.pl;
+  const double* T[6] = {pl->T0.ptr, pl->T1.ptr, pl->T0.ptr, pl->T2.ptr, pl->T1.ptr, pl->T0.ptr};
+  const int dphi[6] = {0, 0, 1, 0, 1, 2};
+  const long long N = ngrid(G.P);
+  for (int k : kinds) {
+    BIE_TRY((launch_leg_synth<double, double>(coef, off, 0, nfield, G.p, T[k], G.P + 1, H, dphi[k], s)));
+    BIE_TRY((launch_phi_synth<double, double>(H, nfield, G.p, G.P, pl->cs.ptr, out + (long long)k * nfield * N,
+                                              nullptr, N, s)));
+  }
+  return BIE_OK;
+}
+
+static long long synth_work(const SurfGroup& G, long long nfield) {
+  return nfield * (G.p + 1) * (long long)(G.P + 1) * 2;
+}
+
+// Galerkin projections of f_E and (when fi is non-null) f_I = inv_pe lap Gamma, Sec. 3.
+static int surf_rates(const SurfLayout& L, const double* x, const double* u, const double* gam, double inv_pe,
+                      double* fe, double* fi, cudaStream_t s) {
+  for (auto& Gp : L.groups) {
+    const SurfGroup& G = *Gp;
+    const long long nd = (long long)G.drops.size(), N = ngrid(G.P);
+    const long long nH = synth_work(G, 3 * nd);
+    DevBuf<double> tmp;
+    BIE_TRY(tmp.alloc(nH + 18 * nd * N + 9 * nd * N + 6 * nd * N + 2 * nd * N));
+    double* H = tmp.ptr;
+    double* X = H + nH;
+    double* U = X + 18 * nd * N;
+    double* Gm = U + 9 * nd * N;
+    double* out = Gm + 6 * nd * N;
+    BIE_TRY(surf_synth(G, x, G.voff.ptr, 3 * nd, {0, 1, 2, 3, 4, 5}, H, X, s));
+    BIE_TRY(surf_synth(G, u, G.voff.ptr, 3 * nd, {0, 1, 2}, H, U, s));
+    BIE_TRY(surf_synth(G, gam, G.soff.ptr, nd, {0, 1, 2, 3, 4, 5}, H, Gm, s));
+    BIE_TRY(launch_surf_rates(X, U, Gm, nd, N, inv_pe, out, fi ? out + nd * N : nullptr, s));
+    // H is free again: it serves as the analysis workspace (nd fields need less than 3 nd)
+    BIE_TRY(launch_analyze(out, nullptr, N, nd, G.P, G.p, G.pl->cs.ptr, G.pl->A.ptr, H, fe, G.soff.ptr, 0, s));
+    if (fi)
+      BIE_TRY(launch_analyze(out + nd * N, nullptr, N, nd, G.P, G.p, G.pl->cs.ptr, G.pl->A.ptr, H, fi, G.soff.ptr,
+                             0, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));  // temporaries are released per group
+  }
+  return BIE_OK;
+}
+
+// Per-drop integrals on the grid of each group (mode 0: volume of x, mode 1: mass of Gamma), host out[d].
+static int surf_integrals(const SurfLayout& L, const double* x, const double* gam, int mode, double* out,
+                          cudaStream_t s) {
+  for (auto& Gp : L.groups) {
+    const SurfGroup& G = *Gp;
+    const long long nd = (long long)G.drops.size(), N = ngrid(G.P);
+    const long long nH = synth_work(G, 3 * nd);
+    DevBuf<double> tmp;
+    BIE_TRY(tmp.alloc(nH + 9 * nd * N + nd * N + nd));
+    double* H = tmp.ptr;
+    double* X = H + nH;
+    double* Gm = X + 9 * nd * N;
+    double* res = Gm + nd * N;
+    if (mode == 0)
+      BIE_TRY(surf_synth(G, x, G.voff.ptr, 3 * nd, {0, 1, 2}, H, X, s));
+    else
+      BIE_TRY(surf_synth(G, x, G.voff.ptr, 3 * nd, {1, 2}, H, X, s));
+    if (mode == 1) BIE_TRY(surf_synth(G, gam, G.soff.ptr, nd, {0}, H, Gm, s));
+    BIE_TRY(launch_drop_integral(X, Gm, nd, G.P, G.pl->wsin.ptr, mode, res, s));
+    std::vector<double> h(nd);
+    BIE_CUDA_TRY(cudaMemcpyAsync(h.data(), res, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+    for (long long i = 0; i < nd; ++i) out[G.drops[i]] = h[i];
+  }
+  return BIE_OK;
+}
+
+// Per-drop max |value| on the grid of each group of ncomp-component coefficient sets (ncomp 3:
+// vector layout, 1: scalar layout), host out[d].
+static int surf_absmax(const SurfLayout& L, const double* coef, int ncomp, double* out, cudaStream_t s) {
+  for (auto& Gp : L.groups) {
+    const SurfGroup& G = *Gp;
+    const long long nd = (long long)G.drops.size(), N = ngrid(G.P), nf = ncomp * nd;
+    const long long nH = synth_work(G, nf);
+    DevBuf<double> tmp;
+    BIE_TRY(tmp.alloc(nH + nf * N + nd));
+    double* H = tmp.ptr;
+    double* F = H + nH;
+    double* res = F + nf * N;
+    BIE_TRY(surf_synth(G, coef, ncomp == 3 ? G.voff.ptr : G.soff.ptr, nf, {0}, H, F, s));
+    BIE_TRY(launch_drop_absmax(F, nd, ncomp, N, res, s));
+    std::vector<double> h(nd);
+    BIE_CUDA_TRY(cudaMemcpyAsync(h.data(), res, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+    for (long long i = 0; i < nd; ++i) out[G.drops[i]] = h[i];
+  }
+  return BIE_OK;
+}
+
+// The implicit operator of Sec. 3 (Preconditioning) for the shapes x, left-preconditioned:
+// y -> (y - a lap y) / (1 + a n(n+1)/R_d^2), R_d the mean radius of drop d.
+struct SurfImplicit {
+  const SurfLayout* L = nullptr;
+  double a = 0;
+  std::vector<std::unique_ptr<DevBuf<double>>> lapc;  // per group [5][nd][N]
+  DevBuf<double> inv_diag, c, work;
+};
+
+static int surf_implicit_setup(const SurfLayout& L, const double* x, double a, SurfImplicit& I, cudaStream_t s) {
+  I.L = &L;
+  I.a = a;
+  long long wmax = 0;
+  for (auto& Gp : L.groups) {
+    const SurfGroup& G = *Gp;
+    const long long nd = (long long)G.drops.size(), N = ngrid(G.P);
+    const long long nH = synth_work(G, 3 * nd);
+    DevBuf<double> tmp;
+    BIE_TRY(tmp.alloc(nH + 18 * nd * N));
+    BIE_TRY(surf_synth(G, x, G.voff.ptr, 3 * nd, {0, 1, 2, 3, 4, 5}, tmp.ptr, tmp.ptr + nH, s));
+    std::unique_ptr<DevBuf<double>> lc(new DevBuf<double>());
+    BIE_TRY(lc->alloc(5 * nd * N));
+    BIE_TRY(launch_lap_coef(tmp.ptr + nH, nd, N, lc->ptr, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+    I.lapc.push_back(std::move(lc));
+    wmax = std::max(wmax, synth_work(G, nd) + 7 * nd * N);
+  }
+  std::vector<double> vol(L.ndrop);
+  BIE_TRY(surf_integrals(L, x, nullptr, 0, vol.data(), s));
+  std::vector<double> inv(L.ns);
+  for (int d = 0; d < L.ndrop; ++d) {
+    const double R = std::cbrt(3.0 * vol[d] / (4.0 * kPi));
+    for (int n = 0; n <= L.p[d]; ++n)
+      for (int i = 0; i < 2 * n + 1; ++i)
+        inv[L.soff[d] + (long long)n * n + i] = 1.0 / (1.0 + a * n * (n + 1.0) / (R * R));
+  }
+  BIE_TRY(I.inv_diag.upload(inv));
+  BIE_TRY(I.c.alloc(L.ns));
+  BIE_TRY(I.work.alloc(wmax));
+  return BIE_OK;
+}
+
+static int surf_implicit_apply(SurfImplicit& I, const double* y, double* w, cudaStream_t s) {
+  const SurfLayout& L = *I.L;
+  for (size_t gi = 0; gi < L.groups.size(); ++gi) {
+    const SurfGroup& G = *L.groups[gi];
+    const long long nd = (long long)G.drops.size(), N = ngrid(G.P);
+    double* H = I.work.ptr;
+    double* S = H + synth_work(G, nd);  // [6][nd][N], kinds 1..5 used
+    double* grid = S + 6 * nd * N;
+    BIE_TRY(surf_synth(G, y, G.soff.ptr, nd, {1, 2, 3, 4, 5}, H, S, s));
+    BIE_TRY(launch_lap_apply(I.lapc[gi]->ptr, S, nd, N, grid, s));
+    BIE_TRY(launch_analyze(grid, nullptr, N, nd, G.P, G.p, G.pl->cs.ptr, G.pl->A.ptr, H, I.c.ptr, G.soff.ptr, 0, s));
+  }
+  return launch_implicit_combine(y, I.c.ptr, I.a, I.inv_diag.ptr, L.ns, w, s);
+}
+
+// Restarted GMRES (classical Gram-Schmidt with one re-orthogonalisation, Givens rotations on the
+// host) for op x = b from x = 0; stops on ||b - op x|| <= tol ||b||.
+struct SurfKrylov {
+  long long n = 0;
+  int m = 0;
+  DevBuf<double> V, partial, hdev, ydev;
+  int init(long long n_, int m_) {
+    n = n_;
+    m = m_;
+    BIE_TRY(V.alloc((size_t)(m + 1) * n));
+    BIE_TRY(partial.alloc((size_t)kRedBlocks * (m + 1)));
+    BIE_TRY(hdev.alloc(m + 1));
+    BIE_TRY(ydev.alloc(m + 1));
+    return BIE_OK;
+  }
+};
+
+// out[i] = V_i . w for i < k (V_i n apart), on the host
+static int surf_dots(SurfKrylov& K, const double* V, int k, const double* w, double* out, cudaStream_t s) {
+  k_multidot<<<dim3(kRedBlocks, k), kRedThreads, 0, s>>>(V, K.n, w, K.n, k, K.partial.ptr);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  k_sum_partials<<<k, 128, 0, s>>>(K.partial.ptr, kRedBlocks, k, K.hdev.ptr);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  BIE_CUDA_TRY(cudaMemcpyAsync(out, K.hdev.ptr, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return BIE_OK;
+}
+
+// x += sum_i c_i V_i (c on the host, k entries)
+static int surf_comb(SurfKrylov& K, double* x, const double* V, const double* c, int k, cudaStream_t s) {
+  BIE_CUDA_TRY(cudaMemcpyAsync(K.ydev.ptr, c, k * sizeof(double), cudaMemcpyHostToDevice, s));
+  k_add_comb<<<nblk(K.n), 256, 0, s>>>(x, V, K.n, K.ydev.ptr, k, K.n);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));  // c may change on return
+  return BIE_OK;
+}
+
+static int surf_gmres(SurfKrylov& K, const std::function<int(const double*, double*)>& op, const double* b,
+                      double* x, double tol, int max_it, int* iters, double* relres, cudaStream_t s) {
+  const long long n = K.n;
+  const int m = K.m;
+  double* V = K.V.ptr;
+  BIE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  double bb;
+  BIE_TRY(surf_dots(K, b, 1, b, &bb, s));
+  const double bnorm = std::sqrt(bb);
+  *iters = 0;
+  *relres = 0;
+  if (bnorm == 0.0) return BIE_OK;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 1), h2(m + 1), y(m);
+  auto Hr = [&](int i, int k) -> double& { return H[(size_t)i * m + k]; };
+  int it = 0;
+  bool xzero = true;
+  while (true) {
+    double* r = V;
+    if (xzero) {
+      BIE_CUDA_TRY(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      BIE_TRY(op(x, r));
+      k_axpby<<<nblk(n), 256, 0, s>>>(1.0, b, -1.0, r, n);
+      count_launch();
+      BIE_CUDA_TRY(cudaGetLastError());
+    }
+    double rr;
+    BIE_TRY(surf_dots(K, r, 1, r, &rr, s));
+    const double beta = std::sqrt(rr);
+    *relres = beta / bnorm;
+    *iters = it;
+    if (beta / bnorm <= tol) return BIE_OK;
+    if (it >= max_it) {
+      set_error("surfactant implicit solve: GMRES did not converge");
+      return BIE_ENOCONV;
+    }
+    k_scale<<<nblk(n), 256, 0, s>>>(1.0 / beta, r, n);
+    count_launch();
+    BIE_CUDA_TRY(cudaGetLastError());
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int used = 0;
+    for (int k = 0; k < m; ++k) {
+      double* w = V + (long long)(k + 1) * n;
+      BIE_TRY(op(V + (long long)k * n, w));
+      BIE_TRY(surf_dots(K, V, k + 1, w, h.data(), s));
+      for (int i = 0; i <= k; ++i) h2[i] = -h[i];
+      BIE_TRY(surf_comb(K, w, V, h2.data(), k + 1, s));
+      BIE_TRY(surf_dots(K, V, k + 1, w, h2.data(), s));
+      for (int i = 0; i <= k; ++i) {
+        h[i] += h2[i];
+        h2[i] = -h2[i];
+      }
+      BIE_TRY(surf_comb(K, w, V, h2.data(), k + 1, s));
+      double ww;
+      BIE_TRY(surf_dots(K, w, 1, w, &ww, s));
+      const double hk1 = std::sqrt(ww);
+      if (hk1 > 0.0) {
+        k_scale<<<nblk(n), 256, 0, s>>>(1.0 / hk1, w, n);
+        count_launch();
+        BIE_CUDA_TRY(cudaGetLastError());
+      }
+      for (int i = 0; i <= k; ++i) Hr(i, k) = h[i];
+      Hr(k + 1, k) = hk1;
+      for (int i = 0; i < k; ++i) {
+        const double t = cs[i] * Hr(i, k) + sn[i] * Hr(i + 1, k);
+        Hr(i + 1, k) = -sn[i] * Hr(i, k) + cs[i] * Hr(i + 1, k);
+        Hr(i, k) = t;
+      }
+      const double den = std::hypot(Hr(k, k), Hr(k + 1, k));
+      cs[k] = Hr(k, k) / den;
+      sn[k] = Hr(k + 1, k) / den;
+      Hr(k, k) = den;
+      Hr(k + 1, k) = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      ++it;
+      used = k + 1;
+      if (std::fabs(g[k + 1]) / bnorm <= tol || it >= max_it || hk1 == 0.0) break;
+    }
+    for (int i = used - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int j = i + 1; j < used; ++j) t -= Hr(i, j) * y[j];
+      y[i] = t / Hr(i, i);
+    }
+    BIE_TRY(surf_comb(K, x, V, y.data(), used, s));
+    xzero = false;
+  }
+}
+
+// y with (I - a lap_x) y = b per drop (Galerkin), left-preconditioned GMRES.
+static int surf_implicit_solve(const SurfLayout& L, const double* x, const double* b, double a, double* y,
+                               double tol, int* iters, cudaStream_t s) {
+  *iters = 0;
+  if (a == 0.0) {
+    BIE_CUDA_TRY(cudaMemcpyAsync(y, b, L.ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return BIE_OK;
+  }
+  SurfImplicit I;
+  BIE_TRY(surf_implicit_setup(L, x, a, I, s));
+  DevBuf<double> bp;
+  BIE_TRY(bp.alloc(L.ns));
+  BIE_TRY(launch_mul(b, I.inv_diag.ptr, L.ns, bp.ptr, s));
+  SurfKrylov K;
+  BIE_TRY(K.init(L.ns, 60));
+  double rel;
+  auto op = [&](const double* in, double* out) { return surf_implicit_apply(I, in, out, s); };
+  return surf_gmres(K, op, bp.ptr, y, tol, 600, iters, &rel, s);
+}
+
+}  // namespace bie
+
 // ---------------------------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------------------------
@@ -2199,30 +2596,10 @@ int bie_step_midpoint(bie_ctx* ctx, int ndrop, const int* p, const int* pq, doub
   BIE_TRY(u.alloc(n));
   // the right-hand side at the solve's FP64-grade precision
   const int rprec = (opts->precision & 0xff) == BIE_FP64 ? BIE_FP64 : opts->residual_precision;
-  // u(x): Eq. main_eq for the shapes x, u_inf = (shear z, 0, 0) (the z coefficients of x, scaled)
+  // u(x): Eq. main_eq for the shapes x with the surfactant held fixed
   auto velocity = [&](const double* x, bie_solve_info* inf) -> int {
-    bie_geom* g = nullptr;
-    BIE_TRY(bie_geometry_setup(ctx, ndrop, p, pq, x, lambda, &g, stream));
-    int st = bie_interfacial_force(ctx, g, gammacoef, elasticity, x_s, f.ptr, stream);
-    if (st == BIE_OK) {
-      if (cudaMemsetAsync(uinf.ptr, 0, n * sizeof(double), s) != cudaSuccess) st = BIE_ECUDA;
-      for (int d = 0; d < ndrop && st == BIE_OK; ++d) {
-        const long long nc = ncoef(p[d]);
-        if (cudaMemcpyAsync(uinf.ptr + off[d], x + off[d] + 2 * nc, nc * sizeof(double), cudaMemcpyDeviceToDevice,
-                            s) != cudaSuccess)
-          st = BIE_ECUDA;
-      }
-      if (st == BIE_OK) {
-        k_scale<<<nblk(n), 256, 0, s>>>(shear, uinf.ptr, n);
-        count_launch();
-        if (cudaGetLastError() != cudaSuccess) st = BIE_ECUDA;
-      }
-    }
-    if (st == BIE_OK) st = bie_rhs(ctx, g, uinf.ptr, f.ptr, b.ptr, rprec, stream);
-    if (st == BIE_OK && cudaMemsetAsync(u.ptr, 0, n * sizeof(double), s) != cudaSuccess) st = BIE_ECUDA;
-    if (st == BIE_OK) st = bie_solve(ctx, g, b.ptr, u.ptr, opts, inf, stream);
-    bie_geometry_destroy(g);
-    return st;
+    return velocity_solve(ctx, ndrop, p, pq, off, n, x, gammacoef, elasticity, x_s, lambda, shear, opts, rprec, f.ptr,
+                          uinf.ptr, b.ptr, u.ptr, inf, stream);
   };
   bie_solve_info tmp[2];
   bie_solve_info* inf = info ? info : tmp;
@@ -2277,6 +2654,203 @@ int bie_profile_read(bie_ctx* ctx, bie_phase_stat* stats, int cap, int* count) {
   }
   P.used = 0;
   P.recs.clear();
+  return BIE_OK;
+}
+
+static int surf_check(bie_ctx* ctx, int ndrop, const int* p) {
+  if (!ctx) {
+    set_error("null argument");
+    return BIE_EINVAL;
+  }
+  BIE_TRY(check_degrees(ndrop, p));
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  return BIE_OK;
+}
+
+int bie_surfactant_rates(bie_ctx* ctx, int ndrop, const int* p, const double* xcoef, const double* ucoef,
+                         const double* gammacoef, double inv_pe, double* fe, double* fi, void* stream) {
+  if (!xcoef || !ucoef || !gammacoef || !fe || inv_pe < 0.0) {
+    set_error("null argument or negative 1/Pe");
+    return BIE_EINVAL;
+  }
+  BIE_TRY(surf_check(ctx, ndrop, p));
+  cudaStream_t s = (cudaStream_t)stream;
+  Phase ph(ctx, "surfactant_rates", s);
+  SurfLayout L;
+  BIE_TRY(surf_layout(ctx, ndrop, p, true, L));
+  return surf_rates(L, xcoef, ucoef, gammacoef, inv_pe, fe, fi, s);
+}
+
+int bie_surfactant_implicit(bie_ctx* ctx, int ndrop, const int* p, const double* xcoef, const double* b, double a,
+                            double* y, double tol, int* iterations, void* stream) {
+  if (!xcoef || !b || !y || a < 0.0 || !(tol > 0.0)) {
+    set_error("null argument, negative a or non-positive tol");
+    return BIE_EINVAL;
+  }
+  BIE_TRY(surf_check(ctx, ndrop, p));
+  cudaStream_t s = (cudaStream_t)stream;
+  Phase ph(ctx, "surfactant_implicit", s);
+  SurfLayout L;
+  BIE_TRY(surf_layout(ctx, ndrop, p, true, L));
+  int it = 0;
+  const int st = surf_implicit_solve(L, xcoef, b, a, y, tol, &it, s);
+  if (iterations) *iterations = it;
+  return st;
+}
+
+int bie_surfactant_mass(bie_ctx* ctx, int ndrop, const int* p, const double* xcoef, const double* gammacoef,
+                        double* mass, void* stream) {
+  if (!xcoef || !gammacoef || !mass) {
+    set_error("null argument");
+    return BIE_EINVAL;
+  }
+  BIE_TRY(surf_check(ctx, ndrop, p));
+  SurfLayout L;
+  BIE_TRY(surf_layout(ctx, ndrop, p, true, L));
+  return surf_integrals(L, xcoef, gammacoef, 1, mass, (cudaStream_t)stream);
+}
+
+int bie_step_coupled(bie_ctx* ctx, int ndrop, const int* p, const int* pq, const double* xcoef,
+                     const double* gammacoef, double* u0, int u0_valid, double elasticity, double x_s,
+                     const double* lambda, double shear, double inv_pe, double dt, int imex1_estimate,
+                     const bie_solve_opts* opts, double* x_out, double* gamma_out, bie_coupled_info* info,
+                     void* stream) {
+  if (!pq || !xcoef || !gammacoef || !u0 || !lambda || !opts || !x_out || !gamma_out || !info) {
+    set_error("null argument");
+    return BIE_EINVAL;
+  }
+  if (x_out == xcoef || gamma_out == gammacoef || !(dt > 0.0) || inv_pe < 0.0) {
+    set_error("outputs must not alias the inputs; dt must be positive and 1/Pe non-negative");
+    return BIE_EINVAL;
+  }
+  BIE_TRY(surf_check(ctx, ndrop, p));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::memset(info, 0, sizeof(*info));
+  info->err_imex1 = -1.0;
+  SurfLayout L, L0;
+  BIE_TRY(surf_layout(ctx, ndrop, p, true, L));
+  BIE_TRY(surf_layout(ctx, ndrop, p, false, L0));
+  const long long n = L.nv, ns = L.ns;
+  DevBuf<double> f, uinf, b, uh, xh, k0, rhs, gh, fe, fi, du, g1;
+  for (DevBuf<double>* v : {&f, &uinf, &b, &uh, &xh, &du}) BIE_TRY(v->alloc(n));
+  for (DevBuf<double>* v : {&k0, &rhs, &gh, &fe, &fi, &g1}) BIE_TRY(v->alloc(ns));
+  const int rprec = (opts->precision & 0xff) == BIE_FP64 ? BIE_FP64 : opts->residual_precision;
+  std::vector<double> m0(ndrop), m1(ndrop), ax(ndrop), ad(ndrop);
+  BIE_TRY(surf_integrals(L, xcoef, gammacoef, 1, m0.data(), s));
+  auto axpby = [&](double a, const double* xv, double bcoef, double* yv, long long len) -> int {
+    k_axpby<<<nblk(len), 256, 0, s>>>(a, xv, bcoef, yv, len);
+    count_launch();
+    BIE_CUDA_TRY(cudaGetLastError());
+    return BIE_OK;
+  };
+  // u^t at (x^t, Gamma^t) unless the caller holds it from a rejected attempt
+  if (!u0_valid) {
+    BIE_TRY(velocity_solve(ctx, ndrop, p, pq, L.voff, n, xcoef, gammacoef, elasticity, x_s, lambda, shear, opts,
+                           rprec, f.ptr, uinf.ptr, b.ptr, u0, &info->solve[0], stream));
+    info->velocity_solves++;
+  }
+  // x^{t+dt/2} = x^t + (dt/2) u^t
+  BIE_CUDA_TRY(cudaMemcpyAsync(xh.ptr, xcoef, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  BIE_TRY(axpby(0.5 * dt, u0, 1.0, xh.ptr, n));
+  // Gamma^{t+dt/2}: (I - (dt/2) (1/Pe) lap_{x^{t+dt/2}}) Gamma_h = Gamma^t + (dt/2) f_E(x^t, u^t, Gamma^t)
+  BIE_TRY(surf_rates(L, xcoef, u0, gammacoef, 0.0, k0.ptr, nullptr, s));
+  BIE_CUDA_TRY(cudaMemcpyAsync(rhs.ptr, gammacoef, ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  BIE_TRY(axpby(0.5 * dt, k0.ptr, 1.0, rhs.ptr, ns));
+  BIE_TRY(surf_implicit_solve(L, xh.ptr, rhs.ptr, 0.5 * dt * inv_pe, gh.ptr, 1e-13, &info->implicit_iterations, s));
+  // u^{t+dt/2} at (x^{t+dt/2}, Gamma^{t+dt/2})
+  BIE_TRY(velocity_solve(ctx, ndrop, p, pq, L.voff, n, xh.ptr, gh.ptr, elasticity, x_s, lambda, shear, opts, rprec,
+                         f.ptr, uinf.ptr, b.ptr, uh.ptr, &info->solve[1], stream));
+  info->velocity_solves++;
+  // x^{t+dt} = x^t + dt u^{t+dt/2};  Gamma^{t+dt} = Gamma^t + dt (f_E + f_I)(x^{t+dt/2}, u^{t+dt/2}, Gamma_h)
+  BIE_CUDA_TRY(cudaMemcpyAsync(x_out, xcoef, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  BIE_TRY(axpby(dt, uh.ptr, 1.0, x_out, n));
+  BIE_TRY(surf_rates(L, xh.ptr, uh.ptr, gh.ptr, inv_pe, fe.ptr, fi.ptr, s));
+  BIE_CUDA_TRY(cudaMemcpyAsync(gamma_out, gammacoef, ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  BIE_TRY(axpby(dt, fe.ptr, 1.0, gamma_out, ns));
+  BIE_TRY(axpby(dt, fi.ptr, 1.0, gamma_out, ns));
+  // error estimates of Alg. 1
+  BIE_CUDA_TRY(cudaMemcpyAsync(du.ptr, uh.ptr, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  BIE_TRY(axpby(-dt, u0, dt, du.ptr, n));
+  BIE_TRY(surf_absmax(L0, du.ptr, 3, ad.data(), s));
+  BIE_TRY(surf_absmax(L0, x_out, 3, ax.data(), s));
+  BIE_TRY(surf_integrals(L, x_out, gamma_out, 1, m1.data(), s));
+  for (int d = 0; d < ndrop; ++d) {
+    info->err_drop = std::max(info->err_drop, ad[d] / ax[d]);
+    info->err_conservation = std::max(info->err_conservation, std::fabs(m1[d] - m0[d]) / std::fabs(m0[d]));
+  }
+  if (imex1_estimate) {
+    // Gamma_IMEX1: (I - dt (1/Pe) lap_{x^{t+dt}}) G1 = Gamma^t + dt f_E(x^t, u^t, Gamma^t)
+    BIE_CUDA_TRY(cudaMemcpyAsync(rhs.ptr, gammacoef, ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    BIE_TRY(axpby(dt, k0.ptr, 1.0, rhs.ptr, ns));
+    int it1 = 0;
+    BIE_TRY(surf_implicit_solve(L, x_out, rhs.ptr, dt * inv_pe, g1.ptr, 1e-13, &it1, s));
+    BIE_TRY(axpby(1.0, gamma_out, -1.0, g1.ptr, ns));
+    std::vector<double> ag(ndrop), an(ndrop);
+    BIE_TRY(surf_absmax(L0, g1.ptr, 1, ag.data(), s));
+    BIE_TRY(surf_absmax(L0, gamma_out, 1, an.data(), s));
+    info->err_imex1 = 0.0;
+    for (int d = 0; d < ndrop; ++d) info->err_imex1 = std::max(info->err_imex1, ag[d] / an[d]);
+  }
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return BIE_OK;
+}
+
+double bie_next_dt(double dt, double err, double tol, double dt_max) {
+  if (!(err > 0.0)) return dt_max;
+  return std::min(dt_max, dt * std::sqrt(0.9 * tol / err));
+}
+
+int bie_run_coupled(bie_ctx* ctx, int ndrop, const int* p, const int* pq, double* xcoef, double* gammacoef,
+                    double elasticity, double x_s, const double* lambda, double shear, double inv_pe, double T,
+                    double dt0, double tol, double dt_max, int estimator, int max_steps, const bie_solve_opts* opts,
+                    bie_run_info* info, void* stream) {
+  if (!ctx || !p || !xcoef || !gammacoef || !info || !(T > 0.0) || !(dt0 > 0.0) || !(tol > 0.0) ||
+      !(dt_max > 0.0) || max_steps < 1 || (estimator != BIE_ERR_CONSERVATION && estimator != BIE_ERR_IMEX1)) {
+    set_error("null argument or bad run parameters");
+    return BIE_EINVAL;
+  }
+  BIE_TRY(surf_check(ctx, ndrop, p));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::memset(info, 0, sizeof(*info));
+  long long n = 0, ns = 0;
+  for (int d = 0; d < ndrop; ++d) {
+    n += 3 * ncoef(p[d]);
+    ns += ncoef(p[d]);
+  }
+  DevBuf<double> u0, x1, g1;
+  BIE_TRY(u0.alloc(n));
+  BIE_TRY(x1.alloc(n));
+  BIE_TRY(g1.alloc(ns));
+  double t = 0.0, dt = std::min(dt0, dt_max);
+  int u0_valid = 0;
+  for (int k = 0; k < max_steps && t < T * (1.0 - 1e-14); ++k) {
+    const double h = std::min(dt, T - t);
+    bie_coupled_info ci;
+    BIE_TRY(bie_step_coupled(ctx, ndrop, p, pq, xcoef, gammacoef, u0.ptr, u0_valid, elasticity, x_s, lambda, shear,
+                             inv_pe, h, estimator == BIE_ERR_IMEX1, opts, x1.ptr, g1.ptr, &ci, stream));
+    info->velocity_solves += ci.velocity_solves;
+    u0_valid = 1;
+    const double es = estimator == BIE_ERR_IMEX1 ? ci.err_imex1 : ci.err_conservation;
+    const double err = std::max(ci.err_drop, es);
+    if (err < tol) {
+      t += h;
+      BIE_CUDA_TRY(cudaMemcpyAsync(xcoef, x1.ptr, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      BIE_CUDA_TRY(cudaMemcpyAsync(gammacoef, g1.ptr, ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      u0_valid = 0;
+      info->steps_accepted++;
+      info->err_max_accepted = std::max(info->err_max_accepted, err);
+    } else {
+      info->steps_rejected++;
+    }
+    dt = bie_next_dt(h, err, tol, dt_max);
+  }
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  info->t = t;
+  info->dt_next = dt;
+  if (t < T * (1.0 - 1e-14)) {
+    set_error("bie_run_coupled: max_steps reached before T");
+    return BIE_ENOCONV;
+  }
   return BIE_OK;
 }
 

@@ -126,4 +126,25 @@ int launch_force(const double* X, const double* Gm, long long N, double es, doub
 // out[i] = (float) in[i]
 int launch_to_float(const double* in, float* out, long long n, cudaStream_t s);
 
+// ---- surfactant transport (surfactant.cu) ----
+// f_E and (fi non-null) inv_pe * lap Gamma at the N grid points of nd drops: X [6][nd*3][N] (x and
+// its derivatives f, t, p, tt, tp, pp), U [3][nd*3][N] (u: f, t, p), Gm [6][nd][N]; fe, fi [nd][N]
+int launch_surf_rates(const double* X, const double* U, const double* Gm, long long nd, long long N, double inv_pe,
+                      double* fe, double* fi, cudaStream_t s);
+// coefficients of the surface Laplacian L[5][nd][N] (s_tt, s_tp, s_pp, s_t, s_p) from X [6][nd*3][N]
+int launch_lap_coef(const double* X, long long nd, long long N, double* L, cudaStream_t s);
+// out[nd][N] = lap s from L and the fields S [6][nd][N] of s (kinds t..pp used)
+int launch_lap_apply(const double* L, const double* S, long long nd, long long N, double* out, cudaStream_t s);
+// per-drop integral on the grid of degree P (mode 0: volume from X kinds f, t, p; mode 1: mass of
+// Gm [nd][N] from X kinds t, p), wsin[j] = (pi/(P+1)) w_j / sin(theta_j); out[nd] on the device
+int launch_drop_integral(const double* X, const double* Gm, long long nd, int P, const double* wsin, int mode,
+                         double* out, cudaStream_t s);
+// out[d] = max |F| over the nper fields of drop d, F [nd*nper][N]
+int launch_drop_absmax(const double* F, long long nd, int nper, long long N, double* out, cudaStream_t s);
+// w = (y - a c) * inv_diag
+int launch_implicit_combine(const double* y, const double* c, double a, const double* inv_diag, long long n,
+                            double* w, cudaStream_t s);
+// y = x * sc (elementwise)
+int launch_mul(const double* x, const double* sc, long long n, double* y, cudaStream_t s);
+
 }  // namespace bie

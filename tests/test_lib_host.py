@@ -78,6 +78,26 @@ def test_null_arguments_are_rejected_before_any_device_work(L):
     assert L.bie_solve(None, None, None, None, ctypes.byref(o), ctypes.byref(info), None) == EINVAL
     assert L.bie_step_midpoint(None, 1, p, p, None, None, 0.2, 0.0, lam, 1.0, 0.01, ctypes.byref(o), None,
                                None) == EINVAL
+    # surfactant entry points
+    x = ctypes.c_void_p(16)
+    cinfo = api.bie_coupled_info()
+    rinfo = api.bie_run_info()
+    assert L.bie_surfactant_rates(None, 1, p, x, x, x, 0.1, x, None, None) == EINVAL
+    assert L.bie_surfactant_rates(None, 1, p, None, x, x, 0.1, x, None, None) == EINVAL
+    assert L.bie_surfactant_implicit(None, 1, p, x, x, 0.1, x, 1e-13, None, None) == EINVAL
+    assert L.bie_surfactant_mass(None, 1, p, x, x, None, None) == EINVAL
+    assert L.bie_step_coupled(None, 1, p, p, x, x, x, 0, 0.2, 0.0, lam, 1.0, 0.1, 0.01, 0, ctypes.byref(o), x, x,
+                              ctypes.byref(cinfo), None) == EINVAL
+    assert L.bie_run_coupled(None, 1, p, p, x, x, 0.2, 0.0, lam, 1.0, 0.1, 1.0, 0.1, 1e-5, 0.1, 0, 10,
+                             ctypes.byref(o), ctypes.byref(rinfo), None) == EINVAL
     # status strings
     assert L.bie_strerror(0) == b"ok"
     assert L.bie_strerror(EINVAL) == b"invalid argument"
+
+
+def test_step_size_rule_matches_oracle(L):
+    # Alg. 1: dt (0.9 tol/err)^(1/2), capped at dt_max; dt_max when err is zero
+    from oracle import surfactant as sf
+    for dt, err, tol, dt_max in ((0.1, 4e-5, 1e-5, 1.0), (0.02, 1e-9, 1e-6, 0.05), (0.3, 2e-3, 1e-4, 1.0),
+                                 (0.1, 0.0, 1e-5, 0.2)):
+        assert api.next_dt(dt, err, tol, dt_max) == pytest.approx(sf.next_dt(dt, err, tol, dt_max), rel=1e-15)
