@@ -16,6 +16,7 @@ Modules, each following the passage of Sorgentone & Tornberg (arXiv 1707.02156) 
   surfactant  surface gradient, divergence and Laplacian; the transport terms of Eq. surfactant0;
             IMEX-2 and IMEX-1 steps with the preconditioned implicit solve; the coupled
             drop/surfactant step and the adaptive step size of Alg. 1 (Sec. 3)
+  reparam   angle reparametrisation with the adaptive cutoff (Sec. 4, Alg. 2)
   brute     adaptive polar quadrature used only to pin the singular rule
 
 Parity unpinned: the absolute accuracy of the near-singular (Omega_2) interpolation on

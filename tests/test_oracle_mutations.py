@@ -11,10 +11,11 @@ import textwrap
 
 import pytest
 
-from oracle import geometry, gmres, layer, near, sh, surfactant, timestep, wigner
+from oracle import geometry, gmres, layer, near, reparam, sh, surfactant, timestep, wigner
 
 import test_oracle_geometry as PG
 import test_oracle_layer as PL
+import test_oracle_reparam as PR
 import test_oracle_sh as PS
 import test_oracle_surfactant as PF
 import test_oracle_timestep as PT
@@ -209,6 +210,23 @@ CASES = [
     ("step_size_rule_without_square_root", surfactant, "next_dt",
      [("dt * math.sqrt(0.9 * tol / err)", "dt * (0.9 * tol / err)")],
      PF.test_adaptive_run_keeps_every_accepted_step_below_tolerance, ()),
+    # angle reparametrisation (Sec. 4, Alg. 2)
+    ("mode_norms_without_negative_orders", reparam, "mode_norms",
+     [("out[n, P - n: P] = a[n, 1: n + 1][::-1]", "out[n, P - n: P] = 0.0")],
+     PR.test_mode_norms_satisfy_parseval_on_the_unit_sphere, ()),
+    ("cutoff_with_the_largest_order_per_degree", reparam, "adaptive_cutoff",
+     [("per_n = np.sum(mode_norms(xcoef, P), axis=1)", "per_n = np.max(mode_norms(xcoef, P), axis=1)")],
+     PR.test_adaptive_cutoff_on_a_designed_spectrum, ()),
+    ("angle_velocity_cross_term_sign", reparam, "angle_velocity",
+     [("return (A22 * b1 - A12 * b2) / det, (-A12 * b1 + A11 * b2) / det",
+       "return (A22 * b1 + A12 * b2) / det, (A12 * b1 + A11 * b2) / det")],
+     PR.test_angle_velocity_moves_the_point_with_the_tangential_velocity, ()),
+    ("pseudo_velocity_up_the_gradient", reparam, "reparametrize",
+     [("al_t, al_p = angle_velocity(e, -gvec)", "al_t, al_p = angle_velocity(e, gvec)")],
+     PR.test_distorted_sphere_returns_to_its_one_mode_parametrisation, ()),
+    ("surfactant_at_the_grid_angles", reparam, "reparametrize",
+     [("gg = sh.evaluate(g0, P, th, ph)", "gg = sh.evaluate(g0, P, T, F)")],
+     PR.test_concentration_linear_in_the_position_is_carried_exactly, ()),
 ]
 
 
