@@ -17,8 +17,9 @@ Modules, each following the passage of Sorgentone & Tornberg (arXiv 1707.02156) 
             IMEX-2 and IMEX-1 steps with the preconditioned implicit solve; the coupled
             drop/surfactant step and the adaptive step size of Alg. 1 (Sec. 3)
   reparam   angle reparametrisation with the adaptive cutoff (Sec. 4, Alg. 2)
-  brute     adaptive polar quadrature used only to pin the singular rule
+  brute     adaptive polar quadrature used only as a reference: the singular self-integral and
+            integrals at points just off the surface
 
-Parity unpinned: the absolute accuracy of the near-singular (Omega_2) interpolation on
-deformed shapes has no closed form; it is reported against brute force, not pinned.
+The near-singular (Omega_2) interpolation on deformed shapes has no closed form; it is pinned by
+its convergence, as the degree grows, to the brute-force integral at points just off the surface.
 """

@@ -187,6 +187,56 @@ def test_newton_closest_point_is_the_nearest_surface_point():
         assert np.linalg.norm(off) <= np.min(np.linalg.norm(std_x - x0[:, None], axis=0))
 
 
+def test_brute_force_exterior_integral_reproduces_the_translating_sphere_field():
+    # the reference used below, checked first: a uniform traction c on a sphere of radius a gives
+    # the translating-sphere field at every exterior point, here 0.05 off the surface
+    p, a = 6, 0.9
+    x = inputs.sphere_coef(p, radius=a, centre=(0.1, -0.2, 0.3))
+    cvec = np.array([0.4, -1.0, 0.7])
+    c = np.zeros((3, (p + 1) ** 2))
+    c[:, 0] = cvec * math.sqrt(4 * math.pi)
+    for d in (np.array([1.0, 2.0, -0.5]), np.array([0.0, 0.0, 1.0])):
+        pt = np.array([0.1, -0.2, 0.3]) + (a + 0.05) * d / np.linalg.norm(d)
+        S = brute.exterior_integral(x, p, c, pt, "S") / (8 * math.pi)
+        exact = _translating_sphere(pt[:, None], (0.1, -0.2, 0.3), a, cvec)[:, 0]
+        assert np.max(np.abs(S - exact)) < 1e-11
+        D = brute.exterior_integral(x, p, c, pt, "D") / (4 * math.pi)
+        assert np.max(np.abs(D)) < 1e-11
+
+
+def test_near_singular_values_converge_to_brute_force_on_a_deformed_drop():
+    # Sec. 2.3 on a deformed drop (no closed form): targets 0.05 off the surface, in Omega_2 for
+    # every degree used.  Shape and density are band-limited at degree 4, so the exact integrals
+    # (brute force) are the same at every p while the rule's resolution h = R pi/(p+1) shrinks; the
+    # error of the interpolation must fall with p (about fifth order here).
+    from oracle import near
+    rng = np.random.default_rng(7)
+    xj = inputs.sphere_coef(4) + inputs.perturbation(rng, 4, 1, 4, 0.06)
+    dens = inputs.random_bandlimited(rng, 4, 3)
+    pts = []
+    for t0, f0 in ((1.0, 0.5), (2.0, 2.5), (0.6, 4.0)):
+        d = [sh.evaluate_derivs(xj[c], 4, np.array([t0]), np.array([f0])) for c in range(3)]
+        n = np.cross([d[c]["t"][0] for c in range(3)], [d[c]["p"][0] for c in range(3)])
+        pts.append(np.array([d[c]["f"][0] for c in range(3)]) + 0.05 * n / np.linalg.norm(n))
+    pts = np.array(pts).T
+    for kind in ("S", "D"):
+        ref = np.stack([brute.exterior_integral(xj, 4, dens, pts[:, i], kind) for i in range(pts.shape[1])], axis=1)
+        errs = []
+        for p in (8, 12, 16):
+            xp = np.zeros((3, (p + 1) ** 2))
+            xp[:, :25] = xj
+            dp = np.zeros((3, (p + 1) ** 2))
+            dp[:, :25] = dens
+            far = inputs.sphere_coef(p, radius=0.3, centre=(10.0, 0.0, 0.0))
+            drops = layer.Drops([far, xp], [p, p], [p, p], [1.0, 1.0], up=4)
+            drops.targets[0] = pts
+            assert np.all(drops.classify(pts, 1) == 2)
+            v = near.near_values(drops, 0, 1, list(range(pts.shape[1])), dp, kind, drops.selfq[1].apply(dp, kind))
+            errs.append(np.max(np.abs(v - ref)) / np.max(np.abs(ref)))
+        assert errs[2] < errs[1] < errs[0], (kind, errs)
+        assert errs[0] / errs[2] > 10 and errs[2] < 1e-3, (kind, errs)
+
+
 def test_gmres_matches_direct_solve():
     rng = np.random.default_rng(0)
     n = 60

@@ -159,6 +159,9 @@ CASES = [
     ("newton_step_uphill", near, "newton_closest",
      [("step = -np.linalg.solve(", "step = np.linalg.solve(")],
      PL.test_newton_closest_point_is_the_nearest_surface_point, ()),
+    ("closest_point_left_at_the_seed", near, "near_values",
+     [("th, ph, xs = newton_closest(xr, p, x0)", "th, ph, xs = newton_closest(xr, p, x0, max_it=0)")],
+     PL.test_near_singular_values_converge_to_brute_force_on_a_deformed_drop, ()),
     ("newton_hessian_without_curvature", near, "newton_closest",
      [('[[d["t"] @ d["t"] + r @ d["tt"],', '[[d["t"] @ d["t"] - r @ d["tt"],')],
      PL.test_newton_closest_point_is_the_nearest_surface_point, ()),
