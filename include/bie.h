@@ -225,7 +225,8 @@ int bie_solve(bie_ctx* ctx, const bie_geom* geom, const double* rhs, double* u, 
  * "self_direct_f64/f32" (rotation + synthesis + the singular pair sum of Thm 1), "kernel_proj"
  * (projected kernel factors, once per geometry and kind), "analyze" (Galerkin
  * projection), "interdrop" (regular and upsampled pair sums), "near" (near-singular step),
- * "source_synth" (source densities on the standard/upsampled grids), "gmres_vec". */
+ * "source_synth" (source densities on the standard/upsampled grids), "gmres_vec",
+ * "surfactant_rates" and "surfactant_implicit" (bie_surfactant_rates, bie_surfactant_implicit). */
 typedef struct bie_phase_stat {
   char name[24];
   double ms;
