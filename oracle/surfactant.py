@@ -37,7 +37,8 @@ Readings of the text:
     mass by the regular rule (Sec. 2.1) on the degree 2(p+1) - 1 grid.
   * The step size follows Alg. 1: err = max(err_drop, err_surfactant); the step is kept when
     err < tol; then dt <- min(dt_max, dt (0.9 tol/err)^(1/2)), with the last step cut to end at T.
-    Reparametrisation (Sec. 4) is not part of this step.
+    A kept step is followed, when asked for, by the angle reparametrisation of Sec. 4 (Alg. 2)
+    of every drop's shape and surfactant, as the adaptivity box of Alg. 1 does.
 """
 from __future__ import annotations
 
@@ -263,8 +264,11 @@ def next_dt(dt: float, err: float, tol: float, dt_max: float) -> float:
 
 
 def run_adaptive(xs, gs, ps, T: float, dt0: float, tol: float, velocity, pe: float, dt_max: float,
-                 estimator: str = "conservation", max_steps: int = 1000):
-    """Alg. 1 from t = 0 to T.  Returns the final shapes and concentrations and the step history."""
+                 estimator: str = "conservation", max_steps: int = 1000, reparam: dict | None = None):
+    """Alg. 1 from t = 0 to T.  Returns the final shapes and concentrations and the step history.
+
+    reparam: None, or the options of reparam.reparametrize (u_rep, p_cutoff, dtau, eps, i_max)
+    applied to every drop after each kept step."""
     t, dt = 0.0, min(dt0, dt_max)
     xs = [np.asarray(x, dtype=np.float64).reshape(3, -1) for x in xs]
     gs = [np.asarray(g, dtype=np.float64).reshape(-1) for g in gs]
@@ -286,5 +290,9 @@ def run_adaptive(xs, gs, ps, T: float, dt0: float, tol: float, velocity, pe: flo
         if accepted:
             t += h
             xs, gs, u0 = st["x"], st["gamma"], None
+            if reparam is not None:
+                from . import reparam as rp
+                out = [rp.reparametrize(x, g, p, **reparam)[:2] for x, g, p in zip(xs, gs, ps)]
+                xs, gs = [o[0] for o in out], [o[1] for o in out]
         dt = next_dt(h, err, tol, dt_max)
     return {"x": xs, "gamma": gs, "t": t, "history": hist, "velocity_calls": calls}

@@ -122,3 +122,42 @@ def test_volume_error_decays_spectrally_with_the_upsampling_factor():
         errs.append(abs(geometry.volume(xo, p, 2 * p + 1) - v0) / v0)
     assert errs[2] < errs[1] < errs[0]
     assert errs[2] < 1e-3 * errs[0]
+
+
+def _differential_rotation(xs, gs):
+    # u = omega(z) (z^ x x) with omega = 1 + 2 z: every latitude circle of a sphere about the origin
+    # turns at its own rate (tangential and surface-divergence-free), so the surface and Gamma as a
+    # field on it stay as they are while the grid twists
+    out = []
+    for x in xs:
+        p = int(round(math.sqrt(x.shape[1]))) - 1
+        P = 2 * p + 1
+        X = np.stack([sh.synthesize(x[c], p, P) for c in range(3)])
+        om = 1.0 + 2.0 * X[2]
+        U = np.stack([-om * X[1], om * X[0], np.zeros_like(X[0])])
+        out.append(np.stack([sh.analyze(U[c], P, p) for c in range(3)]))
+    return out
+
+
+def test_reparametrisation_after_each_kept_step_removes_the_grid_twist_only():
+    # Alg. 1 with Alg. 2 after every kept step: the grid energy stays low while the surface and the
+    # surfactant field are those of the run without reparametrisation (mass, volume, int Gamma^2 dS)
+    from oracle import surfactant as sf
+    p = 8
+    x = _twisted(p, 0.0)
+    rng = np.random.default_rng(3)
+    g = 0.2 * rp.upsample(rng.standard_normal((1, 16)), 3, p)[0]
+    g[0] += math.sqrt(4 * math.pi)
+    runs = {}
+    for name, rep_opts in (("plain", None), ("reparam", {"u_rep": 2, "p_cutoff": 0.3, "dtau": 0.5, "i_max": 6})):
+        res = sf.run_adaptive([x], [g], [p], 0.3, 0.1, 1e-3, _differential_rotation, math.inf, 0.1,
+                              reparam=rep_opts)
+        xo, go = res["x"][0], res["gamma"][0]
+        S = sf.Surface(xo, p, sf.grid_degree(p))
+        G = sf.scalar_fields(go, p, S.P)["f"]
+        runs[name] = {"mass": S.integral(G), "second": S.integral(G * G), "volume": geometry.volume(xo, p, 2 * p + 1),
+                      "high": float(np.sum(rp.mode_norms(xo, p)[2:] ** 2))}
+    a, b = runs["plain"], runs["reparam"]
+    assert a["high"] > 0.1 and b["high"] < 1e-6 * a["high"]
+    for k in ("mass", "second", "volume"):
+        assert abs(a[k] - b[k]) < 1e-7 * abs(a[k]), (k, a[k], b[k])
