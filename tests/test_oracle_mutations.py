@@ -235,8 +235,8 @@ CASES = [
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_planted_mistake_fails_its_pin(monkeypatch, case):
+    # each pin also runs on the oracle as it stands, as a test of its own module
     _, module, name, edits, pin, args = case
-    pin(*args)  # the pin holds on the oracle as it stands
     plant(monkeypatch, module, name, edits)
     with pytest.raises(AssertionError):
         pin(*args)
