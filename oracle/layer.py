@@ -28,8 +28,6 @@ Readings of the text:
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 from . import geometry, sh, wigner

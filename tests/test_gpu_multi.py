@@ -1,7 +1,6 @@
 """GPU parity of the multi-drop layer operators (Sec. 2.1, 2.3) against the FP64 oracle: drops of
 uneven degree and viscosity ratio at gaps where both the regular (Omega_0) and the upsampled (Omega_1)
 rules occur; exact region counts; and the solve."""
-import math
 
 import numpy as np
 import pytest

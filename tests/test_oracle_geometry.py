@@ -3,7 +3,7 @@ import math
 
 import numpy as np
 
-from oracle import geometry, layer, sh, wigner
+from oracle import geometry, layer, sh
 from paper_1707_02156_gb300 import inputs
 
 

@@ -1,6 +1,5 @@
 """Pins of the oracle's Wigner rotation (App. B): the printed factorial sum, unitarity, and the
 defining property g(s) = f(R s) checked by direct evaluation at rotated points."""
-import math
 
 import numpy as np
 import pytest
