@@ -51,3 +51,24 @@ def test_two_gloo_ranks(tmp_path):
         assert res["t_max"] == 2.0                   # the slowest rank's time on every rank
         assert res["rate"] == pytest.approx(100.0)   # 2 ranks x 100 units / 2 s
         assert res["ref_out"] == ""
+
+
+def test_apply_summary_and_guard():
+    # per-precision summary against the FP64 apply (2-norm and infinity-norm relative errors), and
+    # an auxiliary measurement that raises is recorded, not propagated
+    sys.path.insert(0, ROOT)
+    import bench
+    ref = torch.tensor([1.0, -2.0, 4.0], dtype=torch.float64)
+    out = ref + torch.tensor([0.0, 1e-6, -2e-6], dtype=torch.float64)
+    s = bench.apply_summary({0: {"out": ref, "ms": 3.0, "phases": {}},
+                             1: {"out": out, "ms": 1.5, "phases": {"k": (1.0, 2)}}})
+    assert s["mixed"]["speedup_vs_fp64"] == pytest.approx(2.0)
+    assert s["mixed"]["rel_err_inf_vs_fp64"] == pytest.approx(2e-6 / 4.0)
+    assert s["mixed"]["rel_err_vs_fp64"] == pytest.approx((1e-12 + 4e-12) ** 0.5 / 21 ** 0.5)
+    assert s["mixed"]["phases_ms"]["k"] == {"ms": 1.0, "calls": 2}
+
+    def boom():
+        raise RuntimeError("no device")
+
+    assert bench.guarded(boom) == {"error": "RuntimeError: no device"}
+    assert bench.guarded(lambda a: a + 1, 2) == 3
