@@ -295,4 +295,4 @@ def run_adaptive(xs, gs, ps, T: float, dt0: float, tol: float, velocity, pe: flo
                 out = [rp.reparametrize(x, g, p, **reparam)[:2] for x, g, p in zip(xs, gs, ps)]
                 xs, gs = [o[0] for o in out], [o[1] for o in out]
         dt = next_dt(h, err, tol, dt_max)
-    return {"x": xs, "gamma": gs, "t": t, "history": hist, "velocity_calls": calls}
+    return {"x": xs, "gamma": gs, "t": t, "dt_next": dt, "history": hist, "velocity_calls": calls}
