@@ -204,6 +204,38 @@ def test_brute_force_exterior_integral_reproduces_the_translating_sphere_field()
         assert np.max(np.abs(D)) < 1e-11
 
 
+def test_regular_and_upsampled_rules_converge_to_brute_force_on_a_deformed_drop():
+    # Sec. 2.1 / 2.3 away from the surface, on a deformed drop: targets 0.35, 0.6 and 1.5 off the
+    # surface fall in Omega_1 (upsampled rule) or Omega_0 (regular rule); both converge spectrally
+    # in p to the brute-force integral (shape and density band-limited at degree 4)
+    rng = np.random.default_rng(7)
+    xj = inputs.sphere_coef(4) + inputs.perturbation(rng, 4, 1, 4, 0.06)
+    dens = inputs.random_bandlimited(rng, 4, 3)
+    pts = []
+    for t0, f0, dist in ((1.0, 0.5, 0.6), (2.0, 2.5, 0.35), (0.6, 4.0, 1.5)):
+        d = [sh.evaluate_derivs(xj[c], 4, np.array([t0]), np.array([f0])) for c in range(3)]
+        n = np.cross([d[c]["t"][0] for c in range(3)], [d[c]["p"][0] for c in range(3)])
+        pts.append(np.array([d[c]["f"][0] for c in range(3)]) + dist * n / np.linalg.norm(n))
+    pts = np.array(pts).T
+    for kind in ("S", "D"):
+        ref = np.stack([brute.exterior_integral(xj, 4, dens, pts[:, i], kind) for i in range(3)], axis=1)
+        errs = []
+        for p in (8, 16):
+            xp = np.zeros((3, (p + 1) ** 2))
+            xp[:, :25] = xj
+            dp = np.zeros((3, (p + 1) ** 2))
+            dp[:, :25] = dens
+            drops = layer.Drops([inputs.sphere_coef(p, radius=0.3, centre=(10.0, 0.0, 0.0)), xp], [p, p], [p, p],
+                                [1.0, 1.0], up=4)
+            reg = drops.classify(pts, 1)
+            assert np.all(reg < 2)
+            v = np.stack([layer.regular_sum(pts[:, i:i + 1], *((drops.std[1], drops.std[1].density(dp)) if reg[i] == 0
+                                                              else (drops.ups[1], drops.ups[1].density(dp))), kind)[:, 0]
+                          for i in range(3)], axis=1)
+            errs.append(np.max(np.abs(v - ref)) / np.max(np.abs(ref)))
+        assert errs[1] < 1e-12 and errs[1] < 1e-2 * errs[0], (kind, errs)
+
+
 def test_near_singular_values_converge_to_brute_force_on_a_deformed_drop():
     # Sec. 2.3 on a deformed drop (no closed form): targets 0.05 off the surface, in Omega_2 for
     # every degree used.  Shape and density are band-limited at degree 4, so the exact integrals
