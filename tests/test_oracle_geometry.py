@@ -79,3 +79,28 @@ def test_rotated_geometry_matches_direct_evaluation_at_rotated_points():
         assert np.max(np.abs(nr[b] - cr / W)) < 1e-12
         J = W / np.sin(th)
         assert np.max(np.abs(wJ[b] - ws[:, None] * J)) < 1e-12 * np.max(np.abs(wJ[b]))
+
+
+def test_interfacial_force_carries_no_net_force_or_torque():
+    # f = sigma (div n) n - grad_gamma sigma is the surface divergence of the symmetric surface stress
+    # sigma (I - n n): on any closed surface, for any tension field, int f dS = 0 and
+    # int x x f dS = 0.  A deformed, rotated drop with a non-uniform surfactant and the Langmuir
+    # equation of state; the projected force converges to zero net force and torque as p grows.
+    res = []
+    for p in (8, 16):
+        x = inputs.sphere_coef(p, axes=(0.8, 1.0, 1.2), rot=inputs.random_rotation(np.random.default_rng(1)))
+        x[:, :25] += inputs.perturbation(np.random.default_rng(2), 4, 1, 4, 0.05)
+        g = np.zeros((p + 1) ** 2)
+        g[:16] = 0.2 * inputs.random_bandlimited(np.random.default_rng(3), 3, 1)[0]
+        g[0] += math.sqrt(4 * math.pi)
+        f = geometry.interfacial_force(x, p, g, 0.3, 0.3)
+        P = 4 * (p + 1) - 1
+        _, w, theta, _ = sh.gauss_grid(P)
+        F = np.stack([sh.synthesize(f[c], p, P) for c in range(3)])
+        G = geometry.forms(geometry.surface_fields(x, p, P))
+        wq = (np.pi / (P + 1)) * w[:, None] * geometry.area_density(G["W"], theta)
+        scale = np.sum(np.linalg.norm(F, axis=0) * wq)
+        force = np.max(np.abs(np.sum(F * wq, axis=(1, 2)))) / scale
+        torque = np.max(np.abs(np.sum(np.cross(G["x"], F, axis=0) * wq, axis=(1, 2)))) / scale
+        res.append(max(force, torque))
+    assert res[1] < 1e-11 and res[1] < 1e-4 * res[0], res

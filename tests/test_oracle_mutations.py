@@ -97,6 +97,10 @@ CASES = [
      [('grad = ((G * sp - F * st) * g["xp"] + (E * st - F * sp) * g["xt"])',
        'grad = ((E * sp - F * st) * g["xp"] + (G * st - F * sp) * g["xt"])')],
      PG.test_marangoni_term_points_down_the_tension_gradient_sign_reading, ()),
+    ("surface_gradient_cross_metric_sign", geometry, "interfacial_force",
+     [('grad = ((G * sp - F * st) * g["xp"] + (E * st - F * sp) * g["xt"])',
+       'grad = ((G * sp + F * st) * g["xp"] + (E * st - F * sp) * g["xt"])')],
+     PG.test_interfacial_force_carries_no_net_force_or_torque, ()),
     ("equation_of_state_sign", geometry, "sigma_of_gamma",
      [("return 1.0 - elasticity * gamma", "return 1.0 + elasticity * gamma")],
      PG.test_clean_sphere_force_is_outward_two_sigma_over_r, ()),
