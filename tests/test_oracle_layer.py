@@ -107,6 +107,28 @@ def _translating_sphere(xt, centre, a, cvec):
     return 0.5 * a * a * (G + a * a / 3.0 * dip)
 
 
+def test_single_layer_is_self_adjoint_on_a_deformed_drop():
+    # int g . S[f] dS = int f . S[g] dS (the Stokeslet is symmetric): on a deformed drop (shape and
+    # densities band-limited at degree 4) the singular rule plus the regular outer rule converge to
+    # that symmetry spectrally as the grid degree grows
+    rng = np.random.default_rng(31)
+    x0 = inputs.sphere_coef(4) + inputs.perturbation(rng, 4, 1, 4, 0.1)
+    f0, g0 = inputs.random_bandlimited(rng, 4, 3), inputs.random_bandlimited(rng, 4, 3)
+    asym = []
+    for p in (8, 16):
+        x, f, g = (np.pad(c, ((0, 0), (0, (p + 1) ** 2 - 25))) for c in (x0, f0, g0))
+        G = geometry.forms(geometry.surface_fields(x, p, p))
+        _, w, theta, _ = sh.gauss_grid(p)
+        wq = (np.pi / (p + 1)) * w[:, None] * geometry.area_density(G["W"], theta)
+        fg = np.stack([sh.synthesize(f[c], p, p) for c in range(3)])
+        gg = np.stack([sh.synthesize(g[c], p, p) for c in range(3)])
+        q = layer.SelfQuadrature(x, p, 2 * (p + 1) - 1)
+        a = np.sum(np.sum(gg * q.apply(f, "S"), axis=0) * wq)
+        b = np.sum(np.sum(fg * q.apply(g, "S"), axis=0) * wq)
+        asym.append(abs(a - b) / abs(a))
+    assert asym[1] < 1e-11 and asym[1] < 1e-3 * asym[0], asym
+
+
 def test_regular_rule_reproduces_translating_sphere_field_far_away():
     p, a = 10, 0.9
     x = inputs.sphere_coef(p, radius=a, centre=(0.0, 0.0, 0.0))
