@@ -22,36 +22,50 @@ STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIME
 
 
 class bie_config(ctypes.Structure):
+    """bie_config of bie.h: device, upsampling factor, A~, L, self-rule form, graph replay."""
+
     _fields_ = [("device", c_int), ("upsample", c_int), ("a_tilde", c_double), ("n_interp", c_int),
                 ("self_direct", c_int), ("use_graphs", c_int)]
 
 
 class bie_geom_info(ctypes.Structure):
+    """bie_geom_info of bie.h: sizes and pair counts of a geometry."""
+
     _fields_ = [("ndrop", c_int), ("ncoef", c_ll), ("ntarget", c_ll), ("self_pairs", c_ll), ("far_pairs", c_ll),
                 ("up_pairs", c_ll), ("near_targets", c_ll), ("near_pairs", c_ll), ("cache_bytes", c_double),
                 ("interdrop_tpt", c_int)]
 
 
 class bie_solve_opts(ctypes.Structure):
+    """bie_solve_opts of bie.h: solve precision, tolerances, restart and refinement limits."""
+
     _fields_ = [("precision", c_int), ("tol", c_double), ("restart", c_int), ("max_iter", c_int),
                 ("inner_tol", c_double), ("max_refine", c_int), ("residual_precision", c_int)]
 
 
 class bie_solve_info(ctypes.Structure):
+    """bie_solve_info of bie.h: iterations, refinements, applies per precision, residual."""
+
     _fields_ = [("iterations", c_int), ("refinements", c_int), ("applies_fp64", c_int), ("applies_mixed", c_int),
                 ("residual", c_double), ("converged", c_int)]
 
 
 class bie_phase_stat(ctypes.Structure):
+    """bie_phase_stat of bie.h: one profiled phase."""
+
     _fields_ = [("name", ctypes.c_char * 24), ("ms", c_double), ("calls", c_ll)]
 
 
 class bie_coupled_info(ctypes.Structure):
+    """bie_coupled_info of bie.h: error estimates and solves of one coupled step."""
+
     _fields_ = [("err_drop", c_double), ("err_conservation", c_double), ("err_imex1", c_double),
                 ("velocity_solves", c_int), ("implicit_iterations", c_int), ("solve", bie_solve_info * 2)]
 
 
 class bie_run_info(ctypes.Structure):
+    """bie_run_info of bie.h: outcome of an adaptive coupled run."""
+
     _fields_ = [("t", c_double), ("dt_next", c_double), ("err_max_accepted", c_double), ("steps_accepted", c_int),
                 ("steps_rejected", c_int), ("velocity_solves", c_int)]
 
@@ -120,6 +134,8 @@ def lib(build_if_missing: bool = False) -> ctypes.CDLL:
 
 
 class BIEError(RuntimeError):
+    """A status other than BIE_OK from the library, with its message."""
+
     def __init__(self, status: int, what: str):
         self.status = status
         super().__init__(f"{what}: {STATUS.get(status, status)}: {lib().bie_last_error().decode()}")
@@ -151,10 +167,12 @@ def _doubles(v):
 
 
 def ncoef(p: int) -> int:
+    """Real-packed coefficients of one scalar of degree p."""
     return (p + 1) * (p + 1)
 
 
 def ngrid(p: int) -> int:
+    """Points of the degree-p grid: (p+1) latitudes times 2p+2 longitudes."""
     return (p + 1) * (2 * p + 2)
 
 
@@ -175,6 +193,7 @@ class Context:
         self.device = device
 
     def close(self):
+        """Release the context (idempotent)."""
         if getattr(self, "h", None):
             lib().bie_destroy(self.h)
             self.h = None
@@ -186,16 +205,19 @@ class Context:
             pass
 
     def sh_analyze(self, p, ncomp: int, grid: torch.Tensor, coef: torch.Tensor):
+        """Grid values [drop][comp][j][k] -> real-packed coefficients [drop][comp][(p+1)^2]."""
         _check(lib().bie_sh_analyze(self.h, len(p), _ints(p), ncomp, _ptr(grid), _ptr(coef), _stream()),
                "bie_sh_analyze")
         return coef
 
     def sh_synthesize(self, p, p_out, ncomp: int, coef: torch.Tensor, grid: torch.Tensor):
+        """Coefficients of degree p -> values on the grid of degree p_out >= p (zero padding)."""
         _check(lib().bie_sh_synthesize(self.h, len(p), _ints(p), _ints(p_out), ncomp, _ptr(coef), _ptr(grid),
                                        _stream()), "bie_sh_synthesize")
         return grid
 
     def rotate(self, p, ncomp: int, coef: torch.Tensor, euler, out: torch.Tensor):
+        """Coefficients of f(R s), R = R_z(alpha) R_y(beta) R_z(gamma), per drop (euler [drop][3])."""
         flat = [float(a) for e in euler for a in e]
         _check(lib().bie_rotate(self.h, len(p), _ints(p), ncomp, _ptr(coef), _doubles(flat), _ptr(out), _stream()),
                "bie_rotate")
@@ -220,6 +242,7 @@ class Context:
         return out
 
     def geometry(self, p, pq, xcoef: torch.Tensor, lam) -> "Geometry":
+        """Set up the shape-dependent data of the drops (see Geometry)."""
         return Geometry(self, p, pq, xcoef, lam)
 
 
@@ -238,6 +261,7 @@ class Geometry:
         self.info = {k: getattr(info, k) for k, _ in bie_geom_info._fields_}
 
     def close(self):
+        """Release the geometry (idempotent)."""
         if getattr(self, "h", None):
             lib().bie_geometry_destroy(self.h)
             self.h = None
@@ -250,17 +274,22 @@ class Geometry:
 
     def apply_single(self, f: torch.Tensor, out: torch.Tensor, precision: int = BIE_FP64, raw: bool = False,
                      grid_out: bool = False):
+        """out = -(1/4pi) sum_j int f.G (raw: (1/8pi) int G.f) projected on the SH basis, or at the grid
+        targets with grid_out."""
         flag = precision | (BIE_RAW if raw else 0) | (BIE_GRID_OUT if grid_out else 0)
         _check(lib().bie_apply_single(self.ctx.h, self.h, _ptr(f), _ptr(out), flag, _stream()), "bie_apply_single")
         return out
 
     def apply_double(self, u: torch.Tensor, out: torch.Tensor, precision: int = BIE_FP64, raw: bool = False,
                      grid_out: bool = False):
+        """out = (1/4pi) sum_j (lambda_j - 1) PV int u.T.n (raw: (1/4pi) PV int u.T.n) projected on the
+        SH basis, or at the grid targets with grid_out."""
         flag = precision | (BIE_RAW if raw else 0) | (BIE_GRID_OUT if grid_out else 0)
         _check(lib().bie_apply_double(self.ctx.h, self.h, _ptr(u), _ptr(out), flag, _stream()), "bie_apply_double")
         return out
 
     def interfacial_force(self, gamma: torch.Tensor, elasticity: float, x_s: float, out: torch.Tensor):
+        """out = f = sigma (div n) n - grad sigma of the surfactant gamma (Langmuir, or linear for x_s = 0)."""
         _check(lib().bie_interfacial_force(self.ctx.h, self.h, _ptr(gamma), elasticity, x_s, _ptr(out), _stream()),
                "bie_interfacial_force")
         return out
@@ -274,10 +303,8 @@ class Geometry:
     def solve(self, rhs: torch.Tensor, u: torch.Tensor, precision: int = BIE_FP64, tol: float = 1e-10,
               restart: int = 30, max_iter: int = 300, inner_tol: float = 1e-5, max_refine: int = 10,
               residual_precision: int = BIE_DF, raise_on_noconv: bool = True) -> dict:
-        o = bie_solve_opts()
-        lib().bie_solve_opts_default(ctypes.byref(o))
-        o.precision, o.tol, o.restart, o.max_iter, o.inner_tol, o.max_refine, o.residual_precision = (
-            precision, tol, restart, max_iter, inner_tol, max_refine, residual_precision)
+        """Solve (lambda + 1) u - D[u] = rhs; u holds the initial guess and receives the solution."""
+        o = _solve_opts(precision, tol, restart, max_iter, inner_tol, max_refine, residual_precision)
         info = bie_solve_info()
         st = lib().bie_solve(self.ctx.h, self.h, _ptr(rhs), _ptr(u), ctypes.byref(o), ctypes.byref(info), _stream())
         res = {k: getattr(info, k) for k, _ in bie_solve_info._fields_}
@@ -296,10 +323,7 @@ def midpoint_step(ctx: "Context", p, pq, x: torch.Tensor, gamma: torch.Tensor, e
     P = (ctypes.c_int * n)(*[int(v) for v in p])
     PQ = (ctypes.c_int * n)(*[int(v) for v in pq])
     L = (ctypes.c_double * n)(*[float(v) for v in lam])
-    o = bie_solve_opts()
-    lib().bie_solve_opts_default(ctypes.byref(o))
-    o.precision, o.tol, o.restart, o.max_iter, o.inner_tol, o.max_refine, o.residual_precision = (
-        precision, tol, restart, max_iter, inner_tol, max_refine, residual_precision)
+    o = _solve_opts(precision, tol, restart, max_iter, inner_tol, max_refine, residual_precision)
     info = (bie_solve_info * 2)()
     _check(lib().bie_step_midpoint(ctx.h, n, P, PQ, _ptr(x), _ptr(gamma), elasticity, x_s, L, shear, dt,
                                    ctypes.byref(o), info, _stream()), "bie_step_midpoint")
