@@ -109,20 +109,21 @@ int bie_rotate(bie_ctx* ctx, int ndrop, const int* p, int ncomp, const double* c
                double* coef_out, void* stream);
 
 /* Allocation-free variant of bie_rotate.  The paper has no counterpart: this is an interface of
- * the library for callers that cannot allocate device memory -- code issuing work while a stream
- * is being captured into a CUDA graph (cudaMalloc/cudaFree are not capturable), frameworks that
- * own all device memory through their own pool and forbid other allocations, and loops that must
- * not touch the allocator or its implicit synchronisation.  bie_rotate allocates and frees small
- * per-call tables; bie_rotate_noalloc stages the same tables in one fixed array of
+ * the library for callers that cannot allocate device memory -- frameworks that own all of the
+ * device's memory through their own pool or arena and forbid any other allocation, and loops that
+ * must not touch the allocator or wait on its implicit synchronisation.  bie_rotate allocates and
+ * frees small per-call tables; bie_rotate_noalloc stages the same tables in one fixed array of
  * BIE_NOALLOC_SCRATCH_DOUBLES doubles (1.4 MiB) compiled into the library, which every GPU that
  * loads the library holds until the process exits.  It calls no cudaMalloc, cudaFree or other
- * allocating routine.
+ * allocating routine, on the device or on the host: the tables are built on the host in a fixed
+ * buffer of the same size and copied into the array with cudaMemcpyAsync on `stream`.
  *   Arguments, layout and result: as bie_rotate; degrees 1 <= p <= BIE_NOALLOC_MAX_P.  A request
  *   whose tables (the Wigner blocks of degree p, 2(p+1) phases and ncomp offsets) do not fit the
  *   array is rejected with BIE_EINVAL and a message in bie_last_error(), before any GPU work.
  *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call before any stream
- *   capture begins.
+ *   (cudaGetSymbolAddress) with that device current.
+ *   Device: the call makes the context's device current while it works and restores the caller's
+ *   current device before it returns, on every path.
  *   Sharing: every call uses the same array and leaves the last drop's tables in it.  Each call
  *   writes every entry it reads before reading it, so nothing needs to start at zero.  Calls whose
  *   GPU work overlaps -- on different streams, or from several host threads -- race on the array:
@@ -209,7 +210,7 @@ typedef struct bie_solve_info {
 
 void bie_solve_opts_default(bie_solve_opts* opts);
 
-/* Solve Eq. main_eq in coefficient space: (lambda_i + 1) u_i - D[u]_i = b_i, Sec. 7 (GMRES).
+/* Solve Eq. main_eq in coefficient space: (lambda_i + 1) u_i - D[u]_i = b_i, Sec. 6 (GMRES).
  * rhs: [drop][3][(p+1)^2] device right-hand side b (form it as 2 u_inf + S[f] with
  * bie_apply_single); u: device initial guess in, solution out.  Synchronous (the Krylov loop reads
  * back one scalar block per iteration).  BIE_ENOCONV if tol was not reached (best iterate kept). */

@@ -11,7 +11,7 @@ Modules, each following the passage of Sorgentone & Tornberg (arXiv 1707.02156) 
   geometry  fundamental forms, normal, curvature, interfacial force (Table 2, Sec. 1)
   layer     singular self quadrature (Thm 1, Sec. 2.2), regular and upsampled pair sums and the
             region split (Sec. 2.3), near-singular interpolation (Sec. 2.3), Galerkin projection (Sec. 1.2)
-  gmres     restarted GMRES with modified Gram-Schmidt (Sec. 7)
+  gmres     restarted GMRES with modified Gram-Schmidt (Sec. 6)
   timestep  midpoint step of the drop shapes with the surfactant held fixed (Sec. 3, Alg. 1)
   surfactant  surface gradient, divergence and Laplacian; the transport terms of Eq. surfactant0;
             IMEX-2 and IMEX-1 steps with the preconditioned implicit solve; the coupled

@@ -1,6 +1,6 @@
 """Restarted GMRES with modified Gram-Schmidt (oracle; test infrastructure only).
 
-Sec. 7: the second-kind system of Eq. main_eq is solved iteratively with GMRES.  Textbook
+Sec. 6: the second-kind system of Eq. main_eq is solved iteratively with GMRES.  Textbook
 algorithm (Saad & Schultz): Arnoldi with modified Gram-Schmidt, Givens rotations on the
 Hessenberg matrix, restart after m steps, stop on the relative residual ||b - A x|| / ||b||.
 """

@@ -19,9 +19,9 @@ Readings of the text:
   * The surface points move with the full velocity (dx/dt = u, Sec. 3), so Gamma is followed at
     fixed parameters.  Next to the term div(Gamma u_tan) of Eq. surfactant0 this adds
     +u_tan . grad Gamma, the rate at which tangentially moving points sample Gamma.  With it a
-    rotating drop keeps any Gamma fixed (the convection test of Sec. 6), and the surfactant mass
+    rotating drop keeps any Gamma fixed (the convection test of Sec. 5), and the surfactant mass
     is conserved.
-  * Stretching term.  Its printed sign clashes with the expanding-sphere test of Sec. 6
+  * Stretching term.  Its printed sign clashes with the expanding-sphere test of Sec. 5
     (Gamma R^2 = Gamma(0), stretching term (div n)(u.n) = (2/R) dR/dt).  With the outward normal
     and K = -1/R on a sphere (the reading taken for the force) the term is -2 K Gamma (u.n) on the
     left-hand side.  Altogether

@@ -1,5 +1,5 @@
 // C ABI entry points: context and plan caches, transforms, geometry set-up, the layer-operator
-// applies (Eq. main_eq) and the GMRES solve (Sec. 7).
+// applies (Eq. main_eq) and the GMRES solve (Sec. 6).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1647,7 +1647,7 @@ static int arnoldi_step_graph(bie_ctx* ctx, const bie_geom* gc, Krylov& K, int p
   return BIE_OK;
 }
 
-// Restarted GMRES (Sec. 7) with classical Gram-Schmidt and one re-orthogonalisation, FP64 Krylov
+// Restarted GMRES (Sec. 6) with classical Gram-Schmidt and one re-orthogonalisation, FP64 Krylov
 // basis; the operator is applied at precision prec.  x holds the initial guess (zero if x_is_zero).
 // Each Arnoldi step runs as the operator apply and three fused kernels that end on the device
 // (k_kry_sub_tail); the host reads the residual estimate of step k - 1 after it has queued step k,

@@ -2,18 +2,17 @@
 //
 // bie_rotate stages each drop's rotation tables (the real Wigner blocks, the e^{i m alpha}
 // phases and the per-component offsets) in device buffers it allocates and frees on every
-// call.  Some callers cannot allow that: code running while a CUDA stream is being captured
-// into a graph (cudaMalloc/cudaFree are not capturable), code that owns the device's memory
-// through its own pool or arena and forbids foreign allocations, and latency-critical loops
-// that must not hit the allocator or its implicit synchronisation.  bie_rotate_noalloc does
-// the same rotation with those tables staged in one fixed array that lives in the library's
-// device image (below), so it never allocates or frees device memory.
+// call.  Some callers cannot allow that: code that owns the device's memory through its own
+// pool or arena and forbids foreign allocations, and latency-critical loops that must not hit
+// the allocator or its implicit synchronisation.  bie_rotate_noalloc does the same rotation
+// with those tables staged in one fixed array that lives in the library's device image
+// (below), so it never allocates or frees device memory; the host side builds the tables in a
+// fixed host buffer, so it does not allocate host memory either.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
 #include <mutex>
-#include <vector>
 
 #include "internal.cuh"
 #include "tables.h"
@@ -31,13 +30,31 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_dev_ptr[kMaxDevices] = {nullptr};
 
+// Host staging buffer of the same size, guarded by g_mu for the whole call: cudaMemcpyAsync from
+// pageable host memory has copied the source out before it returns, so the next drop may
+// overwrite it.
+static double g_host_stage[kScratchDoubles];
+
+// Makes `device` current for the guard's lifetime and restores the caller's current device.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int device) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != device) err = cudaSetDevice(device);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 // Device address of the staging array on the current device (looked up once per device).
 int scratch_address(int device, double** out) {
   if (device < 0 || device >= kMaxDevices) {
     set_error("bie_rotate_noalloc: device ordinal out of range");
     return BIE_EINVAL;
   }
-  std::lock_guard<std::mutex> lk(g_mu);
   if (!g_dev_ptr[device]) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -77,18 +94,24 @@ extern "C" int bie_rotate_noalloc(bie_ctx* ctx, int ndrop, const int* p, int nco
     }
   }
   const int device = ctx_device(ctx);
-  BIE_CUDA_TRY(cudaSetDevice(device));
+  DeviceGuard guard(device);
+  if (guard.err != cudaSuccess) {
+    set_error(std::string("bie_rotate_noalloc: selecting the device: ") + cudaGetErrorString(guard.err));
+    return BIE_ECUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
   double* scratch = nullptr;
   BIE_TRY(scratch_address(device, &scratch));
   cudaStream_t s = (cudaStream_t)stream;
   long long co = 0;
-  std::vector<double> host;
+  double* host = g_host_stage;
   for (int d = 0; d < ndrop; ++d) {
     const int pd = p[d];
     const long long stride = wigner_block_stride(pd);
-    host.assign(stride + 2 * (pd + 1) + ncomp, 0.0);
-    wigner_blocks(pd, euler[3 * d + 1], host.data());
-    double* ph = host.data() + stride;
+    const long long len = stride + 2 * (pd + 1) + ncomp;
+    std::memset(host, 0, len * sizeof(double));
+    wigner_blocks(pd, euler[3 * d + 1], host);
+    double* ph = host + stride;
     for (int m = 0; m <= pd; ++m) {
       ph[2 * m] = std::cos(m * euler[3 * d]);
       ph[2 * m + 1] = std::sin(m * euler[3 * d]);
@@ -96,7 +119,7 @@ extern "C" int bie_rotate_noalloc(bie_ctx* ctx, int ndrop, const int* p, int nco
     long long* foff = reinterpret_cast<long long*>(ph + 2 * (pd + 1));
     for (int c = 0; c < ncomp; ++c) foff[c] = co + c * (long long)(pd + 1) * (pd + 1);
     // the copy is stream-ordered after the previous drop's kernel, which read the same array
-    BIE_CUDA_TRY(cudaMemcpyAsync(scratch, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    BIE_CUDA_TRY(cudaMemcpyAsync(scratch, host, len * sizeof(double), cudaMemcpyHostToDevice, s));
     const double* dblk = scratch;
     const double* dph = scratch + stride;
     const long long* dfo = reinterpret_cast<const long long*>(scratch + stride + 2 * (pd + 1));

@@ -36,6 +36,16 @@ def test_round_trip_is_exact(tmp_path):
     assert s["params"] == {"shear": 1.0, "elasticity": 0.2, "inv_pe": 0.1}
     with pytest.raises(ValueError):
         checkpoint.save(f, p=p, pq=p, lam=[1, 1], x=x[:-1], gamma=g, t=0.0, dt_next=0.1)
+    # per-drop arrays of the wrong length, and self-rule degrees outside p <= p_q <= 2p+1
+    for bad in ({"pq": [7], "lam": [1, 1]}, {"pq": [7, 11], "lam": [1.0]}, {"pq": [2, 11], "lam": [1, 1]},
+                {"pq": [8, 11], "lam": [1, 1]}):
+        with pytest.raises(ValueError):
+            checkpoint.save(f, p=p, x=x, gamma=g, t=0.0, dt_next=0.1, **bad)
+    # an archive written by other means is checked on load too
+    np.savez(f, p=np.array(p), pq=np.array([7]), lam=np.array([0.5, 2.0]), x=x, gamma=g, t=0.0, dt_next=0.1,
+             params=np.array("{}"))
+    with pytest.raises(ValueError):
+        checkpoint.load(f)
 
 
 def test_resumed_run_reproduces_the_uninterrupted_run(tmp_path):

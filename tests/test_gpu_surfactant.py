@@ -73,7 +73,7 @@ def test_rates_match_oracle(ctx):
 
 
 def test_rigid_rotation_rate_vanishes_on_the_gpu(ctx):
-    # the rotating-drop test of Sec. 6 on the device path: f_E = 0 for u = Omega x x + V
+    # the rotating-drop test of Sec. 5 on the device path: f_E = 0 for u = Omega x x + V
     from paper_1707_02156_gb300 import api
     ps, xs, _, gs, _ = _three_drops(2)
     Om, V = np.array([0.4, -0.1, 0.8]), np.array([0.2, 0.0, -0.5])

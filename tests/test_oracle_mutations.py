@@ -169,7 +169,7 @@ CASES = [
     ("newton_hessian_without_curvature", near, "newton_closest",
      [('[[d["t"] @ d["t"] + r @ d["tt"],', '[[d["t"] @ d["t"] - r @ d["tt"],')],
      PL.test_newton_closest_point_is_the_nearest_surface_point, ()),
-    # GMRES (Sec. 7) and the drop update (Sec. 3)
+    # GMRES (Sec. 6) and the drop update (Sec. 3)
     ("givens_rotation_sign", gmres, "gmres",
      [("H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]", "H[i + 1, k] = sn[i] * H[i, k] + cs[i] * H[i + 1, k]")],
      PL.test_gmres_iterate_minimises_the_residual_over_the_krylov_space, ()),

@@ -1,5 +1,5 @@
 """Pins of the oracle's surfactant transport and coupled step (Eq. surfactant0, Sec. 3, Alg. 1)
-against closed forms, geometric identities, the paper's own validation cases (Sec. 6: pure
+against closed forms, geometric identities, the paper's own validation cases (Sec. 5: pure
 diffusion, the expanding sphere with Gamma R^2 = Gamma(0), the rotating sphere) and the
 conservation of surfactant mass."""
 import math
@@ -80,7 +80,7 @@ def test_green_identities_of_the_laplacian_on_a_deformed_drop():
 
 
 def test_stretching_term_of_an_expanding_sphere():
-    # Sec. 6, stretching test: u = c n on a sphere of radius R gives dGamma/dt = -(2c/R) Gamma,
+    # Sec. 5, stretching test: u = c n on a sphere of radius R gives dGamma/dt = -(2c/R) Gamma,
     # for any Gamma (the tangential velocity is zero).
     p, R, c = 7, 1.2, 0.3
     centre = np.array([0.1, 0.4, -0.3])
@@ -93,7 +93,7 @@ def test_stretching_term_of_an_expanding_sphere():
 
 
 def test_rigid_motion_leaves_any_concentration_unchanged():
-    # Sec. 6, convection test: the points of a rigidly moving drop carry Gamma with them.
+    # Sec. 5, convection test: the points of a rigidly moving drop carry Gamma with them.
     p = 7
     x, rng = _deformed(p, 5)
     Om, V = np.array([0.4, -0.1, 0.8]), np.array([0.2, 0.0, -0.5])
@@ -142,7 +142,7 @@ def test_implicit_solve_preconditioned_exactly_on_a_sphere_and_equal_to_a_dense_
 
 
 def test_imex2_step_of_pure_diffusion_on_a_resting_sphere():
-    # Sec. 6, diffusion test.  With u = 0 the scheme is, per SH mode, the rational factor
+    # Sec. 5, diffusion test.  With u = 0 the scheme is, per SH mode, the rational factor
     # (1 - a)/(1 + a), a = dt n(n+1)/(2 Pe R^2): the exact closed form of the IMEX-2 step, which
     # matches exp(-2a) to second order and decays every mode n > 0.
     p, R, pe, dt = 6, 1.1, 5.0, 0.2
@@ -172,7 +172,7 @@ def _radial(c, centre):
 
 
 def test_expanding_sphere_keeps_gamma_r_squared_to_second_order():
-    # Sec. 6: uniform expansion R(t) = R0 + c t at infinite Peclet number gives Gamma R^2 = Gamma(0).
+    # Sec. 5: uniform expansion R(t) = R0 + c t at infinite Peclet number gives Gamma R^2 = Gamma(0).
     p, R0, c, T = 4, 1.0, 0.5, 0.8
     x = inputs.sphere_coef(p, radius=R0)
     g = np.zeros((p + 1) ** 2)
