@@ -338,6 +338,19 @@ int bie_run_coupled(bie_ctx* ctx, int ndrop, const int* p, const int* pq, double
                     double dt0, double tol, double dt_max, int estimator, int max_steps, const bie_solve_opts* opts,
                     bie_run_info* info, void* stream);
 
+/* Measured arithmetic rate of the context's GPU, the denominator of the pair kernels' ALU
+ * rooflines (the paper has no counterpart; a measurement utility).  which: BIE_PEAK_FP32 (fma.rn.f32),
+ * BIE_PEAK_FP32X2 (fma.rn.f32x2, two FP32 FMAs per instruction) or BIE_PEAK_FP64 (fma.rn.f64).
+ * Runs a kernel of eight independent FMA chains per thread at full occupancy (eight 256-thread
+ * blocks per SM), once to warm up and five times timed with CUDA events on the legacy default
+ * stream; *tflops = 2 x FMAs / best time (FMA = 2 flops).  Synchronous; allocates one word of
+ * device memory for the call; changes no setting of the GPU (the rate is whatever its clocks
+ * give meanwhile).  BIE_EINVAL for a null pointer or an unknown `which`. */
+#define BIE_PEAK_FP32 0
+#define BIE_PEAK_FP32X2 1
+#define BIE_PEAK_FP64 2
+int bie_alu_peak(bie_ctx* ctx, int which, double* tflops);
+
 /* Number of CUDA kernels the library has launched in this process (all contexts). */
 long long bie_launch_count(void);
 

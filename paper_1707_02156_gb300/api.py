@@ -71,6 +71,7 @@ class bie_run_info(ctypes.Structure):
 
 
 BIE_ERR_CONSERVATION, BIE_ERR_IMEX1 = 0, 1
+BIE_PEAK_FP32, BIE_PEAK_FP32X2, BIE_PEAK_FP64 = 0, 1, 2
 
 
 EXPORTS = {
@@ -96,6 +97,7 @@ EXPORTS = {
     "bie_profile": (c_int, [c_void, c_int]),
     "bie_profile_read": (c_int, [c_void, ctypes.POINTER(bie_phase_stat), c_int, P_int]),
     "bie_launch_count": (c_ll, []),
+    "bie_alu_peak": (c_int, [c_void, c_int, P_double]),
     "bie_step_midpoint": (c_int, [c_void, c_int, P_int, P_int, c_void, c_void, c_double, c_double, P_double,
                                   c_double, c_double, c_void, c_void, c_void]),
     "bie_surfactant_rates": (c_int, [c_void, c_int, P_int, c_void, c_void, c_void, c_double, c_void, c_void, c_void]),
@@ -240,6 +242,13 @@ class Context:
         _check(lib().bie_rotate_noalloc(self.h, len(p), _ints(p), ncomp, _ptr(coef), _doubles(flat), _ptr(out),
                                         _stream()), "bie_rotate_noalloc")
         return out
+
+    def alu_peak(self, which: int) -> float:
+        """Measured rate in TFLOP/s of FP32 FMA (0), packed FP32 FMA f32x2 (1) or FP64 FMA (2) on this
+        context's GPU (bie_alu_peak)."""
+        v = ctypes.c_double()
+        _check(lib().bie_alu_peak(self.h, int(which), ctypes.byref(v)), "bie_alu_peak")
+        return v.value
 
     def geometry(self, p, pq, xcoef: torch.Tensor, lam) -> "Geometry":
         """Set up the shape-dependent data of the drops (see Geometry)."""

@@ -133,6 +133,7 @@ const dff* WigPlan::blk_<dff>() const {
 
 struct bie_ctx {
   bie_config cfg;
+  int sms = 0;  // streaming multiprocessors of the device (sizes the work lists)
   struct Prof {
     bool on = false;
     std::vector<cudaEvent_t> pool;
@@ -690,7 +691,7 @@ static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s);
 // Autotuner of the FP32 pair kernel: for large work lists, time the targets-per-thread variants
 // (1, 2, 4) once on this geometry's work list (double layer, zero densities: the cost does not
 // depend on the values) and keep the fastest.
-static int autotune_interdrop(bie_geom* g, cudaStream_t s) {
+static int autotune_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   const long long pairs = g->info.far_pairs + g->info.up_pairs;
   g->info.interdrop_tpt = g->tpt32;
   if (pairs < 500000000LL || g->nblk == 0) return BIE_OK;
@@ -706,7 +707,7 @@ static int autotune_interdrop(bie_geom* g, cudaStream_t s) {
   // time a leading part of the work list of about 5e10 pairs (at least 32 blocks per SM); blocks carry
   // similar work, so its ranking is the full list's
   const int nsample = (int)std::min<long long>(
-      g->nblk, std::max<long long>(32LL * 152, (long long)((double)g->nblk * std::min(1.0, 5e10 / (double)pairs))));
+      g->nblk, std::max<long long>(32LL * ctx->sms, (long long)((double)g->nblk * std::min(1.0, 5e10 / (double)pairs))));
   for (int ci = 0; ci < 3; ++ci) {
     cudaEventRecord(e0, s);
     int st = launch_interdrop<float>(1, cand[ci], nsample, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr,
@@ -867,7 +868,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
       const TileMask& tmj = tmask[(size_t)ti * nd + j];
       all_sources += (popc(tmj.m[0]) ? ngd[j] : 0) + (popc(tmj.m[1]) ? g->up_n[j] : 0);
     }
-  const long long cap_global = std::max<long long>(2048, std::min<long long>(65536, all_sources / (8 * 152)));
+  const long long cap_global = std::max<long long>(2048, std::min<long long>(65536, all_sources / (8LL * ctx->sms)));
   std::vector<PairItem> items;
   std::vector<int> blk_item, tile_blk(ntile + 1, 0);
   long long far_pairs = 0, up_pairs = 0;
@@ -962,7 +963,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   BIE_TRY(g->up_off_d.upload(g->up_off));
   BIE_TRY(g->up_n_d.upload(g->up_n));
   stage.reset(new Phase(ctx, "setup_autotune", s));
-  BIE_TRY(autotune_interdrop(g, s));
+  BIE_TRY(autotune_interdrop(ctx, g, s));
   stage.reset();
   for (auto& G : g->groups) {
     std::vector<long long> so, uo2;
@@ -2197,8 +2198,11 @@ int bie_create(bie_ctx** out, const bie_config* cfg) {
     return BIE_EINVAL;
   }
   BIE_CUDA_TRY(cudaSetDevice(c.device));
+  int sms = 0;
+  BIE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
   bie_ctx* ctx = new bie_ctx();
   ctx->cfg = c;
+  ctx->sms = sms;
   *out = ctx;
   return BIE_OK;
 }

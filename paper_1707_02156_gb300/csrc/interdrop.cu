@@ -201,6 +201,188 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop(
   }
 }
 
+// ---- FP32 pair sums on packed lane pairs ----
+// Two targets share one 64-bit register pair and every FP32 operation of their two pairs issues as
+// one fma/mul/sub.rn.f32x2 instruction: half the issue slots of the scalar kernel for the same
+// FP32-pipe work, which leaves room for the shared-memory loads and the two MUFU rsqrt of each
+// source without starving the FMA pipe.  Rounding is that of the scalar operations (each lane is
+// an IEEE round-to-nearest FP32 operation).
+typedef unsigned long long fx2;  // lanes (lo, hi) = two FP32 values
+
+__device__ __forceinline__ fx2 x2_pack(float lo, float hi) {
+  fx2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void x2_unpack(fx2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ fx2 x2_sub(fx2 a, fx2 b) {
+  fx2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ fx2 x2_mul(fx2 a, fx2 b) {
+  fx2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ fx2 x2_fma(fx2 a, fx2 b, fx2 c) {
+  fx2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ fx2 x2_rsqrt(fx2 v) {
+  float lo, hi;
+  x2_unpack(v, lo, hi);
+  return x2_pack(rsqrtf(lo), rsqrtf(hi));
+}
+
+constexpr int kChunkX2 = 64;  // sources staged per pass of the packed kernel
+
+// Staged source of the packed kernel: each value duplicated into both lanes, in the order
+// x, y, z, q0, q1, q2, n0, n1, n2 (and one pad), read with 128-bit shared-memory loads (three for
+// the single layer, five for the double layer).
+struct alignas(16) SrcRecX2 {
+  fx2 v[10];
+};
+
+// Same work list, layout and result as k_interdrop<float, KIND, TPT>; TPT even, the thread's
+// targets tid + u * (128/TPT) taken two by two (u = 2w, 2w + 1 share lane pair w).
+template <int KIND, int TPT>
+__global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
+    const PairItem* __restrict__ items, const int* __restrict__ blk_item, const long long* __restrict__ tile_t0,
+    const int* __restrict__ tile_n, const int* __restrict__ tile_drop, const long long* __restrict__ tgt_loc,
+    const long long* __restrict__ toff_std, const int* __restrict__ ngd, const double* __restrict__ rec_std,
+    const double* __restrict__ centre, const float* __restrict__ Xs, const float* __restrict__ Ns,
+    const float* __restrict__ Qs, long long nstd, const float* __restrict__ Xu, const float* __restrict__ Nu,
+    const float* __restrict__ Qu, long long nup, const double* __restrict__ wts, double* __restrict__ partial) {
+  static_assert(TPT % 2 == 0, "targets are taken in lane pairs");
+  constexpr int NT = kTile / TPT;
+  constexpr int NW = TPT / 2;  // lane pairs per thread
+  constexpr int NV = KIND ? 9 : 6;
+  __shared__ SrcRecX2 src[kChunkX2];
+  const int b = blockIdx.x;
+  const int it0 = blk_item[b], it1 = blk_item[b + 1];
+  const int tile = items[it0].tile;
+  const int tid = threadIdx.x;
+  const int nt = tile_n[tile];
+  const int di = tile_drop[tile];
+  double tx[TPT], ty[TPT], tz[TPT], acc[TPT][3];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int k = tid + u * NT;
+    tx[u] = ty[u] = tz[u] = 0;
+    acc[u][0] = acc[u][1] = acc[u][2] = 0;
+    if (k < nt) {
+      const long long t = tile_t0[tile] + k;
+      const long long ng = ngd[di];
+      const double* ri = rec_std + 7 * toff_std[di];
+      const long long l = tgt_loc[t];
+      tx[u] = ri[l];
+      ty[u] = ri[ng + l];
+      tz[u] = ri[2 * ng + l];
+    }
+  }
+  for (int it = it0; it < it1; ++it) {
+    const PairItem item = items[it];
+    const int j = item.src_drop;
+    bool act[TPT], any = false;
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const int k = tid + u * NT;
+      act[u] = k < nt && ((item.mask[k >> 5] >> (k & 31)) & 1u);
+      any = any || act[u];
+    }
+    const double cx = centre[3 * j], cy = centre[3 * j + 1], cz = centre[3 * j + 2];
+    fx2 px[NW], py[NW], pz[NW], s[NW][3];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      px[w] = x2_pack((float)(tx[2 * w] - cx), (float)(tx[2 * w + 1] - cx));
+      py[w] = x2_pack((float)(ty[2 * w] - cy), (float)(ty[2 * w + 1] - cy));
+      pz[w] = x2_pack((float)(tz[2 * w] - cz), (float)(tz[2 * w + 1] - cz));
+      s[w][0] = s[w][1] = s[w][2] = 0ull;  // +0.0f in both lanes
+    }
+    const float* X = item.grid ? Xu : Xs;
+    const float* N = item.grid ? Nu : Ns;
+    const float* Q = item.grid ? Qu : Qs;
+    const long long ld = item.grid ? nup : nstd;
+    for (long long c0 = item.s0; c0 < item.s1; c0 += kChunkX2) {
+      const int cn = (int)min((long long)kChunkX2, item.s1 - c0);
+      for (int k = tid; k < cn; k += NT) {
+        const long long sidx = c0 + k;
+        float v[NV];
+        v[0] = X[sidx];
+        v[1] = X[ld + sidx];
+        v[2] = X[2 * ld + sidx];
+        v[3] = Q[sidx];
+        v[4] = Q[ld + sidx];
+        v[5] = Q[2 * ld + sidx];
+        if (KIND) {
+          v[6] = N[sidx];
+          v[7] = N[ld + sidx];
+          v[8] = N[2 * ld + sidx];
+        }
+        SrcRecX2 r;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) r.v[q] = x2_pack(v[q], v[q]);
+#pragma unroll
+        for (int q = NV; q < 10; ++q) r.v[q] = 0ull;
+        src[k] = r;
+      }
+      __syncthreads();
+      if (any) {
+        for (int k = 0; k < cn; ++k) {
+          fx2 v[10];
+          constexpr int nv = (NV + 1) / 2;  // 128-bit loads
+#pragma unroll
+          for (int q = 0; q < nv; ++q)
+            *reinterpret_cast<ulonglong2*>(v + 2 * q) = reinterpret_cast<const ulonglong2*>(&src[k])[q];
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            const fx2 dx = x2_sub(px[w], v[0]), dy = x2_sub(py[w], v[1]), dz = x2_sub(pz[w], v[2]);
+            const fx2 r2 = x2_fma(dz, dz, x2_fma(dy, dy, x2_mul(dx, dx)));
+            const fx2 ri = x2_rsqrt(r2);
+            const fx2 xq = x2_fma(dz, v[5], x2_fma(dy, v[4], x2_mul(dx, v[3])));
+            const fx2 ri2 = x2_mul(ri, ri);
+            if (KIND == 0) {  // Stokeslet: q/r + (xh.q) xh/r^3
+              const fx2 c = x2_mul(x2_mul(xq, ri2), ri);
+              s[w][0] = x2_fma(c, dx, x2_fma(v[3], ri, s[w][0]));
+              s[w][1] = x2_fma(c, dy, x2_fma(v[4], ri, s[w][1]));
+              s[w][2] = x2_fma(c, dz, x2_fma(v[5], ri, s[w][2]));
+            } else {  // stresslet without its factor -6: (xh.q)(xh.n) xh/r^5
+              const fx2 xn = x2_fma(dz, v[8], x2_fma(dy, v[7], x2_mul(dx, v[6])));
+              const fx2 c = x2_mul(x2_mul(x2_mul(x2_mul(xq, xn), ri2), ri2), ri);
+              s[w][0] = x2_fma(c, dx, s[w][0]);
+              s[w][1] = x2_fma(c, dy, s[w][1]);
+              s[w][2] = x2_fma(c, dz, s[w][2]);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const double wj = KIND ? -6.0 * wts[j] : wts[j];
+#pragma unroll
+    for (int w = 0; w < NW; ++w)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float lo, hi;
+        x2_unpack(s[w][c], lo, hi);
+        acc[2 * w][c] += (act[2 * w] ? wj : 0.0) * (double)lo;
+        acc[2 * w + 1][c] += (act[2 * w + 1] ? wj : 0.0) * (double)hi;
+      }
+  }
+  double* pp = partial + (long long)b * 3 * kTile;
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int k = tid + u * NT;
+    pp[k] = acc[u][0];
+    pp[kTile + k] = acc[u][1];
+    pp[2 * kTile + k] = acc[u][2];
+  }
+}
+
 // ---- double-float pair sums ----
 // A double-float value is an unevaluated sum hi + lo of two FP32 numbers (about 44 significant
 // bits).  Sums use Knuth's TwoSum and products the FMA-based TwoProduct (both error-free
@@ -500,6 +682,18 @@ static void interdrop_kernel(int kind, int nblk, const PairItem* items, const in
                              const long long* toff_std, const int* ngd, const double* rec_std, const double* centre,
                              const R* Xs, const R* Ns, const R* Qs, long long nstd, const R* Xu, const R* Nu,
                              const R* Qu, long long nup, const double* wts, double* partial, cudaStream_t s) {
+  if constexpr (std::is_same<R, float>::value && TPT % 2 == 0) {
+    // FP32 with two or more targets per thread: packed lane pairs
+    if (kind == 0)
+      k_interdrop_x2<0, TPT><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
+                                                          toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu,
+                                                          Qu, nup, wts, partial);
+    else
+      k_interdrop_x2<1, TPT><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
+                                                          toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu,
+                                                          Qu, nup, wts, partial);
+    return;
+  }
   if (kind == 0)
     k_interdrop<R, 0, TPT><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
                                                         toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu,

@@ -138,9 +138,11 @@ def test_batch_of_64_uneven_degree_drops_full_size(cuda_ok):
 
 
 def test_512_deformed_drops_full_size(cuda_ok):
+    # FP64, mixed and double-float applies of the 512 drops, at two sampled (drop, latitude) pairs
     w = inputs.config("c5")
-    i, lats = 137, [3]
-    g = _gpu_grid(w, "D", (1, 2))
-    ref = _far_only_oracle(w, "D", i, lats)
-    assert _relerr(_drop_block(w, g[1], i, lats), ref) < MIXED_TOL
-    assert _relerr(_drop_block(w, g[2], i, lats), ref) < DF_TOL
+    g = _gpu_grid(w, "D", (0, 1, 2))
+    for i, lats in ((137, [3]), (400, [12])):
+        ref = _far_only_oracle(w, "D", i, lats)
+        assert _relerr(_drop_block(w, g[0], i, lats), ref) < FP64_TOL, i
+        assert _relerr(_drop_block(w, g[1], i, lats), ref) < MIXED_TOL, i
+        assert _relerr(_drop_block(w, g[2], i, lats), ref) < DF_TOL, i
