@@ -13,7 +13,7 @@ from paper_1707_02156_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-MIXED_TOL = 2e-5
+MIXED_TOL = 5e-6  # FP32 rounding of multi-drop applies: measured 5.8e-8 .. 1.3e-6 relative; about 4x the largest
 DF_TOL = 1e-11  # 2^-44 per operation, grown over ~10^4-term sums with magnitudes up to the 1/r peak
 
 

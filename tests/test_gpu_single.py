@@ -1,5 +1,5 @@
 """GPU parity of the C-ABI library against the FP64 oracle: transforms, rotation, and the
-single-drop layer operators and solve.  FP64 path: 1e-12 relative; mixed path: 2e-5 relative
+single-drop layer operators and solve.  FP64 path: 1e-12 relative; mixed path: 2e-6 relative
 for one apply (FP32 rotation, synthesis and pair sums), 1e-8 after refinement in the solve."""
 import math
 
@@ -14,7 +14,7 @@ from paper_1707_02156_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-MIXED_TOL = 2e-5
+MIXED_TOL = 2e-6  # FP32 rounding of the single-drop applies: measured 5.9e-8 .. 5.3e-7 relative; about 4x the largest
 DF_TOL = 1e-11  # double-float: about 44 bits per operation
 
 
