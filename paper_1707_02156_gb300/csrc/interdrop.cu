@@ -248,7 +248,10 @@ struct alignas(16) SrcRecX2 {
 };
 
 // Same work list, layout and result as k_interdrop<float, KIND, TPT>; TPT even, the thread's
-// targets tid + u * (128/TPT) taken two by two (u = 2w, 2w + 1 share lane pair w).
+// targets tid + u * (128/TPT) taken two by two (u = 2w, 2w + 1 share lane pair w).  The tile's FP64
+// target coordinates and the FP64 accumulators live in shared memory, not in registers, so that
+// more warps fit per SM; the source loop takes two sources per iteration (2 x TPT/2 independent
+// chains per thread).
 template <int KIND, int TPT>
 __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
     const PairItem* __restrict__ items, const int* __restrict__ blk_item, const long long* __restrict__ tile_t0,
@@ -261,67 +264,82 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
   constexpr int NT = kTile / TPT;
   constexpr int NW = TPT / 2;  // lane pairs per thread
   constexpr int NV = KIND ? 9 : 6;
+  constexpr int nv = (NV + 1) / 2;  // 128-bit loads per staged source
   __shared__ SrcRecX2 src[kChunkX2];
+  __shared__ double tgt[3][kTile];  // the tile's target coordinates (zero past the tile's end)
+  __shared__ double acc[3][kTile];  // per-target sums over the block's items
   const int b = blockIdx.x;
   const int it0 = blk_item[b], it1 = blk_item[b + 1];
   const int tile = items[it0].tile;
   const int tid = threadIdx.x;
   const int nt = tile_n[tile];
   const int di = tile_drop[tile];
-  double tx[TPT], ty[TPT], tz[TPT], acc[TPT][3];
-#pragma unroll
-  for (int u = 0; u < TPT; ++u) {
-    const int k = tid + u * NT;
-    tx[u] = ty[u] = tz[u] = 0;
-    acc[u][0] = acc[u][1] = acc[u][2] = 0;
-    if (k < nt) {
-      const long long t = tile_t0[tile] + k;
-      const long long ng = ngd[di];
-      const double* ri = rec_std + 7 * toff_std[di];
-      const long long l = tgt_loc[t];
-      tx[u] = ri[l];
-      ty[u] = ri[ng + l];
-      tz[u] = ri[2 * ng + l];
+  {
+    const long long ng = ngd[di];
+    const double* ri = rec_std + 7 * toff_std[di];
+    for (int k = tid; k < kTile; k += NT) {
+      double x = 0, y = 0, z = 0;
+      if (k < nt) {
+        const long long l = tgt_loc[tile_t0[tile] + k];
+        x = ri[l];
+        y = ri[ng + l];
+        z = ri[2 * ng + l];
+      }
+      tgt[0][k] = x;
+      tgt[1][k] = y;
+      tgt[2][k] = z;
+      acc[0][k] = acc[1][k] = acc[2][k] = 0.0;
     }
   }
+  // the block's shared arrays are written before any thread reads them (the first staging barrier
+  // below comes after the target loads; each thread reads only its own targets' entries)
+  __syncthreads();
   for (int it = it0; it < it1; ++it) {
-    const PairItem item = items[it];
-    const int j = item.src_drop;
-    bool act[TPT], any = false;
+    const int j = items[it].src_drop;
+    unsigned act = 0u;  // bit u: target tid + u * NT is in this item
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
       const int k = tid + u * NT;
-      act[u] = k < nt && ((item.mask[k >> 5] >> (k & 31)) & 1u);
-      any = any || act[u];
+      if (k < nt && ((items[it].mask[k >> 5] >> (k & 31)) & 1u)) act |= 1u << u;
     }
     const double cx = centre[3 * j], cy = centre[3 * j + 1], cz = centre[3 * j + 2];
     fx2 px[NW], py[NW], pz[NW], s[NW][3];
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
-      px[w] = x2_pack((float)(tx[2 * w] - cx), (float)(tx[2 * w + 1] - cx));
-      py[w] = x2_pack((float)(ty[2 * w] - cy), (float)(ty[2 * w + 1] - cy));
-      pz[w] = x2_pack((float)(tz[2 * w] - cz), (float)(tz[2 * w + 1] - cz));
+      const int k0 = tid + 2 * w * NT, k1 = k0 + NT;
+      px[w] = x2_pack((float)(tgt[0][k0] - cx), (float)(tgt[0][k1] - cx));
+      py[w] = x2_pack((float)(tgt[1][k0] - cy), (float)(tgt[1][k1] - cy));
+      pz[w] = x2_pack((float)(tgt[2][k0] - cz), (float)(tgt[2][k1] - cz));
       s[w][0] = s[w][1] = s[w][2] = 0ull;  // +0.0f in both lanes
     }
-    const float* X = item.grid ? Xu : Xs;
-    const float* N = item.grid ? Nu : Ns;
-    const float* Q = item.grid ? Qu : Qs;
-    const long long ld = item.grid ? nup : nstd;
-    for (long long c0 = item.s0; c0 < item.s1; c0 += kChunkX2) {
-      const int cn = (int)min((long long)kChunkX2, item.s1 - c0);
-      for (int k = tid; k < cn; k += NT) {
-        const long long sidx = c0 + k;
+    const int grid = items[it].grid;
+    const float* X = grid ? Xu : Xs;
+    const float* N = grid ? Nu : Ns;
+    const float* Q = grid ? Qu : Qs;
+    const long long ld = grid ? nup : nstd;
+    const long long s0 = items[it].s0, s1 = items[it].s1;
+    for (long long c0 = s0; c0 < s1; c0 += kChunkX2) {
+      const int cn = (int)min((long long)kChunkX2, s1 - c0);
+      for (int k = tid; k < kChunkX2; k += NT) {
+        // sources past the item's end are staged as zero weight (q = 0), so the loop below runs
+        // over whole pairs of sources; their distance is |target - 0|, never zero for a target
+        // outside the source drop
         float v[NV];
-        v[0] = X[sidx];
-        v[1] = X[ld + sidx];
-        v[2] = X[2 * ld + sidx];
-        v[3] = Q[sidx];
-        v[4] = Q[ld + sidx];
-        v[5] = Q[2 * ld + sidx];
-        if (KIND) {
-          v[6] = N[sidx];
-          v[7] = N[ld + sidx];
-          v[8] = N[2 * ld + sidx];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = 0.f;
+        if (k < cn) {
+          const long long sidx = c0 + k;
+          v[0] = X[sidx];
+          v[1] = X[ld + sidx];
+          v[2] = X[2 * ld + sidx];
+          v[3] = Q[sidx];
+          v[4] = Q[ld + sidx];
+          v[5] = Q[2 * ld + sidx];
+          if (KIND) {
+            v[6] = N[sidx];
+            v[7] = N[ld + sidx];
+            v[8] = N[2 * ld + sidx];
+          }
         }
         SrcRecX2 r;
 #pragma unroll
@@ -331,31 +349,37 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
         src[k] = r;
       }
       __syncthreads();
-      if (any) {
-        for (int k = 0; k < cn; ++k) {
-          fx2 v[10];
-          constexpr int nv = (NV + 1) / 2;  // 128-bit loads
+      if (act) {
+        const int cn2 = (cn + 1) & ~1;
+        for (int k = 0; k < cn2; k += 2) {
+          fx2 va[10], vb[10];
 #pragma unroll
-          for (int q = 0; q < nv; ++q)
-            *reinterpret_cast<ulonglong2*>(v + 2 * q) = reinterpret_cast<const ulonglong2*>(&src[k])[q];
+          for (int q = 0; q < nv; ++q) {
+            *reinterpret_cast<ulonglong2*>(va + 2 * q) = reinterpret_cast<const ulonglong2*>(&src[k])[q];
+            *reinterpret_cast<ulonglong2*>(vb + 2 * q) = reinterpret_cast<const ulonglong2*>(&src[k + 1])[q];
+          }
 #pragma unroll
-          for (int w = 0; w < NW; ++w) {
-            const fx2 dx = x2_sub(px[w], v[0]), dy = x2_sub(py[w], v[1]), dz = x2_sub(pz[w], v[2]);
-            const fx2 r2 = x2_fma(dz, dz, x2_fma(dy, dy, x2_mul(dx, dx)));
-            const fx2 ri = x2_rsqrt(r2);
-            const fx2 xq = x2_fma(dz, v[5], x2_fma(dy, v[4], x2_mul(dx, v[3])));
-            const fx2 ri2 = x2_mul(ri, ri);
-            if (KIND == 0) {  // Stokeslet: q/r + (xh.q) xh/r^3
-              const fx2 c = x2_mul(x2_mul(xq, ri2), ri);
-              s[w][0] = x2_fma(c, dx, x2_fma(v[3], ri, s[w][0]));
-              s[w][1] = x2_fma(c, dy, x2_fma(v[4], ri, s[w][1]));
-              s[w][2] = x2_fma(c, dz, x2_fma(v[5], ri, s[w][2]));
-            } else {  // stresslet without its factor -6: (xh.q)(xh.n) xh/r^5
-              const fx2 xn = x2_fma(dz, v[8], x2_fma(dy, v[7], x2_mul(dx, v[6])));
-              const fx2 c = x2_mul(x2_mul(x2_mul(x2_mul(xq, xn), ri2), ri2), ri);
-              s[w][0] = x2_fma(c, dx, s[w][0]);
-              s[w][1] = x2_fma(c, dy, s[w][1]);
-              s[w][2] = x2_fma(c, dz, s[w][2]);
+          for (int h = 0; h < 2; ++h) {
+            const fx2* v = h ? vb : va;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+              const fx2 dx = x2_sub(px[w], v[0]), dy = x2_sub(py[w], v[1]), dz = x2_sub(pz[w], v[2]);
+              const fx2 r2 = x2_fma(dz, dz, x2_fma(dy, dy, x2_mul(dx, dx)));
+              const fx2 ri = x2_rsqrt(r2);
+              const fx2 xq = x2_fma(dz, v[5], x2_fma(dy, v[4], x2_mul(dx, v[3])));
+              const fx2 ri2 = x2_mul(ri, ri);
+              if (KIND == 0) {  // Stokeslet: q/r + (xh.q) xh/r^3
+                const fx2 c = x2_mul(x2_mul(xq, ri2), ri);
+                s[w][0] = x2_fma(c, dx, x2_fma(v[3], ri, s[w][0]));
+                s[w][1] = x2_fma(c, dy, x2_fma(v[4], ri, s[w][1]));
+                s[w][2] = x2_fma(c, dz, x2_fma(v[5], ri, s[w][2]));
+              } else {  // stresslet without its factor -6: (xh.q)(xh.n) xh/r^5
+                const fx2 xn = x2_fma(dz, v[8], x2_fma(dy, v[7], x2_mul(dx, v[6])));
+                const fx2 c = x2_mul(x2_mul(x2_mul(x2_mul(xq, xn), ri2), ri2), ri);
+                s[w][0] = x2_fma(c, dx, s[w][0]);
+                s[w][1] = x2_fma(c, dy, s[w][1]);
+                s[w][2] = x2_fma(c, dz, s[w][2]);
+              }
             }
           }
         }
@@ -364,22 +388,24 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
     }
     const double wj = KIND ? -6.0 * wts[j] : wts[j];
 #pragma unroll
-    for (int w = 0; w < NW; ++w)
+    for (int w = 0; w < NW; ++w) {
+      const int k0 = tid + 2 * w * NT, k1 = k0 + NT;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         float lo, hi;
         x2_unpack(s[w][c], lo, hi);
-        acc[2 * w][c] += (act[2 * w] ? wj : 0.0) * (double)lo;
-        acc[2 * w + 1][c] += (act[2 * w + 1] ? wj : 0.0) * (double)hi;
+        if (act & (1u << (2 * w))) acc[c][k0] += wj * (double)lo;
+        if (act & (1u << (2 * w + 1))) acc[c][k1] += wj * (double)hi;
       }
+    }
   }
   double* pp = partial + (long long)b * 3 * kTile;
 #pragma unroll
   for (int u = 0; u < TPT; ++u) {
     const int k = tid + u * NT;
-    pp[k] = acc[u][0];
-    pp[kTile + k] = acc[u][1];
-    pp[2 * kTile + k] = acc[u][2];
+    pp[k] = acc[0][k];
+    pp[kTile + k] = acc[1][k];
+    pp[2 * kTile + k] = acc[2][k];
   }
 }
 
