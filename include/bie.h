@@ -78,9 +78,14 @@ typedef struct bie_config {
   int use_graphs;    /* 1: an apply (kind, flags) is captured into a CUDA graph at its second call and
                         replayed afterwards (input and output pass through fixed internal buffers);
                         0: every apply launches its kernels one by one */
+  int tensor_rotation; /* 1 (default): in BIE_MIXED applies the Wigner rotation of the projected self
+                          form (App. B) runs on the tensor cores (TF32 with a 3-pass split, FP32
+                          accumulation, about FP32 accuracy); 0: on the CUDA cores in FP32.  FP64 and
+                          BIE_DF applies always rotate on the CUDA cores */
 } bie_config;
 
-/* Fill a config with the paper's defaults: device 0, U = 4, A = 5, L = 8, Fourier form, graphs on. */
+/* Fill a config with the paper's defaults: device 0, U = 4, A = 5, L = 8, projected self form, graphs
+ * on, tensor-core rotation on. */
 void bie_config_default(bie_config* cfg);
 
 /* Create a context on cfg->device.  Plan tables are built lazily per degree and cached. */
@@ -325,18 +330,62 @@ typedef struct bie_run_info {
   double dt_next;           /* the step size the rule proposes next */
   double err_max_accepted;  /* largest err = max(err_drop, err_surfactant) of a kept step */
   int steps_accepted, steps_rejected, velocity_solves;
+  int reparam_iterations;   /* angle steps of Alg. 2 over the run (summed over the kept steps) */
 } bie_run_info;
+
+/* ---- Angle reparametrisation (Sec. 4, Alg. 2) ----
+ * The parameter points of each drop's working grid of degree P = u_rep (p+1) - 1 (zero-padded
+ * coefficients) move in pseudo-time so that the spectral energy E = sum_n a_n sum_{m=-n..n} |x_n^m|^2
+ * of the surface's parametrisation (Eq. energy_rep, |x_n^m| the Euclidean norm of the three complex
+ * coefficients) decreases while the surface stays the same: the pseudo-velocity is the tangential
+ * part g = (I - n n) grad E of the L2 gradient grad E = 2 sum a_n x_n^m Y_n^m (Eq. pseudo_rep, n the
+ * normal of the original surface at the point), the angles follow the chain rule of Eq. system_rep
+ * by forward Euler steps of size dtau, and after each step the original expansion, evaluated at the
+ * new angles, is analysed on the grid (Eq. rep_trasf1).  a_n comes from the adaptive cutoff of
+ * Eq. ncutoff_adaptive: n_cutoff = the smallest l with 1 < l <= P and
+ * sum_{n >= l} sum_m |x_n^m| / sum_{n >= 1} sum_m |x_n^m| < p_cutoff (P if none), recomputed every
+ * iteration; a_n = 1 (perfect filter) or n/P (smooth) for n >= n_cutoff, 0 below.  A drop stops when
+ * max |g| over its points is below eps (the stopping test of Alg. 2) or after max_iter steps.  The
+ * surfactant is evaluated at the final angles (Eq. rep_trasf2); shape and surfactant are analysed
+ * back to degree p.  Readings: the working grid, the gradient and the pole crossing (an angle step
+ * across a pole maps back to theta in [0, pi] with phi + pi) are those of the FP64 oracle. */
+typedef struct bie_reparam_opts {
+  int u_rep;        /* working-grid factor, >= 1 (P = u_rep (p+1) - 1 <= 4 BIE_MAX_P) */
+  double p_cutoff;  /* fraction of Eq. ncutoff_adaptive, 0 < p_cutoff < 1 */
+  int smooth;       /* 0: perfect low-pass filter, 1: smooth filter a_n = n/P */
+  double dtau;      /* pseudo-time step (forward Euler is stable for dtau < 1/max a_n) */
+  double eps;       /* stopping threshold on max |g| */
+  int max_iter;     /* angle steps allowed per drop */
+} bie_reparam_opts;
+
+typedef struct bie_reparam_info {
+  int iterations;           /* the largest number of angle steps a drop took */
+  int converged;            /* drops that met the stopping test */
+  double g_max;             /* the largest last max |g| over the drops */
+  double energy_first_max;  /* the largest energy E at the first iteration */
+  double energy_last_max;   /* the largest energy at the last evaluated iteration */
+} bie_reparam_info;
+
+/* Fill the options with u_rep 2, p_cutoff 0.05, perfect filter, dtau 0.5, eps 1e-10, max_iter 200. */
+void bie_reparam_opts_default(bie_reparam_opts* opts);
+
+/* Reparametrise ndrop drops in place: xcoef [drop][3][(p+1)^2] and, when non-NULL, gammacoef
+ * [drop][(p+1)^2] (device), per-drop degrees p on the host; drops of one degree share every launch.
+ * All in FP64.  Synchronous.  BIE_EINVAL for bad options or degrees (at most 65535 drops). */
+int bie_reparametrize(bie_ctx* ctx, int ndrop, const int* p, double* xcoef, double* gammacoef,
+                      const bie_reparam_opts* opts, bie_reparam_info* info, void* stream);
 
 /* Alg. 1 from t = 0 to T with adaptive dt: each attempt is bie_step_coupled; it is kept when
  * err = max(err_drop, err_surfactant) < tol (estimator BIE_ERR_CONSERVATION or BIE_ERR_IMEX1);
  * after every attempt dt <- bie_next_dt(dt, err, tol, dt_max), the last step cut to end at T;
  * a rejected attempt reuses u^t.  xcoef, gammacoef: device, in at 0, out at the time reached.
- * Reparametrisation (Sec. 4) is not part of the run.  BIE_ENOCONV when max_steps attempts end
+ * reparam: NULL, or the options of an angle reparametrisation (bie_reparametrize, Sec. 4) applied to
+ * the shapes and the surfactant after every kept step.  BIE_ENOCONV when max_steps attempts end
  * before T.  Synchronous. */
 int bie_run_coupled(bie_ctx* ctx, int ndrop, const int* p, const int* pq, double* xcoef, double* gammacoef,
                     double elasticity, double x_s, const double* lambda, double shear, double inv_pe, double T,
                     double dt0, double tol, double dt_max, int estimator, int max_steps, const bie_solve_opts* opts,
-                    bie_run_info* info, void* stream);
+                    const bie_reparam_opts* reparam, bie_run_info* info, void* stream);
 
 /* Measured arithmetic rate of the context's GPU, the denominator of the pair kernels' ALU
  * rooflines (the paper has no counterpart; a measurement utility).  which: BIE_PEAK_FP32 (fma.rn.f32),

@@ -22,10 +22,11 @@ STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIME
 
 
 class bie_config(ctypes.Structure):
-    """bie_config of bie.h: device, upsampling factor, A~, L, self-rule form, graph replay."""
+    """bie_config of bie.h: device, upsampling factor, A~, L, self-rule form, graph replay, tensor-core
+    rotation."""
 
     _fields_ = [("device", c_int), ("upsample", c_int), ("a_tilde", c_double), ("n_interp", c_int),
-                ("self_direct", c_int), ("use_graphs", c_int)]
+                ("self_direct", c_int), ("use_graphs", c_int), ("tensor_rotation", c_int)]
 
 
 class bie_geom_info(ctypes.Structure):
@@ -67,7 +68,21 @@ class bie_run_info(ctypes.Structure):
     """bie_run_info of bie.h: outcome of an adaptive coupled run."""
 
     _fields_ = [("t", c_double), ("dt_next", c_double), ("err_max_accepted", c_double), ("steps_accepted", c_int),
-                ("steps_rejected", c_int), ("velocity_solves", c_int)]
+                ("steps_rejected", c_int), ("velocity_solves", c_int), ("reparam_iterations", c_int)]
+
+
+class bie_reparam_opts(ctypes.Structure):
+    """bie_reparam_opts of bie.h: options of the angle reparametrisation (Alg. 2)."""
+
+    _fields_ = [("u_rep", c_int), ("p_cutoff", c_double), ("smooth", c_int), ("dtau", c_double), ("eps", c_double),
+                ("max_iter", c_int)]
+
+
+class bie_reparam_info(ctypes.Structure):
+    """bie_reparam_info of bie.h: outcome of an angle reparametrisation."""
+
+    _fields_ = [("iterations", c_int), ("converged", c_int), ("g_max", c_double), ("energy_first_max", c_double),
+                ("energy_last_max", c_double)]
 
 
 BIE_ERR_CONSERVATION, BIE_ERR_IMEX1 = 0, 1
@@ -110,7 +125,11 @@ EXPORTS = {
     "bie_next_dt": (c_double, [c_double, c_double, c_double, c_double]),
     "bie_run_coupled": (c_int, [c_void, c_int, P_int, P_int, c_void, c_void, c_double, c_double, P_double, c_double,
                                 c_double, c_double, c_double, c_double, c_double, c_int, c_int,
-                                ctypes.POINTER(bie_solve_opts), ctypes.POINTER(bie_run_info), c_void]),
+                                ctypes.POINTER(bie_solve_opts), ctypes.POINTER(bie_reparam_opts),
+                                ctypes.POINTER(bie_run_info), c_void]),
+    "bie_reparam_opts_default": (None, [ctypes.POINTER(bie_reparam_opts)]),
+    "bie_reparametrize": (c_int, [c_void, c_int, P_int, c_void, c_void, ctypes.POINTER(bie_reparam_opts),
+                                  ctypes.POINTER(bie_reparam_info), c_void]),
     "bie_debug_table": (c_ll, [c_int, c_int, c_int, c_int, c_double, P_double, c_ll]),
 }
 
@@ -182,13 +201,14 @@ class Context:
     """A library context on one CUDA device (plan tables cached per degree)."""
 
     def __init__(self, device: int = 0, upsample: int = 4, a_tilde: float = 5.0, n_interp: int = 8,
-                 self_direct: bool = False, use_graphs: bool = True):
+                 self_direct: bool = False, use_graphs: bool = True, tensor_rotation: bool = True):
         L = lib()
         cfg = bie_config()
         L.bie_config_default(ctypes.byref(cfg))
         cfg.device, cfg.upsample, cfg.a_tilde, cfg.n_interp = device, upsample, a_tilde, n_interp
         cfg.self_direct = 1 if self_direct else 0
         cfg.use_graphs = 1 if use_graphs else 0
+        cfg.tensor_rotation = 1 if tensor_rotation else 0
         h = c_void()
         _check(L.bie_create(ctypes.byref(h), ctypes.byref(cfg)), "bie_create")
         self.h = h
@@ -398,14 +418,36 @@ def run_coupled(ctx: "Context", p, pq, x: torch.Tensor, gamma: torch.Tensor, ela
                 shear: float, inv_pe: float, T: float, dt0: float, tol: float, dt_max: float,
                 estimator: int = BIE_ERR_CONSERVATION, max_steps: int = 1000, precision: int = BIE_MIXED,
                 solve_tol: float = 1e-10, restart: int = 30, max_iter: int = 300, inner_tol: float = 1e-5,
-                max_refine: int = 10, residual_precision: int = BIE_DF) -> dict:
-    """Alg. 1 from 0 to T with adaptive dt; x and gamma are updated in place."""
+                max_refine: int = 10, residual_precision: int = BIE_DF, reparam: dict | None = None) -> dict:
+    """Alg. 1 from 0 to T with adaptive dt; x and gamma are updated in place.  reparam: None, or the
+    options of reparametrize (u_rep, p_cutoff, smooth, dtau, eps, max_iter) applied after every kept
+    step."""
     o = _solve_opts(precision, solve_tol, restart, max_iter, inner_tol, max_refine, residual_precision)
     info = bie_run_info()
+    ro = _reparam_opts(**reparam) if reparam is not None else None
     _check(lib().bie_run_coupled(ctx.h, len(p), _ints(p), _ints(pq), _ptr(x), _ptr(gamma), elasticity, x_s,
                                  _doubles(lam), shear, inv_pe, T, dt0, tol, dt_max, estimator, max_steps,
-                                 ctypes.byref(o), ctypes.byref(info), _stream()), "bie_run_coupled")
+                                 ctypes.byref(o), ctypes.byref(ro) if ro is not None else None, ctypes.byref(info),
+                                 _stream()), "bie_run_coupled")
     return {k: getattr(info, k) for k, _ in bie_run_info._fields_}
+
+
+def _reparam_opts(u_rep: int = 2, p_cutoff: float = 0.05, smooth: bool = False, dtau: float = 0.5, eps: float = 1e-10,
+                  max_iter: int = 200) -> bie_reparam_opts:
+    o = bie_reparam_opts()
+    lib().bie_reparam_opts_default(ctypes.byref(o))
+    o.u_rep, o.p_cutoff, o.smooth, o.dtau, o.eps, o.max_iter = u_rep, p_cutoff, 1 if smooth else 0, dtau, eps, max_iter
+    return o
+
+
+def reparametrize(ctx: "Context", p, x: torch.Tensor, gamma: torch.Tensor | None = None, **opts) -> dict:
+    """Angle reparametrisation (Alg. 2) of the drops' shapes x and surfactant gamma, in place; opts as
+    _reparam_opts.  Returns the bie_reparam_info fields."""
+    o = _reparam_opts(**opts)
+    info = bie_reparam_info()
+    _check(lib().bie_reparametrize(ctx.h, len(p), _ints(p), _ptr(x), _ptr(gamma) if gamma is not None else None,
+                                   ctypes.byref(o), ctypes.byref(info), _stream()), "bie_reparametrize")
+    return {k: getattr(info, k) for k, _ in bie_reparam_info._fields_}
 
 
 def launch_count() -> int:

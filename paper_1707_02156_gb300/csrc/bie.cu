@@ -446,6 +446,9 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
   }
   if (!proj.empty()) {  // every projected-form group in one launch; it reads the FP64 density directly
     Phase ph(ctx, self_phase_name<R>(), s);
+    if constexpr (std::is_same<R, float>::value) {
+      if (ctx->cfg.tensor_rotation) return launch_self_tc(proj, dens, g->vals.ptr, s);
+    }
     BIE_TRY((launch_self_proj<R, double>(proj, dens, g->vals.ptr, s)));
   }
   return BIE_OK;
@@ -2163,6 +2166,7 @@ void bie_config_default(bie_config* cfg) {
   cfg->n_interp = 8;
   cfg->self_direct = 0;
   cfg->use_graphs = 1;
+  cfg->tensor_rotation = 1;
 }
 
 const char* bie_strerror(int st) {
@@ -2799,6 +2803,185 @@ int bie_step_coupled(bie_ctx* ctx, int ndrop, const int* p, const int* pq, const
   return BIE_OK;
 }
 
+void bie_reparam_opts_default(bie_reparam_opts* o) {
+  if (!o) return;
+  o->u_rep = 2;
+  o->p_cutoff = 0.05;
+  o->smooth = 0;
+  o->dtau = 0.5;
+  o->eps = 1e-10;
+  o->max_iter = 200;
+}
+
+}  // extern "C"
+
+namespace bie {
+
+// Alg. 2 for one degree group: drops `drops` of degree p, coefficients at voff[d] (shape) and
+// soff[d] (surfactant) in the caller's arrays.
+static int reparam_group(bie_ctx* ctx, int p, const std::vector<int>& drops, const std::vector<long long>& voff,
+                         const std::vector<long long>& soff, double* xcoef, double* gammacoef,
+                         const bie_reparam_opts* o, bie_reparam_info* info, cudaStream_t s) {
+  const int P = o->u_rep * (p + 1) - 1;
+  const long long nd = (long long)drops.size();
+  const long long N = ngrid(P), nC = ncoef(P);
+  Plan *plP, *plp;
+  BIE_TRY(get_plan(ctx, P, P, &plP));  // synthesis of the energy gradient, analysis at degree P
+  BIE_TRY(get_plan(ctx, p, P, &plp));  // the final analysis to degree p
+  // recursion coefficients (a, b) of the normalised associated Legendre functions, rows of order m
+  std::vector<double> ab(2 * (size_t)(P + 1) * (P + 2) / 2, 0.0);
+  for (int m = 0; m <= P; ++m)
+    for (int n = m + 2; n <= P; ++n) {
+      const long long r = 2 * ((long long)m * (P + 1) - (long long)m * (m - 1) / 2 + (n - m));
+      ab[r] = std::sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+      ab[r + 1] = -std::sqrt(((double)(n - 1) * (n - 1) - (double)m * m) / (4.0 * (n - 1) * (n - 1) - 1.0));
+    }
+  std::vector<double> tn, wn;
+  gauss_legendre(P + 1, tn, wn);
+  std::vector<long long> vo, so, vof, sof;
+  for (int d : drops) {
+    vo.push_back(voff[d]);
+    so.push_back(soff[d]);
+    for (int c = 0; c < 3; ++c) vof.push_back(voff[d] + c * ncoef(p));
+    sof.push_back(soff[d]);
+  }
+  DevBuf<double> dab, dnodes, x0, xt, sc, th, ph, E, gradE, gv, gmax, H, F, a_d, norms, gE;
+  DevBuf<long long> dvo, dso, dvof, dsof;
+  DevBuf<int> active;
+  BIE_TRY(dab.upload(ab));
+  BIE_TRY(dnodes.upload(tn));
+  BIE_TRY(dvo.upload(vo));
+  BIE_TRY(dso.upload(so));
+  BIE_TRY(dvof.upload(vof));
+  BIE_TRY(dsof.upload(sof));
+  for (DevBuf<double>* b : {&x0, &xt, &sc}) BIE_TRY(b->alloc(nd * 3 * nC));
+  for (DevBuf<double>* b : {&th, &ph}) BIE_TRY(b->alloc(nd * N));
+  BIE_TRY(E.alloc(nd * 9 * N));
+  for (DevBuf<double>* b : {&gradE, &gv}) BIE_TRY(b->alloc(nd * 3 * N));
+  BIE_TRY(gmax.alloc(nd));
+  BIE_TRY(H.alloc(nd * 3 * (P + 1) * (size_t)(P + 1) * 2));
+  BIE_TRY(F.alloc(nd * 3 * (P + 1) * (size_t)(P + 1) * 2));
+  BIE_TRY(a_d.alloc(nd * (P + 1)));
+  BIE_TRY(norms.alloc(nd * (P + 1) * 2));
+  BIE_TRY(active.alloc(nd));
+  // x~ = x0 = the shape zero-padded to degree P; the angles start at the grid points
+  BIE_TRY(launch_pad_coef(xcoef, dvo.ptr, p, P, nd, 3, x0.ptr, s));
+  BIE_CUDA_TRY(cudaMemcpyAsync(xt.ptr, x0.ptr, nd * 3 * nC * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  BIE_TRY(launch_grid_points(dnodes.ptr, P, nd, th.ptr, ph.ptr, s));
+  BIE_TRY(launch_eval_points(x0.ptr, 3, P, nd, N, th.ptr, ph.ptr, dab.ptr, 1, E.ptr, s));
+  std::vector<int> act(nd, 1), steps(nd, 0);
+  std::vector<double> nrm(nd * (P + 1) * 2), av(nd * (P + 1)), gm(nd, 0.0), en(nd, 0.0);
+  for (int it = 0; it < o->max_iter; ++it) {
+    // adaptive cutoff (Eq. ncutoff_adaptive) and attenuation per drop, from the current x~
+    BIE_TRY(launch_mode_norms(xt.ptr, P, nd, norms.ptr, s));
+    BIE_CUDA_TRY(cudaMemcpyAsync(nrm.data(), norms.ptr, nrm.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+    for (long long d = 0; d < nd; ++d) {
+      const double* nd_ = nrm.data() + d * (P + 1) * 2;
+      double n1 = 0.0;
+      for (int n = 1; n <= P; ++n) n1 += nd_[2 * n];
+      int ncut = P;
+      double tail = n1;  // sum over n >= l of the per-degree norm sums
+      for (int l = 2; l <= P; ++l) {
+        tail -= nd_[2 * (l - 1)];
+        if (tail / n1 < o->p_cutoff) {
+          ncut = l;
+          break;
+        }
+      }
+      double e = 0.0;
+      for (int n = 0; n <= P; ++n) {
+        const double a = n >= ncut ? (o->smooth ? (double)n / P : 1.0) : 0.0;
+        av[d * (P + 1) + n] = a;
+        e += a * nd_[2 * n + 1];
+      }
+      if (it == 0) info->energy_first_max = std::max(info->energy_first_max, e);
+      if (act[d]) en[d] = e;
+    }
+    BIE_CUDA_TRY(cudaMemcpyAsync(a_d.ptr, av.data(), av.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    // grad E = 2 sum_n a_n x~_n^m Y_n^m on the grid (Eq. energy_rep), its tangential part at the points
+    BIE_TRY(launch_scale_degrees(xt.ptr, a_d.ptr, P, nd, 3, 2.0, sc.ptr, s));
+    BIE_TRY((launch_leg_synth<double, double>(sc.ptr, nullptr, nC, nd * 3, P, plP->T0.ptr, P + 1, H.ptr, 0, s)));
+    BIE_TRY((launch_phi_synth<double, double>(H.ptr, nd * 3, P, P, plP->cs.ptr, gradE.ptr, nullptr, N, s)));
+    BIE_TRY(launch_rep_gradient(E.ptr, gradE.ptr, N, nd, gv.ptr, gmax.ptr, s));
+    BIE_CUDA_TRY(cudaMemcpyAsync(gm.data(), gmax.ptr, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+    int nact = 0;
+    for (long long d = 0; d < nd; ++d) {
+      if (act[d] && !(gm[d] >= o->eps)) act[d] = 0;  // the stopping test of Alg. 2 (NaN stops too)
+      nact += act[d];
+    }
+    if (!nact) break;
+    // forward Euler step of the angles, then the original expansion at the new angles analysed on the
+    // grid (Eq. rep_trasf1)
+    BIE_CUDA_TRY(cudaMemcpyAsync(active.ptr, act.data(), nd * sizeof(int), cudaMemcpyHostToDevice, s));
+    BIE_TRY(launch_rep_step(E.ptr, gv.ptr, N, nd, active.ptr, o->dtau, th.ptr, ph.ptr, s));
+    for (long long d = 0; d < nd; ++d) steps[d] += act[d];
+    BIE_TRY(launch_eval_points(x0.ptr, 3, P, nd, N, th.ptr, ph.ptr, dab.ptr, 1, E.ptr, s));
+    BIE_TRY(launch_analyze(E.ptr, nullptr, 3 * N, nd * 3, P, P, plP->cs.ptr, plP->A.ptr, F.ptr, xt.ptr, nullptr, nC,
+                           s));
+  }
+  for (long long d = 0; d < nd; ++d) {
+    info->iterations = std::max(info->iterations, steps[d]);
+    info->converged += act[d] ? 0 : 1;
+    info->g_max = std::max(info->g_max, gm[d]);
+    info->energy_last_max = std::max(info->energy_last_max, en[d]);
+  }
+  // Eq. rep_trasf2: the surfactant at the final angles; shape and surfactant analysed to degree p
+  BIE_TRY(launch_analyze(E.ptr, nullptr, 3 * N, nd * 3, P, p, plp->cs.ptr, plp->A.ptr, F.ptr, xcoef, dvof.ptr, 0, s));
+  if (gammacoef) {
+    BIE_TRY(launch_pad_coef(gammacoef, dso.ptr, p, P, nd, 1, x0.ptr, s));
+    BIE_TRY(gE.alloc(nd * N));
+    BIE_TRY(launch_eval_points(x0.ptr, 1, P, nd, N, th.ptr, ph.ptr, dab.ptr, 0, gE.ptr, s));
+    BIE_TRY(launch_analyze(gE.ptr, nullptr, N, nd, P, p, plp->cs.ptr, plp->A.ptr, F.ptr, gammacoef, dsof.ptr, 0, s));
+  }
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return BIE_OK;
+}
+
+}  // namespace bie
+
+extern "C" {
+
+int bie_reparametrize(bie_ctx* ctx, int ndrop, const int* p, double* xcoef, double* gammacoef,
+                      const bie_reparam_opts* opts, bie_reparam_info* info, void* stream) {
+  if (!ctx || !p || !xcoef || !opts || !info || ndrop <= 0) {
+    set_error("bie_reparametrize: null or empty argument");
+    return BIE_EINVAL;
+  }
+  if (opts->u_rep < 1 || !(opts->p_cutoff > 0.0 && opts->p_cutoff < 1.0) || !(opts->dtau > 0.0) ||
+      !(opts->eps > 0.0) || opts->max_iter < 0) {
+    set_error("bie_reparametrize: need u_rep >= 1, 0 < p_cutoff < 1, dtau > 0, eps > 0, max_iter >= 0");
+    return BIE_EINVAL;
+  }
+  BIE_TRY(check_degrees(ndrop, p));
+  for (int d = 0; d < ndrop; ++d)
+    if (opts->u_rep * (p[d] + 1) - 1 > 4 * BIE_MAX_P) {
+      set_error("bie_reparametrize: working degree u_rep (p+1) - 1 above 4 BIE_MAX_P");
+      return BIE_EINVAL;
+    }
+  if (ndrop > 65535) {
+    set_error("bie_reparametrize: at most 65535 drops per call");
+    return BIE_EINVAL;
+  }
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::memset(info, 0, sizeof(*info));
+  Phase ph(ctx, "reparametrize", s);
+  std::vector<long long> voff(ndrop), soff(ndrop);
+  std::map<int, std::vector<int>> byp;
+  long long v = 0, g = 0;
+  for (int d = 0; d < ndrop; ++d) {
+    voff[d] = v;
+    soff[d] = g;
+    v += 3 * ncoef(p[d]);
+    g += ncoef(p[d]);
+    byp[p[d]].push_back(d);
+  }
+  for (auto& kv : byp) BIE_TRY(reparam_group(ctx, kv.first, kv.second, voff, soff, xcoef, gammacoef, opts, info, s));
+  return BIE_OK;
+}
+
 double bie_next_dt(double dt, double err, double tol, double dt_max) {
   if (!(err > 0.0)) return dt_max;
   return std::min(dt_max, dt * std::sqrt(0.9 * tol / err));
@@ -2807,7 +2990,7 @@ double bie_next_dt(double dt, double err, double tol, double dt_max) {
 int bie_run_coupled(bie_ctx* ctx, int ndrop, const int* p, const int* pq, double* xcoef, double* gammacoef,
                     double elasticity, double x_s, const double* lambda, double shear, double inv_pe, double T,
                     double dt0, double tol, double dt_max, int estimator, int max_steps, const bie_solve_opts* opts,
-                    bie_run_info* info, void* stream) {
+                    const bie_reparam_opts* reparam, bie_run_info* info, void* stream) {
   if (!ctx || !p || !xcoef || !gammacoef || !info || !(T > 0.0) || !(dt0 > 0.0) || !(tol > 0.0) ||
       !(dt_max > 0.0) || max_steps < 1 || (estimator != BIE_ERR_CONSERVATION && estimator != BIE_ERR_IMEX1)) {
     set_error("null argument or bad run parameters");
@@ -2843,6 +3026,11 @@ int bie_run_coupled(bie_ctx* ctx, int ndrop, const int* p, const int* pq, double
       u0_valid = 0;
       info->steps_accepted++;
       info->err_max_accepted = std::max(info->err_max_accepted, err);
+      if (reparam) {  // Alg. 2 after every kept step
+        bie_reparam_info ri;
+        BIE_TRY(bie_reparametrize(ctx, ndrop, p, xcoef, gammacoef, reparam, &ri, stream));
+        info->reparam_iterations += ri.iterations;
+      }
     } else {
       info->steps_rejected++;
     }

@@ -121,6 +121,9 @@ int launch_split_dff(const double* in, dff* out, long long n, cudaStream_t s);
 // All projected-form groups in one launch (eight groups per launch at most).
 template <typename R, typename CT>
 int launch_self_proj(std::vector<SelfGroup<R>> groups, const CT* dens, double* vals, cudaStream_t s);
+// The FP32 projected form with the Wigner rotation on the tensor cores (self_tc.cu).
+int launch_self_tc(std::vector<SelfGroup<float>> groups, const double* dens, double* vals, cudaStream_t s);
+size_t self_tc_smem(int p, int nbl);
 // interfacial force at N grid points from x derivatives [6][3][N] and Gamma derivatives [3][N]
 int launch_force(const double* X, const double* Gm, long long N, double es, double xs, double* f, cudaStream_t s);
 // out[i] = (float) in[i]
@@ -146,5 +149,27 @@ int launch_implicit_combine(const double* y, const double* c, double a, const do
                             double* w, cudaStream_t s);
 // y = x * sc (elementwise)
 int launch_mul(const double* x, const double* sc, long long n, double* y, cudaStream_t s);
+
+// ---- angle reparametrisation (reparam.cu) ----
+// zero-padded copies [d][c][(P+1)^2] of degree-p coefficients at src + off[d] + c (p+1)^2
+int launch_pad_coef(const double* src, const long long* off, int p, int P, long long nd, int ncomp, double* dst,
+                    cudaStream_t s);
+// values (and, with derivs, theta and phi derivatives) of nf (1 or 3) expansions of degree P per drop at the
+// N points (th, ph)[d][N]: out[d][f][kind][N]; ab = recursion coefficients (a, b) per (m, n), rows of order m
+int launch_eval_points(const double* coef, int nf, int P, long long nd, long long N, const double* th,
+                       const double* ph, const double* ab, int derivs, double* out, cudaStream_t s);
+// norms[d][n][2] = (sum_m |x_n^m|, sum_m |x_n^m|^2), m = -n..n, of [d][3][(P+1)^2]
+int launch_mode_norms(const double* coef, int P, long long nd, double* norms, cudaStream_t s);
+// out = scale * a[d][n] * in, per drop and degree
+int launch_scale_degrees(const double* in, const double* a, int P, long long nd, int ncomp, double scale, double* out,
+                         cudaStream_t s);
+// g = tangential part of gradE at the points (E = x0 and its derivatives there), gmax[d] = max |g|
+int launch_rep_gradient(const double* E, const double* gradE, long long N, long long nd, double* g, double* gmax,
+                        cudaStream_t s);
+// forward Euler step of the angles of the active drops with the pseudo-velocity -g
+int launch_rep_step(const double* E, const double* g, long long N, long long nd, const int* active, double dtau,
+                    double* th, double* ph, cudaStream_t s);
+// the degree-P grid's parameter points for nd drops, from the Gauss nodes t_j
+int launch_grid_points(const double* nodes, int P, long long nd, double* th, double* ph, cudaStream_t s);
 
 }  // namespace bie

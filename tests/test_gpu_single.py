@@ -18,13 +18,17 @@ MIXED_TOL = 2e-6  # FP32 rounding of the single-drop applies: measured 5.9e-8 ..
 DF_TOL = 1e-11  # double-float: about 44 bits per operation
 
 
-@pytest.fixture(scope="module", params=[False, True], ids=["projected", "direct"])
+@pytest.fixture(scope="module", params=[(False, True), (True, True), (False, False)],
+                ids=["projected", "direct", "projected-cuda-core-rotation"])
 def ctx(request):
+    # projected self form with the mixed rotation on the tensor cores (default), the direct form, and
+    # the projected form with the mixed rotation on the CUDA cores
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1707_02156_gb300 import api, build
     build.build()
-    return api.Context(0, self_direct=request.param)
+    direct, tc = request.param
+    return api.Context(0, self_direct=direct, tensor_rotation=tc)
 
 
 def dev(a):

@@ -89,7 +89,21 @@ def test_null_arguments_are_rejected_before_any_device_work(L):
     assert L.bie_step_coupled(None, 1, p, p, x, x, x, 0, 0.2, 0.0, lam, 1.0, 0.1, 0.01, 0, ctypes.byref(o), x, x,
                               ctypes.byref(cinfo), None) == EINVAL
     assert L.bie_run_coupled(None, 1, p, p, x, x, 0.2, 0.0, lam, 1.0, 0.1, 1.0, 0.1, 1e-5, 0.1, 0, 10,
-                             ctypes.byref(o), ctypes.byref(rinfo), None) == EINVAL
+                             ctypes.byref(o), None, ctypes.byref(rinfo), None) == EINVAL
+    # angle reparametrisation: null handles, then options out of range
+    ro = api.bie_reparam_opts()
+    L.bie_reparam_opts_default(ctypes.byref(ro))
+    assert (ro.u_rep, ro.p_cutoff, ro.smooth, ro.dtau, ro.eps, ro.max_iter) == (2, 0.05, 0, 0.5, 1e-10, 200)
+    pinfo = api.bie_reparam_info()
+    assert L.bie_reparametrize(None, 1, p, x, x, ctypes.byref(ro), ctypes.byref(pinfo), None) == EINVAL
+    assert L.bie_reparametrize(ctypes.c_void_p(16), 1, p, None, x, ctypes.byref(ro), ctypes.byref(pinfo),
+                               None) == EINVAL
+    for field, bad in (("u_rep", 0), ("p_cutoff", 1.0), ("dtau", 0.0), ("eps", -1.0)):
+        r2 = api.bie_reparam_opts()
+        L.bie_reparam_opts_default(ctypes.byref(r2))
+        setattr(r2, field, bad)
+        assert L.bie_reparametrize(ctypes.c_void_p(16), 1, p, x, x, ctypes.byref(r2), ctypes.byref(pinfo),
+                                   None) == EINVAL, field
     # status strings
     assert L.bie_strerror(0) == b"ok"
     assert L.bie_strerror(EINVAL) == b"invalid argument"
