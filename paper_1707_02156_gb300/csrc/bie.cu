@@ -315,6 +315,7 @@ struct bie_geom {
   bie::DevBuf<double> centre_d, partial, wS_all, wD_all, wSr_all, wDr_all;
   int nblk = 0, ntile = 0;
   int tpt32 = 2, tpt64 = 2;                         // targets per thread of the pair kernel (autotuned FP32)
+  bie::DevBuf<float> eo32;                          // rotated sums of the tensor-core self path (one chunk of drops)
   std::vector<std::pair<long long, int>> near;      // (target, source drop) pairs in Omega_2
   // near-singular step (Omega_2), Sec. 2.3
   int nnear_tgt = 0;
@@ -447,7 +448,12 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
   if (!proj.empty()) {  // every projected-form group in one launch; it reads the FP64 density directly
     Phase ph(ctx, self_phase_name<R>(), s);
     if constexpr (std::is_same<R, float>::value) {
-      if (ctx->cfg.tensor_rotation) return launch_self_tc(proj, dens, g->vals.ptr, s);
+      if (ctx->cfg.tensor_rotation) {
+        // E/O sums of a chunk of drops kept within 32 MB, so that they stay in L2 between the two kernels
+        const long long budget = 8LL << 20;
+        BIE_TRY(g->eo32.alloc((size_t)self_tc_eo_floats(proj, budget)));
+        return launch_self_tc(proj, dens, g->vals.ptr, g->eo32.ptr, budget, s);
+      }
     }
     BIE_TRY((launch_self_proj<R, double>(proj, dens, g->vals.ptr, s)));
   }
@@ -691,9 +697,10 @@ static int drop_stats(const double* rec, long long N, const double* c, double* v
 
 static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s);
 
-// Autotuner of the FP32 pair kernel: for large work lists, time the targets-per-thread variants
-// (1, 2, 4) once on this geometry's work list (double layer, zero densities: the cost does not
-// depend on the values) and keep the fastest.
+// Autotuner of the FP32 pair kernel: for large work lists, time the variants (targets per thread 1,
+// 2, 4; packed lane pairs for 2 and 4; with or without pipelined source staging) once on this
+// geometry's work list (double layer, zero densities: the cost does not depend on the values) and
+// keep the fastest.
 static int autotune_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   const long long pairs = g->info.far_pairs + g->info.up_pairs;
   g->info.interdrop_tpt = g->tpt32;
@@ -706,12 +713,14 @@ static int autotune_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   BIE_CUDA_TRY(cudaEventCreate(&e0));
   BIE_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  const int cand[3] = {1, 2, 4};
+  // targets per thread 1 (scalar FP32), 2 and 4 (packed lane pairs), and 12, 14 (packed, with the
+  // next chunk of sources loaded while the current one is summed)
+  const int cand[5] = {1, 2, 4, 12, 14};
   // time a leading part of the work list of about 5e10 pairs (at least 32 blocks per SM); blocks carry
   // similar work, so its ranking is the full list's
   const int nsample = (int)std::min<long long>(
       g->nblk, std::max<long long>(32LL * ctx->sms, (long long)((double)g->nblk * std::min(1.0, 5e10 / (double)pairs))));
-  for (int ci = 0; ci < 3; ++ci) {
+  for (int ci = 0; ci < 5; ++ci) {
     cudaEventRecord(e0, s);
     int st = launch_interdrop<float>(1, cand[ci], nsample, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr,
                                      g->tile_n.ptr, g->tile_drop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr,

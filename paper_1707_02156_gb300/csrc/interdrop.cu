@@ -251,8 +251,10 @@ struct alignas(16) SrcRecX2 {
 // targets tid + u * (128/TPT) taken two by two (u = 2w, 2w + 1 share lane pair w).  The tile's FP64
 // target coordinates and the FP64 accumulators live in shared memory, not in registers, so that
 // more warps fit per SM; the source loop takes two sources per iteration (2 x TPT/2 independent
-// chains per thread).
-template <int KIND, int TPT>
+// chains per thread).  PF = 1 software-pipelines the staging: the next chunk's sources are loaded
+// into registers while the current chunk is summed, so the global-memory latency of the staging
+// overlaps the arithmetic.
+template <int KIND, int TPT, int PF>
 __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
     const PairItem* __restrict__ items, const int* __restrict__ blk_item, const long long* __restrict__ tile_t0,
     const int* __restrict__ tile_n, const int* __restrict__ tile_drop, const long long* __restrict__ tgt_loc,
@@ -265,6 +267,7 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
   constexpr int NW = TPT / 2;  // lane pairs per thread
   constexpr int NV = KIND ? 9 : 6;
   constexpr int nv = (NV + 1) / 2;  // 128-bit loads per staged source
+  constexpr int RPT = kChunkX2 / NT;  // staged sources per thread and chunk
   __shared__ SrcRecX2 src[kChunkX2];
   __shared__ double tgt[3][kTile];  // the tile's target coordinates (zero past the tile's end)
   __shared__ double acc[3][kTile];  // per-target sums over the block's items
@@ -294,6 +297,40 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
   // the block's shared arrays are written before any thread reads them (the first staging barrier
   // below comes after the target loads; each thread reads only its own targets' entries)
   __syncthreads();
+  // sources c0 + tid + r NT of a chunk, r < RPT (zero past the item's end: zero weight)
+  auto load_chunk = [&](float (&v)[RPT][NV], const float* X, const float* N, const float* Q, long long ld,
+                        long long c0, long long s1) {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const long long sidx = c0 + tid + r * NT;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) v[r][q] = 0.f;
+      if (sidx < s1) {
+        v[r][0] = X[sidx];
+        v[r][1] = X[ld + sidx];
+        v[r][2] = X[2 * ld + sidx];
+        v[r][3] = Q[sidx];
+        v[r][4] = Q[ld + sidx];
+        v[r][5] = Q[2 * ld + sidx];
+        if (KIND) {
+          v[r][6] = N[sidx];
+          v[r][7] = N[ld + sidx];
+          v[r][8] = N[2 * ld + sidx];
+        }
+      }
+    }
+  };
+  auto store_chunk = [&](const float (&v)[RPT][NV]) {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      SrcRecX2 rec;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) rec.v[q] = x2_pack(v[r][q], v[r][q]);
+#pragma unroll
+      for (int q = NV; q < 10; ++q) rec.v[q] = 0ull;
+      src[tid + r * NT] = rec;
+    }
+  };
   for (int it = it0; it < it1; ++it) {
     const int j = items[it].src_drop;
     unsigned act = 0u;  // bit u: target tid + u * NT is in this item
@@ -318,37 +355,14 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
     const float* Q = grid ? Qu : Qs;
     const long long ld = grid ? nup : nstd;
     const long long s0 = items[it].s0, s1 = items[it].s1;
+    float pre[RPT][NV];
+    if (PF) load_chunk(pre, X, N, Q, ld, s0, s1);
     for (long long c0 = s0; c0 < s1; c0 += kChunkX2) {
       const int cn = (int)min((long long)kChunkX2, s1 - c0);
-      for (int k = tid; k < kChunkX2; k += NT) {
-        // sources past the item's end are staged as zero weight (q = 0), so the loop below runs
-        // over whole pairs of sources; their distance is |target - 0|, never zero for a target
-        // outside the source drop
-        float v[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] = 0.f;
-        if (k < cn) {
-          const long long sidx = c0 + k;
-          v[0] = X[sidx];
-          v[1] = X[ld + sidx];
-          v[2] = X[2 * ld + sidx];
-          v[3] = Q[sidx];
-          v[4] = Q[ld + sidx];
-          v[5] = Q[2 * ld + sidx];
-          if (KIND) {
-            v[6] = N[sidx];
-            v[7] = N[ld + sidx];
-            v[8] = N[2 * ld + sidx];
-          }
-        }
-        SrcRecX2 r;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) r.v[q] = x2_pack(v[q], v[q]);
-#pragma unroll
-        for (int q = NV; q < 10; ++q) r.v[q] = 0ull;
-        src[k] = r;
-      }
+      if (!PF) load_chunk(pre, X, N, Q, ld, c0, s1);
+      store_chunk(pre);
       __syncthreads();
+      if (PF && c0 + kChunkX2 < s1) load_chunk(pre, X, N, Q, ld, c0 + kChunkX2, s1);  // next chunk, in flight
       if (act) {
         const int cn2 = (cn + 1) & ~1;
         for (int k = 0; k < cn2; k += 2) {
@@ -702,7 +716,7 @@ int launch_classify(const double* rec_std, long long ntarget, const int* tdrop, 
   return BIE_OK;
 }
 
-template <typename R, int TPT>
+template <typename R, int TPT, int PF = 0>
 static void interdrop_kernel(int kind, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
                              const int* tile_n, const int* tile_drop, const long long* tgt_loc,
                              const long long* toff_std, const int* ngd, const double* rec_std, const double* centre,
@@ -711,13 +725,13 @@ static void interdrop_kernel(int kind, int nblk, const PairItem* items, const in
   if constexpr (std::is_same<R, float>::value && TPT % 2 == 0) {
     // FP32 with two or more targets per thread: packed lane pairs
     if (kind == 0)
-      k_interdrop_x2<0, TPT><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
-                                                          toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu,
-                                                          Qu, nup, wts, partial);
+      k_interdrop_x2<0, TPT, PF><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
+                                                              toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu,
+                                                              Nu, Qu, nup, wts, partial);
     else
-      k_interdrop_x2<1, TPT><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
-                                                          toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu,
-                                                          Qu, nup, wts, partial);
+      k_interdrop_x2<1, TPT, PF><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
+                                                              toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu,
+                                                              Nu, Qu, nup, wts, partial);
     return;
   }
   if (kind == 0)
@@ -737,6 +751,17 @@ int launch_interdrop(int kind, int tpt, int nblk, const PairItem* items, const i
                      const R* Qs, long long nstd, const R* Xu, const R* Nu, const R* Qu, long long nup,
                      const double* wts, double* partial, cudaStream_t s) {
   if (nblk == 0) return BIE_OK;
+  if (std::is_same<R, float>::value && (tpt == 12 || tpt == 14)) {  // packed FP32, pipelined staging
+    if (tpt == 12)
+      interdrop_kernel<R, 2, 1>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
+                                rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);
+    else
+      interdrop_kernel<R, 4, 1>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
+                                rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);
+    count_launch();
+    BIE_CUDA_TRY(cudaGetLastError());
+    return BIE_OK;
+  }
   if (tpt == 1)
     interdrop_kernel<R, 1>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd, rec_std,
                            centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);

@@ -121,9 +121,12 @@ int launch_split_dff(const double* in, dff* out, long long n, cudaStream_t s);
 // All projected-form groups in one launch (eight groups per launch at most).
 template <typename R, typename CT>
 int launch_self_proj(std::vector<SelfGroup<R>> groups, const CT* dens, double* vals, cudaStream_t s);
-// The FP32 projected form with the Wigner rotation on the tensor cores (self_tc.cu).
-int launch_self_tc(std::vector<SelfGroup<float>> groups, const double* dens, double* vals, cudaStream_t s);
-size_t self_tc_smem(int p, int nbl);
+// The FP32 projected form with the Wigner rotation on the tensor cores (self_tc.cu): per chunk of
+// drops of one degree, the rotation products into eo (at most `budget` floats per chunk, at least one
+// drop's worth), then the contraction with the factors.  self_tc_eo_floats = the buffer it needs.
+long long self_tc_eo_floats(const std::vector<SelfGroup<float>>& groups, long long budget);
+int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* dens, double* vals, float* eo,
+                   long long budget, cudaStream_t s);
 // interfacial force at N grid points from x derivatives [6][3][N] and Gamma derivatives [3][N]
 int launch_force(const double* X, const double* Gm, long long N, double es, double xs, double* f, cudaStream_t s);
 // out[i] = (float) in[i]

@@ -6,17 +6,16 @@
 //     Re rho'_{n m'} = sum_{m=0..n} C[m'][m] Re g_m,   Im rho'_{n m'} = sum_{m=1..n} S[m'-1][m-1] Im g_m.
 // Splitting the input orders m by parity gives the even and odd partial sums E, O, from which the
 // four targets (theta_a, phi_b), (theta_a, phi_b + pi), (pi - theta_a, phi_b), (pi - theta_a,
-// phi_b + pi) follow exactly (the symmetries are those of the CUDA-core kernel k_self_proj).  With
-// the block's NB longitudes b, three components and two parities as columns, each degree is the
-// matrix product
-//     [E | O](m', (b, c, parity)) = W_n(m', m) G_n(m, (b, c, parity)),
-// W_n = C (rows m' = 0..n) or S (rows m' = 1..n), G_n(m, (b, c, par)) = g_m(b, c) when m has the
-// column's parity and 0 otherwise.  It runs as mma.sync m16n8k8 in TF32 with the 3-pass split
-// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (a = a_hi + a_lo, each part a TF32 number), accumulated in
-// FP32, which keeps the products to about FP32 accuracy.  The result goes to shared memory and is
-// contracted there with the targets' projected kernel factors Q (CUDA cores, Q streamed from HBM).
-//
-// One block per (drop, latitude pair a, chunk of NB longitudes); 8 warps share the degree tiles.
+// phi_b + pi) follow exactly (the symmetries of the CUDA-core kernel k_self_proj).  With every
+// longitude b < p+1 of the latitude, the three components and the two parities as columns, each
+// (latitude, degree) is one matrix product
+//     [E | O](m', (b, c, parity)) = W(m', m) G(m, (b, c, parity)),
+// W = C (rows m' = 0..n) or S (rows m' = 1..n), G(m, (b, c, par)) = g_m(b, c) when m has the
+// column's parity, else 0.  k_rot_tc runs these products as mma.sync m16n8k8 in TF32 with the
+// 3-pass split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (x = x_hi + x_lo, both TF32), accumulated in
+// FP32 (about FP32 accuracy), and writes E and O to a buffer that stays in L2 for one drop's worth
+// of latitudes (drops are taken in chunks whose sums fit a fixed buffer); k_contract_eo then streams the projected kernel factors Q from HBM and contracts
+// them with E +- O, one block per target quadruple.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,131 +57,122 @@ __device__ __forceinline__ void sym_mul_add_f(const float* q, const float* v, fl
   acc[2] = fmaf(q[2], v[2], fmaf(q[5], v[1], fmaf(q[4], v[0], acc[2])));
 }
 
-// Number of 16-row tiles of the degree-n products: real part n+1 rows, imaginary part n rows.
-__device__ __forceinline__ int tiles_of(int n) { return (n + 1 + 15) / 16 + (n + 15) / 16; }
+// Offset of the rotated sums of (drop ld, latitude pair a, longitude b) in the E/O buffer of one
+// launch (a chunk of drops of one degree): [ld][a][b][packed (n, m')][c][parity].
+__device__ __forceinline__ long long eo_offset(long long ld, int a, int b, int p) {
+  const int hb = p + 1, na2 = (p + 2) / 2, nc = (p + 1) * (p + 1);
+  return (((ld * na2 + a) * hb + b) * (long long)nc) * 6;
+}
 
-template <int NB>
-__global__ void __launch_bounds__(kTcThreads) k_self_tc(SelfGroups<float> G, const double* __restrict__ dens,
-                                                        double* __restrict__ vals) {
-  constexpr int NCOL = NB * 6;             // columns (b, c, parity)
-  constexpr int NTN = (NCOL + 7) / 8;      // 8-column tiles
+// One block per (drop, latitude pair a, degree n): stage the Wigner blocks C, S of (a, n) and the
+// phase-shifted coefficients G of every longitude, then the two products on the tensor cores.
+__global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const double* __restrict__ dens,
+                                                       float* __restrict__ EO) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float red[kTcWarps][NB * 12];
-  SelfGroup<float> A = G.g[0];
+  const int p = A.p;
+  const int hb = p + 1, nb = 2 * p + 2;
+  const long long bid = blockIdx.x;
+  const int n = (int)(bid % (p + 1));
+  const long long r = bid / (p + 1);
+  const int na2 = (p + 2) / 2;
+  const int a = (int)(r % na2);
+  const long long ld = r / na2;
+  const int NCOL = hb * 6;            // columns (b, c, parity)
+  const int NTN = (NCOL + 7) / 8;     // 8-column tiles
+  float* Wc = reinterpret_cast<float*>(smem_raw);  // (n+1)^2 column-major, then n^2
+  float* Ws = Wc + (n + 1) * (n + 1);
+  float* Gs = Ws + n * n;                           // [n + mm][b][c], mm = -n..n: Re g (mm >= 0), Im g (mm < 0)
+  const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
+  const float* blk = A.wblk + (long long)a * A.wstride + boff;
+  for (int i = threadIdx.x; i < (n + 1) * (n + 1) + n * n; i += blockDim.x) Wc[i] = blk[i];
+  for (int i = threadIdx.x; i < (2 * n + 1) * hb * 3; i += blockDim.x) {
+    const int c = i % 3, b = (i / 3) % hb, mm = i / (3 * hb) - n;
+    const int m = mm < 0 ? -mm : mm;
+    const double* f = dens + A.foff3[ld * 3 + c];
+    const float fr = (float)f[n * (n + 1) + m];
+    const float fi = m > 0 ? (float)f[n * (n + 1) - m] : 0.f;
+    const float co = A.ph[((long long)m * nb + b) * 2], si = A.ph[((long long)m * nb + b) * 2 + 1];
+    Gs[i] = mm >= 0 ? fr * co - fi * si : fr * si + fi * co;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gq = lane >> 2, tq = lane & 3;
+  const int mt_re = (n + 1 + 15) / 16, mt_im = (n + 15) / 16;
+  const int units = (mt_re + mt_im) * NTN;
+  for (int u = warp; u < units; u += kTcWarps) {
+    const int nt = u % NTN, mu = u / NTN;
+    const bool im = mu >= mt_re;
+    const int mt = im ? mu - mt_re : mu;
+    const int M = im ? n : n + 1;  // rows = output orders; K = input orders (as many)
+    const float* W = im ? Ws : Wc;
+    const int r0 = mt * 16 + gq, r1 = r0 + 8;
+    const int j = nt * 8 + gq;     // this lane's B column
+    const int jb = j / 6, jc = (j >> 1) % 3, jp = j & 1;
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < M; k0 += 8) {
+      const int c0 = k0 + tq, c1 = c0 + 4;
+      // A fragment: W(row, col) column-major with M rows
+      const float a0 = (r0 < M && c0 < M) ? W[c0 * M + r0] : 0.f;
+      const float a1 = (r1 < M && c0 < M) ? W[c0 * M + r1] : 0.f;
+      const float a2 = (r0 < M && c1 < M) ? W[c1 * M + r0] : 0.f;
+      const float a3 = (r1 < M && c1 < M) ? W[c1 * M + r1] : 0.f;
+      unsigned ahi[4], alo[4];
+      tf32_split(a0, ahi[0], alo[0]);
+      tf32_split(a1, ahi[1], alo[1]);
+      tf32_split(a2, ahi[2], alo[2]);
+      tf32_split(a3, ahi[3], alo[3]);
+      // B fragment: rows k (input order index k, or k + 1 for the imaginary part), column j
+      unsigned bhi[2], blo[2];
+      const int kk[2] = {c0, c1};
 #pragma unroll
-  for (int i = 1; i < kMaxSelfGroups; ++i)
-    if (i < G.n && (long long)blockIdx.x >= G.g[i].begin) A = G.g[i];
+      for (int e = 0; e < 2; ++e) {
+        float bv = 0.f;
+        const int m = im ? kk[e] + 1 : kk[e];
+        if (kk[e] < M && j < NCOL && (m & 1) == jp) bv = Gs[((n + (im ? -m : m)) * hb + jb) * 3 + jc];
+        tf32_split(bv, bhi[e], blo[e]);
+      }
+      mma_tf32(d, alo, bhi);
+      mma_tf32(d, ahi, blo);
+      mma_tf32(d, ahi, bhi);
+    }
+    // D fragment: rows r0 / r1 (output order m' = row, or row + 1 for the imaginary part), columns
+    // nt*8 + 2 tq and + 1
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int row = e < 2 ? r0 : r1, col = nt * 8 + 2 * tq + (e & 1);
+      if (row < M && col < NCOL) {
+        const int pk = im ? n * (n + 1) - (row + 1) : n * (n + 1) + row;
+        const int b = col / 6, cp = col % 6;  // (c, parity) pair index
+        EO[eo_offset(ld, a, b, p) + (long long)pk * 6 + cp] = d[e];
+      }
+    }
+  }
+}
+
+// One block per target quadruple (drop, latitude pair a, longitude b): the E / O sums of every rotated
+// coefficient contracted with the four targets' projected factors (as k_self_proj: real parts with
+// the real planes, imaginary parts with the imaginary planes, whose signs the factors carry).
+__global__ void __launch_bounds__(kTcThreads) k_contract_eo(SelfGroup<float> A, const float* __restrict__ EO,
+                                                            double* __restrict__ vals) {
+  __shared__ float red[kTcWarps][12];
   const int p = A.p;
   const int ntri = (p + 1) * (p + 2) / 2;
   const int nc = (p + 1) * (p + 1);
   const int ng = (p + 1) * (2 * p + 2);
   const int hb = p + 1, nb = 2 * p + 2, na2 = (p + 2) / 2;
-  const int nbc = (hb + NB - 1) / NB;
-  const long long bid = (long long)blockIdx.x - A.begin;
-  const long long ld = bid / ((long long)na2 * nbc);
-  const int r = (int)(bid - ld * na2 * nbc);
-  const int a = r / nbc, b0 = (r - a * nbc) * NB;
-  const int nbh = min(NB, hb - b0);
+  const long long bid = blockIdx.x;
+  const long long ld = bid / ((long long)na2 * hb);
+  const int r = (int)(bid - ld * na2 * hb);
+  const int a = r / hb, b = r - a * hb;
   const int a2 = p - a;
   const bool quad = a2 != a;
-  float* gs = reinterpret_cast<float*>(smem_raw);  // [packed (n, m)][NB][3]: Re g (m >= 0), Im g (m < 0)
-  float* V = gs + (long long)nc * NB * 3;          // [packed (n, m')][(b, c, parity)]: E, O
-  // stage 0: g = e^{i m phi_b} rho_n^m for the block's longitudes (zero past the last one)
-  for (int i = threadIdx.x; i < nc * NB * 3; i += blockDim.x) {
-    const int c = i % 3, bb = (i / 3) % NB, rr = i / (3 * NB);
-    const int n = degree_of(rr);
-    const int m = rr - n * (n + 1);
-    float v = 0.f;
-    if (bb < nbh) {
-      const double* f = dens + A.foff3[ld * 3 + c];
-      const int mm = m < 0 ? -m : m;
-      const float fr = (float)f[n * (n + 1) + mm];
-      const float fi = mm > 0 ? (float)f[n * (n + 1) - mm] : 0.f;
-      const float co = A.ph[((long long)mm * nb + b0 + bb) * 2], si = A.ph[((long long)mm * nb + b0 + bb) * 2 + 1];
-      v = m >= 0 ? fr * co - fi * si : fr * si + fi * co;
-    }
-    gs[i] = v;
-  }
-  __syncthreads();
-  // stage 1: the rotation products on the tensor cores; the warps take the (degree, part, row tile)
-  // units in turn, highest degree first
-  const float* blk = A.wblk + (long long)a * A.wstride;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gq = lane >> 2, tq = lane & 3;
-  int unit = 0;
-  for (int n = p; n >= 0; --n) {
-    const int nt_re = (n + 1 + 15) / 16, nt_all = tiles_of(n);
-    const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
-    for (int u = 0; u < nt_all; ++u, ++unit) {
-      if ((unit % kTcWarps) != warp) continue;
-      const bool im = u >= nt_re;
-      const int mt = im ? u - nt_re : u;
-      const int M = im ? n : n + 1;  // rows = output orders; K = input orders (as many)
-      float d[NTN][4];
-#pragma unroll
-      for (int t = 0; t < NTN; ++t) d[t][0] = d[t][1] = d[t][2] = d[t][3] = 0.f;
-      const int r0 = mt * 16 + gq, r1 = r0 + 8;
-      for (int k0 = 0; k0 < M; k0 += 8) {
-        const int c0 = k0 + tq, c1 = c0 + 4;
-        // A fragment: W(row, col), W = C column-major (n+1)^2, or S column-major n^2 after C
-        float av[4];
-        const int rows[4] = {r0, r1, r0, r1}, cols[4] = {c0, c0, c1, c1};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const bool ok = rows[e] < M && cols[e] < M;
-          const long long off = im ? boff + (long long)(n + 1) * (n + 1) + (long long)cols[e] * n + rows[e]
-                                   : boff + (long long)cols[e] * (n + 1) + rows[e];
-          av[e] = ok ? __ldg(blk + off) : 0.f;
-        }
-        unsigned ahi[4], alo[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) tf32_split(av[e], ahi[e], alo[e]);
-#pragma unroll
-        for (int t = 0; t < NTN; ++t) {
-          // B fragment: rows k (input order index), column j = (b, c, parity)
-          const int j = t * 8 + gq;
-          const int kk[2] = {k0 + tq, k0 + tq + 4};
-          unsigned bhi[2], blo[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            float bv = 0.f;
-            const int m = im ? kk[e] + 1 : kk[e];
-            if (kk[e] < M && j < NCOL && (m & 1) == (j & 1)) {
-              const int bb = j / 6, c = (j >> 1) % 3;
-              const int pk = im ? n * (n + 1) - m : n * (n + 1) + m;
-              bv = gs[(pk * NB + bb) * 3 + c];
-            }
-            tf32_split(bv, bhi[e], blo[e]);
-          }
-          mma_tf32(d[t], alo, bhi);
-          mma_tf32(d[t], ahi, blo);
-          mma_tf32(d[t], ahi, bhi);
-        }
-      }
-      // D fragment: rows r0 / r1 (output order m' = row, or row + 1 for the imaginary part), columns
-      // 2 tq, 2 tq + 1 of each tile
-#pragma unroll
-      for (int t = 0; t < NTN; ++t)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int row = e < 2 ? r0 : r1, col = t * 8 + 2 * tq + (e & 1);
-          if (row < M && col < NCOL) {
-            const int pk = im ? n * (n + 1) - (row + 1) : n * (n + 1) + row;
-            V[pk * NCOL + col] = d[t][e];
-          }
-        }
-    }
-  }
-  __syncthreads();
-  // stage 2: contraction of every rotated coefficient with the four targets' factors (as k_self_proj:
-  // real parts with the real planes, imaginary parts with the imaginary planes, whose signs the
-  // factors carry)
-  float acc[NB][4][3];
-#pragma unroll
-  for (int bb = 0; bb < NB; ++bb)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[bb][k][0] = acc[bb][k][1] = acc[bb][k][2] = 0.f;
+  const float* eo = EO + eo_offset(ld, a, b, p);
   const long long qstride = 12 * (long long)ntri;
+  const float* Qk_[4] = {A.Q + (ld * ng + a * nb + b) * qstride, A.Q + (ld * ng + a * nb + b + hb) * qstride,
+                         A.Q + (ld * ng + a2 * nb + b) * qstride, A.Q + (ld * ng + a2 * nb + b + hb) * qstride};
+  float acc[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
   for (int i = threadIdx.x; i < nc; i += blockDim.x) {
     const int n = degree_of(i);
     const int o = i - n * n;
@@ -191,51 +181,38 @@ __global__ void __launch_bounds__(kTcThreads) k_self_tc(SelfGroups<float> G, con
     const int t = n * (n + 1) / 2 + mo;
     const int ri = re ? 0 : 1;
     const int pk = re ? n * (n + 1) + mo : n * (n + 1) - mo;
+    const float2 v01 = *reinterpret_cast<const float2*>(eo + (long long)pk * 6);
+    const float2 v23 = *reinterpret_cast<const float2*>(eo + (long long)pk * 6 + 2);
+    const float2 v45 = *reinterpret_cast<const float2*>(eo + (long long)pk * 6 + 4);
+    const float vp[3] = {v01.x + v01.y, v23.x + v23.y, v45.x + v45.y};
+    const float vm[3] = {v01.x - v01.y, v23.x - v23.y, v45.x - v45.y};
 #pragma unroll
-    for (int bb = 0; bb < NB; ++bb) {
-      if (bb >= nbh) break;
-      const int b = b0 + bb;
-      const float* v = V + pk * NCOL + bb * 6;
-      float vp[3], vm[3];
+    for (int k = 0; k < 4; ++k) {
+      if (k >= 2 && !quad) break;
+      const float* Qk = Qk_[k] + t;
+      float q[6];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        vp[c] = v[2 * c] + v[2 * c + 1];
-        vm[c] = v[2 * c] - v[2 * c + 1];
-      }
-      const long long tl[4] = {a * nb + b, a * nb + b + hb, a2 * nb + b, a2 * nb + b + hb};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (k >= 2 && !quad) break;
-        const float* Qk = A.Q + (ld * ng + tl[k]) * qstride + t;
-        float q[6];
-#pragma unroll
-        for (int e = 0; e < 6; ++e) q[e] = __ldg(Qk + (2 * e + ri) * (long long)ntri);
-        sym_mul_add_f(q, (k == 0 || k == 3) ? vp : vm, acc[bb][k]);
-      }
+      for (int e = 0; e < 6; ++e) q[e] = __ldg(Qk + (2 * e + ri) * (long long)ntri);
+      sym_mul_add_f(q, (k == 0 || k == 3) ? vp : vm, acc[k]);
     }
   }
-  // block reduction of the NB x 12 sums
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int bb = 0; bb < NB; ++bb)
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      for (int off = 16; off > 0; off >>= 1) acc[k][c] += __shfl_down_sync(0xffffffffu, acc[k][c], off);
+  if (lane == 0)
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        for (int off = 16; off > 0; off >>= 1) acc[bb][k][c] += __shfl_down_sync(0xffffffffu, acc[bb][k][c], off);
-  if (lane == 0)
-#pragma unroll
-    for (int bb = 0; bb < NB; ++bb)
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) red[warp][(bb * 4 + k) * 3 + c] = acc[bb][k][c];
+      for (int c = 0; c < 3; ++c) red[warp][k * 3 + c] = acc[k][c];
   __syncthreads();
-  for (int i = threadIdx.x; i < NB * 12; i += blockDim.x) {
-    const int bb = i / 12, k = (i / 3) % 4, c = i % 3;
-    if (bb >= nbh || (k >= 2 && !quad)) continue;
+  const int nt = quad ? 4 : 2;
+  if (threadIdx.x < 3 * nt) {
     float v = 0.f;
-    for (int w = 0; w < kTcWarps; ++w) v += red[w][i];
-    const int b = b0 + bb;
+    for (int w = 0; w < kTcWarps; ++w) v += red[w][threadIdx.x];
+    const int k = threadIdx.x / 3, c = threadIdx.x - 3 * k;
     const int tl = (k < 2 ? a * nb : a2 * nb) + b + (k & 1) * hb;
     vals[A.val_off[ld] + (long long)c * ng + tl] = A.wts[ld] * (double)v;
   }
@@ -243,34 +220,46 @@ __global__ void __launch_bounds__(kTcThreads) k_self_tc(SelfGroups<float> G, con
 
 }  // namespace
 
-size_t self_tc_smem(int p, int nbl) { return sizeof(float) * 9 * (size_t)(p + 1) * (p + 1) * nbl; }
+// E/O floats of one drop of degree p
+static long long eo_per_drop(int p) { return (long long)((p + 2) / 2) * (p + 1) * (long long)(p + 1) * (p + 1) * 6; }
 
-int launch_self_tc(std::vector<SelfGroup<float>> groups, const double* dens, double* vals, cudaStream_t s) {
-  std::sort(groups.begin(), groups.end(), [](const SelfGroup<float>& x, const SelfGroup<float>& y) { return x.p > y.p; });
-  for (size_t g0 = 0; g0 < groups.size(); g0 += kMaxSelfGroups) {
-    SelfGroups<float> G{};
-    G.n = (int)std::min<size_t>(kMaxSelfGroups, groups.size() - g0);
-    long long nblk = 0;
-    size_t smem = 0;
-    for (int i = 0; i < G.n; ++i) {
-      G.g[i] = groups[g0 + i];
-      const int p = G.g[i].p;
-      G.g[i].begin = nblk;
-      nblk += G.g[i].ndrop * ((p + 2) / 2) * (long long)(p + 1);  // NB = 1: one block per longitude
-      smem = std::max(smem, self_tc_smem(p, 1));
-      if (G.g[i].ndrop * (long long)(p + 1) * (2 * p + 2) > 0x7fffffffLL) return BIE_EINVAL;
+// Drops per launch of a group: as many as keep the chunk's E/O sums within `budget` floats (at least one).
+static long long chunk_drops(int p, long long budget) { return std::max(1LL, budget / eo_per_drop(p)); }
+
+long long self_tc_eo_floats(const std::vector<SelfGroup<float>>& groups, long long budget) {
+  long long n = 0;
+  for (const auto& g : groups) n = std::max(n, std::min(g.ndrop, chunk_drops(g.p, budget)) * eo_per_drop(g.p));
+  return n;
+}
+
+int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* dens, double* vals, float* eo,
+                   long long budget, cudaStream_t s) {
+  for (const auto& g : groups) {
+    const int p = g.p;
+    const int ng = (p + 1) * (2 * p + 2), ntri = (p + 1) * (p + 2) / 2;
+    if (g.ndrop * (long long)ng > 0x7fffffffLL) return BIE_EINVAL;
+    const size_t smem = sizeof(float) * ((size_t)(p + 1) * (p + 1) + (size_t)p * p + (2 * (size_t)p + 1) * (p + 1) * 3);
+    if (smem > 227 * 1024) return BIE_EINVAL;
+    if (smem > 48 * 1024)
+      BIE_CUDA_TRY(cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long per = chunk_drops(p, budget);
+    for (long long d0 = 0; d0 < g.ndrop; d0 += per) {
+      // the chunk's drops d0 .. d0 + nd - 1 of the group, as a group of their own
+      SelfGroup<float> c = g;
+      c.begin = 0;
+      c.ndrop = std::min(per, g.ndrop - d0);
+      c.foff3 = g.foff3 + 3 * d0;
+      c.Q = g.Q + d0 * ng * 12LL * ntri;
+      c.wts = g.wts + d0;
+      c.val_off = g.val_off + d0;
+      const long long nblk = c.ndrop * ((p + 2) / 2) * (long long)(p + 1);
+      k_rot_tc<<<(unsigned)nblk, kTcThreads, smem, s>>>(c, dens, eo);
+      count_launch();
+      BIE_CUDA_TRY(cudaGetLastError());
+      k_contract_eo<<<(unsigned)nblk, kTcThreads, 0, s>>>(c, eo, vals);
+      count_launch();
+      BIE_CUDA_TRY(cudaGetLastError());
     }
-    if (nblk == 0) continue;
-    if (nblk > 0x7fffffffLL) return BIE_EINVAL;
-    if (smem > 227 * 1024) {
-      set_error("degree too large for the tensor-core self kernel (shared memory)");
-      return BIE_ENOTSUP;
-    }
-    auto kern = k_self_tc<1>;
-    if (smem > 48 * 1024) BIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)nblk, kTcThreads, smem, s>>>(G, dens, vals);
-    count_launch();
-    BIE_CUDA_TRY(cudaGetLastError());
   }
   return BIE_OK;
 }
