@@ -279,7 +279,7 @@ struct bie_geom {
   struct Group {
     int p = 0, pq = 0;
     std::vector<int> drops;
-    bie::DevBuf<long long> foff3, goff3, val_off;
+    bie::DevBuf<long long> foff3, goff3, val_off, roff;  // roff: 7 * first target, per group drop
     bie::DevBuf<double> wS, wD, wSraw, wDraw;
     bie::DevBuf<double> cache64;            // [gdrop][N_g][7][nq] rotated geometry (Sec. 2.2)
     bie::DevBuf<float> cache32;             // FP32 copy, made on the first direct-form mixed apply
@@ -586,7 +586,7 @@ static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream
   const long long ng = ngrid(p), nq = ngrid(pq), nc = ncoef(p);
   const int nd = (int)G.drops.size();
   // offsets
-  std::vector<long long> foff3(3 * nd), goff3(3 * nd), voff(nd);
+  std::vector<long long> foff3(3 * nd), goff3(3 * nd), voff(nd), roff(nd);
   std::vector<double> wS(nd), wD(nd), wSr(nd), wDr(nd);
   for (int i = 0; i < nd; ++i) {
     int d = G.drops[i];
@@ -595,6 +595,7 @@ static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream
       goff3[3 * i + c] = 3 * g->tgt_off[d] + c * ng;
     }
     voff[i] = 3 * g->tgt_off[d];
+    roff[i] = 7 * g->tgt_off[d];
     wS[i] = -1.0 / (4 * kPi);
     wD[i] = (g->lambda[d] - 1.0) / (4 * kPi);
     wSr[i] = 1.0 / (8 * kPi);
@@ -603,6 +604,7 @@ static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream
   BIE_TRY(G.foff3.upload(foff3));
   BIE_TRY(G.goff3.upload(goff3));
   BIE_TRY(G.val_off.upload(voff));
+  BIE_TRY(G.roff.upload(roff));
   BIE_TRY(G.wS.upload(wS));
   BIE_TRY(G.wD.upload(wD));
   BIE_TRY(G.wSraw.upload(wSr));
@@ -649,8 +651,9 @@ static int setup_group(bie_ctx* ctx, bie_geom* g, bie_geom::Group& G, cudaStream
     BIE_TRY((launch_rotate<double, double>(g->xcoef.ptr, G.foff3.ptr + 3 * c0, 3, cn, p, wp->blk.ptr, wp->stride,
                                            p + 1, 2 * p + 2, pp->cs.ptr, RC, ng * 3 * nc, s)));
     BIE_TRY(synth_xderivs(ctx, RC, nullptr, nc, cn * ng * 3, p, pq, H, X, Xt, Xp, s));
-    const double* rec0 = g->rec_std.ptr + 7 * g->tgt_off[G.drops[c0]];
-    BIE_TRY(launch_rotgeo<double>(X, Xt, Xp, cn, (int)ng, pq, rec0, pl->wsq.ptr,
+    // the targets x0 of the chunk's drops, wherever each drop's records lie (a degree group's drops
+    // are in general not adjacent in rec_std)
+    BIE_TRY(launch_rotgeo<double>(X, Xt, Xp, cn, (int)ng, pq, g->rec_std.ptr, G.roff.ptr + c0, pl->wsq.ptr,
                                   G.cache64.ptr + (long long)c0 * ng * 7 * nq, s));
     BIE_CUDA_TRY(cudaStreamSynchronize(s));
   }

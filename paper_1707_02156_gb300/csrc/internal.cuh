@@ -79,10 +79,11 @@ int launch_phase(double* coef, long long nfield, int p, double gamma, cudaStream
 int launch_surface(const double* X, const double* Xt, const double* Xp, long long ndrop, int P,
                    const double* wsin /*[j] = w_j pi/(P+1)/sin theta_j*/, double* rec, cudaStream_t s);
 // Rotated-grid cache for ndrop drops of ng targets each: cache[t][7][nq] = (x0 - x', n',
-// w^s_j W'/sin theta_j) on the degree-pq grid; x0 read from the standard-grid records rec_std.
+// w^s_j W'/sin theta_j) on the degree-pq grid; x0 of drop ld's targets read from the standard-grid
+// records at rec_std + rec_off[ld] ([7][ng] per drop; the drops need not be adjacent there).
 template <typename R>
 int launch_rotgeo(const double* X, const double* Xt, const double* Xp, long long ndrop, int ng, int pq,
-                  const double* rec_std, const double* wsq, R* cache, cudaStream_t s);
+                  const double* rec_std, const long long* rec_off, const double* wsq, R* cache, cudaStream_t s);
 // Singular self interaction (Thm 1, Sec. 2.2), one block per target of ndrop drops of degree p:
 // direct form against the rotated-geometry cache, or projected form against Q (see self.cu).
 template <typename R>

@@ -50,7 +50,8 @@ __global__ void k_surface(const double* __restrict__ X, const double* __restrict
 template <typename R>
 __global__ void k_rotgeo(const double* __restrict__ X, const double* __restrict__ Xt, const double* __restrict__ Xp,
                          long long ndrop, int ng, int pq, const double* __restrict__ rec_std,
-                         const double* __restrict__ wsq, R* __restrict__ cache) {
+                         const long long* __restrict__ rec_off, const double* __restrict__ wsq,
+                         R* __restrict__ cache) {
   const int nk = 2 * pq + 2;
   const long long nq = (long long)(pq + 1) * nk;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -70,7 +71,7 @@ __global__ void k_rotgeo(const double* __restrict__ X, const double* __restrict_
   double W = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
   R* o = cache + t * 7 * nq;
   for (int i = 0; i < 3; ++i) {
-    double x0 = rec_std[(ld * 7 + i) * ng + tl];
+    double x0 = rec_std[rec_off[ld] + (long long)i * ng + tl];
     o[i * nq + q] = (R)(x0 - x[i]);
     o[(3 + i) * nq + q] = (R)(c[i] / W);
   }
@@ -154,18 +155,18 @@ int launch_surface(const double* X, const double* Xt, const double* Xp, long lon
 
 template <typename R>
 int launch_rotgeo(const double* X, const double* Xt, const double* Xp, long long ndrop, int ng, int pq,
-                  const double* rec_std, const double* wsq, R* cache, cudaStream_t s) {
+                  const double* rec_std, const long long* rec_off, const double* wsq, R* cache, cudaStream_t s) {
   long long n = ndrop * ng * (long long)(pq + 1) * (2 * pq + 2);
   if (n == 0) return BIE_OK;
-  k_rotgeo<R><<<blocks_for(n), kThreads, 0, s>>>(X, Xt, Xp, ndrop, ng, pq, rec_std, wsq, cache);
+  k_rotgeo<R><<<blocks_for(n), kThreads, 0, s>>>(X, Xt, Xp, ndrop, ng, pq, rec_std, rec_off, wsq, cache);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;
 }
 
 template int launch_rotgeo<double>(const double*, const double*, const double*, long long, int, int, const double*,
-                                   const double*, double*, cudaStream_t);
+                                   const long long*, const double*, double*, cudaStream_t);
 template int launch_rotgeo<float>(const double*, const double*, const double*, long long, int, int, const double*,
-                                  const double*, float*, cudaStream_t);
+                                  const long long*, const double*, float*, cudaStream_t);
 }  // namespace bie
 

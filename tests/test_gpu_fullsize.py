@@ -127,14 +127,22 @@ def test_near_contact_pair_full_size(cuda_ok, kind):
 
 
 def test_batch_of_64_uneven_degree_drops_full_size(cuda_ok):
+    # one drop of each degree that is not the first of its degree group in memory, and the first
+    # degree-48 drop; drop 23 (degree 48) is the one whose surfactant-conservation outlier led to
+    # the fault these samples now cover
     w = inputs.config("c4")
-    i = int(np.argmax(w.p))  # a p = 48 drop
-    lats = [7]
     g = _gpu_grid(w, "D", (0, 1, 2))
-    ref = _far_only_oracle(w, "D", i, lats)
-    assert _relerr(_drop_block(w, g[0], i, lats), ref) < FP64_TOL
-    assert _relerr(_drop_block(w, g[1], i, lats), ref) < MIXED_TOL
-    assert _relerr(_drop_block(w, g[2], i, lats), ref) < DF_TOL
+    first48 = int(np.argmax(w.p))
+    picks = [first48, 23]
+    for deg in (16, 24, 32):
+        members = [i for i, p in enumerate(w.p) if p == deg]
+        picks.append(members[len(members) // 2])
+    for i in picks:
+        lats = [w.p[i] // 3]
+        ref = _far_only_oracle(w, "D", i, lats)
+        assert _relerr(_drop_block(w, g[0], i, lats), ref) < FP64_TOL, i
+        assert _relerr(_drop_block(w, g[1], i, lats), ref) < MIXED_TOL, i
+        assert _relerr(_drop_block(w, g[2], i, lats), ref) < DF_TOL, i
 
 
 def test_512_deformed_drops_full_size(cuda_ok):

@@ -205,3 +205,38 @@ def test_double_float_single_drop_matches_fp64():
     assert _relerr(b.cpu().numpy(), a.cpu().numpy()) < DF_TOL
     geo.close()
     ctx.close()
+
+
+def test_interleaved_degree_groups_match_oracle(ctx):
+    # five drops whose degrees alternate (6, 8, 6, 8, 6): each degree group's drops are separated in
+    # memory by drops of the other degree, as in a batch of seeded random degrees.  The singular
+    # rule's rotated geometry of every drop must use that drop's own targets (a set-up that read the
+    # targets of a group's later drops from the slots after its first drop gave O(1) errors on them).
+    rng = np.random.default_rng(17)
+    ps = [6, 8, 6, 8, 6]
+    centres = [(0.0, 0.0, 0.0), (2.7, 0.0, 0.3), (5.3, 0.4, 0.0), (0.2, 2.8, 0.5), (2.9, 2.6, -0.4)]
+    xs, fs = [], []
+    for p, c in zip(ps, centres):
+        x = inputs.sphere_coef(p, centre=c, axes=(1.0, 0.9, 1.1), rot=inputs.random_rotation(rng))
+        xs.append(x + inputs.perturbation(rng, p, 2, 4, 0.04))
+        fs.append(inputs.random_bandlimited(rng, p, 3))
+    lam = np.array([0.5, 2.0, 3.5, 1.5, 4.0])
+    drops = layer.Drops(xs, ps, ps, lam, up=3)
+    geo = ctx.geometry(ps, ps, torch.tensor(inputs.pack_drops(xs), device="cuda"), lam)
+    f = torch.tensor(inputs.pack_drops(fs), device="cuda")
+    for kind in ("S", "D"):
+        ref = (drops.apply_single_grid if kind == "S" else drops.apply_double_grid)(fs)
+        ref = np.concatenate([r.ravel() for r in ref])
+        out = torch.zeros(ref.size, dtype=torch.float64, device="cuda")
+        fn = geo.apply_single if kind == "S" else geo.apply_double
+        for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL), (2, DF_TOL)):
+            fn(f, out, precision=prec, grid_out=True)
+            torch.cuda.synchronize()
+            o = out.cpu().numpy()
+            # every drop on its own, so that a fault confined to some drops cannot hide in the norm
+            off = 0
+            for p in ps:
+                n = 3 * (p + 1) * (2 * p + 2)
+                assert _relerr(o[off:off + n], ref[off:off + n]) < tol, (kind, prec, p, off)
+                off += n
+    geo.close()
