@@ -248,9 +248,9 @@ struct alignas(16) SrcRecX2 {
 };
 
 // Same work list, layout and result as k_interdrop<float, KIND, TPT>; TPT even, the thread's
-// targets tid + u * (128/TPT) taken two by two (u = 2w, 2w + 1 share lane pair w).  The tile's FP64
-// target coordinates and the FP64 accumulators live in shared memory, not in registers, so that
-// more warps fit per SM; the source loop takes two sources per iteration (2 x TPT/2 independent
+// targets tid + u * (128/TPT) taken two by two (u = 2w, 2w + 1 share lane pair w).  The tile's target
+// coordinates (FP32, relative to their drop's centre) and the FP64 accumulators live in shared
+// memory, not in registers, so that more warps fit per SM; the source loop takes two sources per iteration (2 x TPT/2 independent
 // chains per thread).  PF = 1 software-pipelines the staging: the next chunk's sources are loaded
 // into registers while the current chunk is summed, so the global-memory latency of the staging
 // overlaps the arithmetic.
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
   constexpr int nv = (NV + 1) / 2;  // 128-bit loads per staged source
   constexpr int RPT = kChunkX2 / NT;  // staged sources per thread and chunk
   __shared__ SrcRecX2 src[kChunkX2];
-  __shared__ double tgt[3][kTile];  // the tile's target coordinates (zero past the tile's end)
+  __shared__ float tgt[3][kTile];   // the tile's targets relative to their own drop's centre (FP32)
   __shared__ double acc[3][kTile];  // per-target sums over the block's items
   const int b = blockIdx.x;
   const int it0 = blk_item[b], it1 = blk_item[b + 1];
@@ -277,20 +277,23 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
   const int tid = threadIdx.x;
   const int nt = tile_n[tile];
   const int di = tile_drop[tile];
+  const double ox = centre[3 * di], oy = centre[3 * di + 1], oz = centre[3 * di + 2];
   {
     const long long ng = ngd[di];
     const double* ri = rec_std + 7 * toff_std[di];
     for (int k = tid; k < kTile; k += NT) {
-      double x = 0, y = 0, z = 0;
+      double x = ox, y = oy, z = oz;
       if (k < nt) {
         const long long l = tgt_loc[tile_t0[tile] + k];
         x = ri[l];
         y = ri[ng + l];
         z = ri[2 * ng + l];
       }
-      tgt[0][k] = x;
-      tgt[1][k] = y;
-      tgt[2][k] = z;
+      // |x - o| is about a drop radius, so its FP32 rounding (2^-24 of it) is far below that of the
+      // target's position relative to a source drop's centre, which the pair sums round to FP32 anyway
+      tgt[0][k] = (float)(x - ox);
+      tgt[1][k] = (float)(y - oy);
+      tgt[2][k] = (float)(z - oz);
       acc[0][k] = acc[1][k] = acc[2][k] = 0.0;
     }
   }
@@ -339,14 +342,15 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
       const int k = tid + u * NT;
       if (k < nt && ((items[it].mask[k >> 5] >> (k & 31)) & 1u)) act |= 1u << u;
     }
-    const double cx = centre[3 * j], cy = centre[3 * j + 1], cz = centre[3 * j + 2];
+    // target relative to the source drop's centre: (x - o) + (o - c_j), the offset in FP64
+    const double cx = ox - centre[3 * j], cy = oy - centre[3 * j + 1], cz = oz - centre[3 * j + 2];
     fx2 px[NW], py[NW], pz[NW], s[NW][3];
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
       const int k0 = tid + 2 * w * NT, k1 = k0 + NT;
-      px[w] = x2_pack((float)(tgt[0][k0] - cx), (float)(tgt[0][k1] - cx));
-      py[w] = x2_pack((float)(tgt[1][k0] - cy), (float)(tgt[1][k1] - cy));
-      pz[w] = x2_pack((float)(tgt[2][k0] - cz), (float)(tgt[2][k1] - cz));
+      px[w] = x2_pack((float)((double)tgt[0][k0] + cx), (float)((double)tgt[0][k1] + cx));
+      py[w] = x2_pack((float)((double)tgt[1][k0] + cy), (float)((double)tgt[1][k1] + cy));
+      pz[w] = x2_pack((float)((double)tgt[2][k0] + cz), (float)((double)tgt[2][k1] + cz));
       s[w][0] = s[w][1] = s[w][2] = 0ull;  // +0.0f in both lanes
     }
     const int grid = items[it].grid;

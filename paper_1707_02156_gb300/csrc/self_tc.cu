@@ -57,11 +57,12 @@ __device__ __forceinline__ void sym_mul_add_f(const float* q, const float* v, fl
   acc[2] = fmaf(q[2], v[2], fmaf(q[5], v[1], fmaf(q[4], v[0], acc[2])));
 }
 
-// Offset of the rotated sums of (drop ld, latitude pair a, longitude b) in the E/O buffer of one
-// launch (a chunk of drops of one degree): [ld][a][b][packed (n, m')][c][parity].
-__device__ __forceinline__ long long eo_offset(long long ld, int a, int b, int p) {
+// The rotated sums of one launch (a chunk of drops of one degree): EO[ld][a][packed (n, m')][b][c][parity],
+// so that a tile row of the products (one output order, eight (b, c, parity) columns) is 32
+// contiguous bytes.  eo_row = the offset of (ld, a, packed index pk).
+__device__ __forceinline__ long long eo_row(long long ld, int a, int pk, int p) {
   const int hb = p + 1, na2 = (p + 2) / 2, nc = (p + 1) * (p + 1);
-  return (((ld * na2 + a) * hb + b) * (long long)nc) * 6;
+  return ((ld * na2 + a) * (long long)nc + pk) * (long long)hb * 6;
 }
 
 // One block per (drop, latitude pair a, degree n): stage the Wigner blocks C, S of (a, n) and the
@@ -142,8 +143,7 @@ __global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const
       const int row = e < 2 ? r0 : r1, col = nt * 8 + 2 * tq + (e & 1);
       if (row < M && col < NCOL) {
         const int pk = im ? n * (n + 1) - (row + 1) : n * (n + 1) + row;
-        const int b = col / 6, cp = col % 6;  // (c, parity) pair index
-        EO[eo_offset(ld, a, b, p) + (long long)pk * 6 + cp] = d[e];
+        EO[eo_row(ld, a, pk, p) + col] = d[e];  // col = (b, c, parity)
       }
     }
   }
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kTcThreads) k_contract_eo(SelfGroup<float> A, 
   const int a = r / hb, b = r - a * hb;
   const int a2 = p - a;
   const bool quad = a2 != a;
-  const float* eo = EO + eo_offset(ld, a, b, p);
+  const float* eo = EO + eo_row(ld, a, 0, p) + (long long)b * 6;  // row pk at + pk * hb * 6
   const long long qstride = 12 * (long long)ntri;
   const float* Qk_[4] = {A.Q + (ld * ng + a * nb + b) * qstride, A.Q + (ld * ng + a * nb + b + hb) * qstride,
                          A.Q + (ld * ng + a2 * nb + b) * qstride, A.Q + (ld * ng + a2 * nb + b + hb) * qstride};
@@ -181,9 +181,10 @@ __global__ void __launch_bounds__(kTcThreads) k_contract_eo(SelfGroup<float> A, 
     const int t = n * (n + 1) / 2 + mo;
     const int ri = re ? 0 : 1;
     const int pk = re ? n * (n + 1) + mo : n * (n + 1) - mo;
-    const float2 v01 = *reinterpret_cast<const float2*>(eo + (long long)pk * 6);
-    const float2 v23 = *reinterpret_cast<const float2*>(eo + (long long)pk * 6 + 2);
-    const float2 v45 = *reinterpret_cast<const float2*>(eo + (long long)pk * 6 + 4);
+    const float* e6 = eo + (long long)pk * hb * 6;
+    const float2 v01 = *reinterpret_cast<const float2*>(e6);
+    const float2 v23 = *reinterpret_cast<const float2*>(e6 + 2);
+    const float2 v45 = *reinterpret_cast<const float2*>(e6 + 4);
     const float vp[3] = {v01.x + v01.y, v23.x + v23.y, v45.x + v45.y};
     const float vm[3] = {v01.x - v01.y, v23.x - v23.y, v45.x - v45.y};
 #pragma unroll
