@@ -126,8 +126,9 @@ int launch_self_proj(std::vector<SelfGroup<R>> groups, const CT* dens, double* v
 // drops of one degree, the rotation products into eo (at most `budget` floats per chunk, at least one
 // drop's worth), then the contraction with the factors.  self_tc_eo_floats = the buffer it needs.
 long long self_tc_eo_floats(const std::vector<SelfGroup<float>>& groups, long long budget);
+long long self_tc_g_floats(const std::vector<SelfGroup<float>>& groups, long long budget);
 int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* dens, double* vals, float* eo,
-                   long long budget, cudaStream_t s);
+                   float* gm, long long budget, cudaStream_t s);
 // interfacial force at N grid points from x derivatives [6][3][N] and Gamma derivatives [3][N]
 int launch_force(const double* X, const double* Gm, long long N, double es, double xs, double* f, cudaStream_t s);
 // out[i] = (float) in[i]

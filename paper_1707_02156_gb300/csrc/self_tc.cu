@@ -13,7 +13,8 @@
 // W = C (rows m' = 0..n) or S (rows m' = 1..n), G(m, (b, c, par)) = g_m(b, c) when m has the
 // column's parity, else 0.  k_rot_tc runs these products as mma.sync m16n8k8 in TF32 with the
 // 3-pass split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (x = x_hi + x_lo, both TF32), accumulated in
-// FP32 (about FP32 accuracy), and writes E and O to a buffer that stays in L2 for one drop's worth
+// FP32 (about FP32 accuracy), from the phase-shifted coefficients that k_phase_g forms once per apply
+// for every longitude, and writes E and O to a buffer that stays in L2 for one drop's worth
 // of latitudes (drops are taken in chunks whose sums fit a fixed buffer); k_contract_eo then streams the projected kernel factors Q from HBM and contracts
 // them with E +- O, one block per target quadruple.
 #include <cuda_runtime.h>
@@ -65,13 +66,34 @@ __device__ __forceinline__ long long eo_row(long long ld, int a, int pk, int p) 
   return ((ld * na2 + a) * (long long)nc + pk) * (long long)hb * 6;
 }
 
+// The phase-shifted coefficients g = e^{i m phi_b} rho_n^m of every longitude b < p+1, shared by all
+// latitudes: Gm[ld][packed (n, mm)][b][c] = Re g (mm >= 0) or Im g (mm < 0) of |mm|, in FP32.
+__global__ void k_phase_g(SelfGroup<float> A, const double* __restrict__ dens, float* __restrict__ Gm) {
+  const int p = A.p;
+  const int hb = p + 1, nb = 2 * p + 2, nc = (p + 1) * (p + 1);
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= A.ndrop * (long long)nc * hb * 3) return;
+  const int c = (int)(idx % 3), b = (int)((idx / 3) % hb);
+  const long long r = idx / (3LL * hb);
+  const int pk = (int)(r % nc);
+  const long long ld = r / nc;
+  const int n = degree_of(pk);
+  const int mm = pk - n * (n + 1);
+  const int m = mm < 0 ? -mm : mm;
+  const double* f = dens + A.foff3[ld * 3 + c];
+  const float fr = (float)f[n * (n + 1) + m];
+  const float fi = m > 0 ? (float)f[n * (n + 1) - m] : 0.f;
+  const float co = A.ph[((long long)m * nb + b) * 2], si = A.ph[((long long)m * nb + b) * 2 + 1];
+  Gm[idx] = mm >= 0 ? fr * co - fi * si : fr * si + fi * co;
+}
+
 // One block per (drop, latitude pair a, degree n): stage the Wigner blocks C, S of (a, n) and the
 // phase-shifted coefficients G of every longitude, then the two products on the tensor cores.
-__global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const double* __restrict__ dens,
+__global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const float* __restrict__ Gm,
                                                        float* __restrict__ EO) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = A.p;
-  const int hb = p + 1, nb = 2 * p + 2;
+  const int hb = p + 1;
   const long long bid = blockIdx.x;
   const int n = (int)(bid % (p + 1));
   const long long r = bid / (p + 1);
@@ -85,16 +107,10 @@ __global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const
   float* Gs = Ws + n * n;                           // [n + mm][b][c], mm = -n..n: Re g (mm >= 0), Im g (mm < 0)
   const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
   const float* blk = A.wblk + (long long)a * A.wstride + boff;
-  for (int i = threadIdx.x; i < (n + 1) * (n + 1) + n * n; i += blockDim.x) Wc[i] = blk[i];
-  for (int i = threadIdx.x; i < (2 * n + 1) * hb * 3; i += blockDim.x) {
-    const int c = i % 3, b = (i / 3) % hb, mm = i / (3 * hb) - n;
-    const int m = mm < 0 ? -mm : mm;
-    const double* f = dens + A.foff3[ld * 3 + c];
-    const float fr = (float)f[n * (n + 1) + m];
-    const float fi = m > 0 ? (float)f[n * (n + 1) - m] : 0.f;
-    const float co = A.ph[((long long)m * nb + b) * 2], si = A.ph[((long long)m * nb + b) * 2 + 1];
-    Gs[i] = mm >= 0 ? fr * co - fi * si : fr * si + fi * co;
-  }
+  for (int i = threadIdx.x; i < (n + 1) * (n + 1) + n * n; i += blockDim.x) Wc[i] = __ldg(blk + i);
+  // degree n's rows of the drop's phase-shifted coefficients: (2n+1) hb 3 contiguous floats
+  const float* gsrc = Gm + ((ld * (p + 1) * (p + 1)) + (long long)n * n) * hb * 3;
+  for (int i = threadIdx.x; i < (2 * n + 1) * hb * 3; i += blockDim.x) Gs[i] = __ldg(gsrc + i);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gq = lane >> 2, tq = lane & 3;
@@ -233,8 +249,15 @@ long long self_tc_eo_floats(const std::vector<SelfGroup<float>>& groups, long lo
   return n;
 }
 
+long long self_tc_g_floats(const std::vector<SelfGroup<float>>& groups, long long budget) {
+  long long n = 0;
+  for (const auto& g : groups)
+    n = std::max(n, std::min(g.ndrop, chunk_drops(g.p, budget)) * (long long)(g.p + 1) * (g.p + 1) * (g.p + 1) * 3);
+  return n;
+}
+
 int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* dens, double* vals, float* eo,
-                   long long budget, cudaStream_t s) {
+                   float* gm, long long budget, cudaStream_t s) {
   for (const auto& g : groups) {
     const int p = g.p;
     const int ng = (p + 1) * (2 * p + 2), ntri = (p + 1) * (p + 2) / 2;
@@ -253,8 +276,12 @@ int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* de
       c.Q = g.Q + d0 * ng * 12LL * ntri;
       c.wts = g.wts + d0;
       c.val_off = g.val_off + d0;
+      const long long ng3 = c.ndrop * (long long)(p + 1) * (p + 1) * (p + 1) * 3;
+      k_phase_g<<<(unsigned)((ng3 + 255) / 256), 256, 0, s>>>(c, dens, gm);
+      count_launch();
+      BIE_CUDA_TRY(cudaGetLastError());
       const long long nblk = c.ndrop * ((p + 2) / 2) * (long long)(p + 1);
-      k_rot_tc<<<(unsigned)nblk, kTcThreads, smem, s>>>(c, dens, eo);
+      k_rot_tc<<<(unsigned)nblk, kTcThreads, smem, s>>>(c, gm, eo);
       count_launch();
       BIE_CUDA_TRY(cudaGetLastError());
       k_contract_eo<<<(unsigned)nblk, kTcThreads, 0, s>>>(c, eo, vals);
