@@ -14,7 +14,7 @@
 // column's parity, else 0.  k_rot_tc runs these products as mma.sync m16n8k8 in TF32 with the
 // 3-pass split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (x = x_hi + x_lo, both TF32), accumulated in
 // FP32 (about FP32 accuracy), from the phase-shifted coefficients that k_phase_g forms once per apply
-// for every longitude, and writes E and O to a buffer that stays in L2 for one drop's worth
+// for every longitude, with K split by the parity of m (no zero padding), and writes E and O to a buffer that stays in L2 for one drop's worth
 // of latitudes (drops are taken in chunks whose sums fit a fixed buffer); k_contract_eo then streams the projected kernel factors Q from HBM and contracts
 // them with E +- O, one block per target quadruple.
 #include <cuda_runtime.h>
@@ -87,8 +87,14 @@ __global__ void k_phase_g(SelfGroup<float> A, const double* __restrict__ dens, f
   Gm[idx] = mm >= 0 ? fr * co - fi * si : fr * si + fi * co;
 }
 
-// One block per (drop, latitude pair a, degree n): stage the Wigner blocks C, S of (a, n) and the
-// phase-shifted coefficients G of every longitude, then the two products on the tensor cores.
+// One block per (drop, latitude pair a, degree n).  The products are split by the parity of the input
+// order, E = W[:, even m] G[even m, (b, c)] and O = W[:, odd m] G[odd m, (b, c)], so that no operand
+// carries zero padding: K = the orders of one parity, N = (b, c) = 3 (p+1) columns.  The block stages
+// W's columns of each parity already split into TF32 hi / lo parts, and the degree's rows of the
+// phase-shifted coefficients G.  A warp owns one (part, parity, 16-row tile, half of N) and runs its
+// k-steps once, building the A fragment once per k-step and reusing it over up to 13 column tiles.
+constexpr int kRotMaxNt = 13;  // 8-column tiles per warp pass (N = 3 (p+1) takes one or two passes for p < 64)
+
 __global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const float* __restrict__ Gm,
                                                        float* __restrict__ EO) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -100,66 +106,108 @@ __global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const
   const int na2 = (p + 2) / 2;
   const int a = (int)(r % na2);
   const long long ld = r / na2;
-  const int NCOL = hb * 6;            // columns (b, c, parity)
-  const int NTN = (NCOL + 7) / 8;     // 8-column tiles
-  float* Wc = reinterpret_cast<float*>(smem_raw);  // (n+1)^2 column-major, then n^2
-  float* Ws = Wc + (n + 1) * (n + 1);
-  float* Gs = Ws + n * n;                           // [n + mm][b][c], mm = -n..n: Re g (mm >= 0), Im g (mm < 0)
+  const int NC3 = hb * 3;                // columns (b, c)
+  const int NTN = (NC3 + 7) / 8;         // 8-column tiles
+  // A operands: for part (re: C, rows m' = 0..n; im: S, rows m' = 1..n) and parity q, column kk is the
+  // input order m = 2 kk + q (re) or m = 2 kk + q + ... (im: m = 1..n), stored [part][q][row][kk] as
+  // TF32 hi and lo bit patterns; kq(part, q) columns, padded to a multiple of 8
+  const int Mre = n + 1, Mim = n;
+  const int kre0 = (n + 2) / 2, kre1 = (n + 1) / 2;  // even / odd orders among 0..n
+  const int kim1 = (n + 1) / 2, kim0 = n / 2;        // odd / even orders among 1..n
+  auto pad8 = [](int v) { return (v + 7) & ~7; };
+  const int ka[2][2] = {{pad8(kre0), pad8(kre1)}, {pad8(kim0), pad8(kim1)}};
+  unsigned* Ahi = reinterpret_cast<unsigned*>(smem_raw);
+  long long aoff[2][2], acur = 0;
+  for (int part = 0; part < 2; ++part)
+    for (int q = 0; q < 2; ++q) {
+      aoff[part][q] = acur;
+      acur += (long long)(part ? Mim : Mre) * ka[part][q];
+    }
+  unsigned* Alo = Ahi + acur;
+  float* Gs = reinterpret_cast<float*>(Alo + acur);  // [n + mm][b][c], mm = -n..n
   const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
   const float* blk = A.wblk + (long long)a * A.wstride + boff;
-  for (int i = threadIdx.x; i < (n + 1) * (n + 1) + n * n; i += blockDim.x) Wc[i] = __ldg(blk + i);
-  // degree n's rows of the drop's phase-shifted coefficients: (2n+1) hb 3 contiguous floats
-  const float* gsrc = Gm + ((ld * (p + 1) * (p + 1)) + (long long)n * n) * hb * 3;
-  for (int i = threadIdx.x; i < (2 * n + 1) * hb * 3; i += blockDim.x) Gs[i] = __ldg(gsrc + i);
+  for (int part = 0; part < 2; ++part)
+    for (int q = 0; q < 2; ++q) {
+      const int M = part ? Mim : Mre, K = ka[part][q];
+      for (int i = threadIdx.x; i < M * K; i += blockDim.x) {
+        const int row = i / K, kk = i - row * K;
+        // input order of column kk: m = 2 kk + q (re, m = 0..n); m = 2 kk + 1 + (1 - q) ... (im, m = 1..n)
+        const int m = part ? (q ? 2 * kk + 1 : 2 * kk + 2) : 2 * kk + q;
+        float v = 0.f;
+        if (part == 0 && m <= n) v = __ldg(blk + (long long)m * (n + 1) + row);                 // C(m' = row, m)
+        if (part == 1 && m <= n) v = __ldg(blk + (long long)(n + 1) * (n + 1) + (long long)(m - 1) * n + row);  // S
+        unsigned hi, lo;
+        tf32_split(v, hi, lo);
+        Ahi[aoff[part][q] + i] = hi;
+        Alo[aoff[part][q] + i] = lo;
+      }
+    }
+  const float* gsrc = Gm + ((ld * (p + 1) * (p + 1)) + (long long)n * n) * NC3;
+  for (int i = threadIdx.x; i < (2 * n + 1) * NC3; i += blockDim.x) Gs[i] = __ldg(gsrc + i);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gq = lane >> 2, tq = lane & 3;
-  const int mt_re = (n + 1 + 15) / 16, mt_im = (n + 15) / 16;
-  const int units = (mt_re + mt_im) * NTN;
+  const int mt[2] = {(Mre + 15) / 16, (Mim + 15) / 16};
+  const int npass = (NTN + kRotMaxNt - 1) / kRotMaxNt;
+  const int units = 2 * (mt[0] + mt[1]) * npass;
   for (int u = warp; u < units; u += kTcWarps) {
-    const int nt = u % NTN, mu = u / NTN;
-    const bool im = mu >= mt_re;
-    const int mt = im ? mu - mt_re : mu;
-    const int M = im ? n : n + 1;  // rows = output orders; K = input orders (as many)
-    const float* W = im ? Ws : Wc;
-    const int r0 = mt * 16 + gq, r1 = r0 + 8;
-    const int j = nt * 8 + gq;     // this lane's B column
-    const int jb = j / 6, jc = (j >> 1) % 3, jp = j & 1;
-    float d[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k0 = 0; k0 < M; k0 += 8) {
+    const int pass = u % npass, uq = u / npass;
+    const int q = uq & 1, mu = uq >> 1;
+    const int t0 = pass * kRotMaxNt;
+    const int part = mu >= mt[0] ? 1 : 0;
+    const int tile = part ? mu - mt[0] : mu;
+    const int M = part ? Mim : Mre, K = ka[part][q];
+    const unsigned* Ah = Ahi + aoff[part][q];
+    const unsigned* Al = Alo + aoff[part][q];
+    const int r0 = tile * 16 + gq, r1 = r0 + 8;
+    float d[kRotMaxNt][4];
+#pragma unroll
+    for (int t = 0; t < kRotMaxNt; ++t) d[t][0] = d[t][1] = d[t][2] = d[t][3] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 8) {
       const int c0 = k0 + tq, c1 = c0 + 4;
-      // A fragment: W(row, col) column-major with M rows
-      const float a0 = (r0 < M && c0 < M) ? W[c0 * M + r0] : 0.f;
-      const float a1 = (r1 < M && c0 < M) ? W[c0 * M + r1] : 0.f;
-      const float a2 = (r0 < M && c1 < M) ? W[c1 * M + r0] : 0.f;
-      const float a3 = (r1 < M && c1 < M) ? W[c1 * M + r1] : 0.f;
       unsigned ahi[4], alo[4];
-      tf32_split(a0, ahi[0], alo[0]);
-      tf32_split(a1, ahi[1], alo[1]);
-      tf32_split(a2, ahi[2], alo[2]);
-      tf32_split(a3, ahi[3], alo[3]);
-      // B fragment: rows k (input order index k, or k + 1 for the imaginary part), column j
-      unsigned bhi[2], blo[2];
-      const int kk[2] = {c0, c1};
+      ahi[0] = r0 < M ? Ah[r0 * K + c0] : 0u;
+      ahi[1] = r1 < M ? Ah[r1 * K + c0] : 0u;
+      ahi[2] = r0 < M ? Ah[r0 * K + c1] : 0u;
+      ahi[3] = r1 < M ? Ah[r1 * K + c1] : 0u;
+      alo[0] = r0 < M ? Al[r0 * K + c0] : 0u;
+      alo[1] = r1 < M ? Al[r1 * K + c0] : 0u;
+      alo[2] = r0 < M ? Al[r0 * K + c1] : 0u;
+      alo[3] = r1 < M ? Al[r1 * K + c1] : 0u;
+      // B rows: column kk of the A operand is input order m (as above); its G row is n + m (re) or n - m (im)
+      const int mk0 = part ? (q ? 2 * c0 + 1 : 2 * c0 + 2) : 2 * c0 + q;
+      const int mk1 = part ? (q ? 2 * c1 + 1 : 2 * c1 + 2) : 2 * c1 + q;
+      const float* g0 = (mk0 <= n) ? Gs + (long long)(n + (part ? -mk0 : mk0)) * NC3 : nullptr;
+      const float* g1 = (mk1 <= n) ? Gs + (long long)(n + (part ? -mk1 : mk1)) * NC3 : nullptr;
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        float bv = 0.f;
-        const int m = im ? kk[e] + 1 : kk[e];
-        if (kk[e] < M && j < NCOL && (m & 1) == jp) bv = Gs[((n + (im ? -m : m)) * hb + jb) * 3 + jc];
-        tf32_split(bv, bhi[e], blo[e]);
+      for (int t = 0; t < kRotMaxNt; ++t) {
+        if (t0 + t < NTN) {
+          const int j = (t0 + t) * 8 + gq;
+          const float b0v = (g0 && j < NC3) ? g0[j] : 0.f;
+          const float b1v = (g1 && j < NC3) ? g1[j] : 0.f;
+          unsigned bhi[2], blo[2];
+          tf32_split(b0v, bhi[0], blo[0]);
+          tf32_split(b1v, bhi[1], blo[1]);
+          mma_tf32(d[t], alo, bhi);
+          mma_tf32(d[t], ahi, blo);
+          mma_tf32(d[t], ahi, bhi);
+        }
       }
-      mma_tf32(d, alo, bhi);
-      mma_tf32(d, ahi, blo);
-      mma_tf32(d, ahi, bhi);
     }
-    // D fragment: rows r0 / r1 (output order m' = row, or row + 1 for the imaginary part), columns
-    // nt*8 + 2 tq and + 1
+    // D: rows r0 / r1 (output order m' = row, or row + 1 for the imaginary part), columns (b, c);
+    // E (q = 0) and O (q = 1) interleave in the buffer's last index
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int row = e < 2 ? r0 : r1, col = nt * 8 + 2 * tq + (e & 1);
-      if (row < M && col < NCOL) {
-        const int pk = im ? n * (n + 1) - (row + 1) : n * (n + 1) + row;
-        EO[eo_row(ld, a, pk, p) + col] = d[e];  // col = (b, c, parity)
+    for (int t = 0; t < kRotMaxNt; ++t) {
+      if (t0 + t < NTN) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = e < 2 ? r0 : r1, col = (t0 + t) * 8 + 2 * tq + (e & 1);
+          if (row < M && col < NC3) {
+            const int pk = part ? n * (n + 1) - (row + 1) : n * (n + 1) + row;
+            EO[eo_row(ld, a, pk, p) + 2 * col + q] = d[t][e];
+          }
+        }
       }
     }
   }
@@ -262,7 +310,9 @@ int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* de
     const int p = g.p;
     const int ng = (p + 1) * (2 * p + 2), ntri = (p + 1) * (p + 2) / 2;
     if (g.ndrop * (long long)ng > 0x7fffffffLL) return BIE_EINVAL;
-    const size_t smem = sizeof(float) * ((size_t)(p + 1) * (p + 1) + (size_t)p * p + (2 * (size_t)p + 1) * (p + 1) * 3);
+    // A hi / lo for both parts and parities (each padded to 8 columns) and the degree-p rows of G
+    const size_t acols = (size_t)(((p + 2) / 2 + 7) & ~7) + (((p + 1) / 2 + 7) & ~7);
+    const size_t smem = sizeof(float) * (2 * (size_t)(p + 1) * acols * 2 + (2 * (size_t)p + 1) * (p + 1) * 3);
     if (smem > 227 * 1024) return BIE_EINVAL;
     if (smem > 48 * 1024)
       BIE_CUDA_TRY(cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
