@@ -127,24 +127,47 @@ __global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const
   float* Gs = reinterpret_cast<float*>(Alo + acur);  // [n + mm][b][c], mm = -n..n
   const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
   const float* blk = A.wblk + (long long)a * A.wstride + boff;
+  // the degree's rows of G go to shared memory by asynchronous 4-byte copies, all in flight at once
+  const float* gsrc = Gm + ((ld * (p + 1) * (p + 1)) + (long long)n * n) * NC3;
+  for (int i = threadIdx.x; i < (2 * n + 1) * NC3; i += blockDim.x) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(Gs + i);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(gsrc + i) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  // W's columns of each parity, split into TF32 hi / lo: the loads of a thread's entries are issued
+  // together (eight per batch) before any is split and stored
   for (int part = 0; part < 2; ++part)
     for (int q = 0; q < 2; ++q) {
       const int M = part ? Mim : Mre, K = ka[part][q];
-      for (int i = threadIdx.x; i < M * K; i += blockDim.x) {
-        const int row = i / K, kk = i - row * K;
-        // input order of column kk: m = 2 kk + q (re, m = 0..n); m = 2 kk + 1 + (1 - q) ... (im, m = 1..n)
-        const int m = part ? (q ? 2 * kk + 1 : 2 * kk + 2) : 2 * kk + q;
-        float v = 0.f;
-        if (part == 0 && m <= n) v = __ldg(blk + (long long)m * (n + 1) + row);                 // C(m' = row, m)
-        if (part == 1 && m <= n) v = __ldg(blk + (long long)(n + 1) * (n + 1) + (long long)(m - 1) * n + row);  // S
-        unsigned hi, lo;
-        tf32_split(v, hi, lo);
-        Ahi[aoff[part][q] + i] = hi;
-        Alo[aoff[part][q] + i] = lo;
+      const int total = M * K;
+      for (int i0 = threadIdx.x; i0 < total; i0 += 8 * blockDim.x) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * blockDim.x;
+          v[u] = 0.f;
+          if (i < total) {
+            const int row = i / K, kk = i - row * K;
+            // input order of column kk: m = 2 kk + q (re, m = 0..n); odd m = 2 kk + 1, even m = 2 kk + 2 (im)
+            const int m = part ? (q ? 2 * kk + 1 : 2 * kk + 2) : 2 * kk + q;
+            if (m <= n)
+              v[u] = part ? __ldg(blk + (long long)(n + 1) * (n + 1) + (long long)(m - 1) * n + row)  // S
+                          : __ldg(blk + (long long)m * (n + 1) + row);                                // C
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * blockDim.x;
+          if (i < total) {
+            unsigned hi, lo;
+            tf32_split(v[u], hi, lo);
+            Ahi[aoff[part][q] + i] = hi;
+            Alo[aoff[part][q] + i] = lo;
+          }
+        }
       }
     }
-  const float* gsrc = Gm + ((ld * (p + 1) * (p + 1)) + (long long)n * n) * NC3;
-  for (int i = threadIdx.x; i < (2 * n + 1) * NC3; i += blockDim.x) Gs[i] = __ldg(gsrc + i);
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gq = lane >> 2, tq = lane & 3;
