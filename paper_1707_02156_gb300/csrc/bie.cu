@@ -315,7 +315,7 @@ struct bie_geom {
   bie::DevBuf<double> centre_d, partial, wS_all, wD_all, wSr_all, wDr_all;
   int nblk = 0, ntile = 0;
   int tpt32 = 2, tpt64 = 2;                         // targets per thread of the pair kernel (autotuned FP32)
-  bie::DevBuf<float> eo32, g32;                     // tensor-core self path: per-degree sums, phase-shifted coefficients
+  bie::DevBuf<float> eo32, g32;                     // tensor-core self path: rotated sums, phase-shifted coefficients
   std::vector<std::pair<long long, int>> near;      // (target, source drop) pairs in Omega_2
   // near-singular step (Omega_2), Sec. 2.3
   int nnear_tgt = 0;
@@ -449,9 +449,9 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
     Phase ph(ctx, self_phase_name<R>(), s);
     if constexpr (std::is_same<R, float>::value) {
       if (ctx->cfg.tensor_rotation) {
-        // per-degree partial sums of a chunk of drops kept within 32 MB, so that they stay in L2
+        // E/O sums of a chunk of drops kept within 32 MB, so that they stay in L2 between the two kernels
         const long long budget = 8LL << 20;
-        BIE_TRY(g->eo32.alloc((size_t)self_tc_part_floats(proj, budget)));
+        BIE_TRY(g->eo32.alloc((size_t)self_tc_eo_floats(proj, budget)));
         BIE_TRY(g->g32.alloc((size_t)self_tc_g_floats(proj, budget)));
         return launch_self_tc(proj, dens, g->vals.ptr, g->eo32.ptr, g->g32.ptr, budget, s);
       }

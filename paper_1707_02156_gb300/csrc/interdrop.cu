@@ -237,20 +237,8 @@ __device__ __forceinline__ fx2 x2_rsqrt(fx2 v) {
   x2_unpack(v, lo, hi);
   return x2_pack(rsqrtf(lo), rsqrtf(hi));
 }
-// 1/v per lane from the MUFU reciprocal estimate (rcp.approx: about 1 ulp), so that 1/r^2 costs an
-// XU-pipe instruction instead of an FMA-pipe multiply of 1/r by itself
-__device__ __forceinline__ fx2 x2_rcp(fx2 v) {
-  float lo, hi, rl, rh;
-  x2_unpack(v, lo, hi);
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rl) : "f"(lo));
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rh) : "f"(hi));
-  return x2_pack(rl, rh);
-}
 
-// sources staged per pass of the packed kernel: 32 for 4 targets per thread (one-warp blocks, whose
-// shared memory then allows 32 blocks per SM), 64 otherwise
-template <int TPT>
-__host__ __device__ constexpr int chunk_x2() { return TPT >= 4 ? 32 : 64; }
+constexpr int kChunkX2 = 64;  // sources staged per pass of the packed kernel
 
 // Staged source of the packed kernel: each value duplicated into both lanes, in the order
 // x, y, z, q0, q1, q2, n0, n1, n2 (and one pad), read with 128-bit shared-memory loads (three for
@@ -267,7 +255,7 @@ struct alignas(16) SrcRecX2 {
 // into registers while the current chunk is summed, so the global-memory latency of the staging
 // overlaps the arithmetic.
 template <int KIND, int TPT, int PF>
-__global__ void __launch_bounds__(kTile / TPT, TPT >= 4 ? 28 : 1) k_interdrop_x2(
+__global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
     const PairItem* __restrict__ items, const int* __restrict__ blk_item, const long long* __restrict__ tile_t0,
     const int* __restrict__ tile_n, const int* __restrict__ tile_drop, const long long* __restrict__ tgt_loc,
     const long long* __restrict__ toff_std, const int* __restrict__ ngd, const double* __restrict__ rec_std,
@@ -279,7 +267,6 @@ __global__ void __launch_bounds__(kTile / TPT, TPT >= 4 ? 28 : 1) k_interdrop_x2
   constexpr int NW = TPT / 2;  // lane pairs per thread
   constexpr int NV = KIND ? 9 : 6;
   constexpr int nv = (NV + 1) / 2;  // 128-bit loads per staged source
-  constexpr int kChunkX2 = chunk_x2<TPT>();
   constexpr int RPT = kChunkX2 / NT;  // staged sources per thread and chunk
   __shared__ SrcRecX2 src[kChunkX2];
   __shared__ float tgt[3][kTile];   // the tile's targets relative to their own drop's centre (FP32)
@@ -398,7 +385,7 @@ __global__ void __launch_bounds__(kTile / TPT, TPT >= 4 ? 28 : 1) k_interdrop_x2
               const fx2 r2 = x2_fma(dz, dz, x2_fma(dy, dy, x2_mul(dx, dx)));
               const fx2 ri = x2_rsqrt(r2);
               const fx2 xq = x2_fma(dz, v[5], x2_fma(dy, v[4], x2_mul(dx, v[3])));
-              const fx2 ri2 = x2_rcp(r2);
+              const fx2 ri2 = x2_mul(ri, ri);
               if (KIND == 0) {  // Stokeslet: q/r + (xh.q) xh/r^3
                 const fx2 c = x2_mul(x2_mul(xq, ri2), ri);
                 s[w][0] = x2_fma(c, dx, x2_fma(v[3], ri, s[w][0]));

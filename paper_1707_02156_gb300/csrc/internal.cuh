@@ -123,12 +123,11 @@ int launch_split_dff(const double* in, dff* out, long long n, cudaStream_t s);
 template <typename R, typename CT>
 int launch_self_proj(std::vector<SelfGroup<R>> groups, const CT* dens, double* vals, cudaStream_t s);
 // The FP32 projected form with the Wigner rotation on the tensor cores (self_tc.cu): per chunk of
-// drops of one degree, the phase-shifted coefficients into gm, the rotation products and their
-// contraction with the factors into per-degree partial sums `part` (at most `budget` floats per chunk,
-// at least one drop's worth), then their sum into vals.  self_tc_*_floats = the buffers it needs.
-long long self_tc_part_floats(const std::vector<SelfGroup<float>>& groups, long long budget);
+// drops of one degree, the rotation products into eo (at most `budget` floats per chunk, at least one
+// drop's worth), then the contraction with the factors.  self_tc_eo_floats = the buffer it needs.
+long long self_tc_eo_floats(const std::vector<SelfGroup<float>>& groups, long long budget);
 long long self_tc_g_floats(const std::vector<SelfGroup<float>>& groups, long long budget);
-int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* dens, double* vals, float* part,
+int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* dens, double* vals, float* eo,
                    float* gm, long long budget, cudaStream_t s);
 // interfacial force at N grid points from x derivatives [6][3][N] and Gamma derivatives [3][N]
 int launch_force(const double* X, const double* Gm, long long N, double es, double xs, double* f, cudaStream_t s);

@@ -7,16 +7,16 @@
 // Splitting the input orders m by parity gives the even and odd partial sums E, O, from which the
 // four targets (theta_a, phi_b), (theta_a, phi_b + pi), (pi - theta_a, phi_b), (pi - theta_a,
 // phi_b + pi) follow exactly (the symmetries of the CUDA-core kernel k_self_proj).  With every
-// longitude b < p+1 of the latitude and the three components as columns, each (latitude, degree,
-// parity) is one matrix product
-//     E or O (m', (b, c)) = W(m', m of that parity) G(m of that parity, (b, c)),
-// W = C (rows m' = 0..n) or S (rows m' = 1..n).  k_self_tc runs these products as mma.sync m16n8k8 in
-// TF32 with the 3-pass split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (x = x_hi + x_lo, both TF32),
-// accumulated in FP32 (about FP32 accuracy), from the phase-shifted coefficients that k_phase_g forms
-// once per apply for every longitude; the sums stay in shared memory, where the same block contracts
-// them with the projected kernel factors Q of the latitude pair's 4 (p+1) targets at that degree
-// (Q streamed from HBM).  The per-degree sums of every target are added in a fixed order by
-// k_self_tc_reduce, so results do not depend on scheduling.
+// longitude b < p+1 of the latitude, the three components and the two parities as columns, each
+// (latitude, degree) is one matrix product
+//     [E | O](m', (b, c, parity)) = W(m', m) G(m, (b, c, parity)),
+// W = C (rows m' = 0..n) or S (rows m' = 1..n), G(m, (b, c, par)) = g_m(b, c) when m has the
+// column's parity, else 0.  k_rot_tc runs these products as mma.sync m16n8k8 in TF32 with the
+// 3-pass split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (x = x_hi + x_lo, both TF32), accumulated in
+// FP32 (about FP32 accuracy), from the phase-shifted coefficients that k_phase_g forms once per apply
+// for every longitude, with K split by the parity of m (no zero padding), and writes E and O to a buffer that stays in L2 for one drop's worth
+// of latitudes (drops are taken in chunks whose sums fit a fixed buffer); k_contract_eo then streams the projected kernel factors Q from HBM and contracts
+// them with E +- O, one block per target quadruple.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,6 +58,14 @@ __device__ __forceinline__ void sym_mul_add_f(const float* q, const float* v, fl
   acc[2] = fmaf(q[2], v[2], fmaf(q[5], v[1], fmaf(q[4], v[0], acc[2])));
 }
 
+// The rotated sums of one launch (a chunk of drops of one degree): EO[ld][a][packed (n, m')][b][c][parity],
+// so that a tile row of the products (one output order, eight (b, c, parity) columns) is 32
+// contiguous bytes.  eo_row = the offset of (ld, a, packed index pk).
+__device__ __forceinline__ long long eo_row(long long ld, int a, int pk, int p) {
+  const int hb = p + 1, na2 = (p + 2) / 2, nc = (p + 1) * (p + 1);
+  return ((ld * na2 + a) * (long long)nc + pk) * (long long)hb * 6;
+}
+
 // The phase-shifted coefficients g = e^{i m phi_b} rho_n^m of every longitude b < p+1, shared by all
 // latitudes: Gm[ld][packed (n, mm)][b][c] = Re g (mm >= 0) or Im g (mm < 0) of |mm|, in FP32.
 __global__ void k_phase_g(SelfGroup<float> A, const double* __restrict__ dens, float* __restrict__ Gm) {
@@ -85,13 +93,10 @@ __global__ void k_phase_g(SelfGroup<float> A, const double* __restrict__ dens, f
 // W's columns of each parity already split into TF32 hi / lo parts, and the degree's rows of the
 // phase-shifted coefficients G.  A warp owns one (part, parity, 16-row tile, half of N) and runs its
 // k-steps once, building the A fragment once per k-step and reusing it over up to 13 column tiles.
-// The E / O sums go to shared memory; then each warp takes longitudes b and contracts the degree's
-// 2n+1 rotated coefficients with the factors of b's four targets (lanes over the coefficients,
-// a shuffle reduction), writing part[target][n][c].
 constexpr int kRotMaxNt = 13;  // 8-column tiles per warp pass (N = 3 (p+1) takes one or two passes for p < 64)
 
-__global__ void __launch_bounds__(kTcThreads) k_self_tc(SelfGroup<float> A, const float* __restrict__ Gm,
-                                                        float* __restrict__ part) {
+__global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const float* __restrict__ Gm,
+                                                       float* __restrict__ EO) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = A.p;
   const int hb = p + 1;
@@ -120,7 +125,6 @@ __global__ void __launch_bounds__(kTcThreads) k_self_tc(SelfGroup<float> A, cons
     }
   unsigned* Alo = Ahi + acur;
   float* Gs = reinterpret_cast<float*>(Alo + acur);  // [n + mm][b][c], mm = -n..n
-  float* EOs = Gs + (2 * n + 1) * NC3;               // [n + mm'][b][c][parity]: E, O of the output orders
   const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
   const float* blk = A.wblk + (long long)a * A.wstride + boff;
   // the degree's rows of G go to shared memory by asynchronous 4-byte copies, all in flight at once
@@ -223,93 +227,96 @@ __global__ void __launch_bounds__(kTcThreads) k_self_tc(SelfGroup<float> A, cons
         for (int e = 0; e < 4; ++e) {
           const int row = e < 2 ? r0 : r1, col = (t0 + t) * 8 + 2 * tq + (e & 1);
           if (row < M && col < NC3) {
-            const int pl = part ? n - (row + 1) : n + row;  // local row n + m' (real) or n - m' (imaginary)
-            EOs[pl * 2 * NC3 + 2 * col + q] = d[t][e];
+            const int pk = part ? n * (n + 1) - (row + 1) : n * (n + 1) + row;
+            EO[eo_row(ld, a, pk, p) + 2 * col + q] = d[t][e];
           }
         }
       }
     }
   }
-  __syncthreads();
-  // contraction with the factors of the four targets of each longitude, at degree n
-  const int ntri = (p + 1) * (p + 2) / 2, ng = (p + 1) * (2 * p + 2), nb = 2 * p + 2;
+}
+
+// One block per target quadruple (drop, latitude pair a, longitude b): the E / O sums of every rotated
+// coefficient contracted with the four targets' projected factors (as k_self_proj: real parts with
+// the real planes, imaginary parts with the imaginary planes, whose signs the factors carry).
+__global__ void __launch_bounds__(kTcThreads) k_contract_eo(SelfGroup<float> A, const float* __restrict__ EO,
+                                                            double* __restrict__ vals) {
+  __shared__ float red[kTcWarps][12];
+  const int p = A.p;
+  const int ntri = (p + 1) * (p + 2) / 2;
+  const int nc = (p + 1) * (p + 1);
+  const int ng = (p + 1) * (2 * p + 2);
+  const int hb = p + 1, nb = 2 * p + 2, na2 = (p + 2) / 2;
+  const long long bid = blockIdx.x;
+  const long long ld = bid / ((long long)na2 * hb);
+  const int r = (int)(bid - ld * na2 * hb);
+  const int a = r / hb, b = r - a * hb;
   const int a2 = p - a;
   const bool quad = a2 != a;
+  const float* eo = EO + eo_row(ld, a, 0, p) + (long long)b * 6;  // row pk at + pk * hb * 6
   const long long qstride = 12 * (long long)ntri;
-  for (int b = warp; b < hb; b += kTcWarps) {
-    const long long tl[4] = {(long long)a * nb + b, (long long)a * nb + b + hb, (long long)a2 * nb + b,
-                             (long long)a2 * nb + b + hb};
-    float acc[4][3];
+  const float* Qk_[4] = {A.Q + (ld * ng + a * nb + b) * qstride, A.Q + (ld * ng + a * nb + b + hb) * qstride,
+                         A.Q + (ld * ng + a2 * nb + b) * qstride, A.Q + (ld * ng + a2 * nb + b + hb) * qstride};
+  float acc[4][3];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
-    for (int o = lane; o < 2 * n + 1; o += 32) {
-      const bool re = o <= n;
-      const int mo = re ? o : o - n;
-      const int t = n * (n + 1) / 2 + mo;
-      const int ri = re ? 0 : 1;
-      const float* v = EOs + (re ? n + mo : n - mo) * 2 * NC3 + b * 6;
-      const float vp[3] = {v[0] + v[1], v[2] + v[3], v[4] + v[5]};
-      const float vm[3] = {v[0] - v[1], v[2] - v[3], v[4] - v[5]};
+  for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.f;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const int n = degree_of(i);
+    const int o = i - n * n;
+    const bool re = o <= n;
+    const int mo = re ? o : o - n;
+    const int t = n * (n + 1) / 2 + mo;
+    const int ri = re ? 0 : 1;
+    const int pk = re ? n * (n + 1) + mo : n * (n + 1) - mo;
+    const float* e6 = eo + (long long)pk * hb * 6;
+    const float2 v01 = *reinterpret_cast<const float2*>(e6);
+    const float2 v23 = *reinterpret_cast<const float2*>(e6 + 2);
+    const float2 v45 = *reinterpret_cast<const float2*>(e6 + 4);
+    const float vp[3] = {v01.x + v01.y, v23.x + v23.y, v45.x + v45.y};
+    const float vm[3] = {v01.x - v01.y, v23.x - v23.y, v45.x - v45.y};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (k >= 2 && !quad) break;
-        const float* Qk = A.Q + (ld * ng + tl[k]) * qstride + t;
-        float qv[6];
+    for (int k = 0; k < 4; ++k) {
+      if (k >= 2 && !quad) break;
+      const float* Qk = Qk_[k] + t;
+      float q[6];
 #pragma unroll
-        for (int e = 0; e < 6; ++e) qv[e] = __ldg(Qk + (2 * e + ri) * (long long)ntri);
-        sym_mul_add_f(qv, (k == 0 || k == 3) ? vp : vm, acc[k]);
-      }
+      for (int e = 0; e < 6; ++e) q[e] = __ldg(Qk + (2 * e + ri) * (long long)ntri);
+      sym_mul_add_f(q, (k == 0 || k == 3) ? vp : vm, acc[k]);
     }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      for (int off = 16; off > 0; off >>= 1) acc[k][c] += __shfl_down_sync(0xffffffffu, acc[k][c], off);
+  if (lane == 0)
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        for (int off = 16; off > 0; off >>= 1) acc[k][c] += __shfl_down_sync(0xffffffffu, acc[k][c], off);
-    if (lane == 0)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (k >= 2 && !quad) break;
-        float* pt = part + ((ld * ng + tl[k]) * (p + 1) + n) * 3;
-        pt[0] = acc[k][0];
-        pt[1] = acc[k][1];
-        pt[2] = acc[k][2];
-      }
+      for (int c = 0; c < 3; ++c) red[warp][k * 3 + c] = acc[k][c];
+  __syncthreads();
+  const int nt = quad ? 4 : 2;
+  if (threadIdx.x < 3 * nt) {
+    float v = 0.f;
+    for (int w = 0; w < kTcWarps; ++w) v += red[w][threadIdx.x];
+    const int k = threadIdx.x / 3, c = threadIdx.x - 3 * k;
+    const int tl = (k < 2 ? a * nb : a2 * nb) + b + (k & 1) * hb;
+    vals[A.val_off[ld] + (long long)c * ng + tl] = A.wts[ld] * (double)v;
   }
-}
-
-// vals = weight * (the per-degree sums of every target, added in degree order, in FP64)
-__global__ void k_self_tc_reduce(SelfGroup<float> A, const float* __restrict__ part, double* __restrict__ vals) {
-  const int p = A.p;
-  const int ng = (p + 1) * (2 * p + 2);
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= A.ndrop * (long long)ng) return;
-  const long long ld = idx / ng;
-  const int tl = (int)(idx - ld * ng);
-  const float* pt = part + idx * (p + 1) * 3;
-  double s0 = 0, s1 = 0, s2 = 0;
-  for (int n = 0; n <= p; ++n) {
-    s0 += (double)pt[3 * n];
-    s1 += (double)pt[3 * n + 1];
-    s2 += (double)pt[3 * n + 2];
-  }
-  const double w = A.wts[ld];
-  double* v = vals + A.val_off[ld] + tl;
-  v[0] = w * s0;
-  v[ng] = w * s1;
-  v[2 * (long long)ng] = w * s2;
 }
 
 }  // namespace
 
-// Per-degree partial sums of one drop of degree p (floats)
-static long long part_per_drop(int p) { return (long long)(p + 1) * (2 * p + 2) * (p + 1) * 3; }
+// E/O floats of one drop of degree p
+static long long eo_per_drop(int p) { return (long long)((p + 2) / 2) * (p + 1) * (long long)(p + 1) * (p + 1) * 6; }
 
-// Drops per launch of a group: as many as keep the chunk's partial sums within `budget` floats.
-static long long chunk_drops(int p, long long budget) { return std::max(1LL, budget / part_per_drop(p)); }
+// Drops per launch of a group: as many as keep the chunk's E/O sums within `budget` floats (at least one).
+static long long chunk_drops(int p, long long budget) { return std::max(1LL, budget / eo_per_drop(p)); }
 
-long long self_tc_part_floats(const std::vector<SelfGroup<float>>& groups, long long budget) {
+long long self_tc_eo_floats(const std::vector<SelfGroup<float>>& groups, long long budget) {
   long long n = 0;
-  for (const auto& g : groups) n = std::max(n, std::min(g.ndrop, chunk_drops(g.p, budget)) * part_per_drop(g.p));
+  for (const auto& g : groups) n = std::max(n, std::min(g.ndrop, chunk_drops(g.p, budget)) * eo_per_drop(g.p));
   return n;
 }
 
@@ -320,23 +327,18 @@ long long self_tc_g_floats(const std::vector<SelfGroup<float>>& groups, long lon
   return n;
 }
 
-size_t self_tc_smem(int p) {
-  // A hi / lo for both parts and parities (each padded to 8 columns), the degree-p rows of G, and
-  // the E / O sums of degree p
-  const size_t acols = (size_t)(((p + 2) / 2 + 7) & ~7) + (((p + 1) / 2 + 7) & ~7);
-  return sizeof(float) * (2 * (size_t)(p + 1) * acols * 2 + (2 * (size_t)p + 1) * (p + 1) * 3 * 3);
-}
-
-int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* dens, double* vals, float* part,
+int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* dens, double* vals, float* eo,
                    float* gm, long long budget, cudaStream_t s) {
   for (const auto& g : groups) {
     const int p = g.p;
     const int ng = (p + 1) * (2 * p + 2), ntri = (p + 1) * (p + 2) / 2;
     if (g.ndrop * (long long)ng > 0x7fffffffLL) return BIE_EINVAL;
-    const size_t smem = self_tc_smem(p);
+    // A hi / lo for both parts and parities (each padded to 8 columns) and the degree-p rows of G
+    const size_t acols = (size_t)(((p + 2) / 2 + 7) & ~7) + (((p + 1) / 2 + 7) & ~7);
+    const size_t smem = sizeof(float) * (2 * (size_t)(p + 1) * acols * 2 + (2 * (size_t)p + 1) * (p + 1) * 3);
     if (smem > 227 * 1024) return BIE_EINVAL;
     if (smem > 48 * 1024)
-      BIE_CUDA_TRY(cudaFuncSetAttribute(k_self_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      BIE_CUDA_TRY(cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long per = chunk_drops(p, budget);
     for (long long d0 = 0; d0 < g.ndrop; d0 += per) {
       // the chunk's drops d0 .. d0 + nd - 1 of the group, as a group of their own
@@ -352,11 +354,10 @@ int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* de
       count_launch();
       BIE_CUDA_TRY(cudaGetLastError());
       const long long nblk = c.ndrop * ((p + 2) / 2) * (long long)(p + 1);
-      k_self_tc<<<(unsigned)nblk, kTcThreads, smem, s>>>(c, gm, part);
+      k_rot_tc<<<(unsigned)nblk, kTcThreads, smem, s>>>(c, gm, eo);
       count_launch();
       BIE_CUDA_TRY(cudaGetLastError());
-      const long long nt = c.ndrop * (long long)ng;
-      k_self_tc_reduce<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(c, part, vals);
+      k_contract_eo<<<(unsigned)nblk, kTcThreads, 0, s>>>(c, eo, vals);
       count_launch();
       BIE_CUDA_TRY(cudaGetLastError());
     }
