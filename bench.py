@@ -14,7 +14,7 @@ value = Stokes pair interactions evaluated per second: (self-rule + regular + up
 near-singular pairs of one operator apply) x (operator applies in the step) / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c1..c5]
-                  [--no-aux] [--timesteps N] [--fp64-solve] [--coupled c4|c5]
+                  [--no-aux] [--timesteps N] [--fp64-solve] [--tensor-rotation] [--coupled c4|c5]
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload, on the host's
 cores.  The other configurations (c1 .. c4) are reported under "also" unless --no-aux.
@@ -55,6 +55,9 @@ STEP = ("rhs 2 u_inf + S[f] (double-float S apply) + mixed solve: FP32 inner GMR
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel on a workload,
 # from one ncu capture, with the SHA-256 prefix of the kernel's source file at the time of the
 # capture: a capture of an older version of the kernel is not reported (traffic null).
+# bie_config.tensor_rotation of every context the bench makes (--tensor-rotation)
+TENSOR_ROTATION = False
+
 PROFILED_TRAFFIC = {
     ("interdrop_f32", "c5"): {"bytes": None, "source": "interdrop.cu", "sha": None},
 }
@@ -72,6 +75,8 @@ def parse(argv=None):
                     help="also time this many midpoint time steps of the workload (two solves each)")
     ap.add_argument("--fp64-solve", action="store_true",
                     help="also time the plain FP64 GMRES solve of the headline workload (minutes on c5)")
+    ap.add_argument("--tensor-rotation", action="store_true",
+                    help="rotate the projected self form on the tensor cores (bie_config.tensor_rotation)")
     ap.add_argument("--coupled", default=None, choices=["c4", "c5"],
                     help="print only the timing of coupled drop/surfactant steps (Alg. 1) on this workload")
     return ap.parse_args(argv)
@@ -295,7 +300,7 @@ class Case:
         build.build()
         self.name = name
         self.w = w = inputs.config(name)
-        self.ctx = api.Context(local, upsample=w.up)
+        self.ctx = api.Context(local, upsample=w.up, tensor_rotation=TENSOR_ROTATION)
         self.x = torch.tensor(w.xcoef, device="cuda")
         torch.cuda.synchronize()
         self.ctx.profile(True)
@@ -433,12 +438,15 @@ def solve_line(name, local, steps, warmup, world, peaks, headline=False, fp64_so
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        # the timed steps are the range a profiler started with --profile-from-start off records
+        torch.cuda.profiler.start()
         times = []
         for _ in range(steps):
             times += timed_each(mixed_step, 1, stream, scrub)
             info = last["info"]
             applies += 1 + info["applies_fp64"] + info["applies_mixed"]
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         if world > 1:
             torch.distributed.barrier()
     launches = api.launch_count() - launches0
@@ -449,7 +457,7 @@ def solve_line(name, local, steps, warmup, world, peaks, headline=False, fp64_so
             "pairs_per_apply": case.pairs, "applies_per_step": applies / steps, "gpu_launches": launches,
             "clocks": clk.summary(), "force": case.force,
             "geometry": {k: case.info[k] for k in ("ndrop", "ntarget", "self_pairs", "far_pairs", "up_pairs",
-                                                      "near_targets", "near_pairs", "interdrop_tpt")},
+                                                      "near_targets", "near_pairs", "interdrop_tpt", "pair_slots")},
             "solve": {k: info[k] for k in ("iterations", "refinements", "applies_fp64", "applies_mixed",
                                            "residual")}}
     u_mixed = case.u.clone()
@@ -842,6 +850,7 @@ def run_ours(args):
 
 if __name__ == "__main__":
     a = parse()
+    TENSOR_ROTATION = a.tensor_rotation
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     if a.impl == "reference":
         run_reference(a)

@@ -78,14 +78,15 @@ typedef struct bie_config {
   int use_graphs;    /* 1: an apply (kind, flags) is captured into a CUDA graph at its second call and
                         replayed afterwards (input and output pass through fixed internal buffers);
                         0: every apply launches its kernels one by one */
-  int tensor_rotation; /* 1 (default): in BIE_MIXED applies the Wigner rotation of the projected self
-                          form (App. B) runs on the tensor cores (TF32 with a 3-pass split, FP32
-                          accumulation, about FP32 accuracy); 0: on the CUDA cores in FP32.  FP64 and
-                          BIE_DF applies always rotate on the CUDA cores */
+  int tensor_rotation; /* 1: in BIE_MIXED applies the Wigner rotation of the projected self form
+                          (App. B) of degrees up to 58 runs on the tensor cores (TF32 with a 3-pass
+                          split, FP32 accumulation, about FP32 accuracy); 0 (default): on the CUDA cores
+                          in FP32, which measured 1.4-1.7 times faster on GB300.  FP64 and BIE_DF
+                          applies always rotate on the CUDA cores */
 } bie_config;
 
 /* Fill a config with the paper's defaults: device 0, U = 4, A = 5, L = 8, projected self form, graphs
- * on, tensor-core rotation on. */
+ * on, CUDA-core rotation. */
 void bie_config_default(bie_config* cfg);
 
 /* Create a context on cfg->device.  Plan tables are built lazily per degree and cached. */
@@ -164,6 +165,9 @@ typedef struct bie_geom_info {
   long long near_pairs;   /* pairs evaluated at Omega_2 check points */
   double cache_bytes;     /* device bytes held by the geometry */
   int interdrop_tpt;      /* targets per thread chosen by the pair-kernel autotuner (FP32) */
+  long long pair_slots;   /* target slots x sources that the inter-drop pair kernels run: every work item
+                             covers the 128 target slots of its tile, so (far_pairs + up_pairs) / pair_slots
+                             is the share of that work that is useful */
 } bie_geom_info;
 int bie_geometry_info(const bie_geom* geom, bie_geom_info* info);
 

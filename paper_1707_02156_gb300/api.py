@@ -34,7 +34,7 @@ class bie_geom_info(ctypes.Structure):
 
     _fields_ = [("ndrop", c_int), ("ncoef", c_ll), ("ntarget", c_ll), ("self_pairs", c_ll), ("far_pairs", c_ll),
                 ("up_pairs", c_ll), ("near_targets", c_ll), ("near_pairs", c_ll), ("cache_bytes", c_double),
-                ("interdrop_tpt", c_int)]
+                ("interdrop_tpt", c_int), ("pair_slots", c_ll)]
 
 
 class bie_solve_opts(ctypes.Structure):
@@ -201,7 +201,7 @@ class Context:
     """A library context on one CUDA device (plan tables cached per degree)."""
 
     def __init__(self, device: int = 0, upsample: int = 4, a_tilde: float = 5.0, n_interp: int = 8,
-                 self_direct: bool = False, use_graphs: bool = True, tensor_rotation: bool = True):
+                 self_direct: bool = False, use_graphs: bool = True, tensor_rotation: bool = False):
         L = lib()
         cfg = bie_config()
         L.bie_config_default(ctypes.byref(cfg))

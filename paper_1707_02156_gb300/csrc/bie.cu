@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <initializer_list>
@@ -144,6 +145,14 @@ struct bie_ctx {
   std::map<std::pair<int, int>, std::unique_ptr<bie::Plan>> plans;
   std::map<int, std::unique_ptr<bie::WigPlan>> wigs;
   bie::DevBuf<double> scratch;  // analysis workspace
+  // pair-kernel variant chosen at earlier geometries: degrees, self-grid degrees, U, pair count, variant
+  struct Tuned {
+    std::vector<int> p, pq;
+    int up;
+    long long pairs;
+    int tpt;
+  };
+  std::vector<Tuned> tuned;
 };
 
 namespace bie {
@@ -315,7 +324,8 @@ struct bie_geom {
   bie::DevBuf<double> centre_d, partial, wS_all, wD_all, wSr_all, wDr_all;
   int nblk = 0, ntile = 0;
   int tpt32 = 2, tpt64 = 2;                         // targets per thread of the pair kernel (autotuned FP32)
-  bie::DevBuf<float> eo32, g32;                     // tensor-core self path: rotated sums, phase-shifted coefficients
+  bie::DevBuf<float> eo32;                          // tensor-core self path: rotated sums
+  bie::DevBuf<unsigned> g32;                        // and the split phase-shifted coefficients
   std::vector<std::pair<long long, int>> near;      // (target, source drop) pairs in Omega_2
   // near-singular step (Omega_2), Sec. 2.3
   int nnear_tgt = 0;
@@ -449,11 +459,19 @@ static int self_apply(bie_geom* g, int kind, bool raw, const double* dens, cudaS
     Phase ph(ctx, self_phase_name<R>(), s);
     if constexpr (std::is_same<R, float>::value) {
       if (ctx->cfg.tensor_rotation) {
-        // E/O sums of a chunk of drops kept within 32 MB, so that they stay in L2 between the two kernels
-        const long long budget = 8LL << 20;
-        BIE_TRY(g->eo32.alloc((size_t)self_tc_eo_floats(proj, budget)));
-        BIE_TRY(g->g32.alloc((size_t)self_tc_g_floats(proj, budget)));
-        return launch_self_tc(proj, dens, g->vals.ptr, g->eo32.ptr, g->g32.ptr, budget, s);
+        // degrees whose rotation block fits one SM's shared memory go to the tensor cores, the rest
+        // (above 58) to the CUDA-core kernel
+        std::vector<SelfGroup<R>> tc, cc;
+        for (const auto& sg : proj) (self_tc_fits(sg.p) ? tc : cc).push_back(sg);
+        if (!tc.empty()) {
+          // E/O sums of a chunk of drops kept within 32 MB, so that they stay in L2 between the kernels
+          const long long budget = 8LL << 20;
+          BIE_TRY(g->eo32.alloc((size_t)self_tc_eo_floats(tc, budget)));
+          BIE_TRY(g->g32.alloc((size_t)self_tc_g_floats(tc, budget)));
+          BIE_TRY(launch_self_tc(tc, dens, g->vals.ptr, g->eo32.ptr, g->g32.ptr, budget, s));
+        }
+        if (!cc.empty()) BIE_TRY((launch_self_proj<R, double>(cc, dens, g->vals.ptr, s)));
+        return BIE_OK;
       }
     }
     BIE_TRY((launch_self_proj<R, double>(proj, dens, g->vals.ptr, s)));
@@ -709,6 +727,17 @@ static int autotune_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   const long long pairs = g->info.far_pairs + g->info.up_pairs;
   g->info.interdrop_tpt = g->tpt32;
   if (pairs < 500000000LL || g->nblk == 0) return BIE_OK;
+  // a geometry of the same drops whose pair count is within 10% of one tuned before in this context
+  // (the next time step's geometry, say) reuses that choice
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (const auto& t : ctx->tuned)
+      if (t.p == g->p && t.pq == g->pq && t.up == ctx->cfg.upsample && std::llabs(pairs - t.pairs) * 10 <= t.pairs) {
+        g->tpt32 = t.tpt;
+        g->info.interdrop_tpt = t.tpt;
+        return BIE_OK;
+      }
+  }
   BIE_TRY(g->sQ32.alloc(3 * g->ntarget));
   BIE_TRY(g->uQ32.alloc(3 * g->nup_total));
   BIE_CUDA_TRY(cudaMemsetAsync(g->sQ32.ptr, 0, 3 * g->ntarget * sizeof(float), s));
@@ -748,6 +777,9 @@ static int autotune_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   g->info.interdrop_tpt = g->tpt32;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->tuned.size() >= 16) ctx->tuned.erase(ctx->tuned.begin());
+  ctx->tuned.push_back({g->p, g->pq, ctx->cfg.upsample, pairs, g->tpt32});
   return BIE_OK;
 }
 
@@ -887,7 +919,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   const long long cap_global = std::max<long long>(2048, std::min<long long>(65536, all_sources / (8LL * ctx->sms)));
   std::vector<PairItem> items;
   std::vector<int> blk_item, tile_blk(ntile + 1, 0);
-  long long far_pairs = 0, up_pairs = 0;
+  long long far_pairs = 0, up_pairs = 0, slots = 0;
   g->near.clear();
   for (int ti = 0; ti < ntile; ++ti) {
     std::vector<PairItem> mine;
@@ -918,6 +950,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
         mine.push_back(a);
         total += ngd[j];
         far_pairs += (long long)n0 * ngd[j];
+        slots += (long long)kTile * ngd[j];
       }
       if (n1) {
         b.tile = ti;
@@ -928,6 +961,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
         mine.push_back(b);
         total += g->up_n[j];
         up_pairs += (long long)n1 * g->up_n[j];
+        slots += (long long)kTile * g->up_n[j];
       }
     }
     // split the tile's items into blocks of at most `cap` sources
@@ -975,6 +1009,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   BIE_TRY(g->wDr_all.upload(wDr));
   g->info.far_pairs = far_pairs;
   g->info.up_pairs = up_pairs;
+  g->info.pair_slots = slots;
   g->info.near_targets = (long long)g->near.size();
   BIE_TRY(g->up_off_d.upload(g->up_off));
   BIE_TRY(g->up_n_d.upload(g->up_n));
@@ -2179,7 +2214,7 @@ void bie_config_default(bie_config* cfg) {
   cfg->n_interp = 8;
   cfg->self_direct = 0;
   cfg->use_graphs = 1;
-  cfg->tensor_rotation = 1;
+  cfg->tensor_rotation = 0;
 }
 
 const char* bie_strerror(int st) {

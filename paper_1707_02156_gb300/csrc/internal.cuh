@@ -127,8 +127,10 @@ int launch_self_proj(std::vector<SelfGroup<R>> groups, const CT* dens, double* v
 // drop's worth), then the contraction with the factors.  self_tc_eo_floats = the buffer it needs.
 long long self_tc_eo_floats(const std::vector<SelfGroup<float>>& groups, long long budget);
 long long self_tc_g_floats(const std::vector<SelfGroup<float>>& groups, long long budget);
+// whether k_rot_tc's shared memory at degree p fits one block (degrees up to 58)
+bool self_tc_fits(int p);
 int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* dens, double* vals, float* eo,
-                   float* gm, long long budget, cudaStream_t s);
+                   unsigned* gm, long long budget, cudaStream_t s);
 // interfacial force at N grid points from x derivatives [6][3][N] and Gamma derivatives [3][N]
 int launch_force(const double* X, const double* Gm, long long N, double es, double xs, double* f, cudaStream_t s);
 // out[i] = (float) in[i]

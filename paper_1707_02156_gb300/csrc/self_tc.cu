@@ -14,7 +14,8 @@
 // column's parity, else 0.  k_rot_tc runs these products as mma.sync m16n8k8 in TF32 with the
 // 3-pass split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (x = x_hi + x_lo, both TF32), accumulated in
 // FP32 (about FP32 accuracy), from the phase-shifted coefficients that k_phase_g forms once per apply
-// for every longitude, with K split by the parity of m (no zero padding), and writes E and O to a buffer that stays in L2 for one drop's worth
+// for every longitude (already split into TF32 hi / lo parts), with K split by the parity of m (no zero
+// padding), and writes E and O to a buffer that stays in L2 for one drop's worth
 // of latitudes (drops are taken in chunks whose sums fit a fixed buffer); k_contract_eo then streams the projected kernel factors Q from HBM and contracts
 // them with E +- O, one block per target quadruple.
 #include <cuda_runtime.h>
@@ -67,8 +68,10 @@ __device__ __forceinline__ long long eo_row(long long ld, int a, int pk, int p) 
 }
 
 // The phase-shifted coefficients g = e^{i m phi_b} rho_n^m of every longitude b < p+1, shared by all
-// latitudes: Gm[ld][packed (n, mm)][b][c] = Re g (mm >= 0) or Im g (mm < 0) of |mm|, in FP32.
-__global__ void k_phase_g(SelfGroup<float> A, const double* __restrict__ dens, float* __restrict__ Gm) {
+// latitudes, already split for the 3-pass products: Ghi, Glo[ld][packed (n, mm)][b][c] = the TF32 hi /
+// lo parts of Re g (mm >= 0) or Im g (mm < 0) of |mm|.
+__global__ void k_phase_g(SelfGroup<float> A, const double* __restrict__ dens, unsigned* __restrict__ Ghi,
+                          unsigned* __restrict__ Glo) {
   const int p = A.p;
   const int hb = p + 1, nb = 2 * p + 2, nc = (p + 1) * (p + 1);
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -84,7 +87,10 @@ __global__ void k_phase_g(SelfGroup<float> A, const double* __restrict__ dens, f
   const float fr = (float)f[n * (n + 1) + m];
   const float fi = m > 0 ? (float)f[n * (n + 1) - m] : 0.f;
   const float co = A.ph[((long long)m * nb + b) * 2], si = A.ph[((long long)m * nb + b) * 2 + 1];
-  Gm[idx] = mm >= 0 ? fr * co - fi * si : fr * si + fi * co;
+  unsigned hi, lo;
+  tf32_split(mm >= 0 ? fr * co - fi * si : fr * si + fi * co, hi, lo);
+  Ghi[idx] = hi;
+  Glo[idx] = lo;
 }
 
 // One block per (drop, latitude pair a, degree n).  The products are split by the parity of the input
@@ -95,8 +101,8 @@ __global__ void k_phase_g(SelfGroup<float> A, const double* __restrict__ dens, f
 // k-steps once, building the A fragment once per k-step and reusing it over up to 13 column tiles.
 constexpr int kRotMaxNt = 13;  // 8-column tiles per warp pass (N = 3 (p+1) takes one or two passes for p < 64)
 
-__global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const float* __restrict__ Gm,
-                                                       float* __restrict__ EO) {
+__global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const unsigned* __restrict__ Ghi,
+                                                       const unsigned* __restrict__ Glo, float* __restrict__ EO) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = A.p;
   const int hb = p + 1;
@@ -124,14 +130,16 @@ __global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const
       acur += (long long)(part ? Mim : Mre) * ka[part][q];
     }
   unsigned* Alo = Ahi + acur;
-  float* Gs = reinterpret_cast<float*>(Alo + acur);  // [n + mm][b][c], mm = -n..n
+  unsigned* Gh = Alo + acur;                  // [n + mm][b][c], mm = -n..n: TF32 hi parts
+  unsigned* Gl = Gh + (2 * n + 1) * NC3;      // and lo parts
   const long long boff = (long long)n * (n + 1) * (2 * n + 1) / 6 + (long long)(n - 1) * n * (2 * n - 1) / 6;
   const float* blk = A.wblk + (long long)a * A.wstride + boff;
   // the degree's rows of G go to shared memory by asynchronous 4-byte copies, all in flight at once
-  const float* gsrc = Gm + ((ld * (p + 1) * (p + 1)) + (long long)n * n) * NC3;
+  const long long goff = ((ld * (p + 1) * (p + 1)) + (long long)n * n) * NC3;
   for (int i = threadIdx.x; i < (2 * n + 1) * NC3; i += blockDim.x) {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(Gs + i);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(gsrc + i) : "memory");
+    const unsigned dh = (unsigned)__cvta_generic_to_shared(Gh + i), dl = (unsigned)__cvta_generic_to_shared(Gl + i);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dh), "l"(Ghi + goff + i) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dl), "l"(Glo + goff + i) : "memory");
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
   // W's columns of each parity, split into TF32 hi / lo: the loads of a thread's entries are issued
@@ -201,17 +209,18 @@ __global__ void __launch_bounds__(kTcThreads) k_rot_tc(SelfGroup<float> A, const
       // B rows: column kk of the A operand is input order m (as above); its G row is n + m (re) or n - m (im)
       const int mk0 = part ? (q ? 2 * c0 + 1 : 2 * c0 + 2) : 2 * c0 + q;
       const int mk1 = part ? (q ? 2 * c1 + 1 : 2 * c1 + 2) : 2 * c1 + q;
-      const float* g0 = (mk0 <= n) ? Gs + (long long)(n + (part ? -mk0 : mk0)) * NC3 : nullptr;
-      const float* g1 = (mk1 <= n) ? Gs + (long long)(n + (part ? -mk1 : mk1)) * NC3 : nullptr;
+      const long long g0 = (mk0 <= n) ? (long long)(n + (part ? -mk0 : mk0)) * NC3 : -1;
+      const long long g1 = (mk1 <= n) ? (long long)(n + (part ? -mk1 : mk1)) * NC3 : -1;
 #pragma unroll
       for (int t = 0; t < kRotMaxNt; ++t) {
         if (t0 + t < NTN) {
           const int j = (t0 + t) * 8 + gq;
-          const float b0v = (g0 && j < NC3) ? g0[j] : 0.f;
-          const float b1v = (g1 && j < NC3) ? g1[j] : 0.f;
           unsigned bhi[2], blo[2];
-          tf32_split(b0v, bhi[0], blo[0]);
-          tf32_split(b1v, bhi[1], blo[1]);
+          const bool ok0 = g0 >= 0 && j < NC3, ok1 = g1 >= 0 && j < NC3;
+          bhi[0] = ok0 ? Gh[g0 + j] : 0u;
+          blo[0] = ok0 ? Gl[g0 + j] : 0u;
+          bhi[1] = ok1 ? Gh[g1 + j] : 0u;
+          blo[1] = ok1 ? Gl[g1 + j] : 0u;
           mma_tf32(d[t], alo, bhi);
           mma_tf32(d[t], ahi, blo);
           mma_tf32(d[t], ahi, bhi);
@@ -322,21 +331,28 @@ long long self_tc_eo_floats(const std::vector<SelfGroup<float>>& groups, long lo
 
 long long self_tc_g_floats(const std::vector<SelfGroup<float>>& groups, long long budget) {
   long long n = 0;
-  for (const auto& g : groups)
-    n = std::max(n, std::min(g.ndrop, chunk_drops(g.p, budget)) * (long long)(g.p + 1) * (g.p + 1) * (g.p + 1) * 3);
+  for (const auto& g : groups)  // hi and lo parts
+    n = std::max(n, 2 * std::min(g.ndrop, chunk_drops(g.p, budget)) * (long long)(g.p + 1) * (g.p + 1) * (g.p + 1) * 3);
   return n;
 }
 
+// shared memory of one k_rot_tc block at degree p: A hi / lo for both parts and parities (each padded
+// to 8 columns) and the hi / lo parts of the degree-p rows of G
+static size_t rot_tc_smem(int p) {
+  const size_t acols = (size_t)(((p + 2) / 2 + 7) & ~7) + (((p + 1) / 2 + 7) & ~7);
+  return sizeof(float) * (2 * (size_t)(p + 1) * acols * 2 + 2 * (2 * (size_t)p + 1) * (p + 1) * 3);
+}
+
+bool self_tc_fits(int p) { return rot_tc_smem(p) <= 227 * 1024; }
+
 int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* dens, double* vals, float* eo,
-                   float* gm, long long budget, cudaStream_t s) {
+                   unsigned* gm, long long budget, cudaStream_t s) {
   for (const auto& g : groups) {
     const int p = g.p;
     const int ng = (p + 1) * (2 * p + 2), ntri = (p + 1) * (p + 2) / 2;
     if (g.ndrop * (long long)ng > 0x7fffffffLL) return BIE_EINVAL;
-    // A hi / lo for both parts and parities (each padded to 8 columns) and the degree-p rows of G
-    const size_t acols = (size_t)(((p + 2) / 2 + 7) & ~7) + (((p + 1) / 2 + 7) & ~7);
-    const size_t smem = sizeof(float) * (2 * (size_t)(p + 1) * acols * 2 + (2 * (size_t)p + 1) * (p + 1) * 3);
-    if (smem > 227 * 1024) return BIE_EINVAL;
+    const size_t smem = rot_tc_smem(p);
+    if (!self_tc_fits(p)) return BIE_EINVAL;
     if (smem > 48 * 1024)
       BIE_CUDA_TRY(cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long per = chunk_drops(p, budget);
@@ -350,11 +366,11 @@ int launch_self_tc(const std::vector<SelfGroup<float>>& groups, const double* de
       c.wts = g.wts + d0;
       c.val_off = g.val_off + d0;
       const long long ng3 = c.ndrop * (long long)(p + 1) * (p + 1) * (p + 1) * 3;
-      k_phase_g<<<(unsigned)((ng3 + 255) / 256), 256, 0, s>>>(c, dens, gm);
+      k_phase_g<<<(unsigned)((ng3 + 255) / 256), 256, 0, s>>>(c, dens, gm, gm + ng3);
       count_launch();
       BIE_CUDA_TRY(cudaGetLastError());
       const long long nblk = c.ndrop * ((p + 2) / 2) * (long long)(p + 1);
-      k_rot_tc<<<(unsigned)nblk, kTcThreads, smem, s>>>(c, gm, eo);
+      k_rot_tc<<<(unsigned)nblk, kTcThreads, smem, s>>>(c, gm, gm + ng3, eo);
       count_launch();
       BIE_CUDA_TRY(cudaGetLastError());
       k_contract_eo<<<(unsigned)nblk, kTcThreads, 0, s>>>(c, eo, vals);
