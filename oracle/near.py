@@ -77,47 +77,60 @@ def lagrange(nodes: np.ndarray, vals: np.ndarray, x: float) -> np.ndarray:
     return out
 
 
+def near_data(drops, j: int, dens_j: np.ndarray, self_raw_j: np.ndarray) -> dict:
+    """What the interpolation over drop j needs for any target: the density's coefficients, its
+    values on the standard and upsampled grids, and the SH coefficients of drop j's own raw
+    self-rule values (the on-surface values) from self_raw_j [3][p_j+1][2p_j+2]."""
+    p = drops.p[j]
+    dens_j = np.asarray(dens_j).reshape(3, sh.ncoef(p))
+    return {"dens": dens_j,
+            "self_coef": np.stack([sh.analyze(self_raw_j[c], p, p) for c in range(3)]),
+            "std_rho": drops.std[j].density(dens_j),
+            "up_rho": drops.ups[j].density(dens_j)}
+
+
+def near_value_at(drops, j: int, x0: np.ndarray, data: dict, kind: str) -> np.ndarray:
+    """Raw integral over drop j at one point x0 of its Omega_2 (outside drop j), [3]."""
+    from .layer import regular_sum
+    p = drops.p[j]
+    h = drops.h[j]
+    xj = drops.xcoef[j]
+    std_x = drops.std[j].x
+    _, _, theta, phi = sh.gauss_grid(p)
+    T, Ph = np.meshgrid(theta, phi, indexing="ij")
+    T, Ph = T.reshape(-1), Ph.reshape(-1)
+    s = int(np.argmin(np.sum((std_x - x0[:, None]) ** 2, axis=0)))
+    al, be = Ph[s], T[s] - np.pi / 2
+    xr = np.stack([wigner.rotate(xj[c], p, al, be) for c in range(3)])
+    th, ph, xs = newton_closest(xr, p, x0)
+    d0 = float(np.linalg.norm(x0 - xs))
+    e = (x0 - xs) / d0
+    nodes = np.concatenate([[0.0], h * np.sqrt(np.arange(1, L_POINTS + 1))])
+    vals = np.zeros((3, L_POINTS + 1))
+    sr = np.stack([wigner.rotate(data["self_coef"][c], p, al, be) for c in range(3)])
+    anchor = np.array([sh.evaluate(sr[c], p, np.array([th]), np.array([ph]))[0] for c in range(3)])
+    if kind == "D":
+        ur = np.stack([wigner.rotate(data["dens"][c], p, al, be) for c in range(3)])
+        u_star = np.array([sh.evaluate(ur[c], p, np.array([th]), np.array([ph]))[0] for c in range(3)])
+        anchor = anchor - 4.0 * np.pi * u_star
+    vals[:, 0] = anchor
+    pts = xs[:, None] + e[:, None] * nodes[None, 1:]
+    reg = drops.classify(pts, j)
+    for l in range(L_POINTS):
+        if reg[l] == 0:
+            vals[:, l + 1] = regular_sum(pts[:, l:l + 1], drops.std[j], data["std_rho"], kind)[:, 0]
+        else:
+            vals[:, l + 1] = regular_sum(pts[:, l:l + 1], drops.ups[j], data["up_rho"], kind)[:, 0]
+    return lagrange(nodes, vals, d0)
+
+
 def near_values(drops, i: int, j: int, sel, dens_j: np.ndarray, kind: str, self_raw_j: np.ndarray) -> np.ndarray:
     """Raw-integral values over drop j at the Omega_2 targets sel of drop i, [3][len(sel)].
 
     self_raw_j: drop j's own raw self-rule values on its grid, [3][p_j+1][2p_j+2].
     """
-    from .layer import regular_sum
-    p = drops.p[j]
-    h = drops.h[j]
-    xj = drops.xcoef[j]
-    dens_j = np.asarray(dens_j).reshape(3, sh.ncoef(p))
-    self_coef = np.stack([sh.analyze(self_raw_j[c], p, p) for c in range(3)])
-    std_x = drops.std[j].x
-    _, _, theta, phi = sh.gauss_grid(p)
-    T, Ph = np.meshgrid(theta, phi, indexing="ij")
-    T, Ph = T.reshape(-1), Ph.reshape(-1)
-    std_rho = drops.std[j].density(dens_j)
-    up_rho = drops.ups[j].density(dens_j)
+    data = near_data(drops, j, dens_j, self_raw_j)
     out = np.zeros((3, len(sel)))
     for col, t in enumerate(sel):
-        x0 = drops.targets[i][:, t]
-        s = int(np.argmin(np.sum((std_x - x0[:, None]) ** 2, axis=0)))
-        al, be = Ph[s], T[s] - np.pi / 2
-        xr = np.stack([wigner.rotate(xj[c], p, al, be) for c in range(3)])
-        th, ph, xs = newton_closest(xr, p, x0)
-        d0 = float(np.linalg.norm(x0 - xs))
-        e = (x0 - xs) / d0
-        nodes = np.concatenate([[0.0], h * np.sqrt(np.arange(1, L_POINTS + 1))])
-        vals = np.zeros((3, L_POINTS + 1))
-        sr = np.stack([wigner.rotate(self_coef[c], p, al, be) for c in range(3)])
-        anchor = np.array([sh.evaluate(sr[c], p, np.array([th]), np.array([ph]))[0] for c in range(3)])
-        if kind == "D":
-            ur = np.stack([wigner.rotate(dens_j[c], p, al, be) for c in range(3)])
-            u_star = np.array([sh.evaluate(ur[c], p, np.array([th]), np.array([ph]))[0] for c in range(3)])
-            anchor = anchor - 4.0 * np.pi * u_star
-        vals[:, 0] = anchor
-        pts = xs[:, None] + e[:, None] * nodes[None, 1:]
-        reg = drops.classify(pts, j)
-        for l in range(L_POINTS):
-            if reg[l] == 0:
-                vals[:, l + 1] = regular_sum(pts[:, l:l + 1], drops.std[j], std_rho, kind)[:, 0]
-            else:
-                vals[:, l + 1] = regular_sum(pts[:, l:l + 1], drops.ups[j], up_rho, kind)[:, 0]
-        out[:, col] = lagrange(nodes, vals, d0)
+        out[:, col] = near_value_at(drops, j, drops.targets[i][:, t], data, kind)
     return out

@@ -11,10 +11,11 @@ import textwrap
 
 import pytest
 
-from oracle import geometry, gmres, layer, near, reparam, sh, surfactant, timestep, wigner
+from oracle import geometry, gmres, layer, near, offsurface, reparam, sh, surfactant, timestep, wigner
 
 import test_oracle_geometry as PG
 import test_oracle_layer as PL
+import test_oracle_offsurface as PO
 import test_oracle_reparam as PR
 import test_oracle_sh as PS
 import test_oracle_surfactant as PF
@@ -154,21 +155,34 @@ CASES = [
     ("far_field_without_factor_two", layer, "Drops",
      [("out.append(2.0 * uinf + s[i])", "out.append(uinf + s[i])")],
      PL.test_force_free_drop_of_matched_viscosity_is_invisible, ()),
-    ("near_anchor_without_jump", near, "near_values",
+    ("near_anchor_without_jump", near, "near_value_at",
      [("anchor = anchor - 4.0 * np.pi * u_star", "anchor = anchor")],
      PL.test_two_drops_near_contact_closed_forms_through_all_regions, ()),
-    ("near_check_points_inside", near, "near_values",
+    ("near_check_points_inside", near, "near_value_at",
      [("pts = xs[:, None] + e[:, None] * nodes[None, 1:]", "pts = xs[:, None] - e[:, None] * nodes[None, 1:]")],
      PL.test_two_drops_near_contact_closed_forms_through_all_regions, ()),
     ("newton_step_uphill", near, "newton_closest",
      [("step = -np.linalg.solve(", "step = np.linalg.solve(")],
      PL.test_newton_closest_point_is_the_nearest_surface_point, ()),
-    ("closest_point_left_at_the_seed", near, "near_values",
+    ("closest_point_left_at_the_seed", near, "near_value_at",
      [("th, ph, xs = newton_closest(xr, p, x0)", "th, ph, xs = newton_closest(xr, p, x0, max_it=0)")],
      PL.test_near_singular_values_converge_to_brute_force_on_a_deformed_drop, ()),
     ("newton_hessian_without_curvature", near, "newton_closest",
      [('[[d["t"] @ d["t"] + r @ d["tt"],', '[[d["t"] @ d["t"] - r @ d["tt"],')],
      PL.test_newton_closest_point_is_the_nearest_surface_point, ()),
+    # off-surface evaluation (Sec. 1 with the rules of Sec. 2.1-2.3)
+    ("offsurface_double_layer_sign", offsurface, "velocity_at",
+     [('layer_at(drops, pts, f_list, "S") + layer_at(', 'layer_at(drops, pts, f_list, "S") - layer_at(')],
+     PO.test_velocity_is_continuous_across_the_interface, ()),
+    ("offsurface_without_half", offsurface, "velocity_at",
+     [("u = 0.5 * (layer_at(", "u = (layer_at(")],
+     PO.test_velocity_is_continuous_across_the_interface, ()),
+    ("offsurface_upsampled_region_on_the_standard_grid", offsurface, "raw_layer_at",
+     [("for r, grid in ((0, drops.std[j]), (1, drops.ups[j])):", "for r, grid in ((0, drops.std[j]), (1, drops.std[j])):")],
+     PO.test_layers_converge_to_brute_force_on_two_deformed_drops, ()),
+    ("offsurface_inside_side_flipped", offsurface, "classify_points",
+     [("codes[s:s + 256] = np.where(side <= 0.0, INSIDE, c)", "codes[s:s + 256] = np.where(side >= 0.0, INSIDE, c)")],
+     PO.test_inside_points_are_rejected, ()),
     # GMRES (Sec. 6) and the drop update (Sec. 3)
     ("givens_rotation_sign", gmres, "gmres",
      [("H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]", "H[i + 1, k] = sn[i] * H[i, k] + cs[i] * H[i + 1, k]")],
