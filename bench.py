@@ -541,6 +541,58 @@ def apply_line(name, local, steps, warmup, peaks):
     return line
 
 
+def fluid_points(w, n, clearance, seed=11):
+    """n seeded points of the workload's box that lie farther than `clearance` from every drop centre
+    (outside every drop when clearance exceeds the largest drop radius), as a [3][n] array."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    cen, o = [], 0
+    for p in w.p:
+        k = (p + 1) ** 2
+        cen.append(w.xcoef[o:o + 3 * k].reshape(3, k)[:, 0] / math.sqrt(4 * math.pi))
+        o += 3 * k
+    cen = np.array(cen)
+    lo, hi = cen.min(axis=0), cen.max(axis=0)
+    keep = []
+    while sum(k.shape[1] for k in keep) < n:
+        cand = lo[:, None] + (hi - lo)[:, None] * rng.random((3, 4 * n))
+        d2 = np.full(cand.shape[1], np.inf)
+        for c in cen:
+            d2 = np.minimum(d2, np.sum((cand - c[:, None]) ** 2, axis=0))
+        keep.append(cand[:, d2 > clearance ** 2])
+    return np.ascontiguousarray(np.concatenate(keep, axis=1)[:, :n])
+
+
+def offsurface_line(name, local, steps, warmup, npoint=131072):
+    """The velocity u_inf + (S[f] + D[u]) / 2 at npoint fluid points among the drops (bie_eval_velocity:
+    region classification, pair sums on the standard / upsampled grids, near-singular interpolation
+    for points within h of a surface), mixed against FP64, with a seeded density for u."""
+    import torch
+    case = Case(name, local)
+    pts = torch.tensor(fluid_points(case.w, npoint, 1.6), device="cuda")
+    u = torch.tensor(case.w.density, device="cuda")
+    uinf = torch.zeros_like(pts)
+    uinf[0] = (case.w.shear if case.w.shear else 1.0) * pts[2]
+    stream = torch.cuda.current_stream()
+    scrub = Scrub()
+    res = {}
+    for prec in (1, 0):
+        out = torch.zeros_like(pts)
+        for _ in range(warmup if prec == 1 else 1):
+            case.geo.velocity_at(pts, case.f, u, out, uinf=uinf, precision=prec)
+        torch.cuda.synchronize()
+        t = timed_each(lambda: case.geo.velocity_at(pts, case.f, u, out, uinf=uinf, precision=prec),
+                       steps if prec == 1 else 1, stream, scrub)
+        res[prec] = {"ms": statistics.median(t), "out": out.clone()}
+    rel = float(torch.linalg.norm(res[1]["out"] - res[0]["out"]) / torch.linalg.norm(res[0]["out"]))
+    line = {"workload": WORKLOADS[name], "points": npoint,
+            "step": "velocity at seeded fluid points farther than 1.6 from every drop centre (bie_eval_velocity)",
+            "ms_mixed": res[1]["ms"], "ms_fp64": res[0]["ms"], "points_per_s_mixed": npoint / (res[1]["ms"] * 1e-3),
+            "speedup_mixed_vs_fp64": res[0]["ms"] / res[1]["ms"], "rel_err_mixed_vs_fp64": rel}
+    case.close()
+    return line
+
+
 def time_midpoint(name, local, nsteps=2, dt=0.01):
     """Wall time of midpoint steps of the drop shapes (two geometries, two right-hand sides and two
     mixed solves with double-float residuals per step) on a workload in shear."""
@@ -826,6 +878,8 @@ def run_ours(args):
                 also[other] = guarded(apply_line, other, local, 20, 5, peaks)
             else:
                 also[other] = guarded(solve_line, other, local, 3, 2, world, peaks, False, other in ("c2", "c3", "c4"))
+    if not args.no_aux and name != "c1":
+        also["offsurface_" + name] = guarded(offsurface_line, name, local, 3, 2)
     if args.timesteps:
         head["time_steps"] = guarded(time_midpoint, name, local, args.timesteps)
     cpu = guarded(cpu_baseline, name, head.get("pairs_per_apply", 1)) if (rank == 0 and not args.no_aux) else None

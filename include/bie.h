@@ -190,6 +190,37 @@ int bie_apply_single(bie_ctx* ctx, const bie_geom* geom, const double* fcoef, do
 int bie_apply_double(bie_ctx* ctx, const bie_geom* geom, const double* ucoef, double* out_coef, int precision,
                      void* stream);
 
+/* Layer potentials at points off the surfaces (Sec. 1: the velocity can be evaluated anywhere in the
+ * fluid from the interface densities).  out[c][t] = S[f](x_t) (bie_eval_single) or D[u](x_t)
+ * (bie_eval_double), with the normalisations of bie_apply_single / bie_apply_double (or BIE_RAW's):
+ * S[f] = -(1/4pi) sum_j int f.G ds, D[u] = (1/4pi) sum_j (lambda_j - 1) int u.T.n ds, ordinary
+ * integrals here.  Each (point, drop j) pair takes the rule of its region, as the drops' own targets
+ * do (Sec. 2.1-2.3): the regular rule on drop j's standard grid in Omega_0, on its upsampled grid in
+ * Omega_1, and in Omega_2 the interpolation along the line through the closest point x* of drop j,
+ * anchored at the exterior limit of drop j's on-surface value at x* (for the double layer the
+ * principal value minus 4 pi (lambda_j - 1)/(4 pi) u(x*)); the check-point values are FP64 in every
+ * precision.  precision: BIE_FP64, BIE_MIXED (FP32 pair sums and self term) or BIE_DF, optionally |
+ * BIE_RAW.
+ * points: [3][npoint] device FP64 (x of every point, then y, then z); fcoef / ucoef: the densities,
+ * [drop][3][(p+1)^2] device; out: [3][npoint] device, overwritten.  0 <= npoint < 2^31.  Points must
+ * lie in the fluid: a point inside (or on the inner side of the tangent plane at the nearest
+ * upsampled grid point of) a drop gives BIE_EOVERLAP, the error text naming its 128-point tile and the
+ * drop.  A single-drop geometry builds its upsampled grid and source data on the first call.  The
+ * call uses the geometry's work buffers (not concurrently with other calls on the same geometry),
+ * allocates its temporaries, and is synchronous. */
+int bie_eval_single(bie_ctx* ctx, const bie_geom* geom, long long npoint, const double* points, const double* fcoef,
+                    double* out, int precision, void* stream);
+int bie_eval_double(bie_ctx* ctx, const bie_geom* geom, long long npoint, const double* points, const double* ucoef,
+                    double* out, int precision, void* stream);
+
+/* Velocity at fluid points: out = u_inf + (S[f] + D[u]) / 2, the representation whose limit onto an
+ * interface is Eq. main_eq (the factor 1 of a fluid point against (lambda_i + 1)/2 there).  u: the
+ * interface velocity (the solution of bie_solve), f: the interfacial force; uinf: [3][npoint] device
+ * values of the far field at the points, or NULL for none.  Arguments otherwise as bie_eval_single;
+ * BIE_RAW is refused (BIE_EINVAL). */
+int bie_eval_velocity(bie_ctx* ctx, const bie_geom* geom, long long npoint, const double* points, const double* fcoef,
+                      const double* ucoef, const double* uinf, double* out, int precision, void* stream);
+
 /* Right-hand side of Eq. main_eq in coefficient space: rhs = 2 u_inf + S[f] with the single layer at
  * precision BIE_FP64 or BIE_DF (both FP64-grade).  uinf: [drop][3][(p+1)^2] device coefficients of the far field at the drop surfaces (a
  * linear flow is exactly band-limited: u_inf = (z, 0, 0) has the z coefficients of x in its first

@@ -106,6 +106,9 @@ EXPORTS = {
     "bie_apply_single": (c_int, [c_void, c_void, c_void, c_void, c_int, c_void]),
     "bie_apply_double": (c_int, [c_void, c_void, c_void, c_void, c_int, c_void]),
     "bie_rhs": (c_int, [c_void, c_void, c_void, c_void, c_void, c_int, c_void]),
+    "bie_eval_single": (c_int, [c_void, c_void, c_ll, c_void, c_void, c_void, c_int, c_void]),
+    "bie_eval_double": (c_int, [c_void, c_void, c_ll, c_void, c_void, c_void, c_int, c_void]),
+    "bie_eval_velocity": (c_int, [c_void, c_void, c_ll, c_void, c_void, c_void, c_void, c_void, c_int, c_void]),
     "bie_solve_opts_default": (None, [ctypes.POINTER(bie_solve_opts)]),
     "bie_solve": (c_int, [c_void, c_void, c_void, c_void, ctypes.POINTER(bie_solve_opts),
                           ctypes.POINTER(bie_solve_info), c_void]),
@@ -315,6 +318,31 @@ class Geometry:
         SH basis, or at the grid targets with grid_out."""
         flag = precision | (BIE_RAW if raw else 0) | (BIE_GRID_OUT if grid_out else 0)
         _check(lib().bie_apply_double(self.ctx.h, self.h, _ptr(u), _ptr(out), flag, _stream()), "bie_apply_double")
+        return out
+
+    def eval_single(self, points: torch.Tensor, f: torch.Tensor, out: torch.Tensor, precision: int = BIE_FP64,
+                    raw: bool = False):
+        """S[f] at fluid points off the surfaces: points and out [3][n] (FP64, device, contiguous)."""
+        n = points.numel() // 3
+        _check(lib().bie_eval_single(self.ctx.h, self.h, n, _ptr(points), _ptr(f), _ptr(out),
+                                     precision | (BIE_RAW if raw else 0), _stream()), "bie_eval_single")
+        return out
+
+    def eval_double(self, points: torch.Tensor, u: torch.Tensor, out: torch.Tensor, precision: int = BIE_FP64,
+                    raw: bool = False):
+        """D[u] at fluid points off the surfaces: points and out [3][n] (FP64, device, contiguous)."""
+        n = points.numel() // 3
+        _check(lib().bie_eval_double(self.ctx.h, self.h, n, _ptr(points), _ptr(u), _ptr(out),
+                                     precision | (BIE_RAW if raw else 0), _stream()), "bie_eval_double")
+        return out
+
+    def velocity_at(self, points: torch.Tensor, f: torch.Tensor, u: torch.Tensor, out: torch.Tensor,
+                    uinf: torch.Tensor | None = None, precision: int = BIE_FP64):
+        """u_inf + (S[f] + D[u]) / 2 at fluid points [3][n]; uinf: far-field values there or None."""
+        n = points.numel() // 3
+        _check(lib().bie_eval_velocity(self.ctx.h, self.h, n, _ptr(points), _ptr(f), _ptr(u),
+                                       _ptr(uinf) if uinf is not None else None, _ptr(out), precision, _stream()),
+               "bie_eval_velocity")
         return out
 
     def interfacial_force(self, gamma: torch.Tensor, elasticity: float, x_s: float, out: torch.Tensor):

@@ -21,6 +21,7 @@
 #include "dfloat.cuh"
 #include "interdrop.h"
 #include "near.h"
+#include "offsurface.h"
 #include "internal.cuh"
 #include "tables.h"
 
@@ -323,6 +324,7 @@ struct bie_geom {
   bie::DevBuf<long long> tile_t0, tgt_loc, toff, val_off_all;
   bie::DevBuf<double> centre_d, partial, wS_all, wD_all, wSr_all, wDr_all;
   int nblk = 0, ntile = 0;
+  bool interdrop_ready = false;  // inter-drop data built: at set-up when ndrop > 1, else at the first off-surface evaluation
   int tpt32 = 2, tpt64 = 2;                         // targets per thread of the pair kernel (autotuned FP32)
   bie::DevBuf<float> eo32;                          // tensor-core self path: rotated sums
   bie::DevBuf<unsigned> g32;                        // and the split phase-shifted coefficients
@@ -1029,6 +1031,7 @@ static int setup_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
     Phase ph(ctx, "setup_near", s);
     BIE_TRY(setup_near(ctx, g, s));
   }
+  g->interdrop_ready = true;
   return BIE_OK;
 }
 
@@ -1069,36 +1072,21 @@ static int source_densities(bie_geom* g, const double* dens, R* Qs, R* Qu, cudaS
   return BIE_OK;
 }
 
-// Near-singular set-up (Sec. 2.3): seeds, closest points by damped Newton in a rotated frame with
-// the seed on the equator, check points x_l = x* + h_j sqrt(l) e and the grid of each.
-static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
-  auto& nr = g->near;
-  std::sort(nr.begin(), nr.end());
-  const int npair = (int)nr.size();
+// Closest points x* of near pairs (Sec. 2.3): damped Newton in a rotated frame that puts the seed
+// (the source drop's standard-grid point nearest to x0) on the equator; then the check points
+// x_l = x* + h_j sqrt(l) e, e = (x0 - x*)/|x0 - x*|, l = 1..L, and the grid (standard or upsampled)
+// each is summed on.  x0: 3 per pair (host); seeds: standard-grid index per pair.  Fills d0 and the
+// parameters of x* in drop j's own frame into the pairs and returns the check points [pair][L][3]
+// and their grids [pair][L] on the device.
+static int near_points(bie_ctx* ctx, bie_geom* g, std::vector<NearPair>& pairs, const std::vector<double>& x0,
+                       const std::vector<int>& hseed, DevBuf<double>& pts_d, DevBuf<int>& grid_d, cudaStream_t s) {
+  const int npair = (int)pairs.size();
   const int L = ctx->cfg.n_interp;
-  std::vector<NearPair> pairs(npair);
-  std::vector<int> tbeg;
-  for (int i = 0; i < npair; ++i) {
-    pairs[i].target = nr[i].first;
-    pairs[i].src_drop = nr[i].second;
-    if (i == 0 || nr[i].first != nr[i - 1].first) tbeg.push_back(i);
-  }
-  g->nnear_tgt = (int)tbeg.size();
-  tbeg.push_back(npair);
-  BIE_TRY(g->npairs.upload(pairs));
-  BIE_TRY(g->ntbeg.upload(tbeg));
-  DevBuf<int> seed;
-  BIE_TRY(seed.alloc(npair));
-  BIE_TRY(launch_near_seed(g->npairs.ptr, npair, g->rec_std.ptr, g->toff.ptr, g->ngd.ptr, g->tgt_loc.ptr,
-                           g->tdrop.ptr, seed.ptr, s));
-  std::vector<int> hseed(npair);
-  BIE_CUDA_TRY(cudaMemcpyAsync(hseed.data(), seed.ptr, npair * sizeof(int), cudaMemcpyDeviceToHost, s));
-  std::vector<double> rec(7 * g->ntarget);
-  BIE_CUDA_TRY(cudaMemcpyAsync(rec.data(), g->rec_std.ptr, rec.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  DevBuf<NearPair> dpairs;
+  BIE_TRY(dpairs.upload(pairs));
   // rotated shape coefficients per pair: (alpha, beta) = (phi_b, theta_a - pi/2) puts the seed at the equator
   std::vector<long long> xr_off(npair);
-  std::vector<double> alpha(npair), beta(npair), x0(3 * npair);
+  std::vector<double> alpha(npair), beta(npair);
   long long xo = 0;
   for (int i = 0; i < npair; ++i) {
     const int j = pairs[i].src_drop, p = g->p[j];
@@ -1110,11 +1098,6 @@ static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
     beta[i] = std::acos(t[a]) - 0.5 * kPi;
     xr_off[i] = xo;
     xo += 3 * ncoef(p);
-    const long long tt = pairs[i].target;
-    int di = 0;
-    while (di + 1 < g->ndrop && g->tgt_off[di + 1] <= tt) ++di;
-    const long long ngi = ngrid(g->p[di]), l = tt - g->tgt_off[di];
-    for (int c = 0; c < 3; ++c) x0[3 * i + c] = rec[7 * g->tgt_off[di] + c * ngi + l];
   }
   DevBuf<double> xr, dx0, res;
   DevBuf<long long> dxo;
@@ -1151,7 +1134,7 @@ static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   BIE_TRY(dxo.upload(xr_off));
   BIE_TRY(dx0.upload(x0));
   BIE_TRY(res.alloc(5 * npair));
-  BIE_TRY(launch_near_newton(g->npairs.ptr, npair, xr.ptr, pdeg.ptr, dxo.ptr, dx0.ptr, res.ptr, s));
+  BIE_TRY(launch_near_newton(dpairs.ptr, npair, xr.ptr, pdeg.ptr, dxo.ptr, dx0.ptr, res.ptr, s));
   std::vector<double> hres(5 * npair);
   BIE_CUDA_TRY(cudaMemcpyAsync(hres.data(), res.ptr, hres.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   BIE_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1178,26 +1161,71 @@ static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
     for (int l = 1; l <= L; ++l)
       for (int c = 0; c < 3; ++c) pts[3 * ((size_t)i * L + (l - 1)) + c] = xs[c] + g->hdrop[j] * std::sqrt((double)l) * e[c];
   }
-  BIE_TRY(g->npairs.upload(pairs));
-  BIE_TRY(g->npts.upload(pts));
-  BIE_TRY(g->ngrid_l.alloc((size_t)npair * L));
-  {
-    DevBuf<double> bnd, hh;
-    DevBuf<long long> uoff, un;
-    BIE_TRY(bnd.upload(g->bound));
-    BIE_TRY(hh.upload(g->hdrop));
-    BIE_TRY(uoff.upload(g->up_off));
-    BIE_TRY(un.upload(g->up_n));
-    BIE_TRY(launch_near_checkgrid(g->npairs.ptr, npair, L, g->npts.ptr, g->centre_d.ptr, bnd.ptr, hh.ptr,
-                                  ctx->cfg.a_tilde, g->rec_up.ptr, uoff.ptr, un.ptr, g->ngrid_l.ptr, s));
-    BIE_CUDA_TRY(cudaStreamSynchronize(s));
-  }
-  BIE_TRY(g->ncv.alloc(3 * (size_t)npair * L));
+  BIE_TRY(pts_d.upload(pts));
+  BIE_TRY(grid_d.alloc((size_t)npair * L));
+  DevBuf<double> bnd, hh;
+  DevBuf<long long> uoff, un;
+  BIE_TRY(bnd.upload(g->bound));
+  BIE_TRY(hh.upload(g->hdrop));
+  BIE_TRY(uoff.upload(g->up_off));
+  BIE_TRY(un.upload(g->up_n));
+  BIE_TRY(launch_near_checkgrid(dpairs.ptr, npair, L, pts_d.ptr, g->centre_d.ptr, bnd.ptr, hh.ptr, ctx->cfg.a_tilde,
+                                g->rec_up.ptr, uoff.ptr, un.ptr, grid_d.ptr, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return BIE_OK;
+}
+
+// Device tables the near-singular interpolation reads (degrees, h, coefficient offsets) and the
+// buffers of the on-surface expansions, made once per geometry.
+static int near_tables(bie_geom* g) {
+  if (g->pdeg_d.ptr) return BIE_OK;
   BIE_TRY(g->selfvals.alloc(3 * g->ntarget));
   BIE_TRY(g->selfcoef.alloc(g->ncoef_total));
   BIE_TRY(g->hdrop_d.upload(g->hdrop));
   BIE_TRY(g->coef_off_d.upload(g->coef_off));
+  std::vector<int> pd(g->p.begin(), g->p.end());
   BIE_TRY(g->pdeg_d.upload(pd));
+  return BIE_OK;
+}
+
+// Near-singular set-up (Sec. 2.3) for the drops' own targets: seeds on the device, then near_points.
+static int setup_near(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
+  auto& nr = g->near;
+  std::sort(nr.begin(), nr.end());
+  const int npair = (int)nr.size();
+  const int L = ctx->cfg.n_interp;
+  std::vector<NearPair> pairs(npair);
+  std::vector<int> tbeg;
+  for (int i = 0; i < npair; ++i) {
+    pairs[i].target = nr[i].first;
+    pairs[i].src_drop = nr[i].second;
+    if (i == 0 || nr[i].first != nr[i - 1].first) tbeg.push_back(i);
+  }
+  g->nnear_tgt = (int)tbeg.size();
+  tbeg.push_back(npair);
+  BIE_TRY(g->npairs.upload(pairs));
+  BIE_TRY(g->ntbeg.upload(tbeg));
+  DevBuf<int> seed;
+  BIE_TRY(seed.alloc(npair));
+  BIE_TRY(launch_near_seed(g->npairs.ptr, npair, g->rec_std.ptr, g->toff.ptr, g->ngd.ptr, g->tgt_loc.ptr,
+                           g->tdrop.ptr, seed.ptr, s));
+  std::vector<int> hseed(npair);
+  BIE_CUDA_TRY(cudaMemcpyAsync(hseed.data(), seed.ptr, npair * sizeof(int), cudaMemcpyDeviceToHost, s));
+  std::vector<double> rec(7 * g->ntarget);
+  BIE_CUDA_TRY(cudaMemcpyAsync(rec.data(), g->rec_std.ptr, rec.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<double> x0(3 * npair);
+  for (int i = 0; i < npair; ++i) {
+    const long long tt = pairs[i].target;
+    int di = 0;
+    while (di + 1 < g->ndrop && g->tgt_off[di + 1] <= tt) ++di;
+    const long long ngi = ngrid(g->p[di]), l = tt - g->tgt_off[di];
+    for (int c = 0; c < 3; ++c) x0[3 * i + c] = rec[7 * g->tgt_off[di] + c * ngi + l];
+  }
+  BIE_TRY(near_points(ctx, g, pairs, x0, hseed, g->npts, g->ngrid_l, s));
+  BIE_TRY(g->npairs.upload(pairs));
+  BIE_TRY(g->ncv.alloc(3 * (size_t)npair * L));
+  BIE_TRY(near_tables(g));
   long long npairs_eval = 0;
   std::vector<int> hgrid((size_t)npair * L);
   BIE_CUDA_TRY(cudaMemcpy(hgrid.data(), g->ngrid_l.ptr, hgrid.size() * sizeof(int), cudaMemcpyDeviceToHost));
@@ -1283,6 +1311,239 @@ static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, 
   Phase ph(ctx, "interdrop_reduce", s);
   return launch_reduce_tiles(g->partial.ptr, g->tile_blk.ptr, g->tile_t0.ptr, g->tile_n.ptr, g->tile_drop.ptr,
                              g->tgt_loc.ptr, g->val_off_all.ptr, g->ngd.ptr, g->ntile, g->vals.ptr, s);
+}
+
+// ---- layer potentials at points off the surfaces (Sec. 1, with the region rules of Sec. 2.1-2.3) ----
+// The points go through the machinery of the drops' own targets: each chunk of points becomes a
+// set of 128-point tiles with a record layout like a drop's (one pseudo-drop per tile, numbered
+// after the real drops, whose centre is the tile's mean point), the region masks of every (tile,
+// drop) pair make a work list for the pair kernels, and the Omega_2 pairs take the near-singular
+// interpolation anchored at the exterior limit of the source drop's on-surface values.
+constexpr long long kPtChunk = 32768;  // points per pass: 256 tiles
+
+static int eval_layer(bie_ctx* ctx, bie_geom* g, int kind, long long npt, const double* pts, const double* dens,
+                      double* out, int precision, cudaStream_t s) {
+  const bool raw = (precision & BIE_RAW) != 0;
+  const int prec = precision & 0xff;
+  if ((precision & ~(0xff | BIE_RAW)) != 0 || (prec != BIE_FP64 && prec != BIE_MIXED && prec != BIE_DF)) {
+    set_error("precision must be BIE_FP64, BIE_MIXED or BIE_DF, optionally | BIE_RAW");
+    return BIE_EINVAL;
+  }
+  if (npt < 0 || npt > 0x7fffffffLL) {
+    set_error("npoint must lie in [0, 2^31)");
+    return BIE_EINVAL;
+  }
+  if (npt == 0) return BIE_OK;
+  BIE_CUDA_TRY(cudaMemsetAsync(out, 0, 3 * npt * sizeof(double), s));
+  if (!g->interdrop_ready) BIE_TRY(setup_interdrop(ctx, g, s));
+  const int nd = g->ndrop;
+  const double* wts = kind == 0 ? (raw ? g->wSr_all.ptr : g->wS_all.ptr) : (raw ? g->wDr_all.ptr : g->wD_all.ptr);
+  // source densities: FP32 for the mixed pair sums, FP64 for the others and for the check points
+  if (prec == BIE_MIXED) {
+    BIE_TRY(g->sQ32.alloc(3 * g->ntarget));
+    BIE_TRY(g->uQ32.alloc(3 * g->nup_total));
+    BIE_TRY(source_densities<float>(g, dens, g->sQ32.ptr, g->uQ32.ptr, s));
+  }
+  BIE_TRY(g->sQ64.alloc(3 * g->ntarget));
+  BIE_TRY(g->uQ64.alloc(3 * g->nup_total));
+  BIE_TRY(source_densities<double>(g, dens, g->sQ64.ptr, g->uQ64.ptr, s));
+  // tile-local tables, the same for every chunk
+  const int mt = (int)((kPtChunk + kTile - 1) / kTile);
+  std::vector<long long> h_t0(mt), h_loc(kPtChunk), h_toff(nd + mt, 0), h_voff(nd + mt, 0);
+  std::vector<int> h_drop(mt), h_ngd(nd + mt, 0);
+  for (int ti = 0; ti < mt; ++ti) {
+    h_t0[ti] = (long long)ti * kTile;
+    h_drop[ti] = nd + ti;
+    h_toff[nd + ti] = (long long)ti * kTile;
+    h_ngd[nd + ti] = kTile;
+    h_voff[nd + ti] = (long long)ti * 3 * kTile;
+  }
+  for (long long k = 0; k < kPtChunk; ++k) h_loc[k] = k % kTile;
+  DevBuf<long long> d_t0, d_loc, d_toff, d_voff, d_uoff, d_un;
+  DevBuf<int> d_drop, d_ngd, d_n, d_blk_item, d_tile_blk;
+  DevBuf<double> d_rec, d_cen, d_vals, d_part, d_bnd, d_h;
+  DevBuf<unsigned char> d_region;
+  DevBuf<TileMask> d_tm;
+  DevBuf<PairItem> d_items;
+  BIE_TRY(d_t0.upload(h_t0));
+  BIE_TRY(d_loc.upload(h_loc));
+  BIE_TRY(d_toff.upload(h_toff));
+  BIE_TRY(d_voff.upload(h_voff));
+  BIE_TRY(d_drop.upload(h_drop));
+  BIE_TRY(d_ngd.upload(h_ngd));
+  BIE_TRY(d_bnd.upload(g->bound));
+  BIE_TRY(d_h.upload(g->hdrop));
+  BIE_TRY(d_uoff.upload(g->up_off));
+  BIE_TRY(d_un.upload(g->up_n));
+  BIE_TRY(d_rec.alloc((size_t)mt * 7 * kTile));
+  BIE_TRY(d_cen.alloc(3 * (size_t)(nd + mt)));
+  BIE_TRY(d_vals.alloc((size_t)mt * 3 * kTile));
+  BIE_TRY(d_region.alloc((size_t)kPtChunk * nd));
+  BIE_TRY(d_tm.alloc((size_t)mt * nd));
+  BIE_CUDA_TRY(cudaMemcpyAsync(d_cen.ptr, g->centre_d.ptr, 3 * nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  std::vector<TileMask> tm((size_t)mt * nd);
+  std::vector<std::pair<long long, int>> near;  // (point, drop) pairs in Omega_2
+  long long all_sources = 0;
+  for (int j = 0; j < nd; ++j) all_sources += ngrid(g->p[j]);
+  const long long cap_global = std::max<long long>(2048, std::min<long long>(65536, all_sources / (8LL * ctx->sms)));
+  auto popc = [](const unsigned* m) {
+    int c = 0;
+    for (int q = 0; q < 4; ++q) c += __builtin_popcount(m[q]);
+    return c;
+  };
+  for (long long t0 = 0; t0 < npt; t0 += kPtChunk) {
+    const long long n = std::min(kPtChunk, npt - t0);
+    const int ntile = (int)((n + kTile - 1) / kTile);
+    std::vector<int> h_n(ntile, kTile);
+    h_n[ntile - 1] = (int)(n - (long long)(ntile - 1) * kTile);
+    BIE_TRY(d_n.upload(h_n));
+    BIE_TRY(launch_point_records(pts, npt, t0, n, ntile, nd, d_rec.ptr, d_cen.ptr, s));
+    BIE_TRY(launch_classify_points(pts, npt, t0, n, nd, g->centre_d.ptr, d_bnd.ptr, d_h.ptr, ctx->cfg.a_tilde,
+                                   g->rec_up.ptr, d_uoff.ptr, d_un.ptr, d_region.ptr, s));
+    BIE_TRY(launch_tile_masks(d_region.ptr, nd, d_t0.ptr, d_n.ptr, ntile, d_tm.ptr, s));
+    BIE_CUDA_TRY(cudaMemcpyAsync(tm.data(), d_tm.ptr, (size_t)ntile * nd * sizeof(TileMask), cudaMemcpyDeviceToHost, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<PairItem> items;
+    std::vector<int> blk_item, tile_blk(ntile + 1, 0);
+    for (int ti = 0; ti < ntile; ++ti) {
+      std::vector<PairItem> mine;
+      long long total = 0;
+      for (int j = 0; j < nd; ++j) {
+        const TileMask& m = tm[(size_t)ti * nd + j];
+        if (m.inside) {
+          set_error("a point of the tile starting at point " + std::to_string(t0 + (long long)ti * kTile) +
+                    " lies inside drop " + std::to_string(j));
+          return BIE_EOVERLAP;
+        }
+        for (int gk = 0; gk < 2; ++gk) {
+          if (!popc(m.m[gk])) continue;
+          PairItem it{};
+          it.tile = ti;
+          it.src_drop = j;
+          it.grid = gk;
+          it.s0 = gk ? g->up_off[j] : g->tgt_off[j];
+          it.s1 = it.s0 + (gk ? g->up_n[j] : (long long)ngrid(g->p[j]));
+          for (int q = 0; q < 4; ++q) it.mask[q] = m.m[gk][q];
+          mine.push_back(it);
+          total += it.s1 - it.s0;
+        }
+        for (int k = 0; k < h_n[ti]; ++k)
+          if ((m.m[2][k >> 5] >> (k & 31)) & 1u) near.emplace_back(t0 + (long long)ti * kTile + k, j);
+      }
+      const long long cap = std::max(cap_global, (total + 15) / 16);  // at most 16 blocks per tile
+      tile_blk[ti] = (int)blk_item.size();
+      long long used = cap;
+      for (auto it : mine) {
+        long long a = it.s0;
+        while (a < it.s1) {
+          if (used >= cap) {
+            blk_item.push_back((int)items.size());
+            used = 0;
+          }
+          const long long take = std::min(it.s1 - a, cap - used);
+          PairItem piece = it;
+          piece.s0 = a;
+          piece.s1 = a + take;
+          items.push_back(piece);
+          used += take;
+          a += take;
+        }
+      }
+    }
+    const int nblk = (int)blk_item.size();
+    tile_blk[ntile] = nblk;
+    if (nblk == 0) continue;
+    blk_item.push_back((int)items.size());
+    BIE_TRY(d_items.upload(items));
+    BIE_TRY(d_blk_item.upload(blk_item));
+    BIE_TRY(d_tile_blk.upload(tile_blk));
+    BIE_TRY(d_part.alloc((size_t)nblk * 3 * kTile));
+    if (prec == BIE_MIXED) {
+      Phase ph(ctx, "offsurface_f32", s);
+      BIE_TRY(launch_interdrop<float>(kind, g->tpt32, nblk, d_items.ptr, d_blk_item.ptr, d_t0.ptr, d_n.ptr, d_drop.ptr,
+                                      d_loc.ptr, d_toff.ptr, d_ngd.ptr, d_rec.ptr, d_cen.ptr, g->sX32.ptr, g->sN32.ptr,
+                                      g->sQ32.ptr, g->ntarget, g->uX32.ptr, g->uN32.ptr, g->uQ32.ptr, g->nup_total, wts,
+                                      d_part.ptr, s));
+    } else if (prec == BIE_DF) {
+      Phase ph(ctx, "offsurface_df", s);
+      BIE_TRY(launch_interdrop_df(kind, nblk, d_items.ptr, d_blk_item.ptr, d_t0.ptr, d_n.ptr, d_drop.ptr, d_loc.ptr,
+                                  d_toff.ptr, d_ngd.ptr, d_rec.ptr, d_cen.ptr, g->sX64.ptr, g->sN64.ptr, g->sQ64.ptr,
+                                  g->ntarget, g->uX64.ptr, g->uN64.ptr, g->uQ64.ptr, g->nup_total, wts, d_part.ptr, s));
+    } else {
+      Phase ph(ctx, "offsurface_f64", s);
+      BIE_TRY(launch_interdrop<double>(kind, g->tpt64, nblk, d_items.ptr, d_blk_item.ptr, d_t0.ptr, d_n.ptr,
+                                       d_drop.ptr, d_loc.ptr, d_toff.ptr, d_ngd.ptr, d_rec.ptr, d_cen.ptr, g->sX64.ptr,
+                                       g->sN64.ptr, g->sQ64.ptr, g->ntarget, g->uX64.ptr, g->uN64.ptr, g->uQ64.ptr,
+                                       g->nup_total, wts, d_part.ptr, s));
+    }
+    BIE_CUDA_TRY(cudaMemsetAsync(d_vals.ptr, 0, (size_t)ntile * 3 * kTile * sizeof(double), s));
+    BIE_TRY(launch_reduce_tiles(d_part.ptr, d_tile_blk.ptr, d_t0.ptr, d_n.ptr, d_drop.ptr, d_loc.ptr, d_voff.ptr,
+                                d_ngd.ptr, ntile, d_vals.ptr, s));
+    BIE_TRY(launch_gather_points(d_vals.ptr, t0, n, npt, out, s));
+    BIE_CUDA_TRY(cudaStreamSynchronize(s));  // the chunk's host tables are reused
+  }
+  if (near.empty()) return BIE_OK;
+  // Omega_2: interpolation along the normal line through the closest point (Sec. 2.3)
+  Phase ph(ctx, "offsurface_near", s);
+  const int npair = (int)near.size(), L = ctx->cfg.n_interp;
+  std::sort(near.begin(), near.end());
+  std::vector<NearPair> pairs(npair);
+  std::vector<int> tbeg;
+  for (int i = 0; i < npair; ++i) {
+    pairs[i].target = near[i].first;
+    pairs[i].src_drop = near[i].second;
+    if (i == 0 || near[i].first != near[i - 1].first) tbeg.push_back(i);
+  }
+  const int ntgt = (int)tbeg.size();
+  tbeg.push_back(npair);
+  DevBuf<NearPair> d_pairs;
+  DevBuf<int> d_seed, d_tbeg, d_grid, d_tdrop, d_ngd1;
+  DevBuf<double> d_npts, d_cv;
+  DevBuf<long long> d_tloc, d_voff1;
+  BIE_TRY(d_pairs.upload(pairs));
+  BIE_TRY(d_seed.alloc(npair));
+  BIE_TRY(launch_near_seed_points(d_pairs.ptr, npair, pts, npt, g->rec_std.ptr, g->toff.ptr, g->ngd.ptr, d_seed.ptr, s));
+  std::vector<int> hseed(npair);
+  std::vector<double> hp(3 * (size_t)npt);
+  BIE_CUDA_TRY(cudaMemcpyAsync(hseed.data(), d_seed.ptr, npair * sizeof(int), cudaMemcpyDeviceToHost, s));
+  BIE_CUDA_TRY(cudaMemcpyAsync(hp.data(), pts, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<double> x0(3 * (size_t)npair);
+  for (int i = 0; i < npair; ++i)
+    for (int c = 0; c < 3; ++c) x0[3 * i + c] = hp[c * npt + pairs[i].target];
+  BIE_TRY(near_points(ctx, g, pairs, x0, hseed, d_npts, d_grid, s));
+  BIE_TRY(d_pairs.upload(pairs));
+  BIE_TRY(d_tbeg.upload(tbeg));
+  BIE_TRY(near_tables(g));
+  // the on-surface values of the source drops in this precision, as SH expansions
+  if (prec == BIE_MIXED)
+    BIE_TRY(self_apply<float>(g, kind, raw, dens, s));
+  else if (prec == BIE_DF)
+    BIE_TRY(self_apply<dff>(g, kind, raw, dens, s));
+  else
+    BIE_TRY(self_apply<double>(g, kind, raw, dens, s));
+  BIE_TRY(near_snapshot(g, s));
+  // the check-point values in FP64 (the interpolation amplifies their errors)
+  BIE_TRY(d_cv.alloc(3 * (size_t)npair * L));
+  BIE_TRY(launch_near_checks<double>(kind, d_pairs.ptr, npair, L, d_npts.ptr, d_grid.ptr, g->centre_d.ptr,
+                                     g->toff.ptr, g->ngd.ptr, g->up_off_d.ptr, g->up_n_d.ptr, g->sX64.ptr, g->sN64.ptr,
+                                     g->sQ64.ptr, g->ntarget, g->uX64.ptr, g->uN64.ptr, g->uQ64.ptr, g->nup_total, wts,
+                                     d_cv.ptr, s));
+  // results go to out[c][t]: one pseudo-drop holding every point, stride npt
+  std::vector<long long> tl(npt);
+  for (long long t = 0; t < npt; ++t) tl[t] = t;
+  BIE_TRY(d_tloc.upload(tl));
+  BIE_TRY(d_tdrop.alloc(npt));
+  BIE_CUDA_TRY(cudaMemsetAsync(d_tdrop.ptr, 0, npt * sizeof(int), s));
+  const std::vector<long long> vo{0};
+  const std::vector<int> ng1{(int)npt};
+  BIE_TRY(d_voff1.upload(vo));
+  BIE_TRY(d_ngd1.upload(ng1));
+  BIE_TRY(launch_near_interp(d_pairs.ptr, d_tbeg.ptr, ntgt, L, kind, g->selfcoef.ptr, dens, g->coef_off_d.ptr,
+                             g->pdeg_d.ptr, g->hdrop_d.ptr, wts, d_cv.ptr, d_tdrop.ptr, d_tloc.ptr, d_voff1.ptr,
+                             d_ngd1.ptr, out, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  return BIE_OK;
 }
 
 }  // namespace bie
@@ -2486,6 +2747,41 @@ int bie_apply_double(bie_ctx* ctx, const bie_geom* g, const double* ucoef, doubl
   if (!ctx) return BIE_EINVAL;
   BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
   return layer_apply(ctx, g, 1, ucoef, out, precision, (cudaStream_t)stream);
+}
+
+int bie_eval_single(bie_ctx* ctx, const bie_geom* g, long long npoint, const double* points, const double* fcoef,
+                    double* out, int precision, void* stream) {
+  if (!ctx || !g || (npoint > 0 && (!points || !fcoef || !out))) return BIE_EINVAL;
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  return bie::eval_layer(ctx, const_cast<bie_geom*>(g), 0, npoint, points, fcoef, out, precision, (cudaStream_t)stream);
+}
+
+int bie_eval_double(bie_ctx* ctx, const bie_geom* g, long long npoint, const double* points, const double* ucoef,
+                    double* out, int precision, void* stream) {
+  if (!ctx || !g || (npoint > 0 && (!points || !ucoef || !out))) return BIE_EINVAL;
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  return bie::eval_layer(ctx, const_cast<bie_geom*>(g), 1, npoint, points, ucoef, out, precision, (cudaStream_t)stream);
+}
+
+int bie_eval_velocity(bie_ctx* ctx, const bie_geom* g, long long npoint, const double* points, const double* fcoef,
+                      const double* ucoef, const double* uinf, double* out, int precision, void* stream) {
+  if (!ctx || !g || (npoint > 0 && (!points || !fcoef || !ucoef || !out))) return BIE_EINVAL;
+  if (precision & BIE_RAW) {
+    set_error("bie_eval_velocity: BIE_RAW is not a velocity");
+    return BIE_EINVAL;
+  }
+  BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
+  if (npoint == 0) return BIE_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  bie_geom* gm = const_cast<bie_geom*>(g);
+  bie::DevBuf<double> S, D;
+  BIE_TRY(S.alloc(3 * npoint));
+  BIE_TRY(D.alloc(3 * npoint));
+  BIE_TRY(bie::eval_layer(ctx, gm, 0, npoint, points, fcoef, S.ptr, precision, s));
+  BIE_TRY(bie::eval_layer(ctx, gm, 1, npoint, points, ucoef, D.ptr, precision, s));
+  BIE_TRY(bie::launch_velocity(uinf, S.ptr, D.ptr, 3 * npoint, out, s));
+  BIE_CUDA_TRY(cudaStreamSynchronize(s));  // S and D are released on return
+  return BIE_OK;
 }
 
 int bie_rhs(bie_ctx* ctx, const bie_geom* g, const double* uinf, const double* fcoef, double* rhs, int precision,
