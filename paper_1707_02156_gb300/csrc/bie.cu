@@ -1321,8 +1321,8 @@ static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, 
 // interpolation anchored at the exterior limit of the source drop's on-surface values.
 constexpr long long kPtChunk = 32768;  // points per pass: 256 tiles
 
-static int eval_layer(bie_ctx* ctx, bie_geom* g, int kind, long long npt, const double* pts, const double* dens,
-                      double* out, int precision, cudaStream_t s) {
+static int eval_layers(bie_ctx* ctx, bie_geom* g, long long npt, const double* pts, const double* const dens[2],
+                       double* const out[2], int precision, cudaStream_t s) {
   const bool raw = (precision & BIE_RAW) != 0;
   const int prec = precision & 0xff;
   if ((precision & ~(0xff | BIE_RAW)) != 0 || (prec != BIE_FP64 && prec != BIE_MIXED && prec != BIE_DF)) {
@@ -1334,19 +1334,31 @@ static int eval_layer(bie_ctx* ctx, bie_geom* g, int kind, long long npt, const 
     return BIE_EINVAL;
   }
   if (npt == 0) return BIE_OK;
-  BIE_CUDA_TRY(cudaMemsetAsync(out, 0, 3 * npt * sizeof(double), s));
+  std::vector<int> kinds;  // the layers asked for: 0 single, 1 double
+  for (int k = 0; k < 2; ++k)
+    if (out[k]) {
+      kinds.push_back(k);
+      BIE_CUDA_TRY(cudaMemsetAsync(out[k], 0, 3 * npt * sizeof(double), s));
+    }
   if (!g->interdrop_ready) BIE_TRY(setup_interdrop(ctx, g, s));
   const int nd = g->ndrop;
-  const double* wts = kind == 0 ? (raw ? g->wSr_all.ptr : g->wS_all.ptr) : (raw ? g->wDr_all.ptr : g->wD_all.ptr);
-  // source densities: FP32 for the mixed pair sums, FP64 for the others and for the check points
-  if (prec == BIE_MIXED) {
-    BIE_TRY(g->sQ32.alloc(3 * g->ntarget));
-    BIE_TRY(g->uQ32.alloc(3 * g->nup_total));
-    BIE_TRY(source_densities<float>(g, dens, g->sQ32.ptr, g->uQ32.ptr, s));
+  auto weights = [&](int kind) {
+    return kind == 0 ? (raw ? g->wSr_all.ptr : g->wS_all.ptr) : (raw ? g->wDr_all.ptr : g->wD_all.ptr);
+  };
+  // source densities of each layer, in the precision of its pair sums
+  DevBuf<float> q32[2][2];
+  DevBuf<double> q64[2][2];
+  for (int k : kinds) {
+    if (prec == BIE_MIXED) {
+      BIE_TRY(q32[k][0].alloc(3 * g->ntarget));
+      BIE_TRY(q32[k][1].alloc(3 * g->nup_total));
+      BIE_TRY(source_densities<float>(g, dens[k], q32[k][0].ptr, q32[k][1].ptr, s));
+    } else {
+      BIE_TRY(q64[k][0].alloc(3 * g->ntarget));
+      BIE_TRY(q64[k][1].alloc(3 * g->nup_total));
+      BIE_TRY(source_densities<double>(g, dens[k], q64[k][0].ptr, q64[k][1].ptr, s));
+    }
   }
-  BIE_TRY(g->sQ64.alloc(3 * g->ntarget));
-  BIE_TRY(g->uQ64.alloc(3 * g->nup_total));
-  BIE_TRY(source_densities<double>(g, dens, g->sQ64.ptr, g->uQ64.ptr, s));
   // tile-local tables, the same for every chunk
   const int mt = (int)((kPtChunk + kTile - 1) / kTile);
   std::vector<long long> h_t0(mt), h_loc(kPtChunk), h_toff(nd + mt, 0), h_voff(nd + mt, 0);
@@ -1396,57 +1408,62 @@ static int eval_layer(bie_ctx* ctx, bie_geom* g, int kind, long long npt, const 
     const int ntile = (int)((n + kTile - 1) / kTile);
     std::vector<int> h_n(ntile, kTile);
     h_n[ntile - 1] = (int)(n - (long long)(ntile - 1) * kTile);
-    BIE_TRY(d_n.upload(h_n));
-    BIE_TRY(launch_point_records(pts, npt, t0, n, ntile, nd, d_rec.ptr, d_cen.ptr, s));
-    BIE_TRY(launch_classify_points(pts, npt, t0, n, nd, g->centre_d.ptr, d_bnd.ptr, d_h.ptr, ctx->cfg.a_tilde,
-                                   g->rec_up.ptr, d_uoff.ptr, d_un.ptr, d_region.ptr, s));
-    BIE_TRY(launch_tile_masks(d_region.ptr, nd, d_t0.ptr, d_n.ptr, ntile, d_tm.ptr, s));
-    BIE_CUDA_TRY(cudaMemcpyAsync(tm.data(), d_tm.ptr, (size_t)ntile * nd * sizeof(TileMask), cudaMemcpyDeviceToHost, s));
-    BIE_CUDA_TRY(cudaStreamSynchronize(s));
     std::vector<PairItem> items;
     std::vector<int> blk_item, tile_blk(ntile + 1, 0);
-    for (int ti = 0; ti < ntile; ++ti) {
-      std::vector<PairItem> mine;
-      long long total = 0;
-      for (int j = 0; j < nd; ++j) {
-        const TileMask& m = tm[(size_t)ti * nd + j];
-        if (m.inside) {
-          set_error("a point of the tile starting at point " + std::to_string(t0 + (long long)ti * kTile) +
-                    " lies inside drop " + std::to_string(j));
-          return BIE_EOVERLAP;
-        }
-        for (int gk = 0; gk < 2; ++gk) {
-          if (!popc(m.m[gk])) continue;
-          PairItem it{};
-          it.tile = ti;
-          it.src_drop = j;
-          it.grid = gk;
-          it.s0 = gk ? g->up_off[j] : g->tgt_off[j];
-          it.s1 = it.s0 + (gk ? g->up_n[j] : (long long)ngrid(g->p[j]));
-          for (int q = 0; q < 4; ++q) it.mask[q] = m.m[gk][q];
-          mine.push_back(it);
-          total += it.s1 - it.s0;
-        }
-        for (int k = 0; k < h_n[ti]; ++k)
-          if ((m.m[2][k >> 5] >> (k & 31)) & 1u) near.emplace_back(t0 + (long long)ti * kTile + k, j);
-      }
-      const long long cap = std::max(cap_global, (total + 15) / 16);  // at most 16 blocks per tile
-      tile_blk[ti] = (int)blk_item.size();
-      long long used = cap;
-      for (auto it : mine) {
-        long long a = it.s0;
-        while (a < it.s1) {
-          if (used >= cap) {
-            blk_item.push_back((int)items.size());
-            used = 0;
+    {
+      Phase ph(ctx, "offsurface_classify", s);
+      BIE_TRY(d_n.upload(h_n));
+      BIE_TRY(launch_point_records(pts, npt, t0, n, ntile, nd, d_rec.ptr, d_cen.ptr, s));
+      BIE_TRY(launch_classify_points(pts, npt, t0, n, nd, g->centre_d.ptr, d_bnd.ptr, d_h.ptr, ctx->cfg.a_tilde,
+                                     g->rec_up.ptr, d_uoff.ptr, d_un.ptr, d_region.ptr, s));
+      BIE_TRY(launch_tile_masks(d_region.ptr, nd, d_t0.ptr, d_n.ptr, ntile, d_tm.ptr, s));
+      BIE_CUDA_TRY(cudaMemcpyAsync(tm.data(), d_tm.ptr, (size_t)ntile * nd * sizeof(TileMask), cudaMemcpyDeviceToHost,
+                                   s));
+      BIE_CUDA_TRY(cudaStreamSynchronize(s));
+      for (int ti = 0; ti < ntile; ++ti) {
+        std::vector<PairItem> mine;
+        long long total = 0;
+        for (int j = 0; j < nd; ++j) {
+          const TileMask& m = tm[(size_t)ti * nd + j];
+          if (m.inside) {
+            set_error("a point of the tile starting at point " + std::to_string(t0 + (long long)ti * kTile) +
+                      " lies inside drop " + std::to_string(j));
+            return BIE_EOVERLAP;
           }
-          const long long take = std::min(it.s1 - a, cap - used);
-          PairItem piece = it;
-          piece.s0 = a;
-          piece.s1 = a + take;
-          items.push_back(piece);
-          used += take;
-          a += take;
+          for (int gk = 0; gk < 2; ++gk) {
+            if (!popc(m.m[gk])) continue;
+            PairItem it{};
+            it.tile = ti;
+            it.src_drop = j;
+            it.grid = gk;
+            it.s0 = gk ? g->up_off[j] : g->tgt_off[j];
+            it.s1 = it.s0 + (gk ? g->up_n[j] : (long long)ngrid(g->p[j]));
+            for (int q = 0; q < 4; ++q) it.mask[q] = m.m[gk][q];
+            mine.push_back(it);
+            total += it.s1 - it.s0;
+          }
+          if (m.m[2][0] | m.m[2][1] | m.m[2][2] | m.m[2][3])
+            for (int k = 0; k < h_n[ti]; ++k)
+              if ((m.m[2][k >> 5] >> (k & 31)) & 1u) near.emplace_back(t0 + (long long)ti * kTile + k, j);
+        }
+        const long long cap = std::max(cap_global, (total + 15) / 16);  // at most 16 blocks per tile
+        tile_blk[ti] = (int)blk_item.size();
+        long long used = cap;
+        for (auto it : mine) {
+          long long a = it.s0;
+          while (a < it.s1) {
+            if (used >= cap) {
+              blk_item.push_back((int)items.size());
+              used = 0;
+            }
+            const long long take = std::min(it.s1 - a, cap - used);
+            PairItem piece = it;
+            piece.s0 = a;
+            piece.s1 = a + take;
+            items.push_back(piece);
+            used += take;
+            a += take;
+          }
         }
       }
     }
@@ -1458,32 +1475,38 @@ static int eval_layer(bie_ctx* ctx, bie_geom* g, int kind, long long npt, const 
     BIE_TRY(d_blk_item.upload(blk_item));
     BIE_TRY(d_tile_blk.upload(tile_blk));
     BIE_TRY(d_part.alloc((size_t)nblk * 3 * kTile));
-    if (prec == BIE_MIXED) {
-      Phase ph(ctx, "offsurface_f32", s);
-      BIE_TRY(launch_interdrop<float>(kind, g->tpt32, nblk, d_items.ptr, d_blk_item.ptr, d_t0.ptr, d_n.ptr, d_drop.ptr,
-                                      d_loc.ptr, d_toff.ptr, d_ngd.ptr, d_rec.ptr, d_cen.ptr, g->sX32.ptr, g->sN32.ptr,
-                                      g->sQ32.ptr, g->ntarget, g->uX32.ptr, g->uN32.ptr, g->uQ32.ptr, g->nup_total, wts,
-                                      d_part.ptr, s));
-    } else if (prec == BIE_DF) {
-      Phase ph(ctx, "offsurface_df", s);
-      BIE_TRY(launch_interdrop_df(kind, nblk, d_items.ptr, d_blk_item.ptr, d_t0.ptr, d_n.ptr, d_drop.ptr, d_loc.ptr,
-                                  d_toff.ptr, d_ngd.ptr, d_rec.ptr, d_cen.ptr, g->sX64.ptr, g->sN64.ptr, g->sQ64.ptr,
-                                  g->ntarget, g->uX64.ptr, g->uN64.ptr, g->uQ64.ptr, g->nup_total, wts, d_part.ptr, s));
-    } else {
-      Phase ph(ctx, "offsurface_f64", s);
-      BIE_TRY(launch_interdrop<double>(kind, g->tpt64, nblk, d_items.ptr, d_blk_item.ptr, d_t0.ptr, d_n.ptr,
-                                       d_drop.ptr, d_loc.ptr, d_toff.ptr, d_ngd.ptr, d_rec.ptr, d_cen.ptr, g->sX64.ptr,
-                                       g->sN64.ptr, g->sQ64.ptr, g->ntarget, g->uX64.ptr, g->uN64.ptr, g->uQ64.ptr,
-                                       g->nup_total, wts, d_part.ptr, s));
+    for (int k : kinds) {
+      const double* wts = weights(k);
+      if (prec == BIE_MIXED) {
+        Phase ph(ctx, "offsurface_f32", s);
+        BIE_TRY(launch_interdrop<float>(k, g->tpt32, nblk, d_items.ptr, d_blk_item.ptr, d_t0.ptr, d_n.ptr, d_drop.ptr,
+                                        d_loc.ptr, d_toff.ptr, d_ngd.ptr, d_rec.ptr, d_cen.ptr, g->sX32.ptr,
+                                        g->sN32.ptr, q32[k][0].ptr, g->ntarget, g->uX32.ptr, g->uN32.ptr,
+                                        q32[k][1].ptr, g->nup_total, wts, d_part.ptr, s));
+      } else if (prec == BIE_DF) {
+        Phase ph(ctx, "offsurface_df", s);
+        BIE_TRY(launch_interdrop_df(k, nblk, d_items.ptr, d_blk_item.ptr, d_t0.ptr, d_n.ptr, d_drop.ptr, d_loc.ptr,
+                                    d_toff.ptr, d_ngd.ptr, d_rec.ptr, d_cen.ptr, g->sX64.ptr, g->sN64.ptr,
+                                    q64[k][0].ptr, g->ntarget, g->uX64.ptr, g->uN64.ptr, q64[k][1].ptr, g->nup_total,
+                                    wts, d_part.ptr, s));
+      } else {
+        Phase ph(ctx, "offsurface_f64", s);
+        BIE_TRY(launch_interdrop<double>(k, g->tpt64, nblk, d_items.ptr, d_blk_item.ptr, d_t0.ptr, d_n.ptr,
+                                         d_drop.ptr, d_loc.ptr, d_toff.ptr, d_ngd.ptr, d_rec.ptr, d_cen.ptr,
+                                         g->sX64.ptr, g->sN64.ptr, q64[k][0].ptr, g->ntarget, g->uX64.ptr, g->uN64.ptr,
+                                         q64[k][1].ptr, g->nup_total, wts, d_part.ptr, s));
+      }
+      Phase ph(ctx, "offsurface_reduce", s);
+      BIE_CUDA_TRY(cudaMemsetAsync(d_vals.ptr, 0, (size_t)ntile * 3 * kTile * sizeof(double), s));
+      BIE_TRY(launch_reduce_tiles(d_part.ptr, d_tile_blk.ptr, d_t0.ptr, d_n.ptr, d_drop.ptr, d_loc.ptr, d_voff.ptr,
+                                  d_ngd.ptr, ntile, d_vals.ptr, s));
+      BIE_TRY(launch_gather_points(d_vals.ptr, t0, n, npt, out[k], s));
     }
-    BIE_CUDA_TRY(cudaMemsetAsync(d_vals.ptr, 0, (size_t)ntile * 3 * kTile * sizeof(double), s));
-    BIE_TRY(launch_reduce_tiles(d_part.ptr, d_tile_blk.ptr, d_t0.ptr, d_n.ptr, d_drop.ptr, d_loc.ptr, d_voff.ptr,
-                                d_ngd.ptr, ntile, d_vals.ptr, s));
-    BIE_TRY(launch_gather_points(d_vals.ptr, t0, n, npt, out, s));
     BIE_CUDA_TRY(cudaStreamSynchronize(s));  // the chunk's host tables are reused
   }
   if (near.empty()) return BIE_OK;
-  // Omega_2: interpolation along the normal line through the closest point (Sec. 2.3)
+  // Omega_2: interpolation along the normal line through the closest point (Sec. 2.3); the closest
+  // points and check points serve both layers
   Phase ph(ctx, "offsurface_near", s);
   const int npair = (int)near.size(), L = ctx->cfg.n_interp;
   std::sort(near.begin(), near.end());
@@ -1498,7 +1521,7 @@ static int eval_layer(bie_ctx* ctx, bie_geom* g, int kind, long long npt, const 
   tbeg.push_back(npair);
   DevBuf<NearPair> d_pairs;
   DevBuf<int> d_seed, d_tbeg, d_grid, d_tdrop, d_ngd1;
-  DevBuf<double> d_npts, d_cv;
+  DevBuf<double> d_npts, d_cv, c64s, c64u;
   DevBuf<long long> d_tloc, d_voff1;
   BIE_TRY(d_pairs.upload(pairs));
   BIE_TRY(d_seed.alloc(npair));
@@ -1515,20 +1538,7 @@ static int eval_layer(bie_ctx* ctx, bie_geom* g, int kind, long long npt, const 
   BIE_TRY(d_pairs.upload(pairs));
   BIE_TRY(d_tbeg.upload(tbeg));
   BIE_TRY(near_tables(g));
-  // the on-surface values of the source drops in this precision, as SH expansions
-  if (prec == BIE_MIXED)
-    BIE_TRY(self_apply<float>(g, kind, raw, dens, s));
-  else if (prec == BIE_DF)
-    BIE_TRY(self_apply<dff>(g, kind, raw, dens, s));
-  else
-    BIE_TRY(self_apply<double>(g, kind, raw, dens, s));
-  BIE_TRY(near_snapshot(g, s));
-  // the check-point values in FP64 (the interpolation amplifies their errors)
   BIE_TRY(d_cv.alloc(3 * (size_t)npair * L));
-  BIE_TRY(launch_near_checks<double>(kind, d_pairs.ptr, npair, L, d_npts.ptr, d_grid.ptr, g->centre_d.ptr,
-                                     g->toff.ptr, g->ngd.ptr, g->up_off_d.ptr, g->up_n_d.ptr, g->sX64.ptr, g->sN64.ptr,
-                                     g->sQ64.ptr, g->ntarget, g->uX64.ptr, g->uN64.ptr, g->uQ64.ptr, g->nup_total, wts,
-                                     d_cv.ptr, s));
   // results go to out[c][t]: one pseudo-drop holding every point, stride npt
   std::vector<long long> tl(npt);
   for (long long t = 0; t < npt; ++t) tl[t] = t;
@@ -1539,9 +1549,33 @@ static int eval_layer(bie_ctx* ctx, bie_geom* g, int kind, long long npt, const 
   const std::vector<int> ng1{(int)npt};
   BIE_TRY(d_voff1.upload(vo));
   BIE_TRY(d_ngd1.upload(ng1));
-  BIE_TRY(launch_near_interp(d_pairs.ptr, d_tbeg.ptr, ntgt, L, kind, g->selfcoef.ptr, dens, g->coef_off_d.ptr,
-                             g->pdeg_d.ptr, g->hdrop_d.ptr, wts, d_cv.ptr, d_tdrop.ptr, d_tloc.ptr, d_voff1.ptr,
-                             d_ngd1.ptr, out, s));
+  for (int k : kinds) {
+    const double* wts = weights(k);
+    // the on-surface values of the source drops in this precision, as SH expansions
+    if (prec == BIE_MIXED)
+      BIE_TRY(self_apply<float>(g, k, raw, dens[k], s));
+    else if (prec == BIE_DF)
+      BIE_TRY(self_apply<dff>(g, k, raw, dens[k], s));
+    else
+      BIE_TRY(self_apply<double>(g, k, raw, dens[k], s));
+    BIE_TRY(near_snapshot(g, s));
+    // the check-point values in FP64 (the interpolation amplifies their errors)
+    const double *qs = q64[k][0].ptr, *qu = q64[k][1].ptr;
+    if (prec == BIE_MIXED) {
+      BIE_TRY(c64s.alloc(3 * g->ntarget));
+      BIE_TRY(c64u.alloc(3 * g->nup_total));
+      BIE_TRY(source_densities<double>(g, dens[k], c64s.ptr, c64u.ptr, s));
+      qs = c64s.ptr;
+      qu = c64u.ptr;
+    }
+    BIE_TRY(launch_near_checks<double>(k, d_pairs.ptr, npair, L, d_npts.ptr, d_grid.ptr, g->centre_d.ptr,
+                                       g->toff.ptr, g->ngd.ptr, g->up_off_d.ptr, g->up_n_d.ptr, g->sX64.ptr,
+                                       g->sN64.ptr, qs, g->ntarget, g->uX64.ptr, g->uN64.ptr, qu, g->nup_total, wts,
+                                       d_cv.ptr, s));
+    BIE_TRY(launch_near_interp(d_pairs.ptr, d_tbeg.ptr, ntgt, L, k, g->selfcoef.ptr, dens[k], g->coef_off_d.ptr,
+                               g->pdeg_d.ptr, g->hdrop_d.ptr, wts, d_cv.ptr, d_tdrop.ptr, d_tloc.ptr, d_voff1.ptr,
+                               d_ngd1.ptr, out[k], s));
+  }
   BIE_CUDA_TRY(cudaStreamSynchronize(s));
   return BIE_OK;
 }
@@ -2753,14 +2787,18 @@ int bie_eval_single(bie_ctx* ctx, const bie_geom* g, long long npoint, const dou
                     double* out, int precision, void* stream) {
   if (!ctx || !g || (npoint > 0 && (!points || !fcoef || !out))) return BIE_EINVAL;
   BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
-  return bie::eval_layer(ctx, const_cast<bie_geom*>(g), 0, npoint, points, fcoef, out, precision, (cudaStream_t)stream);
+  const double* dens[2] = {fcoef, nullptr};
+  double* outs[2] = {out, nullptr};
+  return bie::eval_layers(ctx, const_cast<bie_geom*>(g), npoint, points, dens, outs, precision, (cudaStream_t)stream);
 }
 
 int bie_eval_double(bie_ctx* ctx, const bie_geom* g, long long npoint, const double* points, const double* ucoef,
                     double* out, int precision, void* stream) {
   if (!ctx || !g || (npoint > 0 && (!points || !ucoef || !out))) return BIE_EINVAL;
   BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
-  return bie::eval_layer(ctx, const_cast<bie_geom*>(g), 1, npoint, points, ucoef, out, precision, (cudaStream_t)stream);
+  const double* dens[2] = {nullptr, ucoef};
+  double* outs[2] = {nullptr, out};
+  return bie::eval_layers(ctx, const_cast<bie_geom*>(g), npoint, points, dens, outs, precision, (cudaStream_t)stream);
 }
 
 int bie_eval_velocity(bie_ctx* ctx, const bie_geom* g, long long npoint, const double* points, const double* fcoef,
@@ -2773,12 +2811,12 @@ int bie_eval_velocity(bie_ctx* ctx, const bie_geom* g, long long npoint, const d
   BIE_CUDA_TRY(cudaSetDevice(ctx->cfg.device));
   if (npoint == 0) return BIE_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  bie_geom* gm = const_cast<bie_geom*>(g);
   bie::DevBuf<double> S, D;
   BIE_TRY(S.alloc(3 * npoint));
   BIE_TRY(D.alloc(3 * npoint));
-  BIE_TRY(bie::eval_layer(ctx, gm, 0, npoint, points, fcoef, S.ptr, precision, s));
-  BIE_TRY(bie::eval_layer(ctx, gm, 1, npoint, points, ucoef, D.ptr, precision, s));
+  const double* dens[2] = {fcoef, ucoef};
+  double* outs[2] = {S.ptr, D.ptr};
+  BIE_TRY(bie::eval_layers(ctx, const_cast<bie_geom*>(g), npoint, points, dens, outs, precision, s));
   BIE_TRY(bie::launch_velocity(uinf, S.ptr, D.ptr, 3 * npoint, out, s));
   BIE_CUDA_TRY(cudaStreamSynchronize(s));  // S and D are released on return
   return BIE_OK;

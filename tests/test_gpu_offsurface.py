@@ -144,7 +144,7 @@ def test_two_chunks_with_a_ragged_tail_match_oracle(ctx):
     x = inputs.sphere_coef(p, radius=1.0, centre=(0.2, -0.1, 0.3))
     rng = np.random.default_rng(4)
     f = inputs.random_bandlimited(rng, p, 3)
-    drops = layer.Drops([x], [p], [p], [2.0], up=2)
+    drops = layer.Drops([x], [p], [p], [2.0], up=4)  # the context's upsampling factor
     n = 32768 + 237
     d = rng.standard_normal((3, n))
     d /= np.linalg.norm(d, axis=0)
