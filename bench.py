@@ -585,7 +585,13 @@ def offsurface_line(name, local, steps, warmup, npoint=131072):
                        steps if prec == 1 else 1, stream, scrub)
         res[prec] = {"ms": statistics.median(t), "out": out.clone()}
     rel = float(torch.linalg.norm(res[1]["out"] - res[0]["out"]) / torch.linalg.norm(res[0]["out"]))
-    line = {"workload": WORKLOADS[name], "points": npoint,
+    # one more mixed call with the library's per-phase events on
+    case.ctx.profile(True)
+    case.geo.velocity_at(pts, case.f, u, res[1]["out"], uinf=uinf, precision=1)
+    torch.cuda.synchronize()
+    phases = {k: {"ms": v[0], "calls": v[1]} for k, v in case.ctx.profile_read().items()}
+    case.ctx.profile(False)
+    line = {"workload": WORKLOADS[name], "points": npoint, "phases_ms_mixed": phases,
             "step": "velocity at seeded fluid points farther than 1.6 from every drop centre (bie_eval_velocity)",
             "ms_mixed": res[1]["ms"], "ms_fp64": res[0]["ms"], "points_per_s_mixed": npoint / (res[1]["ms"] * 1e-3),
             "speedup_mixed_vs_fp64": res[0]["ms"] / res[1]["ms"], "rel_err_mixed_vs_fp64": rel}
