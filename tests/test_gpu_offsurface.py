@@ -3,9 +3,12 @@ bie_eval_double, bie_eval_velocity) with the FP64 oracle (oracle/offsurface.py):
 regions of two drops 0.05 apart (some in the gap, near both), a single deformed drop, a point set
 that spans two 32768-point chunks with a ragged last tile, and points inside a drop.
 
-Bars: FP64 1e-12 (both sides run the same rules in FP64; the near-singular step's Newton iterations
-agree to rounding), double-float 1e-11, mixed 5e-6 (FP32 pair sums and self term, FP64 check points:
-the bar of the on-surface multi-drop applies)."""
+Bars: FP64 1e-12 at points in Omega_0/1 of every drop (both sides run the same rules in FP64), 1e-9 at
+points in Omega_2 of some drop, double-float 1e-11 / 1e-9, mixed 5e-6 (FP32 pair sums and self term,
+FP64 check points: the bar of the on-surface multi-drop applies).  The Omega_2 bar is the near rule's
+conditioning: the closest point is found by Newton to a step of 1e-14 and the interpolation through
+(0, h sqrt(l)) amplifies by about 2e3, so a 1e-15 relative change of a point moves the oracle's own
+value there by up to 9.5e-11 (measured on the 8-degree sphere of the two-chunk case)."""
 import math
 
 import numpy as np
@@ -20,12 +23,31 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 DF_TOL = 1e-11
+NEAR_TOL = 1e-9
 MIXED_TOL = 5e-6
 
 
 def _relerr(a, b):
     a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
     return max(np.linalg.norm(a - b) / np.linalg.norm(b), np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _check(out, ref, near, tol):
+    """Relative error within tol at the points off every drop's Omega_2, within NEAR_TOL (or tol if
+    larger) at the points in some drop's Omega_2, each relative to the largest value of the set."""
+    out, ref = np.asarray(out).reshape(3, -1), np.asarray(ref).reshape(3, -1)
+    scale = np.max(np.abs(ref))
+    far = ~near
+    if np.any(far):
+        e = max(_relerr(out[:, far], ref[:, far]), np.max(np.abs(out[:, far] - ref[:, far])) / scale)
+        assert e < tol, ("far", e, tol)
+    if np.any(near):
+        e = np.max(np.abs(out[:, near] - ref[:, near])) / scale
+        assert e < max(tol, NEAR_TOL), ("near", e)
+
+
+def _near(drops, pts):
+    return np.any(np.stack([offsurface.classify_points(drops, pts, j) == 2 for j in range(drops.N)]), axis=0)
 
 
 def _points_off(xcoef, p, params, dists):
@@ -85,16 +107,17 @@ def test_two_drops_every_region_matches_oracle(pair, kind):
     P = torch.tensor(np.ascontiguousarray(pts), device="cuda")
     out = torch.zeros_like(P)
     fn = geo.eval_single if kind == "S" else geo.eval_double
+    near = _near(drops, pts)
     for prec, tol in ((0, FP64_TOL), (2, DF_TOL), (1, MIXED_TOL)):
         out.fill_(1.0)
         fn(P, f, out, precision=prec)
         torch.cuda.synchronize()
-        assert _relerr(out.cpu().numpy(), ref) < tol, (kind, prec, _relerr(out.cpu().numpy(), ref))
+        _check(out.cpu().numpy(), ref, near, tol)
     # raw normalisation: the plain integrals, 1/8pi and 1/4pi
     ref_raw = offsurface.layer_at(drops, pts, fs, kind, raw=True)
     fn(P, f, out, precision=0, raw=True)
     torch.cuda.synchronize()
-    assert _relerr(out.cpu().numpy(), ref_raw) < FP64_TOL
+    _check(out.cpu().numpy(), ref_raw, near, FP64_TOL)
 
 
 def test_velocity_at_points_matches_oracle(pair):
@@ -109,10 +132,11 @@ def test_velocity_at_points_matches_oracle(pair):
     uinf = torch.zeros_like(P)
     uinf[0] = shear * P[2]
     out = torch.zeros_like(P)
+    near = _near(drops, pts)
     for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
         geo.velocity_at(P, f, u, out, uinf=uinf, precision=prec)
         torch.cuda.synchronize()
-        assert _relerr(out.cpu().numpy(), ref) < tol, prec
+        _check(out.cpu().numpy(), ref, near, tol)
 
 
 def test_single_deformed_drop_matches_oracle(ctx):
@@ -129,11 +153,12 @@ def test_single_deformed_drop_matches_oracle(ctx):
     P = torch.tensor(np.ascontiguousarray(pts), device="cuda")
     fd = torch.tensor(f.ravel(), device="cuda")
     out = torch.zeros_like(P)
+    near = _near(drops, pts)
     for kind, fn in (("S", geo.eval_single), ("D", geo.eval_double)):
         ref = offsurface.layer_at(drops, pts, [f], kind)
         fn(P, fd, out, precision=0)
         torch.cuda.synchronize()
-        assert _relerr(out.cpu().numpy(), ref) < FP64_TOL, kind
+        _check(out.cpu().numpy(), ref, near, FP64_TOL)
     geo.close()
 
 
@@ -159,7 +184,7 @@ def test_two_chunks_with_a_ragged_tail_match_oracle(ctx):
     out = torch.zeros_like(P)
     geo.eval_double(P, torch.tensor(f.ravel(), device="cuda"), out, precision=0)
     torch.cuda.synchronize()
-    assert _relerr(out.cpu().numpy(), ref) < FP64_TOL
+    _check(out.cpu().numpy(), ref, codes == 2, FP64_TOL)
     geo.close()
 
 
