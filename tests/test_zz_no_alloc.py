@@ -1,6 +1,5 @@
 """GPU check of bie_rotate_noalloc, the rotation entry point for callers that cannot allocate device
-memory (stream capture into CUDA graphs, frameworks that own all device memory, allocator-free
-loops).  It must give the same rotated coefficients as bie_rotate, on consecutive calls that reuse
+memory (frameworks that own all device memory, loops that must not touch the allocator).  It must give the same rotated coefficients as bie_rotate, on consecutive calls that reuse
 its fixed staging array, and reject requests too large for that array before touching the GPU.
 This file is collected last so that a failure here cannot hide the result of any other test."""
 import numpy as np
