@@ -60,8 +60,8 @@ TENSOR_ROTATION = False
 
 PROFILED_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum -k regex:k_interdrop_x2
-    #     -s 12 -c 1 python bench.py --no-aux --steps 1 --warmup 3   (one pass; 183.97 MB read, 132.42 MB written)
-    ("interdrop_f32", "c5"): {"bytes": 316.39e6, "source": "interdrop.cu", "sha": "0e3c67105e267752"},
+    #     -s 16 -c 1 python bench.py --no-aux --steps 1 --warmup 3   (one pass; 183.82 MB read, 132.60 MB written)
+    ("interdrop_f32", "c5"): {"bytes": 316.42e6, "source": "interdrop.cu", "sha": "3d31e48d7720c587"},
     # ncu --set full --kernel-name-base demangled -k regex:"k_self_proj<float" -s 4 -c 1
     #     python bench.py --workload c2 --no-aux --steps 1 --warmup 3   (60.35 MB read, 0.70 MB written)
     ("self_proj_f32", "c2"): {"bytes": 61.05e6, "source": "self.cu", "sha": "ea9853933df42712"},

@@ -748,14 +748,14 @@ static int autotune_interdrop(bie_ctx* ctx, bie_geom* g, cudaStream_t s) {
   BIE_CUDA_TRY(cudaEventCreate(&e0));
   BIE_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  // targets per thread 1 (scalar FP32), 2 and 4 (packed lane pairs), and 12, 14 (packed, with the
-  // next chunk of sources loaded while the current one is summed)
-  const int cand[5] = {1, 2, 4, 12, 14};
+  // targets per thread 1 (scalar FP32), 2 and 4 (packed lane pairs), 12, 14 (packed, with the next
+  // chunk of sources loaded while the current one is summed), 24, 34 (4 targets, 32-source chunks)
+  const int cand[7] = {1, 2, 4, 12, 14, 24, 34};
   // time a leading part of the work list of about 5e10 pairs (at least 32 blocks per SM); blocks carry
   // similar work, so its ranking is the full list's
   const int nsample = (int)std::min<long long>(
       g->nblk, std::max<long long>(32LL * ctx->sms, (long long)((double)g->nblk * std::min(1.0, 5e10 / (double)pairs))));
-  for (int ci = 0; ci < 5; ++ci) {
+  for (int ci = 0; ci < 7; ++ci) {
     cudaEventRecord(e0, s);
     int st = launch_interdrop<float>(1, cand[ci], nsample, g->items.ptr, g->blk_item.ptr, g->tile_t0.ptr,
                                      g->tile_n.ptr, g->tile_drop.ptr, g->tgt_loc.ptr, g->toff.ptr, g->ngd.ptr,
@@ -1319,7 +1319,7 @@ static int interdrop_apply(bie_geom* g, int kind, bool raw, const double* dens, 
 // after the real drops, whose centre is the tile's mean point), the region masks of every (tile,
 // drop) pair make a work list for the pair kernels, and the Omega_2 pairs take the near-singular
 // interpolation anchored at the exterior limit of the source drop's on-surface values.
-constexpr long long kPtChunk = 32768;  // points per pass: 256 tiles
+constexpr long long kPtChunk = 32768;  // points per pass at most: 256 tiles
 
 static int eval_layers(bie_ctx* ctx, bie_geom* g, long long npt, const double* pts, const double* const dens[2],
                        double* const out[2], int precision, cudaStream_t s) {
@@ -1342,6 +1342,10 @@ static int eval_layers(bie_ctx* ctx, bie_geom* g, long long npt, const double* p
     }
   if (!g->interdrop_ready) BIE_TRY(setup_interdrop(ctx, g, s));
   const int nd = g->ndrop;
+  // points per pass: kPtChunk, fewer when there are so many drops that the per-(point, drop) scratch
+  // of the classification would pass 2^26 entries
+  const long long chunk =
+      std::max<long long>(kTile, std::min<long long>(kPtChunk, ((1LL << 26) / nd) / kTile * kTile));
   auto weights = [&](int kind) {
     return kind == 0 ? (raw ? g->wSr_all.ptr : g->wS_all.ptr) : (raw ? g->wDr_all.ptr : g->wD_all.ptr);
   };
@@ -1360,8 +1364,8 @@ static int eval_layers(bie_ctx* ctx, bie_geom* g, long long npt, const double* p
     }
   }
   // tile-local tables, the same for every chunk
-  const int mt = (int)((kPtChunk + kTile - 1) / kTile);
-  std::vector<long long> h_t0(mt), h_loc(kPtChunk), h_toff(nd + mt, 0), h_voff(nd + mt, 0);
+  const int mt = (int)((chunk + kTile - 1) / kTile);
+  std::vector<long long> h_t0(mt), h_loc(chunk), h_toff(nd + mt, 0), h_voff(nd + mt, 0);
   std::vector<int> h_drop(mt), h_ngd(nd + mt, 0);
   for (int ti = 0; ti < mt; ++ti) {
     h_t0[ti] = (long long)ti * kTile;
@@ -1370,7 +1374,7 @@ static int eval_layers(bie_ctx* ctx, bie_geom* g, long long npt, const double* p
     h_ngd[nd + ti] = kTile;
     h_voff[nd + ti] = (long long)ti * 3 * kTile;
   }
-  for (long long k = 0; k < kPtChunk; ++k) h_loc[k] = k % kTile;
+  for (long long k = 0; k < chunk; ++k) h_loc[k] = k % kTile;
   DevBuf<long long> d_t0, d_loc, d_toff, d_voff, d_uoff, d_un;
   DevBuf<int> d_drop, d_ngd, d_n, d_blk_item, d_tile_blk;
   DevBuf<double> d_rec, d_cen, d_vals, d_part, d_bnd, d_h;
@@ -1390,7 +1394,10 @@ static int eval_layers(bie_ctx* ctx, bie_geom* g, long long npt, const double* p
   BIE_TRY(d_rec.alloc((size_t)mt * 7 * kTile));
   BIE_TRY(d_cen.alloc(3 * (size_t)(nd + mt)));
   BIE_TRY(d_vals.alloc((size_t)mt * 3 * kTile));
-  BIE_TRY(d_region.alloc((size_t)kPtChunk * nd));
+  BIE_TRY(d_region.alloc((size_t)chunk * nd));
+  DevBuf<unsigned> d_list, d_count;
+  BIE_TRY(d_list.alloc((size_t)chunk * nd));
+  BIE_TRY(d_count.alloc(1));
   BIE_TRY(d_tm.alloc((size_t)mt * nd));
   BIE_CUDA_TRY(cudaMemcpyAsync(d_cen.ptr, g->centre_d.ptr, 3 * nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
   std::vector<TileMask> tm((size_t)mt * nd);
@@ -1403,8 +1410,8 @@ static int eval_layers(bie_ctx* ctx, bie_geom* g, long long npt, const double* p
     for (int q = 0; q < 4; ++q) c += __builtin_popcount(m[q]);
     return c;
   };
-  for (long long t0 = 0; t0 < npt; t0 += kPtChunk) {
-    const long long n = std::min(kPtChunk, npt - t0);
+  for (long long t0 = 0; t0 < npt; t0 += chunk) {
+    const long long n = std::min(chunk, npt - t0);
     const int ntile = (int)((n + kTile - 1) / kTile);
     std::vector<int> h_n(ntile, kTile);
     h_n[ntile - 1] = (int)(n - (long long)(ntile - 1) * kTile);
@@ -1415,7 +1422,8 @@ static int eval_layers(bie_ctx* ctx, bie_geom* g, long long npt, const double* p
       BIE_TRY(d_n.upload(h_n));
       BIE_TRY(launch_point_records(pts, npt, t0, n, ntile, nd, d_rec.ptr, d_cen.ptr, s));
       BIE_TRY(launch_classify_points(pts, npt, t0, n, nd, g->centre_d.ptr, d_bnd.ptr, d_h.ptr, ctx->cfg.a_tilde,
-                                     g->rec_up.ptr, d_uoff.ptr, d_un.ptr, d_region.ptr, s));
+                                     g->rec_up.ptr, d_uoff.ptr, d_un.ptr, d_region.ptr, d_list.ptr, d_count.ptr,
+                                     ctx->sms, s));
       BIE_TRY(launch_tile_masks(d_region.ptr, nd, d_t0.ptr, d_n.ptr, ntile, d_tm.ptr, s));
       BIE_CUDA_TRY(cudaMemcpyAsync(tm.data(), d_tm.ptr, (size_t)ntile * nd * sizeof(TileMask), cudaMemcpyDeviceToHost,
                                    s));

@@ -254,7 +254,7 @@ struct alignas(16) SrcRecX2 {
 // chains per thread).  PF = 1 software-pipelines the staging: the next chunk's sources are loaded
 // into registers while the current chunk is summed, so the global-memory latency of the staging
 // overlaps the arithmetic.
-template <int KIND, int TPT, int PF>
+template <int KIND, int TPT, int PF, int CH = kChunkX2>
 __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
     const PairItem* __restrict__ items, const int* __restrict__ blk_item, const long long* __restrict__ tile_t0,
     const int* __restrict__ tile_n, const int* __restrict__ tile_drop, const long long* __restrict__ tgt_loc,
@@ -267,8 +267,9 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
   constexpr int NW = TPT / 2;  // lane pairs per thread
   constexpr int NV = KIND ? 9 : 6;
   constexpr int nv = (NV + 1) / 2;  // 128-bit loads per staged source
-  constexpr int RPT = kChunkX2 / NT;  // staged sources per thread and chunk
-  __shared__ SrcRecX2 src[kChunkX2];
+  static_assert(CH % NT == 0 && CH >= NT, "a chunk is a whole number of sources per thread");
+  constexpr int RPT = CH / NT;  // staged sources per thread and chunk
+  __shared__ SrcRecX2 src[CH];
   __shared__ float tgt[3][kTile];   // the tile's targets relative to their own drop's centre (FP32)
   __shared__ double acc[3][kTile];  // per-target sums over the block's items
   const int b = blockIdx.x;
@@ -361,12 +362,12 @@ __global__ void __launch_bounds__(kTile / TPT) k_interdrop_x2(
     const long long s0 = items[it].s0, s1 = items[it].s1;
     float pre[RPT][NV];
     if (PF) load_chunk(pre, X, N, Q, ld, s0, s1);
-    for (long long c0 = s0; c0 < s1; c0 += kChunkX2) {
-      const int cn = (int)min((long long)kChunkX2, s1 - c0);
+    for (long long c0 = s0; c0 < s1; c0 += CH) {
+      const int cn = (int)min((long long)CH, s1 - c0);
       if (!PF) load_chunk(pre, X, N, Q, ld, c0, s1);
       store_chunk(pre);
       __syncthreads();
-      if (PF && c0 + kChunkX2 < s1) load_chunk(pre, X, N, Q, ld, c0 + kChunkX2, s1);  // next chunk, in flight
+      if (PF && c0 + CH < s1) load_chunk(pre, X, N, Q, ld, c0 + CH, s1);  // next chunk, in flight
       if (act) {
         const int cn2 = (cn + 1) & ~1;
         for (int k = 0; k < cn2; k += 2) {
@@ -720,7 +721,7 @@ int launch_classify(const double* rec_std, long long ntarget, const int* tdrop, 
   return BIE_OK;
 }
 
-template <typename R, int TPT, int PF = 0>
+template <typename R, int TPT, int PF = 0, int CH = kChunkX2>
 static void interdrop_kernel(int kind, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
                              const int* tile_n, const int* tile_drop, const long long* tgt_loc,
                              const long long* toff_std, const int* ngd, const double* rec_std, const double* centre,
@@ -729,11 +730,11 @@ static void interdrop_kernel(int kind, int nblk, const PairItem* items, const in
   if constexpr (std::is_same<R, float>::value && TPT % 2 == 0) {
     // FP32 with two or more targets per thread: packed lane pairs
     if (kind == 0)
-      k_interdrop_x2<0, TPT, PF><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
+      k_interdrop_x2<0, TPT, PF, CH><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
                                                               toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu,
                                                               Nu, Qu, nup, wts, partial);
     else
-      k_interdrop_x2<1, TPT, PF><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
+      k_interdrop_x2<1, TPT, PF, CH><<<nblk, kTile / TPT, 0, s>>>(items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc,
                                                               toff_std, ngd, rec_std, centre, Xs, Ns, Qs, nstd, Xu,
                                                               Nu, Qu, nup, wts, partial);
     return;
@@ -755,13 +756,21 @@ int launch_interdrop(int kind, int tpt, int nblk, const PairItem* items, const i
                      const R* Qs, long long nstd, const R* Xu, const R* Nu, const R* Qu, long long nup,
                      const double* wts, double* partial, cudaStream_t s) {
   if (nblk == 0) return BIE_OK;
-  if (std::is_same<R, float>::value && (tpt == 12 || tpt == 14)) {  // packed FP32, pipelined staging
+  if (std::is_same<R, float>::value && (tpt == 12 || tpt == 14 || tpt == 24 || tpt == 34)) {
+    // packed FP32: 12, 14 = 2 or 4 targets per thread with pipelined staging; 24, 34 = 4 targets per
+    // thread with 32-source chunks, without and with pipelined staging
     if (tpt == 12)
       interdrop_kernel<R, 2, 1>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
                                 rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);
-    else
+    else if (tpt == 14)
       interdrop_kernel<R, 4, 1>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
                                 rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);
+    else if (tpt == 24)
+      interdrop_kernel<R, 4, 0, 32>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
+                                    rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);
+    else
+      interdrop_kernel<R, 4, 1, 32>(kind, nblk, items, blk_item, tile_t0, tile_n, tile_drop, tgt_loc, toff_std, ngd,
+                                    rec_std, centre, Xs, Ns, Qs, nstd, Xu, Nu, Qu, nup, wts, partial, s);
     count_launch();
     BIE_CUDA_TRY(cudaGetLastError());
     return BIE_OK;

@@ -28,8 +28,9 @@ int launch_classify(const double* rec_std, long long ntarget, const int* tdrop, 
                     const long long* toff_std, const int* ngd, int ndrop, const double* centre, const double* bound,
                     const double* h, double a_tilde, const double* rec_up, const long long* up_off,
                     const long long* up_n, unsigned char* region, cudaStream_t s);
-// tpt: targets per thread (1, 2 or 4; chosen per geometry by timing, see setup_interdrop); for FP32,
-// 12 and 14 select the packed kernel with 2 or 4 targets per thread and pipelined source staging
+// tpt: targets per thread (1, 2 or 4; chosen per geometry by timing, see autotune_interdrop); for FP32,
+// 12 and 14 select the packed kernel with 2 or 4 targets per thread and pipelined source staging,
+// 24 and 34 the packed kernel with 4 targets per thread and 32-source chunks (34: pipelined)
 template <typename R>
 int launch_interdrop(int kind, int tpt, int nblk, const PairItem* items, const int* blk_item, const long long* tile_t0,
                      const int* tile_n, const int* tile_drop, const long long* tgt_loc, const long long* toff_std,

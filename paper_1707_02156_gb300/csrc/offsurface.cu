@@ -18,12 +18,14 @@ inline unsigned blocks_for(long long n, int t = kThreads) { return (unsigned)((n
 // region[t * nd + j] for the points t0 .. t0 + n - 1 of pts [3][ld]: 0 / 1 / 2 for Omega_0/1/2 of
 // drop j, 3 when the point lies inside drop j.  The tests are those of the drops' own targets: the
 // distance to the nearest point of drop j's upsampled grid against h_j and A h_j (after the bounding-
-// sphere test), inside when the point is on the inner side of the tangent plane there.
-__global__ void k_classify_points(const double* __restrict__ pts, long long ld, long long t0, long long n, int nd,
-                                  const double* __restrict__ centre, const double* __restrict__ bound,
-                                  const double* __restrict__ h, double a_tilde, const double* __restrict__ rec_up,
-                                  const long long* __restrict__ up_off, const long long* __restrict__ up_n,
-                                  unsigned char* __restrict__ region) {
+// sphere test), inside when the point is on the inner side of the tangent plane there.  Two passes:
+// one thread per (point, drop) settles the pairs outside the bounding sphere widened by A h_j and
+// lists the others; then one warp per listed pair scans the upsampled grid, its lanes striding over
+// the points (the first nearest point wins ties, as in a sequential scan).
+__global__ void k_classify_points_far(const double* __restrict__ pts, long long ld, long long t0, long long n, int nd,
+                                      const double* __restrict__ centre, const double* __restrict__ bound,
+                                      const double* __restrict__ h, double a_tilde, unsigned char* __restrict__ region,
+                                      unsigned* __restrict__ list, unsigned* __restrict__ count) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * nd) return;
   const long long t = idx / nd;
@@ -34,23 +36,52 @@ __global__ void k_classify_points(const double* __restrict__ pts, long long ld, 
     region[idx] = 0;
     return;
   }
-  const long long N = up_n[j];
-  const double* r = rec_up + 7 * up_off[j];
-  double best = 1e300;
-  long long bi = 0;
-  for (long long s = 0; s < N; ++s) {
-    const double d0 = x0 - r[s], d1 = x1 - r[N + s], d2 = x2 - r[2 * N + s];
-    const double d = d0 * d0 + d1 * d1 + d2 * d2;
-    if (d < best) {
-      best = d;
-      bi = s;
+  list[atomicAdd(count, 1u)] = (unsigned)idx;
+}
+
+__global__ void k_classify_points_near(const double* __restrict__ pts, long long ld, long long t0, int nd,
+                                       const double* __restrict__ h, double a_tilde,
+                                       const double* __restrict__ rec_up, const long long* __restrict__ up_off,
+                                       const long long* __restrict__ up_n, const unsigned* __restrict__ list,
+                                       const unsigned* __restrict__ count, unsigned char* __restrict__ region) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned total = *count;
+  for (long long w = warp; w < total; w += nwarp) {
+    const long long idx = list[w];
+    const long long t = idx / nd;
+    const int j = (int)(idx - t * nd);
+    const double x0 = pts[t0 + t], x1 = pts[ld + t0 + t], x2 = pts[2 * ld + t0 + t];
+    const long long N = up_n[j];
+    const double* r = rec_up + 7 * up_off[j];
+    double best = 1e300;
+    long long bi = N;
+    for (long long s = lane; s < N; s += 32) {
+      const double d0 = x0 - r[s], d1 = x1 - r[N + s], d2 = x2 - r[2 * N + s];
+      const double d = d0 * d0 + d1 * d1 + d2 * d2;
+      if (d < best) {
+        best = d;
+        bi = s;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {  // smallest distance, then smallest index
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob < best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      const double dist = sqrt(best);
+      const double side = (x0 - r[bi]) * r[3 * N + bi] + (x1 - r[N + bi]) * r[4 * N + bi] +
+                          (x2 - r[2 * N + bi]) * r[5 * N + bi];
+      unsigned char code = dist <= h[j] ? 2 : (dist <= a_tilde * h[j] ? 1 : 0);
+      if (side <= 0.0) code = 3;
+      region[idx] = code;
     }
   }
-  const double dist = sqrt(best);
-  const double side = (x0 - r[bi]) * r[3 * N + bi] + (x1 - r[N + bi]) * r[4 * N + bi] + (x2 - r[2 * N + bi]) * r[5 * N + bi];
-  unsigned char code = dist <= h[j] ? 2 : (dist <= a_tilde * h[j] ? 1 : 0);
-  if (side <= 0.0) code = 3;
-  region[idx] = code;
 }
 
 // rec[tile][7][128]: rows 0-2 the chunk's points (zero past its end), rows 3-6 zero; and the tile's
@@ -128,10 +159,17 @@ __global__ void k_velocity(const double* __restrict__ uinf, const double* __rest
 
 int launch_classify_points(const double* pts, long long ld, long long t0, long long n, int nd, const double* centre,
                            const double* bound, const double* h, double a_tilde, const double* rec_up,
-                           const long long* up_off, const long long* up_n, unsigned char* region, cudaStream_t s) {
+                           const long long* up_off, const long long* up_n, unsigned char* region, unsigned* list,
+                           unsigned* count, int sms, cudaStream_t s) {
   if (n * nd == 0) return BIE_OK;
-  k_classify_points<<<blocks_for(n * nd), kThreads, 0, s>>>(pts, ld, t0, n, nd, centre, bound, h, a_tilde, rec_up,
-                                                            up_off, up_n, region);
+  if (n * nd > 0xffffffffLL) return BIE_EINVAL;
+  BIE_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
+  k_classify_points_far<<<blocks_for(n * nd), kThreads, 0, s>>>(pts, ld, t0, n, nd, centre, bound, h, a_tilde, region,
+                                                                list, count);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  k_classify_points_near<<<8 * sms, kThreads, 0, s>>>(pts, ld, t0, nd, h, a_tilde, rec_up, up_off, up_n, list, count,
+                                                      region);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;

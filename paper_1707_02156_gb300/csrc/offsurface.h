@@ -8,10 +8,12 @@
 namespace bie {
 
 // region[t * nd + j], t < n: the points t0 + t of pts [3][ld] against drop j (0 / 1 / 2 = Omega_0/1/2,
-// 3 = inside drop j)
+// 3 = inside drop j).  list: n * nd entries of scratch, count: one (device); n * nd < 2^32; sms: the
+// device's multiprocessors (sizes the second pass)
 int launch_classify_points(const double* pts, long long ld, long long t0, long long n, int nd, const double* centre,
                            const double* bound, const double* h, double a_tilde, const double* rec_up,
-                           const long long* up_off, const long long* up_n, unsigned char* region, cudaStream_t s);
+                           const long long* up_off, const long long* up_n, unsigned char* region, unsigned* list,
+                           unsigned* count, int sms, cudaStream_t s);
 // the n points t0.. of pts as target records rec [ntile][7][kTile] and the tiles' centres
 // centre[3 * (nd + tile)]
 int launch_point_records(const double* pts, long long ld, long long t0, long long n, int ntile, int nd, double* rec,
