@@ -75,6 +75,9 @@ def test_null_arguments_are_rejected_before_any_device_work(L):
     assert L.bie_apply_single(None, None, None, None, 0, None) == EINVAL
     assert L.bie_apply_double(None, None, None, None, 0, None) == EINVAL
     assert L.bie_rhs(None, None, None, None, None, 0, None) == EINVAL
+    assert L.bie_eval_single(None, None, 4, None, None, None, 0, None) == EINVAL
+    assert L.bie_eval_double(None, None, 4, None, None, None, 0, None) == EINVAL
+    assert L.bie_eval_velocity(None, None, 4, None, None, None, None, None, 0, None) == EINVAL
     assert L.bie_solve(None, None, None, None, ctypes.byref(o), ctypes.byref(info), None) == EINVAL
     assert L.bie_step_midpoint(None, 1, p, p, None, None, 0.2, 0.0, lam, 1.0, 0.01, ctypes.byref(o), None,
                                None) == EINVAL
