@@ -563,6 +563,31 @@ def fluid_points(w, n, clearance, seed=11):
     return np.ascontiguousarray(np.concatenate(keep, axis=1)[:, :n])
 
 
+def near_surface_points(ctx, w, n, offset, seed=12):
+    """n seeded points `offset` outside the drops: random standard-grid points of random drops moved
+    out along the ray from the drop's centre (outward for these convex, near-spherical shapes), as a
+    [3][n] device array; with offset below h = R pi/(p+1) they lie in that drop's Omega_2."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    grid = torch.zeros(sum(3 * (p + 1) * (2 * p + 2) for p in w.p), dtype=torch.float64, device="cuda")
+    ctx.sh_synthesize(w.p, w.p, 3, torch.tensor(w.xcoef, device="cuda"), grid)
+    g = grid.cpu().numpy()
+    blocks, o, oc = [], 0, 0
+    for p in w.p:
+        ng, k = (p + 1) * (2 * p + 2), (p + 1) ** 2
+        c = w.xcoef[oc:oc + 3 * k].reshape(3, k)[:, 0] / math.sqrt(4 * math.pi)
+        blocks.append((g[o:o + 3 * ng].reshape(3, ng), c))
+        o += 3 * ng
+        oc += 3 * k
+    out = np.empty((3, n))
+    for i in range(n):
+        x, c = blocks[rng.integers(len(blocks))]
+        y = x[:, rng.integers(x.shape[1])]
+        out[:, i] = y + offset * (y - c) / np.linalg.norm(y - c)
+    return torch.tensor(out, device="cuda")
+
+
 def offsurface_line(name, local, steps, warmup, npoint=131072):
     """The velocity u_inf + (S[f] + D[u]) / 2 at npoint fluid points among the drops (bie_eval_velocity:
     region classification, pair sums on the standard / upsampled grids, near-singular interpolation
@@ -591,7 +616,25 @@ def offsurface_line(name, local, steps, warmup, npoint=131072):
     torch.cuda.synchronize()
     phases = {k: {"ms": v[0], "calls": v[1]} for k, v in case.ctx.profile_read().items()}
     case.ctx.profile(False)
+    # points 0.06 off the surfaces (in Omega_2 of the nearest drop): the near-singular step's cost
+    nn = 8192
+    near_pts = near_surface_points(case.ctx, case.w, nn, 0.06)
+    uinf_n = torch.zeros_like(near_pts)
+    uinf_n[0] = (case.w.shear if case.w.shear else 1.0) * near_pts[2]
+    near_res = {}
+    for prec in (1, 0):
+        out = torch.zeros_like(near_pts)
+        case.ctx.profile(prec == 1)
+        t = timed_each(lambda: case.geo.velocity_at(near_pts, case.f, u, out, uinf=uinf_n, precision=prec), 1, stream,
+                       scrub)
+        near_res[prec] = {"ms": t[0], "out": out.clone()}
+        if prec == 1:
+            near_res["phases"] = {k: {"ms": v[0], "calls": v[1]} for k, v in case.ctx.profile_read().items()}
+            case.ctx.profile(False)
+    near_rel = float(torch.linalg.norm(near_res[1]["out"] - near_res[0]["out"]) / torch.linalg.norm(near_res[0]["out"]))
     line = {"workload": WORKLOADS[name], "points": npoint, "phases_ms_mixed": phases,
+            "near_surface": {"points": nn, "offset": 0.06, "ms_mixed": near_res[1]["ms"], "ms_fp64": near_res[0]["ms"],
+                             "rel_err_mixed_vs_fp64": near_rel, "phases_ms_mixed": near_res["phases"]},
             "step": "velocity at seeded fluid points farther than 1.6 from every drop centre (bie_eval_velocity)",
             "ms_mixed": res[1]["ms"], "ms_fp64": res[0]["ms"], "points_per_s_mixed": npoint / (res[1]["ms"] * 1e-3),
             "speedup_mixed_vs_fp64": res[0]["ms"] / res[1]["ms"], "rel_err_mixed_vs_fp64": rel}

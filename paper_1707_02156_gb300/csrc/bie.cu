@@ -1084,60 +1084,78 @@ static int near_points(bie_ctx* ctx, bie_geom* g, std::vector<NearPair>& pairs, 
   const int L = ctx->cfg.n_interp;
   DevBuf<NearPair> dpairs;
   BIE_TRY(dpairs.upload(pairs));
-  // rotated shape coefficients per pair: (alpha, beta) = (phi_b, theta_a - pi/2) puts the seed at the equator
-  std::vector<long long> xr_off(npair);
-  std::vector<double> alpha(npair), beta(npair);
-  long long xo = 0;
+  // rotated shape coefficients: (alpha, beta) = (phi_b, theta_a - pi/2) puts the seed (latitude a,
+  // longitude b) at the equator.  The phases e^{i m alpha} of every pair are applied in one launch;
+  // then the pairs of one degree and one seed latitude share one rotation launch (the small-d blocks
+  // of that beta), and one Newton launch serves every pair.  The rotated coefficients lie in group
+  // order, [pair][3][(p+1)^2].
+  std::unique_ptr<Phase> stage(new Phase(ctx, "near_newton", s));
+  std::vector<double> alpha(npair), beta(npair), hres(5 * (size_t)npair);
+  std::map<std::pair<int, int>, std::vector<int>> groups;  // (degree, seed latitude) -> pairs
+  int pmax = 0;
   for (int i = 0; i < npair; ++i) {
-    const int j = pairs[i].src_drop, p = g->p[j];
+    const int p = g->p[pairs[i].src_drop];
+    pmax = std::max(pmax, p);
+    groups[{p, hseed[i] / (2 * p + 2)}].push_back(i);
+  }
+  struct RotGroup {
+    int p, n;
+    long long base, fo_at, blk_at, blk_n;
+  };
+  std::vector<RotGroup> rg;
+  std::vector<long long> xr_off(npair), fo_all;
+  std::vector<double> blocks_all, ph(2 * (size_t)npair * (pmax + 1), 0.0);
+  long long xo = 0;
+  for (const auto& kv : groups) {
+    const int p = kv.first.first, a = kv.first.second;
+    const std::vector<int>& idx = kv.second;
     const int nb = 2 * p + 2;
+    const long long nc = ncoef(p);
     std::vector<double> t, w;
     gauss_legendre(p + 1, t, w);
-    const int a = hseed[i] / nb, b = hseed[i] % nb;
-    alpha[i] = kPi * b / (p + 1);
-    beta[i] = std::acos(t[a]) - 0.5 * kPi;
-    xr_off[i] = xo;
-    xo += 3 * ncoef(p);
-  }
-  DevBuf<double> xr, dx0, res;
-  DevBuf<long long> dxo;
-  DevBuf<int> pdeg;
-  BIE_TRY(xr.alloc(xo));
-  std::map<std::pair<int, double>, std::vector<double>> blk_cache;  // (degree, beta) -> blocks
-  for (int i = 0; i < npair; ++i) {
-    const int j = pairs[i].src_drop, p = g->p[j];
-    auto key = std::make_pair(p, beta[i]);
-    if (!blk_cache.count(key)) {
-      std::vector<double> b(wigner_block_stride(p));
-      wigner_blocks(p, beta[i], b.data());
-      blk_cache[key] = std::move(b);
+    const double be = std::acos(t[a]) - 0.5 * kPi;
+    std::vector<double> blk(wigner_block_stride(p));
+    wigner_blocks(p, be, blk.data());
+    rg.push_back({p, (int)idx.size(), xo, (long long)fo_all.size(), (long long)blocks_all.size(), (long long)blk.size()});
+    blocks_all.insert(blocks_all.end(), blk.begin(), blk.end());
+    for (size_t k = 0; k < idx.size(); ++k) {
+      const int i = idx[k];
+      alpha[i] = kPi * (hseed[i] % nb) / (p + 1);
+      beta[i] = be;
+      xr_off[i] = xo + (long long)k * 3 * nc;
+      for (int c = 0; c < 3; ++c) fo_all.push_back(xr_off[i] + c * nc);
+      for (int m = 0; m <= p; ++m) {
+        ph[2 * ((size_t)i * (pmax + 1) + m)] = std::cos(m * alpha[i]);
+        ph[2 * ((size_t)i * (pmax + 1) + m) + 1] = std::sin(m * alpha[i]);
+      }
     }
-    const std::vector<double>& blk = blk_cache[key];
-    std::vector<double> ph(2 * (p + 1));
-    for (int m = 0; m <= p; ++m) {
-      ph[2 * m] = std::cos(m * alpha[i]);
-      ph[2 * m + 1] = std::sin(m * alpha[i]);
-    }
-    std::vector<long long> fo(3);
-    for (int c = 0; c < 3; ++c) fo[c] = g->coef_off[j] + c * ncoef(p);
-    DevBuf<double> dblk, dph;
-    DevBuf<long long> dfo;
-    BIE_TRY(dblk.upload(blk));
-    BIE_TRY(dph.upload(ph));
-    BIE_TRY(dfo.upload(fo));
-    BIE_TRY((launch_rotate<double, double>(g->xcoef.ptr, dfo.ptr, 3, 1, p, dblk.ptr, (long long)blk.size(), 1, 1,
-                                           dph.ptr, xr.ptr + xr_off[i], 0, s)));
-    BIE_CUDA_TRY(cudaStreamSynchronize(s));
+    xo += (long long)idx.size() * 3 * nc;
   }
   std::vector<int> pd(g->p.begin(), g->p.end());
+  DevBuf<int> pdeg;
+  DevBuf<double> shifted, xr, dblk, dph, dx0, res;
+  DevBuf<long long> dfo, dxo, dcoef_off;
   BIE_TRY(pdeg.upload(pd));
+  BIE_TRY(dcoef_off.upload(g->coef_off));
+  BIE_TRY(dph.upload(ph));
   BIE_TRY(dxo.upload(xr_off));
+  BIE_TRY(dfo.upload(fo_all));
+  BIE_TRY(dblk.upload(blocks_all));
   BIE_TRY(dx0.upload(x0));
-  BIE_TRY(res.alloc(5 * npair));
+  BIE_TRY(shifted.alloc(xo));
+  BIE_TRY(xr.alloc(xo));
+  BIE_TRY(res.alloc(5 * (size_t)npair));
+  BIE_TRY(launch_near_phase_shift(dpairs.ptr, npair, g->xcoef.ptr, dcoef_off.ptr, pdeg.ptr, pmax, dph.ptr, dxo.ptr,
+                                  shifted.ptr, s));
+  for (const auto& G : rg) {
+    const long long nc = ncoef(G.p);
+    BIE_TRY((launch_rotate<double, double>(shifted.ptr, dfo.ptr + G.fo_at, 3, G.n, G.p, dblk.ptr + G.blk_at, G.blk_n,
+                                           1, 1, (const double*)nullptr, xr.ptr + G.base, 3 * nc, s)));
+  }
   BIE_TRY(launch_near_newton(dpairs.ptr, npair, xr.ptr, pdeg.ptr, dxo.ptr, dx0.ptr, res.ptr, s));
-  std::vector<double> hres(5 * npair);
   BIE_CUDA_TRY(cudaMemcpyAsync(hres.data(), res.ptr, hres.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   BIE_CUDA_TRY(cudaStreamSynchronize(s));
+  stage.reset(new Phase(ctx, "near_checkpoints", s));
   std::vector<double> pts(3 * (size_t)npair * L);
   for (int i = 0; i < npair; ++i) {
     const int j = pairs[i].src_drop;
@@ -1533,7 +1551,11 @@ static int eval_layers(bie_ctx* ctx, bie_geom* g, long long npt, const double* p
   DevBuf<long long> d_tloc, d_voff1;
   BIE_TRY(d_pairs.upload(pairs));
   BIE_TRY(d_seed.alloc(npair));
-  BIE_TRY(launch_near_seed_points(d_pairs.ptr, npair, pts, npt, g->rec_std.ptr, g->toff.ptr, g->ngd.ptr, d_seed.ptr, s));
+  {
+    Phase phs(ctx, "near_seed", s);
+    BIE_TRY(launch_near_seed_points(d_pairs.ptr, npair, pts, npt, g->rec_std.ptr, g->toff.ptr, g->ngd.ptr, d_seed.ptr,
+                                    s));
+  }
   std::vector<int> hseed(npair);
   std::vector<double> hp(3 * (size_t)npt);
   BIE_CUDA_TRY(cudaMemcpyAsync(hseed.data(), d_seed.ptr, npair * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1576,6 +1598,7 @@ static int eval_layers(bie_ctx* ctx, bie_geom* g, long long npt, const double* p
       qs = c64s.ptr;
       qu = c64u.ptr;
     }
+    Phase phc(ctx, "near_checks", s);
     BIE_TRY(launch_near_checks<double>(k, d_pairs.ptr, npair, L, d_npts.ptr, d_grid.ptr, g->centre_d.ptr,
                                        g->toff.ptr, g->ngd.ptr, g->up_off_d.ptr, g->up_n_d.ptr, g->sX64.ptr,
                                        g->sN64.ptr, qs, g->ntarget, g->uX64.ptr, g->uN64.ptr, qu, g->nup_total, wts,

@@ -331,7 +331,47 @@ __global__ void k_near_interp(const NearPair* __restrict__ pairs, const int* __r
   v[2 * ng] += acc[2];
 }
 
+// The source drop's shape coefficients of pair i with the phases of its seed longitude applied,
+// g_n^m = e^{i m alpha_i} x_n^m (real-packed; ph[i][m] = (cos m alpha_i, sin m alpha_i)), written to
+// out + dst_off[i] as [3][(p+1)^2]: the first step of the rotation R_z(alpha) R_y(beta), so that the
+// pairs of one seed latitude then share one rotation launch.  One block per pair.
+__global__ void k_near_phase_shift(const NearPair* __restrict__ pairs, int npair, const double* __restrict__ coef,
+                                   const long long* __restrict__ coef_off, const int* __restrict__ pdeg, int pmax,
+                                   const double* __restrict__ ph, const long long* __restrict__ dst_off,
+                                   double* __restrict__ out) {
+  const int i = blockIdx.x;
+  if (i >= npair) return;
+  const int j = pairs[i].src_drop;
+  const int p = pdeg[j];
+  const long long nc = (long long)(p + 1) * (p + 1);
+  const double* phi = ph + (long long)i * 2 * (pmax + 1);
+  for (long long q = threadIdx.x; q < 3 * nc; q += blockDim.x) {
+    const int c = (int)(q / nc);
+    const long long k = q - c * nc;
+    int n = (int)sqrt((double)k);
+    while ((long long)n * n > k) --n;
+    while ((long long)(n + 1) * (n + 1) <= k) ++n;
+    const int mm = (int)(k - (long long)n * (n + 1));
+    const int m = mm < 0 ? -mm : mm;
+    const double* f = coef + coef_off[j] + c * nc;
+    const double fr = f[n * (n + 1) + m];
+    const double fi = m > 0 ? f[n * (n + 1) - m] : 0.0;
+    const double cr = phi[2 * m], ci = phi[2 * m + 1];
+    out[dst_off[i] + c * nc + k] = mm >= 0 ? fr * cr - fi * ci : fr * ci + fi * cr;
+  }
+}
+
 }  // namespace
+
+int launch_near_phase_shift(const NearPair* pairs, int npair, const double* coef, const long long* coef_off,
+                            const int* pdeg, int pmax, const double* ph, const long long* dst_off, double* out,
+                            cudaStream_t s) {
+  if (!npair) return BIE_OK;
+  k_near_phase_shift<<<npair, 128, 0, s>>>(pairs, npair, coef, coef_off, pdeg, pmax, ph, dst_off, out);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
 
 int launch_near_seed(const NearPair* pairs, int npair, const double* rec_std, const long long* toff, const int* ngd,
                      const long long* tgt_loc, const int* tdrop, int* seed, cudaStream_t s) {

@@ -16,6 +16,11 @@ struct NearPair {
 
 int launch_near_seed(const NearPair* pairs, int npair, const double* rec_std, const long long* toff, const int* ngd,
                      const long long* tgt_loc, const int* tdrop, int* seed, cudaStream_t s);
+// shape coefficients of each pair's source drop with its seed longitude's phases applied (ph:
+// [pair][pmax+1][2] cos, sin of m alpha), to out + dst_off[pair] as [3][(p+1)^2]
+int launch_near_phase_shift(const NearPair* pairs, int npair, const double* coef, const long long* coef_off,
+                            const int* pdeg, int pmax, const double* ph, const long long* dst_off, double* out,
+                            cudaStream_t s);
 int launch_near_newton(const NearPair* pairs, int npair, const double* xr, const int* pdeg, const long long* xr_off,
                        const double* x0, double* result, cudaStream_t s);
 int launch_near_checkgrid(const NearPair* pairs, int npair, int L, const double* pts, const double* centre,
