@@ -1152,7 +1152,10 @@ static int near_points(bie_ctx* ctx, bie_geom* g, std::vector<NearPair>& pairs, 
     BIE_TRY((launch_rotate<double, double>(shifted.ptr, dfo.ptr + G.fo_at, 3, G.n, G.p, dblk.ptr + G.blk_at, G.blk_n,
                                            1, 1, (const double*)nullptr, xr.ptr + G.base, 3 * nc, s)));
   }
-  BIE_TRY(launch_near_newton(dpairs.ptr, npair, xr.ptr, pdeg.ptr, dxo.ptr, dx0.ptr, res.ptr, s));
+  DevBuf<double> rtab;
+  BIE_TRY(rtab.alloc(near_rec_table_doubles(pmax)));
+  BIE_TRY(launch_near_rec_table(pmax, rtab.ptr, s));
+  BIE_TRY(launch_near_newton(dpairs.ptr, npair, xr.ptr, pdeg.ptr, dxo.ptr, dx0.ptr, rtab.ptr, res.ptr, s));
   BIE_CUDA_TRY(cudaMemcpyAsync(hres.data(), res.ptr, hres.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   BIE_CUDA_TRY(cudaStreamSynchronize(s));
   stage.reset(new Phase(ctx, "near_checkpoints", s));

@@ -14,12 +14,37 @@ namespace {
 
 constexpr double kPiD = 3.14159265358979323846;
 
+// Coefficients of the normalised Legendre recursion of App. A at (n, m):
+// P_n^m = rec_a (cos(theta) P_{n-1}^m - rec_b P_{n-2}^m) for n >= m + 2, and the factor rec_c of the
+// derivative identity dP_n^m = rec_c P_n^{m+1} + m cot(theta) P_n^m.
+__device__ __forceinline__ double rec_a(int n, int m) {
+  return sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+}
+__device__ __forceinline__ double rec_b(int n, int m) {
+  return sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+}
+__device__ __forceinline__ double rec_c(int n, int m) { return sqrt((double)(n - m) * (n + m + 1.0)); }
+__device__ __forceinline__ long long tri(int n, int m) { return (long long)n * (n + 1) / 2 + m; }
+
+// tab[3 tri(n, m) + k] = rec_a, rec_b (0 for n < m + 2), rec_c, for 0 <= m <= n <= P
+__global__ void k_rec_table(int P, double* __restrict__ tab) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tri(P + 1, 0)) return;
+  int n = (int)((sqrt(8.0 * t + 1.0) - 1.0) / 2.0);
+  while (tri(n + 1, 0) <= t) ++n;
+  while (tri(n, 0) > t) --n;
+  const int m = (int)(t - tri(n, 0));
+  tab[3 * t] = n >= m + 2 ? rec_a(n, m) : 0.0;
+  tab[3 * t + 1] = n >= m + 2 ? rec_b(n, m) : 0.0;
+  tab[3 * t + 2] = rec_c(n, m);
+}
+
 // Value and first/second parameter derivatives of three real SH series (coefficients c[3][(p+1)^2])
 // at (theta, phi), with the Legendre recursion of App. A and the derivative identities
 // dP = alpha P^{m+1} + m cot(theta) P^m and the Legendre equation (theta away from the poles).
 // out[k][c], k: 0 f, 1 f_t, 2 f_p, 3 f_tt, 4 f_tp, 5 f_pp.
 __device__ void sh_eval_d2(const double* __restrict__ c, long long cstride, int p, double th, double ph,
-                           double out[6][3]) {
+                           const double* __restrict__ tab, double out[6][3]) {
   for (int k = 0; k < 6; ++k)
     for (int q = 0; q < 3; ++q) out[k][q] = 0;
   double st, ct;
@@ -38,8 +63,7 @@ __device__ void sh_eval_d2(const double* __restrict__ c, long long cstride, int 
       else if (n == m + 1)
         P = sqrt(2.0 * m + 3.0) * ct * dm;
       else
-        P = sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m)) *
-            (ct * pm1 - sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0)) * pm2);
+        P = tab[3 * tri(n, m)] * (ct * pm1 - tab[3 * tri(n, m) + 1] * pm2);
       double Q = 0;  // P~_n^{m+1}
       const int m1 = m + 1;
       if (n == m1)
@@ -47,15 +71,14 @@ __device__ void sh_eval_d2(const double* __restrict__ c, long long cstride, int 
       else if (n == m1 + 1)
         Q = sqrt(2.0 * m1 + 3.0) * ct * dm1;
       else if (n > m1 + 1)
-        Q = sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m1 * m1)) *
-            (ct * qm1 - sqrt(((n - 1.0) * (n - 1.0) - (double)m1 * m1) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0)) * qm2);
+        Q = tab[3 * tri(n, m1)] * (ct * qm1 - tab[3 * tri(n, m1) + 1] * qm2);
       pm2 = pm1;
       pm1 = P;
       if (n >= m1) {
         qm2 = qm1;
         qm1 = Q;
       }
-      const double dP = sqrt((double)(n - m) * (n + m + 1.0)) * Q + m * cot * P;
+      const double dP = tab[3 * tri(n, m) + 2] * Q + m * cot * P;
       const double d2P = -cot * dP + ((double)m * m / s2 - n * (n + 1.0)) * P;
       for (int q = 0; q < 3; ++q) {
         const double re = c[q * cstride + n * (n + 1) + m];
@@ -150,7 +173,8 @@ __global__ void k_near_seed(const NearPair* __restrict__ pairs, int npair, const
 // equator).  One thread per pair; rotated coefficients xr[pair][3][(p+1)^2].
 __global__ void k_near_newton(const NearPair* __restrict__ pairs, int npair, const double* __restrict__ xr,
                               const int* __restrict__ pdeg, const long long* __restrict__ xr_off,
-                              const double* __restrict__ x0all, double* __restrict__ result) {
+                              const double* __restrict__ x0all, const double* __restrict__ tab,
+                              double* __restrict__ result) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npair) return;
   const int p = pdeg[pairs[i].src_drop];
@@ -159,7 +183,7 @@ __global__ void k_near_newton(const NearPair* __restrict__ pairs, int npair, con
   const double x0[3] = {x0all[3 * i], x0all[3 * i + 1], x0all[3 * i + 2]};
   double th = 0.5 * kPiD, ph = 0.0;
   double d[6][3];
-  sh_eval_d2(c, cs, p, th, ph, d);
+  sh_eval_d2(c, cs, p, th, ph, tab, d);
   auto half_sq = [&](const double* x) {
     const double a = x[0] - x0[0], b = x[1] - x0[1], e = x[2] - x0[2];
     return 0.5 * (a * a + b * b + e * e);
@@ -187,7 +211,7 @@ __global__ void k_near_newton(const NearPair* __restrict__ pairs, int npair, con
       s0 = -(e * g0 - b * g1) / det;
       s1 = -(a * g1 - b * g0) / det;
       double dn[6][3];
-      sh_eval_d2(c, cs, p, th + s0, ph + s1, dn);
+      sh_eval_d2(c, cs, p, th + s0, ph + s1, tab, dn);
       if (half_sq(dn[0]) <= F) {
         accepted = true;
         break;
@@ -197,7 +221,7 @@ __global__ void k_near_newton(const NearPair* __restrict__ pairs, int npair, con
     if (!accepted) break;
     th += s0;
     ph += s1;
-    sh_eval_d2(c, cs, p, th, ph, d);
+    sh_eval_d2(c, cs, p, th, ph, tab, d);
     F = half_sq(d[0]);
     if (fmax(fabs(s0), fabs(s1)) < 1e-14) break;
   }
@@ -382,10 +406,20 @@ int launch_near_seed(const NearPair* pairs, int npair, const double* rec_std, co
   return BIE_OK;
 }
 
+int near_rec_table_doubles(int P) { return 3 * (P + 1) * (P + 2) / 2; }
+
+int launch_near_rec_table(int P, double* tab, cudaStream_t s) {
+  const int n = (P + 1) * (P + 2) / 2;
+  k_rec_table<<<(n + 127) / 128, 128, 0, s>>>(P, tab);
+  count_launch();
+  BIE_CUDA_TRY(cudaGetLastError());
+  return BIE_OK;
+}
+
 int launch_near_newton(const NearPair* pairs, int npair, const double* xr, const int* pdeg, const long long* xr_off,
-                       const double* x0, double* result, cudaStream_t s) {
+                       const double* x0, const double* tab, double* result, cudaStream_t s) {
   if (!npair) return BIE_OK;
-  k_near_newton<<<(npair + 63) / 64, 64, 0, s>>>(pairs, npair, xr, pdeg, xr_off, x0, result);
+  k_near_newton<<<(npair + 63) / 64, 64, 0, s>>>(pairs, npair, xr, pdeg, xr_off, x0, tab, result);
   count_launch();
   BIE_CUDA_TRY(cudaGetLastError());
   return BIE_OK;

@@ -21,8 +21,12 @@ int launch_near_seed(const NearPair* pairs, int npair, const double* rec_std, co
 int launch_near_phase_shift(const NearPair* pairs, int npair, const double* coef, const long long* coef_off,
                             const int* pdeg, int pmax, const double* ph, const long long* dst_off, double* out,
                             cudaStream_t s);
+// the Legendre recursion's coefficients for degrees up to P (near_rec_table_doubles(P) doubles), which
+// the closest-point Newton iteration reads
+int near_rec_table_doubles(int P);
+int launch_near_rec_table(int P, double* tab, cudaStream_t s);
 int launch_near_newton(const NearPair* pairs, int npair, const double* xr, const int* pdeg, const long long* xr_off,
-                       const double* x0, double* result, cudaStream_t s);
+                       const double* x0, const double* tab, double* result, cudaStream_t s);
 int launch_near_checkgrid(const NearPair* pairs, int npair, int L, const double* pts, const double* centre,
                           const double* bound, const double* h, double a_tilde, const double* rec_up,
                           const long long* up_off, const long long* up_n, int* grid, cudaStream_t s);
